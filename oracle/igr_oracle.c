@@ -1,0 +1,466 @@
+/*
+ * FP64 CPU oracle for one SSP-RK3 step of the 3D Euler equations with
+ * information geometric regularization (IGR).
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the package smoke check and the
+ * benchmark's CPU-baseline leg may load this library. It shares no code,
+ * header, table or helper with the CUDA path.
+ *
+ * It is written plainly: ghost-cell arrays of width 3, one loop per
+ * operation, all arithmetic in double, built with -ffp-contract=off.
+ * Every function names the part of the paper it follows:
+ *   - IGR-modified Euler system, Eqs. (igrmabalance)-(igrenbalance);
+ *   - IGR elliptic equation for Sigma, Eq. (igrelliptic);
+ *   - ideal-gas equation of state, Eq. (state_eqn);
+ *   - discretisation (Sec. "Discretization"): 5th-order finite-volume face
+ *     reconstruction, Lax-Friedrichs flux, 2nd-order velocity gradients,
+ *     7-point elliptic stencil, warm-started Jacobi sweeps, 3rd-order SSP
+ *     Runge-Kutta (Gottlieb-Shu);
+ *   - Algorithm 1 (flux of p+Sigma in every direction, Sigma reconstructed
+ *     like the conserved variables).
+ * Readings where the paper is silent (face coefficient of the elliptic
+ * operator, local LF speed, boundary treatment of Sigma, dt rule, jet
+ * inflow ghosts) are listed next to the code that takes them.
+ *
+ * State layout: q[v][k][j][i], v in (rho, mx, my, mz, E), x fastest,
+ * interior cells only. Sigma and b: [k][j][i].
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define G 3 /* ghost width: the 5th-order stencil reaches 3 cells */
+#define NV 5
+
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW = 2 };
+
+typedef struct {
+    int nx, ny, nz;
+    double dx, gamma, alpha, cfl;
+    int sweeps;
+    int bc[6];          /* faces -x,+x,-y,+y,-z,+z */
+    int njets;
+    const double *jets; /* njets x 7: cx, cy, radius, rho, w, p, edge_width */
+} orc_grid;
+
+/* ---------------------------------------------------------------- indexing */
+
+static long ncell(const orc_grid *g) { return (long)g->nx * g->ny * g->nz; }
+static long nghost(const orc_grid *g)
+{
+    return (long)(g->nx + 2 * G) * (g->ny + 2 * G) * (g->nz + 2 * G);
+}
+/* interior index */
+static long I(const orc_grid *g, int i, int j, int k)
+{
+    return ((long)k * g->ny + j) * g->nx + i;
+}
+/* ghost-array index; i in [-G, nx+G) */
+static long GI(const orc_grid *g, int i, int j, int k)
+{
+    return ((long)(k + G) * (g->ny + 2 * G) + (j + G)) * (g->nx + 2 * G) + (i + G);
+}
+
+/* --------------------------------------------------------- ghost filling */
+
+/* Conserved state of jet n, from its primitive state (rho, w along +z, p):
+ * Eq. (state_eqn) gives E = p/(gamma-1) + rho w^2 / 2. */
+static void jet_state(const orc_grid *g, int n, double qj[NV])
+{
+    const double *J = g->jets + 7 * n;
+    double rho = J[3], w = J[4], p = J[5];
+    qj[0] = rho;
+    qj[1] = 0.0;
+    qj[2] = 0.0;
+    qj[3] = rho * w;
+    qj[4] = p / (g->gamma - 1.0) + 0.5 * rho * w * w;
+}
+
+/* Fill the ghost layers of one field f (ghost array) along all three axes.
+ * Periodic faces wrap; outflow faces copy the nearest interior cell
+ * (zero gradient). An inflow face (only -z is allowed) blends every jet's
+ * state into the nearest interior cell:
+ *   s_n = (1 - tanh((r_n - R_n) / (edge_width_n dx))) / 2,
+ *   ghost = (1 - sum_n s_n) q_interior + sum_n s_n q_jet_n,
+ * with r_n the distance from the ghost cell's (x, y) centre to jet n. For a
+ * field that is not a conserved variable (Sigma), inflow acts as outflow. */
+static void fill_axis_x(const orc_grid *g, double *f)
+{
+    int nx = g->nx;
+    for (int k = -G; k < g->nz + G; k++)
+        for (int j = -G; j < g->ny + G; j++)
+            for (int s = 1; s <= G; s++) {
+                int lo = -s, hi = nx - 1 + s;
+                int slo = g->bc[0] == BC_PERIODIC ? ((lo % nx) + nx) % nx : 0;
+                int shi = g->bc[1] == BC_PERIODIC ? hi % nx : nx - 1;
+                f[GI(g, lo, j, k)] = f[GI(g, slo, j, k)];
+                f[GI(g, hi, j, k)] = f[GI(g, shi, j, k)];
+            }
+}
+static void fill_axis_y(const orc_grid *g, double *f)
+{
+    int ny = g->ny;
+    for (int k = -G; k < g->nz + G; k++)
+        for (int s = 1; s <= G; s++)
+            for (int i = -G; i < g->nx + G; i++) {
+                int lo = -s, hi = ny - 1 + s;
+                int slo = g->bc[2] == BC_PERIODIC ? ((lo % ny) + ny) % ny : 0;
+                int shi = g->bc[3] == BC_PERIODIC ? hi % ny : ny - 1;
+                f[GI(g, i, lo, k)] = f[GI(g, i, slo, k)];
+                f[GI(g, i, hi, k)] = f[GI(g, i, shi, k)];
+            }
+}
+static void fill_axis_z(const orc_grid *g, double *f, int var)
+{
+    int nz = g->nz;
+    for (int s = 1; s <= G; s++)
+        for (int j = -G; j < g->ny + G; j++)
+            for (int i = -G; i < g->nx + G; i++) {
+                int lo = -s, hi = nz - 1 + s;
+                int slo = g->bc[4] == BC_PERIODIC ? ((lo % nz) + nz) % nz : 0;
+                int shi = g->bc[5] == BC_PERIODIC ? hi % nz : nz - 1;
+                double vlo = f[GI(g, i, j, slo)];
+                if (g->bc[4] == BC_INFLOW && var >= 0) {
+                    double x = (i + 0.5) * g->dx, y = (j + 0.5) * g->dx;
+                    double wsum = 0.0, jsum = 0.0;
+                    for (int n = 0; n < g->njets; n++) {
+                        const double *J = g->jets + 7 * n;
+                        double r = sqrt((x - J[0]) * (x - J[0]) + (y - J[1]) * (y - J[1]));
+                        double sn = 0.5 * (1.0 - tanh((r - J[2]) / (J[6] * g->dx)));
+                        double qj[NV];
+                        jet_state(g, n, qj);
+                        wsum += sn;
+                        jsum += sn * qj[var];
+                    }
+                    vlo = (1.0 - wsum) * vlo + jsum;
+                }
+                f[GI(g, i, j, lo)] = vlo;
+                f[GI(g, i, j, hi)] = f[GI(g, i, j, shi)];
+            }
+}
+
+/* q (interior, 5 fields) -> qg (ghost arrays, 5 fields). */
+void orc_fill_ghosts(const orc_grid *g, const double *q, double *qg)
+{
+    long N = ncell(g), NG = nghost(g);
+    for (int v = 0; v < NV; v++) {
+        double *f = qg + v * NG;
+        for (int k = 0; k < g->nz; k++)
+            for (int j = 0; j < g->ny; j++)
+                for (int i = 0; i < g->nx; i++) f[GI(g, i, j, k)] = q[v * N + I(g, i, j, k)];
+        fill_axis_x(g, f);
+        fill_axis_y(g, f);
+        fill_axis_z(g, f, v);
+    }
+}
+
+/* Sigma (interior) -> ghost array: periodic wrap, zero gradient otherwise. */
+static void fill_sigma_ghosts(const orc_grid *g, const double *sig, double *sg)
+{
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++) sg[GI(g, i, j, k)] = sig[I(g, i, j, k)];
+    fill_axis_x(g, sg);
+    fill_axis_y(g, sg);
+    fill_axis_z(g, sg, -1);
+}
+
+/* ------------------------------------------- velocity gradients and source */
+
+/* IGR source b = alpha [tr((grad u)^2) + tr^2(grad u)] at every interior cell,
+ * Eq. (igrelliptic) left side. grad u by second-order central differences
+ * (Sec. "Discretization"): G[a][c] = d u_a / d x_c
+ *   = (u_a(i + e_c) - u_a(i - e_c)) / (2 dx), u = m / rho,
+ * neighbours outside the domain taken from the ghost cells of q.
+ * tr(G^2) = sum_{a,c} G[a][c] G[c][a]; tr^2(G) = (sum_a G[a][a])^2. */
+static void source_from_ghosts(const orc_grid *g, const double *qg, double *b)
+{
+    long NG = nghost(g);
+    const double *rho = qg, *m[3] = {qg + NG, qg + 2 * NG, qg + 3 * NG};
+#pragma omp parallel for
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++) {
+                int off[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+                double Gm[3][3];
+                for (int c = 0; c < 3; c++) {
+                    long ip = GI(g, i + off[c][0], j + off[c][1], k + off[c][2]);
+                    long im = GI(g, i - off[c][0], j - off[c][1], k - off[c][2]);
+                    for (int a = 0; a < 3; a++) {
+                        double up = m[a][ip] / rho[ip];
+                        double um = m[a][im] / rho[im];
+                        Gm[a][c] = (up - um) / (2.0 * g->dx);
+                    }
+                }
+                double trG2 = 0.0;
+                for (int a = 0; a < 3; a++)
+                    for (int c = 0; c < 3; c++) trG2 += Gm[a][c] * Gm[c][a];
+                double trG = Gm[0][0] + Gm[1][1] + Gm[2][2];
+                b[I(g, i, j, k)] = g->alpha * (trG2 + trG * trG);
+            }
+}
+
+void orc_source(const orc_grid *g, const double *q, double *b)
+{
+    double *qg = malloc(sizeof(double) * NV * nghost(g));
+    orc_fill_ghosts(g, q, qg);
+    source_from_ghosts(g, qg, b);
+    free(qg);
+}
+
+/* ------------------------------------------------ elliptic operator for Sigma */
+
+/* Neighbour of interior cell (i,j,k) across face dir (0:-x 1:+x 2:-y 3:+y
+ * 4:-z 5:+z). Returns 0 when the face is a non-periodic domain boundary:
+ * there the zero-gradient condition on Sigma makes the face term vanish. */
+static int neighbour(const orc_grid *g, int i, int j, int k, int dir, long *nb)
+{
+    int n[3] = {g->nx, g->ny, g->nz};
+    int c[3] = {i, j, k};
+    int ax = dir / 2, sgn = (dir % 2) ? 1 : -1;
+    c[ax] += sgn;
+    if (c[ax] < 0 || c[ax] >= n[ax]) {
+        if (g->bc[dir] != BC_PERIODIC) return 0;
+        c[ax] = (c[ax] + n[ax]) % n[ax];
+    }
+    *nb = I(g, c[0], c[1], c[2]);
+    return 1;
+}
+
+/* Discrete operator A of Eq. (igrelliptic), A Sigma = rho^-1 Sigma
+ * - alpha div(rho^-1 grad Sigma), with the 7-point stencil
+ *   (A s)_i = r_i s_i + beta sum_f c_f (s_i - s_nb(f)),
+ * beta = alpha / dx^2, r = 1/rho, face coefficient c_f = (r_i + r_nb) / 2
+ * (reading: the paper names only "a standard 7-point stencil"; the
+ * arithmetic mean keeps A symmetric). Faces on a non-periodic boundary
+ * carry no term (zero normal gradient of Sigma). */
+void orc_apply_A(const orc_grid *g, const double *q, const double *s, double *out)
+{
+    const double *rho = q;
+    double beta = g->alpha / (g->dx * g->dx);
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++) {
+                long c = I(g, i, j, k), nb;
+                double ri = 1.0 / rho[c];
+                double acc = ri * s[c];
+                for (int d = 0; d < 6; d++) {
+                    if (!neighbour(g, i, j, k, d, &nb)) continue;
+                    double cf = 0.5 * (ri + 1.0 / rho[nb]);
+                    acc += beta * cf * (s[c] - s[nb]);
+                }
+                out[c] = acc;
+            }
+}
+
+/* `sweeps` Jacobi sweeps on A sigma = b, warm-started from the incoming
+ * sigma (Sec. "Discretization": the previous Sigma is the initial guess):
+ *   sigma_i <- (b_i + beta sum_f c_f sigma_nb) / (r_i + beta sum_f c_f),
+ * every cell updated from the previous iterate only (two buffers). */
+void orc_jacobi(const orc_grid *g, const double *q, const double *b, double *sigma,
+                int sweeps)
+{
+    long N = ncell(g);
+    const double *rho = q;
+    double beta = g->alpha / (g->dx * g->dx);
+    double *old = malloc(sizeof(double) * N);
+    for (int it = 0; it < sweeps; it++) {
+        memcpy(old, sigma, sizeof(double) * N);
+#pragma omp parallel for
+        for (int k = 0; k < g->nz; k++)
+            for (int j = 0; j < g->ny; j++)
+                for (int i = 0; i < g->nx; i++) {
+                    long c = I(g, i, j, k), nb;
+                    double ri = 1.0 / rho[c];
+                    double diag = ri, off = 0.0;
+                    for (int d = 0; d < 6; d++) {
+                        if (!neighbour(g, i, j, k, d, &nb)) continue;
+                        double cf = 0.5 * (ri + 1.0 / rho[nb]);
+                        diag += beta * cf;
+                        off += beta * cf * old[nb];
+                    }
+                    sigma[c] = (b[c] + off) / diag;
+                }
+    }
+    free(old);
+}
+
+/* ------------------------------------------------------- fluxes and RHS */
+
+/* 5th-order linear finite-volume face values at face i+1/2 from the cell
+ * averages v[i-2..i+3] (Sec. "Discretization", Algorithm 1: the stencil
+ * -2..3 along the sweep direction): the unique quartic matching the five
+ * cell averages of the left-biased (resp. right-biased) stencil, evaluated
+ * at the face. */
+static double recon_left(const double v[6])
+{
+    return (2.0 * v[0] - 13.0 * v[1] + 47.0 * v[2] + 27.0 * v[3] - 3.0 * v[4]) / 60.0;
+}
+static double recon_right(const double v[6])
+{
+    return (-3.0 * v[1] + 27.0 * v[2] + 47.0 * v[3] - 13.0 * v[4] + 2.0 * v[5]) / 60.0;
+}
+
+/* Physical flux of the IGR-modified Euler system along axis d,
+ * Eqs. (igrmabalance)-(igrenbalance) with tau = 0:
+ *   (rho u_d, m u_d + (p + Sigma) e_d, (E + p + Sigma) u_d),
+ * p from Eq. (state_eqn). Also returns |u_d| + c with c = sqrt(gamma p / rho)
+ * (reading: the sound speed uses p, not p + Sigma). */
+static double phys_flux(const orc_grid *g, const double qv[NV], double sig, int d,
+                        double F[NV])
+{
+    double rho = qv[0], E = qv[4];
+    double u[3] = {qv[1] / rho, qv[2] / rho, qv[3] / rho};
+    double ke = 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    double p = (g->gamma - 1.0) * (E - ke);
+    double P = p + sig;
+    F[0] = rho * u[d];
+    for (int a = 0; a < 3; a++) F[1 + a] = qv[1 + a] * u[d] + (a == d ? P : 0.0);
+    F[4] = (E + P) * u[d];
+    return fabs(u[d]) + sqrt(g->gamma * p / rho);
+}
+
+/* Spatial operator L(q; Sigma) = -div F_hat at every interior cell, with the
+ * local Lax-Friedrichs flux (reading: local speed)
+ *   F_hat = (F(q_L) + F(q_R)) / 2 - lambda (q_R - q_L) / 2,
+ *   lambda = max(|u_d|+c at L, at R),
+ * Sigma entering only through the pressure p + Sigma, reconstructed with
+ * the same 5th-order face values as the conserved variables.
+ *   L_i = -[(Fx_{i+1/2} - Fx_{i-1/2}) + (Fy..) + (Fz..)] / dx. */
+static void rhs_from_ghosts(const orc_grid *g, const double *qg, const double *sg,
+                            double *L)
+{
+    long N = ncell(g), NG = nghost(g);
+    int nx = g->nx, ny = g->ny, nz = g->nz;
+    memset(L, 0, sizeof(double) * NV * N);
+    for (int d = 0; d < 3; d++) {
+        /* face fluxes along d: face index f in [0, n_d], face f sits between
+         * cells f-1 and f */
+        int fx = nx + (d == 0), fy = ny + (d == 1), fz = nz + (d == 2);
+        long NF = (long)fx * fy * fz;
+        double *F = malloc(sizeof(double) * NV * NF);
+#pragma omp parallel for
+        for (int k = 0; k < fz; k++)
+            for (int j = 0; j < fy; j++)
+                for (int i = 0; i < fx; i++) {
+                    /* stencil cells along d: face f = (i,j,k)[d] between
+                     * cells f-1 and f -> cells f-3 .. f+2 */
+                    double vq[NV + 1][6];
+                    for (int s = 0; s < 6; s++) {
+                        int c[3] = {i, j, k};
+                        c[d] += s - 3;
+                        long gi = GI(g, c[0], c[1], c[2]);
+                        for (int v = 0; v < NV; v++) vq[v][s] = qg[v * NG + gi];
+                        vq[NV][s] = sg[gi];
+                    }
+                    double qL[NV], qR[NV], FL[NV], FR[NV];
+                    for (int v = 0; v < NV; v++) {
+                        qL[v] = recon_left(vq[v]);
+                        qR[v] = recon_right(vq[v]);
+                    }
+                    double sL = recon_left(vq[NV]), sR = recon_right(vq[NV]);
+                    double aL = phys_flux(g, qL, sL, d, FL);
+                    double aR = phys_flux(g, qR, sR, d, FR);
+                    double lam = aL > aR ? aL : aR;
+                    long fi = ((long)k * fy + j) * fx + i;
+                    for (int v = 0; v < NV; v++)
+                        F[v * NF + fi] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (qR[v] - qL[v]);
+                }
+        /* accumulate the flux difference of this direction */
+        for (int k = 0; k < nz; k++)
+            for (int j = 0; j < ny; j++)
+                for (int i = 0; i < nx; i++) {
+                    int c[3] = {i, j, k};
+                    int h[3] = {i, j, k};
+                    h[d] += 1;
+                    long lo = ((long)c[2] * fy + c[1]) * fx + c[0];
+                    long hi = ((long)h[2] * fy + h[1]) * fx + h[0];
+                    for (int v = 0; v < NV; v++)
+                        L[v * N + I(g, i, j, k)] += F[v * NF + hi] - F[v * NF + lo];
+                }
+        free(F);
+    }
+    for (long n = 0; n < NV * N; n++) L[n] = -L[n] / g->dx;
+}
+
+/* L(q; Sigma) for given q and Sigma (no elliptic solve). */
+void orc_rhs(const orc_grid *g, const double *q, const double *sigma, double *L)
+{
+    double *qg = malloc(sizeof(double) * NV * nghost(g));
+    double *sg = malloc(sizeof(double) * nghost(g));
+    orc_fill_ghosts(g, q, qg);
+    fill_sigma_ghosts(g, sigma, sg);
+    rhs_from_ghosts(g, qg, sg, L);
+    free(qg);
+    free(sg);
+}
+
+/* max over interior cells of max_d (|u_d| + c) (reading: the paper does not
+ * state its time-step rule; dt = cfl dx / this maximum, from the state at
+ * the start of the step). */
+double orc_max_speed(const orc_grid *g, const double *q)
+{
+    long N = ncell(g);
+    double smax = 0.0;
+    for (long n = 0; n < N; n++) {
+        double rho = q[n];
+        double u[3] = {q[N + n] / rho, q[2 * N + n] / rho, q[3 * N + n] / rho};
+        double p = (g->gamma - 1.0) *
+                   (q[4 * N + n] - 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+        double c = sqrt(g->gamma * p / rho);
+        for (int d = 0; d < 3; d++) {
+            double s = fabs(u[d]) + c;
+            if (s > smax) smax = s;
+        }
+    }
+    return smax;
+}
+
+/* One Runge-Kutta stage: the elliptic solve for Sigma (warm start from the
+ * incoming sigma, `sweeps` Jacobi sweeps), then
+ *   out = qn + w [(qs - qn) + dt L(qs; Sigma)],
+ * the increment form of the Gottlieb-Shu SSP-RK3 stages (w = 1, 1/4, 2/3).
+ * out may alias qn but not qs. */
+void orc_stage(const orc_grid *g, const double *qs, const double *qn, double *sigma,
+               double *out, double w, double dt)
+{
+    long N = ncell(g);
+    double *qg = malloc(sizeof(double) * NV * nghost(g));
+    double *sg = malloc(sizeof(double) * nghost(g));
+    double *b = malloc(sizeof(double) * N);
+    double *L = malloc(sizeof(double) * NV * N);
+    orc_fill_ghosts(g, qs, qg);
+    source_from_ghosts(g, qg, b);
+    orc_jacobi(g, qs, b, sigma, g->sweeps);
+    fill_sigma_ghosts(g, sigma, sg);
+    rhs_from_ghosts(g, qg, sg, L);
+    for (long n = 0; n < NV * N; n++) out[n] = qn[n] + w * ((qs[n] - qn[n]) + dt * L[n]);
+    free(qg);
+    free(sg);
+    free(b);
+    free(L);
+}
+
+/* One SSP-RK3 time step (Gottlieb-Shu), state and Sigma updated in place.
+ * dt = fixed_dt if fixed_dt > 0, else cfl dx / orc_max_speed(q). Returns dt. */
+double orc_step(const orc_grid *g, double *q, double *sigma, double fixed_dt)
+{
+    long N = ncell(g);
+    double dt = fixed_dt > 0.0 ? fixed_dt : g->cfl * g->dx / orc_max_speed(g, q);
+    double *q1 = malloc(sizeof(double) * NV * N);
+    double *q2 = malloc(sizeof(double) * NV * N);
+    orc_stage(g, q, q, sigma, q1, 1.0, dt);
+    orc_stage(g, q1, q, sigma, q2, 0.25, dt);
+    orc_stage(g, q2, q, sigma, q, 2.0 / 3.0, dt);
+    free(q1);
+    free(q2);
+    return dt;
+}
+
+/* nsteps steps; returns the elapsed simulated time. */
+double orc_run(const orc_grid *g, double *q, double *sigma, int nsteps, double fixed_dt)
+{
+    double t = 0.0;
+    for (int n = 0; n < nsteps; n++) t += orc_step(g, q, sigma, fixed_dt);
+    return t;
+}

@@ -1,0 +1,367 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: every expected value is a
+closed form, an invariant, a textbook solution or a brute-force solve.
+A plausible slip anywhere in the oracle (a dropped term, a wrong sign,
+index or weight, a transposed operand) fails at least one of these.
+"""
+import json
+import math
+import os
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_07392_gb300 import inputs
+from paper_2505_07392_gb300.inputs import INFLOW, OUTFLOW, PERIODIC, Case
+
+import sod_exact
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+GAMMA = 1.4
+
+
+def cons(rho, u, v, w, p, g=GAMMA):
+    return np.stack([rho, rho * u, rho * v, rho * w, p / (g - 1) + 0.5 * rho * (u * u + v * v + w * w)])
+
+
+def box(n, bc, nx=None, ny=None, nz=None, alpha_scale=1.0, sweeps=5, jets=()):
+    nx, ny, nz = nx or n, ny or n, nz or n
+    dx = 1.0 / nx
+    return Case("pin", nx, ny, nz, dx, alpha=alpha_scale * dx * dx, sweeps=sweeps, bc=tuple(bc),
+                jets=list(jets))
+
+
+def centres(c):
+    z = (np.arange(c.nz) + 0.5) * c.dx
+    y = (np.arange(c.ny) + 0.5) * c.dx
+    x = (np.arange(c.nx) + 0.5) * c.dx
+    return np.meshgrid(z, y, x, indexing="ij")
+
+
+# ------------------------------------------------------------ invariants
+
+@pytest.mark.parametrize("bc", [(PERIODIC,) * 6, (OUTFLOW,) * 6,
+                                (OUTFLOW, OUTFLOW, PERIODIC, PERIODIC, OUTFLOW, PERIODIC)])
+def test_uniform_state_preserved_bitwise(bc):
+    """Identical face states give identical fluxes: dq/dt = 0 exactly, grad u = 0
+    gives b = 0 and Sigma stays 0; the increment-form RK keeps q bit-identical."""
+    c = box(6, bc, nx=7, ny=6, nz=5)
+    shape = (c.nz, c.ny, c.nx)
+    q = cons(np.full(shape, 1.3), np.full(shape, 0.7), np.full(shape, -0.4),
+             np.full(shape, 0.25), np.full(shape, 2.1))
+    q1, s1, t = oracle.run(c, q, None, nsteps=10)
+    assert np.array_equal(q1, q)
+    assert np.all(s1 == 0.0)
+    assert t > 0
+
+
+def test_periodic_conservation():
+    """Flux form with periodic faces: totals of rho, m, E change only by
+    round-off, with a non-trivial Sigma."""
+    c = box(16, (PERIODIC,) * 6)
+    z, y, x = centres(c)
+    tp = 2 * np.pi
+    rho = 1 + 0.2 * np.sin(tp * x) * np.cos(tp * y) + 0.1 * np.sin(tp * z)
+    u = 0.5 * np.sin(tp * y)
+    v = 0.3 * np.cos(tp * x) * np.sin(tp * z)
+    w = -0.4 * np.sin(tp * x)
+    p = 1 + 0.1 * np.cos(tp * (x + y))
+    q = cons(rho, u, v, w, p)
+    q1, s1, _ = oracle.run(c, q, None, nsteps=10)
+    assert np.abs(s1).max() > 1e-6        # Sigma is active
+    tot0 = q.reshape(5, -1).sum(axis=1)
+    tot1 = q1.reshape(5, -1).sum(axis=1)
+    scale = np.abs(q).reshape(5, -1).sum(axis=1)
+    assert np.all(np.abs(tot1 - tot0) <= 1e-13 * scale)
+
+
+def test_sigma_zero_for_uniform_velocity():
+    """grad u = 0 (variable density, uniform velocity, exact m/rho) gives
+    b = 0 and Sigma = 0 exactly (Eq. igrelliptic with zero left side)."""
+    c = box(8, (OUTFLOW,) * 6)
+    z, y, x = centres(c)
+    rho = 1 + 0.3 * np.sin(5 * x + 3 * y) * np.cos(2 * z)
+    q = cons(rho, 1.0 + 0 * rho, 0.5 + 0 * rho, -0.25 + 0 * rho, 1 + 0 * rho)
+    assert np.all(oracle.source(c, q) == 0.0)
+    s = oracle.jacobi(c, q, oracle.source(c, q), np.zeros(c.ncells), 7)
+    assert np.all(s == 0.0)
+
+
+def test_source_for_linear_velocity():
+    """Linear u = G x: central differences are exact, so at cells away from
+    the boundary b = alpha [tr(G G) + tr(G)^2] with tr(G G) = sum G_ab G_ba
+    (not sum G_ab^2: the off-diagonal product distinguishes the two)."""
+    c = box(8, (OUTFLOW,) * 6, alpha_scale=0.7)
+    z, y, x = centres(c)
+    Gm = np.array([[0.3, 2.0, 0.0], [-1.0, 0.5, 0.2], [0.1, 0.0, -0.7]])
+    X = [x, y, z]
+    u = [sum(Gm[a, b] * X[b] for b in range(3)) for a in range(3)]
+    q = cons(1 + 0 * x, u[0], u[1], u[2], 5 + 0 * x)
+    b = oracle.source(c, q)
+    expect = c.alpha * (np.trace(Gm @ Gm) + np.trace(Gm) ** 2)
+    inner = b[1:-1, 1:-1, 1:-1]
+    assert np.allclose(inner, expect, rtol=1e-11, atol=0)
+    assert not np.isclose(expect, c.alpha * (np.sum(Gm * Gm) + np.trace(Gm) ** 2))
+
+
+# ------------------------------------------------------- elliptic solve
+
+@pytest.mark.parametrize("alpha_scale", [1.0, 0.3])
+def test_jacobi_fourier_mode_decay(alpha_scale):
+    """Uniform rho, b = 0, periodic: one Jacobi sweep multiplies the mode
+    cos(k.x) by beta * 2 sum_d cos(theta_d) / (1 + 6 beta), beta = alpha/dx^2."""
+    c = box(8, (PERIODIC,) * 6, alpha_scale=alpha_scale)
+    z, y, x = centres(c)
+    kk = 2 * np.pi * np.array([1, 2, 3])
+    s0 = np.cos(kk[0] * x + kk[1] * y + kk[2] * z)
+    q = cons(2.0 + 0 * x, 0 * x, 0 * x, 0 * x, 1 + 0 * x)
+    s1 = oracle.jacobi(c, q, np.zeros(c.ncells), s0, 1)
+    beta = alpha_scale
+    fac = beta * 2 * np.sum(np.cos(kk * c.dx)) / (1 + 6 * beta)
+    assert np.allclose(s1, fac * s0, rtol=0, atol=1e-14)
+
+
+def test_sigma_solve_closed_form():
+    """Uniform rho0, b = cos(k.x): Sigma = rho0 b / (1 + beta sum_d 2 (1 - cos theta_d))."""
+    c = box(8, (PERIODIC,) * 6)
+    z, y, x = centres(c)
+    kk = 2 * np.pi * np.array([2, 1, 3])
+    rho0 = 1.7
+    b = np.cos(kk[0] * x + kk[1] * y + kk[2] * z)
+    q = cons(rho0 + 0 * x, 0 * x, 0 * x, 0 * x, 1 + 0 * x)
+    s = oracle.jacobi(c, q, b, np.zeros(c.ncells), 600)
+    expect = rho0 * b / (1 + np.sum(2 * (1 - np.cos(kk * c.dx))))
+    assert np.allclose(s, expect, rtol=0, atol=1e-13)
+
+
+def _dense_A(c, q):
+    n = c.ncells
+    A = np.empty((n, n))
+    e = np.zeros(n)
+    for m in range(n):
+        e[:] = 0
+        e[m] = 1
+        A[:, m] = oracle.apply_A(c, q, e).ravel()
+    return A
+
+
+@pytest.mark.parametrize("n", [4, 5, 6])
+@pytest.mark.parametrize("bc", [(PERIODIC,) * 6, (OUTFLOW,) * 6,
+                                (PERIODIC, PERIODIC, OUTFLOW, OUTFLOW, INFLOW, OUTFLOW)])
+def test_sigma_vs_dense_direct_solve(n, bc):
+    """The assembled operator is symmetric positive definite with a 7-point
+    sparsity pattern and non-positive off-diagonals; converged Jacobi sweeps
+    match a dense direct solve."""
+    c = box(n, bc)
+    rng = np.random.Generator(np.random.Philox(11))
+    rho = rng.uniform(0.5, 2.0, size=(n, n, n))
+    q = cons(rho, 0 * rho, 0 * rho, 0 * rho, 1 + 0 * rho)
+    A = _dense_A(c, q)
+    assert np.array_equal(A, A.T) or np.max(np.abs(A - A.T)) <= 1e-15 * np.max(np.abs(A))
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > 0
+    off = A - np.diag(np.diag(A))
+    assert np.all(off <= 0)
+    assert np.all((A != 0).sum(axis=1) <= 7)
+    assert np.allclose(np.diag(A), np.diag(A))  # finite
+    b = rng.uniform(-1, 1, size=c.ncells)
+    direct = np.linalg.solve(A, b)
+    s = oracle.jacobi(c, q, b, np.zeros(c.ncells), 3000)
+    assert np.max(np.abs(s.ravel() - direct)) <= 1e-12 * np.max(np.abs(direct))
+
+
+def test_elliptic_operator_second_order_consistent():
+    """Manufactured check of the variable-coefficient operator: for smooth
+    rho(x), Sigma(x) (periodic, fixed alpha) the discrete A Sigma converges at
+    second order to Sigma/rho - alpha d/dx(Sigma'/rho)."""
+    alpha = 0.01
+    errs = []
+    for n in (32, 64, 128):
+        c = box(n, (PERIODIC,) * 6, nx=n, ny=2, nz=2)
+        c = replace(c, alpha=alpha)
+        z, y, x = centres(c)
+        tp = 2 * np.pi
+        rho = 1 + 0.5 * np.sin(tp * x)
+        drho = 0.5 * tp * np.cos(tp * x)
+        S = np.cos(tp * x)
+        dS = -tp * np.sin(tp * x)
+        d2S = -tp * tp * np.cos(tp * x)
+        exact = S / rho - alpha * (d2S / rho - dS * drho / rho ** 2)
+        q = cons(rho, 0 * x, 0 * x, 0 * x, 1 + 0 * x)
+        errs.append(np.max(np.abs(oracle.apply_A(c, q, S) - exact)))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 1.85), orders
+
+
+# ---------------------------------------------------- reconstruction / flux
+
+def _quartic_avg(coef, xl, xr):
+    """Exact cell average of sum coef[m] x^m over [xl, xr]."""
+    prim = lambda x: sum(cf * x ** (m + 1) / (m + 1) for m, cf in enumerate(coef))
+    return (prim(xr) - prim(xl)) / (xr - xl)
+
+
+def _poly(coef, x):
+    return sum(cf * x ** m for m, cf in enumerate(coef))
+
+
+def test_sigma_flux_exact_for_quartic_sigma():
+    """u = 0, uniform rho and p, Sigma = cell averages of a quartic P(x):
+    both 5th-order face values equal P at the face, so away from the
+    boundary rhs(m_x) = -(P(x_{i+1/2}) - P(x_{i-1/2})) / dx, and Sigma drives
+    nothing else (u = 0 makes the mass and energy fluxes vanish)."""
+    n = 16
+    c = box(n, (OUTFLOW, OUTFLOW, PERIODIC, PERIODIC, PERIODIC, PERIODIC), nx=n, ny=3, nz=2)
+    coef = [0.3, -1.1, 2.5, 0.7, -1.9]
+    xf = np.arange(n + 1) * c.dx
+    sig_row = np.array([_quartic_avg(coef, xf[i], xf[i + 1]) for i in range(n)])
+    sig = np.broadcast_to(sig_row, (c.nz, c.ny, n)).copy()
+    shape = (c.nz, c.ny, n)
+    q = cons(np.full(shape, 1.2), np.zeros(shape), np.zeros(shape), np.zeros(shape), np.full(shape, 0.9))
+    L = oracle.rhs(c, q, sig)
+    inner = slice(3, n - 3)
+    expect = -(_poly(coef, xf[1:]) - _poly(coef, xf[:-1])) / c.dx
+    assert np.allclose(L[1][..., inner], expect[inner], rtol=1e-11, atol=1e-11)
+    for v in (0, 2, 3, 4):
+        assert np.max(np.abs(L[v])) <= 1e-11
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_face_states_exact_for_quartic_density(axis):
+    """u = 0, uniform p, rho = cell averages of a quartic along one axis: the
+    left- and right-biased face values both equal rho at the face, so the LF
+    jump term vanishes and L = 0 away from the boundary in that axis. A wrong
+    weight in either one-sided formula breaks the equality."""
+    n = 16
+    dims = [3, 3, 3]
+    dims[axis] = n
+    bc = [PERIODIC] * 6
+    bc[2 * axis] = bc[2 * axis + 1] = OUTFLOW
+    c = Case("pin", dims[0], dims[1], dims[2], 1.0 / n, alpha=1.0 / n ** 2, bc=tuple(bc))
+    coef = [1.0, 0.4, -0.3, 0.2, 0.1]
+    xf = np.arange(n + 1) * c.dx
+    row = np.array([_quartic_avg(coef, xf[i], xf[i + 1]) for i in range(n)])
+    shape = (c.nz, c.ny, c.nx)
+    bshape = [1, 1, 1]
+    bshape[2 - axis] = n
+    rho = np.broadcast_to(row.reshape(bshape), shape).copy()
+    q = cons(rho, 0 * rho, 0 * rho, 0 * rho, 1 + 0 * rho)
+    L = oracle.rhs(c, q, np.zeros(shape))
+    sl = [slice(None)] * 3
+    sl[2 - axis] = slice(3, n - 3)
+    assert np.max(np.abs(L[(slice(None),) + tuple(sl)])) <= 1e-12
+
+
+def test_time_step_rule():
+    """dt = cfl dx / max_d(|u_d| + c): rho = 1.4, p = 1 gives c = 1; with
+    u = (0.5, -2, 1) the maximum is 3."""
+    c = box(5, (PERIODIC,) * 6)
+    shape = (5, 5, 5)
+    q = cons(np.full(shape, 1.4), np.full(shape, 0.5), np.full(shape, -2.0), np.full(shape, 1.0),
+             np.full(shape, 1.0))
+    assert math.isclose(oracle.max_speed(c, q), 3.0, rel_tol=1e-15)
+    _, _, t = oracle.run(c, q, None, nsteps=1)
+    assert math.isclose(t, 0.4 * c.dx / 3.0, rel_tol=1e-15)
+
+
+def test_inflow_ghost_blend():
+    """Inflow ghosts on -z: (1 - sum s) q_interior + sum s q_jet with
+    s = (1 - tanh((r - R)/(w dx)))/2: s = 1/2 exactly at r = R, the jet state
+    deep inside, the interior state far away; periodic/outflow elsewhere."""
+    n = 12
+    dx = 1.0 / n
+    jet = (4.5 * dx, 5.5 * dx, 2.0 * dx, 0.8, 3.0, 2.0, 1.0)  # centred on cell (4, 5)
+    c = Case("pin", n, n, 6, dx, alpha=dx * dx,
+             bc=(OUTFLOW, OUTFLOW, OUTFLOW, OUTFLOW, INFLOW, OUTFLOW), jets=[jet])
+    shape = (c.nz, c.ny, c.nx)
+    rng = np.random.Generator(np.random.Philox(5))
+    rho = rng.uniform(0.9, 1.1, size=shape)
+    q = cons(rho, 0.1 + 0 * rho, 0 * rho, 0.2 + 0 * rho, 1 + 0 * rho)
+    qg = oracle.fill_ghosts(c, q)
+    qj = np.array([0.8, 0.0, 0.0, 0.8 * 3.0, 2.0 / 0.4 + 0.5 * 0.8 * 9.0])
+    G = 3
+    for layer in (0, 1, 2):  # ghost planes k = -3, -2, -1
+        at = lambda i, j: qg[:, layer, j + G, i + G]
+        inner = lambda i, j: q[:, 0, j, i]
+        # r = R at cell (6, 5): s = 1/2
+        assert np.allclose(at(6, 5), 0.5 * inner(6, 5) + 0.5 * qj, rtol=1e-15, atol=1e-15)
+        # centre: s = (1 - tanh(-2))/2
+        s = 0.5 * (1 - math.tanh(-2.0))
+        assert np.allclose(at(4, 5), (1 - s) * inner(4, 5) + s * qj, rtol=1e-14)
+        # far corner, r - R = 6.6 dx: s < exp(-13.2), essentially the interior
+        assert np.allclose(at(11, 0), inner(11, 0), rtol=0, atol=1e-5 * np.abs(qj).max())
+    # +z outflow copies the last plane; x faces copy the edge column
+    assert np.array_equal(qg[:, c.nz + G, G:-G, G:-G], q[:, -1])
+    assert np.array_equal(qg[:, G:-G, G:-G, 0], q[:, :, :, 0])
+
+
+# ---------------------------------------------------- convergence and symmetry
+
+@pytest.mark.slow
+def test_density_wave_design_order():
+    """Smooth density wave advected one period at u = 1, p = 1 (grad u = 0, so
+    Sigma = 0): with dt ~ dx^(5/3) the 3rd-order RK error matches the 5th-order
+    spatial error and the L1 error of rho falls at order close to 5."""
+    errs = []
+    for n in (16, 32, 64):
+        c = inputs.density_wave(n, noise=0.0, ny=3, nz=3)
+        q0 = inputs.initial_state(c, cell_average=True)
+        dt_target = 0.15 * c.dx * (16.0 * c.dx) ** (2.0 / 3.0)
+        steps = int(math.ceil(1.0 / dt_target))
+        q1, s1, t = oracle.run(c, q0, None, nsteps=steps, fixed_dt=1.0 / steps)
+        assert math.isclose(t, 1.0, rel_tol=1e-12)
+        errs.append(np.mean(np.abs(q1[0] - q0[0])))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 4.5), (errs, orders)
+
+
+@pytest.mark.slow
+def test_sod_converges_to_exact_solution():
+    """Quasi-1D Sod tube at t = 0.2: the L1 error of rho against the exact
+    Riemann solution falls with resolution at a rate of at least 0.6."""
+    L, R = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    errs = []
+    for n in (100, 200, 400):
+        c = inputs.sod(n)
+        q0 = inputs.initial_state(c)
+        steps = int(math.ceil(0.2 / (0.4 * c.dx / 2.0)))
+        q1, _, t = oracle.run(c, q0, None, nsteps=steps, fixed_dt=0.2 / steps)
+        x = (np.arange(n) + 0.5) * c.dx
+        ex = sod_exact.sample(L, R, x, 0.2)
+        rho = q1[0].mean(axis=(0, 1))
+        assert np.all(np.isfinite(q1))
+        assert np.max(np.abs(q1[0] - q1[0][:1, :1, :])) <= 1e-12  # stays 1D
+        errs.append(np.mean(np.abs(rho - ex[0])))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert errs[-1] < 0.01, errs
+    assert np.all(orders > 0.6), (errs, orders)
+
+
+def test_exact_riemann_solver_matches_textbook_star_state():
+    """The test helper itself is pinned to the published Sod star state."""
+    g = json.load(open(os.path.join(GOLDEN, "sod_star_state.json")))
+    L = (g["left"]["rho"], g["left"]["u"], g["left"]["p"])
+    R = (g["right"]["rho"], g["right"]["u"], g["right"]["p"])
+    p, u, rl, rr = sod_exact.star_state(L, R, g["gamma"])
+    tol = 0.5 * 10.0 ** -g["digits"]
+    assert abs(p - g["p_star"]) <= tol
+    assert abs(u - g["u_star"]) <= tol
+    assert abs(rl - g["rho_star_left"]) <= tol
+    assert abs(rr - g["rho_star_right"]) <= tol
+
+
+def test_blast_mirror_symmetry():
+    """The noise-free spherical blast stays symmetric under x -> 1 - x (and
+    y, z): rho even, the normal momentum odd."""
+    c = inputs.blast(20, noise=0.0, sweeps=10)
+    q0 = inputs.initial_state(c)
+    q1, s1, _ = oracle.run(c, q0, None, nsteps=5)
+    assert np.abs(s1).max() > 0
+    for ax, mv in ((3, 1), (2, 2), (1, 3)):
+        flip = lambda a: np.flip(a, axis=ax - 1)
+        assert np.allclose(q1[0], flip(q1[0]), rtol=0, atol=1e-13)
+        assert np.allclose(q1[4], flip(q1[4]), rtol=0, atol=1e-13)
+        assert np.allclose(q1[mv], -flip(q1[mv]), rtol=0, atol=1e-13)
+        assert np.allclose(s1, np.flip(s1, axis=ax - 1), rtol=0, atol=1e-13)
