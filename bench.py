@@ -1,0 +1,399 @@
+"""Benchmark of the IGR Euler step on one GB300 (or N independent replicas).
+
+Workload: the many-jet plume, 1024 x 1024 x 2048 cells (2.15e9), 33 Mach-3
+inflow jets on z = 0, outflow elsewhere, alpha = dx^2, 5 Jacobi sweeps per
+stage, CFL 0.4. A step is one full SSP-RK3 step (3 stages x [source, 5
+sweeps, flux/divergence/RK] plus the on-device dt), so the metric is grid
+cell-updates per second including the Sigma solve. The headline form is
+FP32 arithmetic with FP16 state storage; plain FP32 is measured beside it.
+
+Timing: W warm-up steps, then K steps between a barrier and device
+synchronisation, CUDA events on the solver's stream, max over ranks. The
+state (21-43 GB) is far larger than L2, so nothing is reused across steps.
+Per-kernel CUDA events inside the same timed region give each kernel's
+average launch time for the roofline line.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+benchmark) on the host cores, on a bounded crop of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2505_07392_gb300 import inputs  # noqa: E402
+
+METRIC = "grid cell-updates/s per RK step incl. Σ solve; % HBM roofline; plain vs 16-bit"
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM bytes per cell of one launch from an ncu capture of each kernel on the
+# plume workload, keyed by a hash of the kernel source they were taken with;
+# a changed source makes the figure stale (reported as null).
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("igr_kernels.cu", "igr_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2505_07392_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, pci_bus_id=None):
+        self.proc = None
+        self.path = None
+        self.pci = pci_bus_id
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.pci:
+                cmd.insert(1, f"--id={self.pci}")
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(r[0] for r in rows)
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def plume_case(args):
+    if args.size:
+        return inputs.plume(*args.size, steps=args.steps)
+    return inputs.plume(steps=args.steps)
+
+
+def fill_initial_state(case, dtype, device):
+    import torch
+    q = torch.empty((5, case.nz, case.ny, case.nx), dtype=dtype, device=device)
+    zc = max(1, (1 << 27) // (case.nx * case.ny))
+    for k0 in range(0, case.nz, zc):
+        k1 = min(case.nz, k0 + zc)
+        q[:, k0:k1] = inputs.jet_initial_state(case, (k0, k1, 0, case.ny, 0, case.nx), xp=torch,
+                                               device=device, dtype=dtype)
+    return q
+
+
+def words_per_cell(sweeps):
+    """Algorithmic words moved per cell by each kernel class over one step:
+    source 4 read + 1 write per stage; a Jacobi sweep reads Sigma, rho, b and
+    writes Sigma; the flux kernel reads q and Sigma, writes q, and reads the
+    RK base in stages 2 and 3."""
+    return {"source": 3 * 5, "jacobi": 3 * sweeps * 4, "flux": 11 + 16 + 16}
+
+
+def run_form(case, precision, steps, warmup, sync_all, e2e_steps=0):
+    """Time `steps` steps of one precision form; returns a result dict."""
+    import torch
+    from paper_2505_07392_gb300 import igr
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st_dtype = igr.storage_torch_dtype(precision)
+    res = {}
+    with igr.Solver(case, precision) as s:
+        q = fill_initial_state(case, st_dtype, dev)
+        s.set_state(q)
+        del q
+        torch.cuda.synchronize()
+        s.step(warmup)
+        stream = s.stream
+        sync_all()
+        torch.cuda.synchronize()
+        s.profile(True)
+        clk = ClockSampler(getattr(torch.cuda.get_device_properties(dev), "pci_bus_id", None))
+        clk.start()
+        time.sleep(0.3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            s.step(1, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sync_all()
+        clocks = clk.stop()
+        ms = e0.elapsed_time(e1)
+        prof = {name: s.profile_read(k) for name, k in
+                (("source", igr.KC_SOURCE), ("jacobi", igr.KC_JACOBI), ("flux", igr.KC_FLUX),
+                 ("other", igr.KC_OTHER))}
+        s.profile(False)
+        s.sync()
+        res.update(ms=ms, prof=prof, clocks=clocks)
+        if e2e_steps:
+            res["e2e"] = run_e2e(s, case, precision, e2e_steps, sync_all)
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_e2e(s, case, precision, steps, sync_all):
+    """The same metric through the C ABI with HOST buffers: every step copies
+    the state (q and Sigma, pinned host memory) in, advances one step, and
+    copies the new state back out."""
+    import ctypes
+    import torch
+    from paper_2505_07392_gb300 import igr
+    dt = igr.storage_torch_dtype(precision)
+    hq = torch.empty((5,) + s.shape, dtype=dt, pin_memory=True)
+    hs = torch.empty(s.shape, dtype=dt, pin_memory=True)
+    code = {torch.float16: igr.DT_F16, torch.bfloat16: igr.DT_BF16, torch.float32: igr.DT_F32,
+            torch.float64: igr.DT_F64}[dt]
+    L = igr.lib()
+    pq, ps = ctypes.c_void_p(hq.data_ptr()), ctypes.c_void_p(hs.data_ptr())
+
+    def check(st):
+        if st != igr.OK:
+            raise igr.IGRError(st, L.igr_last_error(s.h).decode())
+
+    check(L.igr_get_state(s.h, pq, ps, code, 0))
+    for _ in range(2):  # warm-up of the host path
+        check(L.igr_set_state(s.h, pq, ps, code, 0))
+        check(L.igr_step(s.h, 1, 0.0, None))
+        check(L.igr_get_state(s.h, pq, ps, code, 0))
+    sync_all()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        check(L.igr_set_state(s.h, pq, ps, code, 0))
+        check(L.igr_step(s.h, 1, 0.0, None))
+        check(L.igr_get_state(s.h, pq, ps, code, 0))
+    sync_all()
+    sec = time.perf_counter() - t0
+    nbytes = hq.numel() * hq.element_size() + hs.numel() * hs.element_size()
+    return {"sec": sec, "steps": steps, "bytes": nbytes}
+
+
+def roofline_of(case, res, precision, peak, peak_kind):
+    wb = 8 if precision == "f64" else 4 if precision == "f32" else 2
+    wpc = words_per_cell(case.sweeps)
+    per = {}
+    for name in ("flux", "jacobi", "source"):
+        n, ms = res["prof"][name]
+        if n == 0 or ms <= 0:
+            continue
+        algo_bytes = wpc[name] * wb * case.ncells * (res["prof_steps"])  # over the timed region
+        gbs = algo_bytes / (ms * 1e-3) / 1e9
+        per[name] = {"launches": n, "total_ms": ms, "avg_ms": ms / n,
+                     "bytes_per_launch": algo_bytes / n, "achieved_gbs": gbs}
+    dom = max(per, key=lambda k: per[k]["total_ms"])
+    d = per[dom]
+    key = f"{dom}_{precision}"
+    t = NCU_TRAFFIC.get(key)
+    traffic = (t["bytes_per_cell"] * case.ncells if t and t.get("src") == kernel_source_hash() else None)
+    return {"bound": "hbm", "kernel": dom, "achieved": round(d["achieved_gbs"], 1), "peak": peak,
+            "unit": "GB/s", "frac": round(d["achieved_gbs"] / peak, 4), "traffic": traffic,
+            "peak_kind": f"of {peak_kind}"}, per
+
+
+# ------------------------------------------------------------ CPU baseline
+
+def oracle_sample_case(full, size):
+    """Centred crop of the plume at the inflow face: real -z inflow, every jet
+    inside, zero-gradient at the cuts."""
+    ny, nx, nz = size
+    i0, j0 = (full.nx - nx) // 2, (full.ny - ny) // 2
+    jets = [(j[0] - i0 * full.dx, j[1] - j0 * full.dx) + tuple(j[2:]) for j in full.jets]
+    bc = (inputs.OUTFLOW,) * 4 + (inputs.INFLOW, inputs.OUTFLOW)
+    c = inputs.Case("plume_crop", nx, ny, nz, full.dx, alpha=full.alpha, cfl=full.cfl,
+                    sweeps=full.sweeps, bc=bc, jets=jets)
+    window = (0, nz, j0, j0 + ny, i0, i0 + nx)
+    return c, window
+
+
+def cpu_baseline(full, steps=1, size=(256, 256, 64)):
+    import oracle
+    c, window = oracle_sample_case(full, size)
+    q0 = inputs.jet_initial_state(full, window)
+    oracle.lib()
+    t0 = time.perf_counter()
+    oracle.run(c, q0, None, nsteps=steps)
+    sec = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": c.ncells * steps / sec, "unit": "cell-updates/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{c.nx}x{c.ny}x{c.nz} crop of the plume at the inflow face (all 33 jets), "
+                      f"{steps} SSP-RK3 step(s) in FP64, {sec:.1f} s"}
+
+
+# -------------------------------------------------------------------- main
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f16", choices=["f16", "bf16", "f32", "f64"])
+    ap.add_argument("--plain", default="f32", help="second form measured beside the headline ('' = none)")
+    ap.add_argument("--size", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"))
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-size", type=int, nargs=3, default=(256, 256, 64))
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world, rank, local = dist_setup(args)
+    full = plume_case(args)
+    workload = f"plume {full.nx}x{full.ny}x{full.nz}, 33 Mach-3 jets, S={full.sweeps}"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # W warm-up steps are accepted for the contract; the oracle keeps no state to warm
+        import oracle
+        c, window = oracle_sample_case(full, tuple(args.cpu_size))
+        q = inputs.jet_initial_state(full, window)
+        sig = None
+        oracle.lib()
+        secs = 0.0
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            q, sig, _t = oracle.run(c, q, sig, nsteps=1)
+            secs += time.perf_counter() - t0
+        value = c.ncells * args.steps / secs
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        cb = {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+              "sample": f"{c.nx}x{c.ny}x{c.nz} crop of the plume at the inflow face (all 33 jets), "
+                        f"{args.steps} SSP-RK3 step(s) in FP64, {secs:.1f} s"}
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * secs / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": workload + " (oracle on a crop)",
+                                                "crop": list(args.cpu_size)},
+                "cpu_baseline": cb,
+                "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+        def sync_all():
+            dist.barrier()
+    else:
+        def sync_all():
+            pass
+
+    from paper_2505_07392_gb300 import build
+    build.build()
+
+    res = run_form(full, args.precision, args.steps, args.warmup, sync_all,
+                   e2e_steps=args.e2e_steps if rank == 0 else 0)
+    res["prof_steps"] = args.steps
+    ms = res["ms"]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells = full.ncells * args.steps * world
+    value = cells / (ms * 1e-3)
+    peak, peak_kind = measured_peaks()
+    roof, per_kernel = roofline_of(full, res, args.precision, peak, peak_kind)
+
+    plain = None
+    if args.plain and args.plain != args.precision:
+        rp = run_form(full, args.plain, args.steps, args.warmup, sync_all)
+        rp["prof_steps"] = args.steps
+        roof_p, _ = roofline_of(full, rp, args.plain, peak, peak_kind)
+        plain = {"precision": args.plain, "value": full.ncells * args.steps * world / (rp["ms"] * 1e-3),
+                 "ms_per_step": rp["ms"] / args.steps, "roofline": roof_p, "clocks": rp["clocks"]}
+
+    if rank != 0:
+        return
+    launches = sum(v[0] for v in res["prof"].values())
+    wb = 2 if args.precision in ("f16", "bf16") else 4 if args.precision == "f32" else 8
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f16": "f32 compute, f16 storage", "bf16": "f32 compute, bf16 storage",
+                  "f32": "f32", "f64": "f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": workload, "cells": full.ncells, "precision": args.precision,
+                   "sweeps": full.sweeps, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (state %.1f GB)" % (6 * full.ncells * wb / 1e9)},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernels": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in v.items()}
+                    for k, v in per_kernel.items()},
+        "clocks": res["clocks"],
+    }
+    if plain:
+        line["plain"] = plain
+        line["speedup_vs_plain"] = value / plain["value"]
+    if "e2e" in res:
+        e = res["e2e"]
+        line["e2e"] = {"value": full.ncells * e["steps"] / e["sec"], "unit": "cell-updates/s",
+                       "h2d_bytes_per_step": e["bytes"], "d2h_bytes_per_step": e["bytes"],
+                       "steps": e["steps"]}
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(full, 1, tuple(args.cpu_size))
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

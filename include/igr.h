@@ -1,0 +1,174 @@
+/*
+ * igr.h - C ABI of the GB300 IGR Euler stage solver.
+ *
+ * One call of igr_step advances the 3D compressible Euler equations with
+ * information geometric regularization (IGR) by SSP-RK3 time steps on a
+ * uniform Cartesian grid. Each of the three stages runs, on one GPU:
+ *   1. velocity gradients and the IGR source
+ *        b = alpha [tr((grad u)^2) + tr^2(grad u)]       (Eq. igrelliptic, left side)
+ *   2. warm-started Jacobi sweeps for the entropic pressure Sigma of
+ *        Sigma/rho - alpha div(grad Sigma / rho) = b      (Eq. igrelliptic)
+ *      with the 7-point stencil and face coefficient (1/rho_i + 1/rho_nb)/2
+ *   3. 5th-order finite-volume face reconstruction of (rho, m, E, Sigma),
+ *      local Lax-Friedrichs flux of the IGR-modified Euler system with
+ *      pressure p + Sigma                         (Eqs. igrmabalance-igrenbalance)
+ *   4. flux divergence and the SSP-RK3 stage update (Gottlieb-Shu)
+ * following Sec. "Discretization" and Algorithm 1 of the paper.
+ *
+ * Conventions for every function:
+ *  - Return value: an igr_status. No exception or longjmp crosses the ABI.
+ *    On failure igr_last_error(ctx) gives a one-line message.
+ *  - State layout: q is [5][nz][ny][nx] contiguous (x fastest), variables
+ *    (rho, rho u, rho v, rho w, E), interior cells only. Sigma is
+ *    [nz][ny][nx]. No ghost cells: boundary conditions act by index mapping.
+ *  - Device pointers are borrowed. Calls that take them are asynchronous on
+ *    the context's stream; the caller keeps the memory alive until that
+ *    stream has passed the call. Host pointers are read or written before
+ *    the call returns.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - Asynchronous faults (CUDA errors, non-finite results) surface at the
+ *    next call that synchronises: igr_get_state, igr_sync, or igr_step with
+ *    a non-NULL t_inout.
+ */
+#ifndef IGR_H
+#define IGR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IGR_OK = 0,
+    IGR_ERR_INVALID_ARG = 1, /* rejected before any launch */
+    IGR_ERR_OOM = 2,         /* an allocation failed */
+    IGR_ERR_CUDA = 3,        /* a CUDA call failed */
+    IGR_ERR_NONFINITE = 4,   /* a stage produced a NaN/Inf (e.g. negative pressure) */
+    IGR_ERR_TIMEOUT = 5,     /* reserved for bounded device-side waits */
+    IGR_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+} igr_status;
+
+/* Arithmetic and storage of a context. */
+typedef enum {
+    IGR_F64 = 0,           /* FP64 storage and arithmetic */
+    IGR_F32 = 1,           /* FP32 storage and arithmetic */
+    IGR_F32_F16STORE = 2,  /* FP32 arithmetic, q/Sigma/b stored as IEEE binary16,
+                              RK combination in FP64, round-to-nearest-even on store */
+    IGR_F32_BF16STORE = 3  /* as above with bfloat16 storage */
+} igr_precision;
+
+/* Element type of a buffer passed across the ABI. */
+typedef enum { IGR_DT_F64 = 0, IGR_DT_F32 = 1, IGR_DT_F16 = 2, IGR_DT_BF16 = 3 } igr_dtype;
+
+/* Boundary condition of one domain face. */
+typedef enum {
+    IGR_BC_PERIODIC = 0, /* wrap (must be set on both faces of an axis) */
+    IGR_BC_OUTFLOW = 1,  /* zero gradient: out-of-domain cells copy the nearest cell */
+    IGR_BC_INFLOW = 2    /* jets (only on the -z face): the out-of-domain state is
+                            (1 - sum_n s_n) q_nearest + sum_n s_n q_jet_n with
+                            s_n = (1 - tanh((r_n - R_n)/(edge_width_n dx)))/2;
+                            Sigma sees zero gradient */
+} igr_bc;
+
+/* A circular jet on the -z face: centre (cx, cy) and radius in length units,
+ * primitive state (rho, w along +z, p), edge width in cells. */
+typedef struct {
+    double cx, cy, radius, rho, w, p, edge_width;
+} igr_jet;
+
+/* Optional caller-supplied device allocator (e.g. a framework's caching
+ * allocator). alloc returns device memory aligned to 256 bytes or NULL. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *user);
+    void (*free)(void *ptr, void *user);
+    void *user;
+} igr_allocator;
+
+typedef struct {
+    int nx, ny, nz;     /* cells per axis, each >= 4 */
+    double dx;          /* cell size (cubic cells) */
+    double gamma;       /* ideal-gas ratio of specific heats, Eq. (state_eqn) */
+    double alpha;       /* IGR alpha, proportional to dx^2 */
+    double cfl;         /* dt = cfl dx / max_cells max_d(|u_d| + c) */
+    int sweeps;         /* Jacobi sweeps per stage, >= 1 */
+    igr_precision prec;
+    igr_bc bc[6];       /* faces -x, +x, -y, +y, -z, +z */
+    const igr_jet *jets;/* njets jets on an IGR_BC_INFLOW -z face (copied) */
+    int njets;
+} igr_config;
+
+typedef struct igr_ctx igr_ctx; /* opaque */
+
+/* Validate cfg and allocate the context on the current CUDA device:
+ * three state buffers (5 fields each), two Sigma buffers, the source b,
+ * the inflow tables and a few scalars, all in the storage type of
+ * cfg->prec. allocator may be NULL (cudaMalloc). cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream). The state and Sigma start
+ * at zero; call igr_set_state before stepping. */
+igr_status igr_create(const igr_config *cfg, const igr_allocator *allocator, void *cuda_stream,
+                      igr_ctx **out);
+
+/* Device bytes igr_create allocates for cfg (0 if cfg is invalid). */
+size_t igr_memory_bytes(const igr_config *cfg);
+
+/* Synchronise the stream, free every buffer, destroy the context. NULL is a no-op. */
+igr_status igr_destroy(igr_ctx *ctx);
+
+/* Copy a state into the context. q holds 5 n values, sigma n values
+ * (NULL sets Sigma = 0, the cold start). dtype is the element type of q
+ * and sigma; on_device = 1 means device pointers (any dtype, converted on
+ * the device), 0 means host pointers (dtype must be the storage type). */
+igr_status igr_set_state(igr_ctx *ctx, const void *q, const void *sigma, igr_dtype dtype,
+                         int on_device);
+
+/* Copy the state out (q: 5 n values, sigma: n values or NULL), same
+ * dtype/on_device rules as igr_set_state. Synchronises the stream and
+ * reports pending asynchronous errors. */
+igr_status igr_get_state(igr_ctx *ctx, void *q, void *sigma, igr_dtype dtype, int on_device);
+
+/* Advance nsteps SSP-RK3 steps. fixed_dt > 0 uses that dt; otherwise each
+ * step takes dt = cfl dx / max_d(|u_d| + c) of the state at its start,
+ * computed on the device (no host round trip). If t_inout is non-NULL the
+ * call synchronises, adds the elapsed simulated time to *t_inout and
+ * reports asynchronous errors; with NULL it only enqueues. */
+igr_status igr_step(igr_ctx *ctx, int nsteps, double fixed_dt, double *t_inout);
+
+/* Sigma solve alone, on caller buffers in the storage dtype (device
+ * pointers): b from q, then `sweeps` Jacobi sweeps warm-started from
+ * sigma_inout; the result overwrites sigma_inout. Uses the context's b and
+ * second Sigma buffer as scratch (the context state is untouched). */
+igr_status igr_solve_sigma(igr_ctx *ctx, const void *q, void *sigma_inout, int sweeps,
+                           igr_dtype dtype);
+
+/* Spatial operator L(q; Sigma) = -div F_hat (no elliptic solve, no RK):
+ * q and sigma are device buffers in the storage dtype (dtype), rhs is a
+ * device buffer of 5 n values in the arithmetic type (FP64 for IGR_F64,
+ * FP32 otherwise). */
+igr_status igr_rhs(igr_ctx *ctx, const void *q, const void *sigma, void *rhs, igr_dtype dtype);
+
+/* Time step dt = cfl dx / max_d(|u_d| + c) of the current state.
+ * Synchronises. */
+igr_status igr_get_dt(igr_ctx *ctx, double *dt);
+
+/* Synchronise the stream and report pending asynchronous errors. */
+igr_status igr_sync(igr_ctx *ctx);
+
+/* Per-kernel timing with CUDA events on the context stream. While enabled,
+ * every launch is bracketed by an event pair; igr_profile_read synchronises
+ * and returns, for kernel class k (0 source, 1 jacobi, 2 flux, 3 other),
+ * the launch count and total milliseconds since enabling. */
+igr_status igr_profile_enable(igr_ctx *ctx, int on);
+igr_status igr_profile_read(igr_ctx *ctx, int kernel_class, long long *launches, double *total_ms);
+
+/* Message of the last failure on ctx (or of the last failed igr_create when
+ * ctx is NULL). Never NULL. */
+const char *igr_last_error(const igr_ctx *ctx);
+
+/* Library version string. */
+const char *igr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGR_H */

@@ -1,0 +1,73 @@
+"""Builds libigr.so, the CUDA library behind include/igr.h, for sm_103a.
+
+The kernel source igr_kernels.cu is compiled once per storage type (FP64,
+FP32, FP16, BF16) and the host runtime igr_api.cu once; the five objects
+compile in parallel and link into paper_2505_07392_gb300/libigr.so.
+"""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+OBJ = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libigr.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "-diag-suppress", "177"]
+
+VARIANTS = [("f64", "double"), ("f32", "float"), ("f16", "__half"), ("bf16", "__nv_bfloat16")]
+
+
+def nvcc():
+    exe = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(exe):
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libigr.so")
+    return exe
+
+
+def _sources():
+    return [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".h", ".cuh"))] + \
+        [os.path.join(HERE, "..", "include", "igr.h")]
+
+
+def _jobs(extra):
+    jobs = []
+    for tag, ty in VARIANTS:
+        jobs.append([nvcc(), *ARCH, *FLAGS, *extra, f"-DIGR_STORAGE={ty}", f"-DIGR_OPS=ops_{tag}",
+                     "-c", os.path.join(CSRC, "igr_kernels.cu"), "-o", os.path.join(OBJ, f"kern_{tag}.o")])
+    jobs.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, "igr_api.cu"),
+                 "-o", os.path.join(OBJ, "api.o")])
+    return jobs
+
+
+def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+    """Compile and link libigr.so if it is missing or older than a source."""
+    if not force and os.path.exists(LIB):
+        newest = max(os.path.getmtime(f) for f in _sources())
+        if os.path.getmtime(LIB) >= newest:
+            return LIB
+    os.makedirs(OBJ, exist_ok=True)
+    jobs = _jobs(list(extra))
+
+    def run(cmd):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+        return r.stdout + r.stderr
+
+    with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        logs = list(ex.map(run, jobs))
+    if verbose:
+        print("\n".join(logs))
+    objs = [j[-1] for j in jobs]
+    tmp = LIB + f".tmp{os.getpid()}"
+    run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    xv = ["-Xptxas", "-v"] if "-v" in sys.argv else []
+    print(build(force=True, verbose=bool(xv), extra=xv))

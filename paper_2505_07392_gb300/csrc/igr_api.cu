@@ -1,0 +1,663 @@
+// Host runtime of the IGR solver: the C ABI of include/igr.h.
+//
+// A context owns, in the storage type of its precision mode:
+//   qA, qB, qC   three state buffers (5 n each). The RK stage reads its
+//                input with a stencil, so it cannot write in place; stage 1
+//                writes qB, stage 2 qC, stage 3 writes back into qA (the RK
+//                base, read only at the same cell by the same thread).
+//   sig[2]       Sigma ping-pong pair; Sigma persists across stages and steps
+//                as the warm start of the Jacobi sweeps.
+//   b            IGR source.
+// plus the -z inflow tables (arithmetic type), the per-block wave-speed
+// maxima and a small block of device scalars (dt, t, speed, error flag).
+// A time step never returns to the host: dt is reduced and applied on the
+// device.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/igr.h"
+#include "igr_internal.h"
+
+using namespace igr;
+
+struct igr_ctx {
+    igr_config cfg;
+    std::vector<igr_jet> jets;
+    Geom g;
+    Phys p;
+    Tiles tiles;
+    const Ops *ops;
+    igr_allocator alloc;
+    bool own_alloc;
+    cudaStream_t st;
+    int device;
+    void *q[3];
+    void *sig[2];
+    void *b;
+    void *W, *J;
+    double *blockmax;
+    long long blockmax_len;
+    Scalars *sc;
+    double *jets_dev;
+    int cur;            // index of the current Sigma buffer
+    int speed_nblocks;  // valid entries of blockmax for the current state (0: stale)
+    bool profiling;
+    std::vector<cudaEvent_t> ev;  // start/stop pairs of the pending launches
+    std::vector<int> ev_class;
+    long long prof_launches[KC_COUNT];
+    double prof_ms[KC_COUNT];
+    char err[512];
+};
+
+static char g_create_err[512] = "";
+
+static igr_status fail(igr_ctx *c, igr_status s, const char *fmt, ...)
+{
+    char *buf = c ? c->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define CU(ctx, call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(ctx, IGR_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+// ------------------------------------------------------------ small kernels
+
+// W[j][i] = sum_n s_n, J[v][j][i] = sum_n s_n q_jet_n[v],
+// s_n = (1 - tanh((r_n - R_n) / (edge_n dx))) / 2 at the cell centre (x, y).
+template <typename T>
+__global__ void k_inflow_tables(int nx, int ny, double dx, double gamma, const double *jets,
+                                int njets, T *W, T *J)
+{
+    long long plane = (long long)nx * ny;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < plane;
+         f += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(f % nx), j = (int)(f / nx);
+        double x = (i + 0.5) * dx, y = (j + 0.5) * dx;
+        double w = 0.0, acc[5] = {0, 0, 0, 0, 0};
+        for (int n = 0; n < njets; n++) {
+            const double *jt = jets + 7 * n;
+            double r = sqrt((x - jt[0]) * (x - jt[0]) + (y - jt[1]) * (y - jt[1]));
+            double s = 0.5 * (1.0 - tanh((r - jt[2]) / (jt[6] * dx)));
+            double rho = jt[3], vw = jt[4], p = jt[5];
+            double qj[5] = {rho, 0.0, 0.0, rho * vw, p / (gamma - 1.0) + 0.5 * rho * vw * vw};
+            w += s;
+            for (int v = 0; v < 5; v++) acc[v] += s * qj[v];
+        }
+        W[f] = (T)w;
+        for (int v = 0; v < 5; v++) J[v * plane + f] = (T)acc[v];
+    }
+}
+
+__device__ __forceinline__ double load_any(const void *p, int dt, long long i)
+{
+    switch (dt) {
+    case IGR_DT_F64: return ((const double *)p)[i];
+    case IGR_DT_F32: return ((const float *)p)[i];
+    case IGR_DT_F16: return __half2float(((const __half *)p)[i]);
+    default: return __bfloat162float(((const __nv_bfloat16 *)p)[i]);
+    }
+}
+__device__ __forceinline__ void store_any(void *p, int dt, long long i, double v)
+{
+    switch (dt) {
+    case IGR_DT_F64: ((double *)p)[i] = v; break;
+    case IGR_DT_F32: ((float *)p)[i] = (float)v; break;
+    case IGR_DT_F16: ((__half *)p)[i] = __double2half(v); break;
+    default: ((__nv_bfloat16 *)p)[i] = __double2bfloat16(v); break;
+    }
+}
+
+// dst[i] = src[i] converted (round to nearest even), or 0 when src is NULL
+__global__ void k_convert(const void *src, int sdt, void *dst, int ddt, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        store_any(dst, ddt, i, src ? load_any(src, sdt, i) : 0.0);
+}
+
+__device__ __forceinline__ double nanmax_d(double a, double b) { return (a > b || a != a) ? a : b; }
+
+// dt from the per-block wave-speed maxima (or the fixed dt), t += dt
+__global__ void k_finalize_dt(const double *blockmax, int nblocks, Scalars *sc, double cfl_dx,
+                              double fixed_dt)
+{
+    __shared__ double red[32];
+    double m = 0.0;
+    if (fixed_dt <= 0.0)
+        for (int t = threadIdx.x; t < nblocks; t += blockDim.x) m = nanmax_d(m, blockmax[t]);
+    for (int o = 16; o > 0; o >>= 1) m = nanmax_d(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = nanmax_d(m, red[w]);
+        double dt = fixed_dt > 0.0 ? fixed_dt : cfl_dx / m;
+        if (fixed_dt <= 0.0) sc->speed = m;
+        if (!(dt > 0.0) || isinf(dt)) sc->err |= 1;
+        sc->dt = dt;
+        sc->t += dt;
+    }
+}
+
+// ------------------------------------------------------------ helpers
+
+static int storage_dtype(igr_precision p)
+{
+    switch (p) {
+    case IGR_F64: return IGR_DT_F64;
+    case IGR_F32: return IGR_DT_F32;
+    case IGR_F32_F16STORE: return IGR_DT_F16;
+    default: return IGR_DT_BF16;
+    }
+}
+static size_t dtype_bytes(int dt) { return dt == IGR_DT_F64 ? 8 : dt == IGR_DT_F32 ? 4 : 2; }
+
+static const Ops *ops_for(igr_precision p)
+{
+    switch (p) {
+    case IGR_F64: return &ops_f64;
+    case IGR_F32: return &ops_f32;
+    case IGR_F32_F16STORE: return &ops_f16;
+    case IGR_F32_BF16STORE: return &ops_bf16;
+    }
+    return nullptr;
+}
+
+static Tiles default_tiles(const Geom &g)
+{
+    Tiles t;
+    t.zc_source = g.nz < 32 ? g.nz : 32;
+    t.zc_jacobi = g.nz < 32 ? g.nz : 32;
+    t.zc_flux = g.nz < 32 ? g.nz : 32;
+    return t;
+}
+
+static const char *validate(const igr_config *c)
+{
+    if (!c) return "cfg is NULL";
+    if (c->nx < 4 || c->ny < 4 || c->nz < 4) return "nx, ny, nz must each be >= 4";
+    if ((long long)c->nx * c->ny > (1ll << 31) - 1) return "nx*ny must fit in a 32-bit int";
+    if (!(c->dx > 0) || !(c->gamma > 1) || !(c->alpha >= 0) || !(c->cfl > 0) || isinf(c->dx))
+        return "need dx > 0, gamma > 1, alpha >= 0, cfl > 0";
+    if (c->sweeps < 1) return "sweeps must be >= 1";
+    if (c->prec < IGR_F64 || c->prec > IGR_F32_BF16STORE) return "unknown precision mode";
+    for (int f = 0; f < 6; f++)
+        if (c->bc[f] < IGR_BC_PERIODIC || c->bc[f] > IGR_BC_INFLOW) return "unknown boundary condition";
+    for (int a = 0; a < 3; a++)
+        if ((c->bc[2 * a] == IGR_BC_PERIODIC) != (c->bc[2 * a + 1] == IGR_BC_PERIODIC))
+            return "a periodic axis must be periodic on both faces";
+    for (int f = 0; f < 6; f++)
+        if (c->bc[f] == IGR_BC_INFLOW && f != 4) return "IGR_BC_INFLOW is supported on the -z face only";
+    if (c->njets < 0 || (c->njets > 0 && !c->jets)) return "jets is NULL with njets > 0";
+    if (c->njets > 0 && c->bc[4] != IGR_BC_INFLOW) return "jets need an IGR_BC_INFLOW -z face";
+    for (int n = 0; n < c->njets; n++) {
+        const igr_jet &j = c->jets[n];
+        if (!(j.rho > 0) || !(j.p > 0) || !(j.edge_width > 0) || !(j.radius >= 0))
+            return "jet needs rho > 0, p > 0, edge_width > 0, radius >= 0";
+    }
+    return nullptr;
+}
+
+struct Layout {
+    size_t state, sig, b, W, J, blockmax, scalars, jets;
+};
+
+static Layout layout_of(const igr_config *c)
+{
+    Geom g;
+    g.nx = c->nx; g.ny = c->ny; g.nz = c->nz;
+    g.plane = (long long)c->nx * c->ny;
+    g.n = g.plane * c->nz;
+    const Ops *o = ops_for(c->prec);
+    Tiles t = default_tiles(g);
+    Layout L;
+    L.state = (size_t)5 * g.n * o->storage_bytes;
+    L.sig = (size_t)g.n * o->storage_bytes;
+    L.b = L.sig;
+    L.W = (size_t)g.plane * o->compute_bytes;
+    L.J = 5 * L.W;
+    long long fb = o->flux_blocks(g, t);
+    L.blockmax = (size_t)(fb > 4096 ? fb : 4096) * sizeof(double);
+    L.scalars = 2 * sizeof(Scalars);  // [0] stepping, [1] igr_get_dt
+    L.jets = (size_t)(c->njets > 0 ? c->njets : 1) * 7 * sizeof(double);
+    return L;
+}
+
+static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static void *default_alloc(size_t bytes, void *)
+{
+    void *p = nullptr;
+    return cudaMalloc(&p, bytes) == cudaSuccess ? p : nullptr;
+}
+static void default_free(void *p, void *) { cudaFree(p); }
+
+static igr_status ctx_alloc(igr_ctx *c, void **out, size_t bytes)
+{
+    *out = c->alloc.alloc(round256(bytes), c->alloc.user);
+    if (!*out) return fail(c, IGR_ERR_OOM, "device allocation of %zu bytes failed", bytes);
+    return IGR_OK;
+}
+
+// ------------------------------------------------------------ profiling
+
+static void prof_begin(igr_ctx *c, int cls)
+{
+    if (!c->profiling) return;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, c->st);
+    c->ev.push_back(a);
+    c->ev.push_back(b);
+    c->ev_class.push_back(cls);
+}
+static void prof_end(igr_ctx *c)
+{
+    if (!c->profiling) return;
+    cudaEventRecord(c->ev.back(), c->st);
+}
+static void prof_collect(igr_ctx *c)
+{
+    for (size_t n = 0; n < c->ev_class.size(); n++) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev[2 * n], c->ev[2 * n + 1]);
+        c->prof_ms[c->ev_class[n]] += ms;
+        c->prof_launches[c->ev_class[n]] += 1;
+        cudaEventDestroy(c->ev[2 * n]);
+        cudaEventDestroy(c->ev[2 * n + 1]);
+    }
+    c->ev.clear();
+    c->ev_class.clear();
+}
+
+// ------------------------------------------------------------ stage logic
+
+static Inflow inflow_of(igr_ctx *c)
+{
+    Inflow in;
+    in.W = c->W;
+    in.J = c->J;
+    return in;
+}
+
+static igr_status launch_sweeps(igr_ctx *c, const void *q, const void *b, void *s_first,
+                                void *s_other, int sweeps, void **result)
+{
+    void *src = s_first, *dst = s_other;
+    for (int it = 0; it < sweeps; it++) {
+        prof_begin(c, KC_JACOBI);
+        CU(c, c->ops->jacobi(c->g, c->p, c->tiles, q, b, src, dst, c->st));
+        prof_end(c);
+        void *t = src;
+        src = dst;
+        dst = t;
+    }
+    *result = src;
+    return IGR_OK;
+}
+
+static igr_status run_stage(igr_ctx *c, int mode, const void *qs, const void *qn, void *out)
+{
+    prof_begin(c, KC_SOURCE);
+    CU(c, c->ops->source(c->g, c->p, c->tiles, inflow_of(c), qs, c->b, c->st));
+    prof_end(c);
+    void *res;
+    igr_status s = launch_sweeps(c, qs, c->b, c->sig[c->cur], c->sig[1 - c->cur], c->cfg.sweeps, &res);
+    if (s != IGR_OK) return s;
+    c->cur = res == c->sig[0] ? 0 : 1;
+    prof_begin(c, KC_FLUX);
+    CU(c, c->ops->flux(c->g, c->p, c->tiles, inflow_of(c), mode, qs, c->sig[c->cur], qn, out,
+                       nullptr, c->sc, c->blockmax, &c->sc->err, c->st));
+    prof_end(c);
+    return IGR_OK;
+}
+
+static igr_status refresh_speed(igr_ctx *c)
+{
+    if (c->speed_nblocks > 0) return IGR_OK;
+    int nb = 0;
+    prof_begin(c, KC_OTHER);
+    CU(c, c->ops->speed(c->g, c->p, c->q[0], c->blockmax, &nb, c->st));
+    prof_end(c);
+    c->speed_nblocks = nb;
+    return IGR_OK;
+}
+
+static igr_status read_flags(igr_ctx *c)
+{
+    CU(c, cudaStreamSynchronize(c->st));
+    if (c->profiling) prof_collect(c);
+    int err = 0;
+    CU(c, cudaMemcpy(&err, &c->sc->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        int zero = 0;
+        CU(c, cudaMemcpy(&c->sc->err, &zero, sizeof(int), cudaMemcpyHostToDevice));
+        return fail(c, IGR_ERR_NONFINITE,
+                    "a stage produced a non-finite value or a non-positive face density/pressure");
+    }
+    return IGR_OK;
+}
+
+// ------------------------------------------------------------ the C ABI
+
+extern "C" {
+
+const char *igr_version(void) { return "igr-gb300 0.1 (sm_103a)"; }
+
+const char *igr_last_error(const igr_ctx *ctx) { return ctx ? ctx->err : g_create_err; }
+
+size_t igr_memory_bytes(const igr_config *cfg)
+{
+    if (validate(cfg)) return 0;
+    Layout L = layout_of(cfg);
+    return 3 * round256(L.state) + 2 * round256(L.sig) + round256(L.b) + round256(L.W) +
+           round256(L.J) + round256(L.blockmax) + round256(L.scalars) + round256(L.jets);
+}
+
+igr_status igr_create(const igr_config *cfg, const igr_allocator *allocator, void *cuda_stream,
+                      igr_ctx **out)
+{
+    if (!out) return fail(nullptr, IGR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (const char *why = validate(cfg)) return fail(nullptr, IGR_ERR_INVALID_ARG, "%s", why);
+    if (allocator && (!allocator->alloc || !allocator->free))
+        return fail(nullptr, IGR_ERR_INVALID_ARG, "allocator needs alloc and free");
+    igr_ctx *c = new (std::nothrow) igr_ctx();
+    if (!c) return fail(nullptr, IGR_ERR_OOM, "host allocation failed");
+    c->cfg = *cfg;
+    c->jets.assign(cfg->jets, cfg->jets + cfg->njets);
+    c->cfg.jets = c->jets.data();
+    c->g.nx = cfg->nx;
+    c->g.ny = cfg->ny;
+    c->g.nz = cfg->nz;
+    for (int f = 0; f < 6; f++) c->g.bc[f] = cfg->bc[f];
+    c->g.plane = (long long)cfg->nx * cfg->ny;
+    c->g.n = c->g.plane * cfg->nz;
+    c->p.dx = cfg->dx;
+    c->p.gamma = cfg->gamma;
+    c->p.alpha = cfg->alpha;
+    c->p.cfl = cfg->cfl;
+    c->tiles = default_tiles(c->g);
+    c->ops = ops_for(cfg->prec);
+    if (allocator) {
+        c->alloc = *allocator;
+    } else {
+        c->alloc.alloc = default_alloc;
+        c->alloc.free = default_free;
+        c->alloc.user = nullptr;
+    }
+    c->st = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&c->device);
+
+    Layout L = layout_of(cfg);
+    igr_status s = IGR_OK;
+    for (int n = 0; n < 3 && s == IGR_OK; n++) s = ctx_alloc(c, &c->q[n], L.state);
+    for (int n = 0; n < 2 && s == IGR_OK; n++) s = ctx_alloc(c, &c->sig[n], L.sig);
+    if (s == IGR_OK) s = ctx_alloc(c, &c->b, L.b);
+    if (s == IGR_OK) s = ctx_alloc(c, &c->W, L.W);
+    if (s == IGR_OK) s = ctx_alloc(c, &c->J, L.J);
+    if (s == IGR_OK) s = ctx_alloc(c, (void **)&c->blockmax, L.blockmax);
+    if (s == IGR_OK) s = ctx_alloc(c, (void **)&c->sc, L.scalars);
+    if (s == IGR_OK) s = ctx_alloc(c, (void **)&c->jets_dev, L.jets);
+    c->blockmax_len = (long long)(L.blockmax / sizeof(double));
+    if (s != IGR_OK) {
+        snprintf(g_create_err, sizeof g_create_err, "%s", c->err);
+        igr_destroy(c);
+        return s;
+    }
+    // zero state, Sigma, scalars; build the inflow tables
+    cudaError_t e = cudaSuccess;
+    for (int n = 0; n < 3 && e == cudaSuccess; n++) e = cudaMemsetAsync(c->q[n], 0, L.state, c->st);
+    for (int n = 0; n < 2 && e == cudaSuccess; n++) e = cudaMemsetAsync(c->sig[n], 0, L.sig, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->b, 0, L.b, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->sc, 0, L.scalars, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->W, 0, L.W, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->J, 0, L.J, c->st);
+    if (e == cudaSuccess && cfg->njets > 0) {
+        std::vector<double> jt(7 * cfg->njets);
+        for (int n = 0; n < cfg->njets; n++) {
+            const igr_jet &j = cfg->jets[n];
+            double v[7] = {j.cx, j.cy, j.radius, j.rho, j.w, j.p, j.edge_width};
+            memcpy(&jt[7 * n], v, sizeof v);
+        }
+        e = cudaMemcpy(c->jets_dev, jt.data(), jt.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            int blocks = (int)((c->g.plane + 255) / 256);
+            if (blocks > 4096) blocks = 4096;
+            if (c->ops->compute_bytes == 8)
+                k_inflow_tables<double><<<blocks, 256, 0, c->st>>>(
+                    cfg->nx, cfg->ny, cfg->dx, cfg->gamma, c->jets_dev, cfg->njets, (double *)c->W,
+                    (double *)c->J);
+            else
+                k_inflow_tables<float><<<blocks, 256, 0, c->st>>>(
+                    cfg->nx, cfg->ny, cfg->dx, cfg->gamma, c->jets_dev, cfg->njets, (float *)c->W,
+                    (float *)c->J);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) {
+        snprintf(g_create_err, sizeof g_create_err, "igr_create: %s", cudaGetErrorString(e));
+        igr_destroy(c);
+        return IGR_ERR_CUDA;
+    }
+    c->cur = 0;
+    c->speed_nblocks = 0;
+    *out = c;
+    return IGR_OK;
+}
+
+igr_status igr_destroy(igr_ctx *c)
+{
+    if (!c) return IGR_OK;
+    cudaStreamSynchronize(c->st);
+    if (c->profiling) prof_collect(c);
+    void *bufs[] = {c->q[0], c->q[1], c->q[2], c->sig[0], c->sig[1], c->b, c->W, c->J,
+                    c->blockmax, c->sc, c->jets_dev};
+    for (void *p : bufs)
+        if (p) c->alloc.free(p, c->alloc.user);
+    delete c;
+    return IGR_OK;
+}
+
+static igr_status copy_in(igr_ctx *c, const void *src, void *dst, long long count, igr_dtype dt,
+                          int on_device)
+{
+    int sdt = storage_dtype(c->cfg.prec);
+    size_t sb = dtype_bytes(sdt);
+    if (!on_device) {
+        if ((int)dt != sdt)
+            return fail(c, IGR_ERR_UNSUPPORTED, "host buffers must use the storage dtype (%d)", sdt);
+        CU(c, cudaMemcpyAsync(dst, src, count * sb, cudaMemcpyHostToDevice, c->st));
+        return IGR_OK;
+    }
+    if ((int)dt == sdt) {
+        CU(c, cudaMemcpyAsync(dst, src, count * sb, cudaMemcpyDeviceToDevice, c->st));
+    } else {
+        k_convert<<<2048, 256, 0, c->st>>>(src, dt, dst, sdt, count);
+        CU(c, cudaGetLastError());
+    }
+    return IGR_OK;
+}
+
+static igr_status copy_out(igr_ctx *c, const void *src, void *dst, long long count, igr_dtype dt,
+                           int on_device)
+{
+    int sdt = storage_dtype(c->cfg.prec);
+    size_t sb = dtype_bytes(sdt);
+    if (!on_device) {
+        if ((int)dt != sdt)
+            return fail(c, IGR_ERR_UNSUPPORTED, "host buffers must use the storage dtype (%d)", sdt);
+        CU(c, cudaMemcpyAsync(dst, src, count * sb, cudaMemcpyDeviceToHost, c->st));
+        return IGR_OK;
+    }
+    if ((int)dt == sdt) {
+        CU(c, cudaMemcpyAsync(dst, src, count * sb, cudaMemcpyDeviceToDevice, c->st));
+    } else {
+        k_convert<<<2048, 256, 0, c->st>>>(src, sdt, dst, dt, count);
+        CU(c, cudaGetLastError());
+    }
+    return IGR_OK;
+}
+
+igr_status igr_set_state(igr_ctx *c, const void *q, const void *sigma, igr_dtype dtype, int on_device)
+{
+    if (!c || !q) return fail(c, IGR_ERR_INVALID_ARG, "ctx and q are required");
+    if (dtype < IGR_DT_F64 || dtype > IGR_DT_BF16) return fail(c, IGR_ERR_INVALID_ARG, "bad dtype");
+    igr_status s = copy_in(c, q, c->q[0], 5 * c->g.n, dtype, on_device);
+    if (s != IGR_OK) return s;
+    c->cur = 0;
+    if (sigma) {
+        s = copy_in(c, sigma, c->sig[0], c->g.n, dtype, on_device);
+        if (s != IGR_OK) return s;
+    } else {
+        CU(c, cudaMemsetAsync(c->sig[0], 0, c->g.n * dtype_bytes(storage_dtype(c->cfg.prec)), c->st));
+    }
+    c->speed_nblocks = 0;
+    if (!on_device) CU(c, cudaStreamSynchronize(c->st));
+    return IGR_OK;
+}
+
+igr_status igr_get_state(igr_ctx *c, void *q, void *sigma, igr_dtype dtype, int on_device)
+{
+    if (!c || !q) return fail(c, IGR_ERR_INVALID_ARG, "ctx and q are required");
+    if (dtype < IGR_DT_F64 || dtype > IGR_DT_BF16) return fail(c, IGR_ERR_INVALID_ARG, "bad dtype");
+    igr_status s = copy_out(c, c->q[0], q, 5 * c->g.n, dtype, on_device);
+    if (s == IGR_OK && sigma) s = copy_out(c, c->sig[c->cur], sigma, c->g.n, dtype, on_device);
+    if (s != IGR_OK) return s;
+    return read_flags(c);
+}
+
+igr_status igr_step(igr_ctx *c, int nsteps, double fixed_dt, double *t_inout)
+{
+    if (!c) return fail(c, IGR_ERR_INVALID_ARG, "ctx is NULL");
+    if (nsteps < 0) return fail(c, IGR_ERR_INVALID_ARG, "nsteps < 0");
+    if (fixed_dt != fixed_dt) return fail(c, IGR_ERR_INVALID_ARG, "fixed_dt is NaN");
+    double t0 = 0.0;
+    if (t_inout) {
+        CU(c, cudaMemcpyAsync(&t0, &c->sc->t, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CU(c, cudaStreamSynchronize(c->st));
+    }
+    for (int n = 0; n < nsteps; n++) {
+        if (fixed_dt <= 0.0) {
+            igr_status s = refresh_speed(c);
+            if (s != IGR_OK) return s;
+        }
+        prof_begin(c, KC_OTHER);
+        k_finalize_dt<<<1, 1024, 0, c->st>>>(c->blockmax, c->speed_nblocks, c->sc,
+                                            c->cfg.cfl * c->cfg.dx, fixed_dt);
+        CU(c, cudaGetLastError());
+        prof_end(c);
+        igr_status s = run_stage(c, FLUX_STAGE1, c->q[0], c->q[0], c->q[1]);
+        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE2, c->q[1], c->q[0], c->q[2]);
+        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE3, c->q[2], c->q[0], c->q[0]);
+        if (s != IGR_OK) return s;
+        c->speed_nblocks = (int)c->ops->flux_blocks(c->g, c->tiles);
+    }
+    if (t_inout) {
+        double t1 = 0.0;
+        CU(c, cudaMemcpyAsync(&t1, &c->sc->t, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        igr_status s = read_flags(c);
+        *t_inout += t1 - t0;
+        if (s != IGR_OK) return s;
+    }
+    return IGR_OK;
+}
+
+igr_status igr_solve_sigma(igr_ctx *c, const void *q, void *sigma_inout, int sweeps, igr_dtype dtype)
+{
+    if (!c || !q || !sigma_inout) return fail(c, IGR_ERR_INVALID_ARG, "ctx, q, sigma are required");
+    if (sweeps < 0) return fail(c, IGR_ERR_INVALID_ARG, "sweeps < 0");
+    if ((int)dtype != storage_dtype(c->cfg.prec))
+        return fail(c, IGR_ERR_UNSUPPORTED, "dtype must be the storage dtype");
+    prof_begin(c, KC_SOURCE);
+    CU(c, c->ops->source(c->g, c->p, c->tiles, inflow_of(c), q, c->b, c->st));
+    prof_end(c);
+    // the context's second Sigma buffer is scratch: sweeps alternate between
+    // the caller's buffer and it, and an odd count copies the result back
+    void *scratch = c->sig[1 - c->cur];
+    void *res;
+    igr_status s = launch_sweeps(c, q, c->b, sigma_inout, scratch, sweeps, &res);
+    if (s != IGR_OK) return s;
+    if (res != sigma_inout)
+        CU(c, cudaMemcpyAsync(sigma_inout, res, c->g.n * (size_t)c->ops->storage_bytes,
+                              cudaMemcpyDeviceToDevice, c->st));
+    return IGR_OK;
+}
+
+igr_status igr_rhs(igr_ctx *c, const void *q, const void *sigma, void *rhs, igr_dtype dtype)
+{
+    if (!c || !q || !sigma || !rhs) return fail(c, IGR_ERR_INVALID_ARG, "ctx, q, sigma, rhs are required");
+    if ((int)dtype != storage_dtype(c->cfg.prec))
+        return fail(c, IGR_ERR_UNSUPPORTED, "dtype must be the storage dtype");
+    prof_begin(c, KC_FLUX);
+    CU(c, c->ops->flux(c->g, c->p, c->tiles, inflow_of(c), FLUX_RHS, q, sigma, nullptr, nullptr,
+                       rhs, c->sc, c->blockmax, &c->sc->err, c->st));
+    prof_end(c);
+    return IGR_OK;
+}
+
+igr_status igr_get_dt(igr_ctx *c, double *dt)
+{
+    if (!c || !dt) return fail(c, IGR_ERR_INVALID_ARG, "ctx and dt are required");
+    igr_status s = refresh_speed(c);
+    if (s != IGR_OK) return s;
+    // reduce into the second scalar slot so the step's scalars are untouched
+    Scalars *tmp = c->sc + 1;
+    CU(c, cudaMemsetAsync(tmp, 0, sizeof(Scalars), c->st));
+    k_finalize_dt<<<1, 1024, 0, c->st>>>(c->blockmax, c->speed_nblocks, tmp, c->cfg.cfl * c->cfg.dx, 0.0);
+    CU(c, cudaGetLastError());
+    Scalars h;
+    CU(c, cudaMemcpyAsync(&h, tmp, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
+    CU(c, cudaStreamSynchronize(c->st));
+    *dt = h.dt;
+    return IGR_OK;
+}
+
+igr_status igr_sync(igr_ctx *c)
+{
+    if (!c) return fail(c, IGR_ERR_INVALID_ARG, "ctx is NULL");
+    return read_flags(c);
+}
+
+igr_status igr_profile_enable(igr_ctx *c, int on)
+{
+    if (!c) return fail(c, IGR_ERR_INVALID_ARG, "ctx is NULL");
+    CU(c, cudaStreamSynchronize(c->st));
+    prof_collect(c);
+    c->profiling = on != 0;
+    for (int k = 0; k < KC_COUNT; k++) {
+        c->prof_launches[k] = 0;
+        c->prof_ms[k] = 0.0;
+    }
+    return IGR_OK;
+}
+
+igr_status igr_profile_read(igr_ctx *c, int kc, long long *launches, double *total_ms)
+{
+    if (!c || kc < 0 || kc >= KC_COUNT || !launches || !total_ms)
+        return fail(c, IGR_ERR_INVALID_ARG, "bad profile query");
+    CU(c, cudaStreamSynchronize(c->st));
+    prof_collect(c);
+    *launches = c->prof_launches[kc];
+    *total_ms = c->prof_ms[kc];
+    return IGR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,76 @@
+// Internal interface between the host runtime (igr_api.cu) and the kernel
+// translation units (igr_kernels.cu, compiled once per storage type).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace igr {
+
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW = 2 };
+
+// Kernel classes for per-launch timing.
+enum { KC_SOURCE = 0, KC_JACOBI = 1, KC_FLUX = 2, KC_OTHER = 3, KC_COUNT = 4 };
+
+struct Geom {
+    int nx, ny, nz;
+    int bc[6];          // faces -x,+x,-y,+y,-z,+z
+    long long plane;    // nx * ny
+    long long n;        // nx * ny * nz
+};
+
+struct Phys {
+    double dx, gamma, alpha, cfl;
+};
+
+// Device-resident scalars of a context.
+struct Scalars {
+    double dt;          // time step of the current step
+    double t;           // accumulated simulated time
+    double speed;       // max_d(|u_d| + c) of the state at the start of the step
+    int err;            // bit 0: non-finite value or non-positive face rho/p
+    int pad;
+};
+
+// Inflow tables on the -z face, in the arithmetic type:
+// W[j][i] = sum_n s_n, J[v][j][i] = sum_n s_n q_jet_n[v].
+struct Inflow {
+    const void *W;
+    const void *J;
+};
+
+// Launch shapes chosen by the runtime.
+struct Tiles {
+    int zc_source;  // z-planes per block of the source kernel
+    int zc_jacobi;  // z-planes per block of the Jacobi kernel
+    int zc_flux;    // z-planes per block of the flux kernel
+};
+
+// Stage modes of the flux kernel.
+enum { FLUX_RHS = 0, FLUX_STAGE1 = 1, FLUX_STAGE2 = 2, FLUX_STAGE3 = 3 };
+
+// Kernel set of one storage type. Every entry enqueues on `st` and returns
+// the launch error (cudaGetLastError) without synchronising.
+struct Ops {
+    int storage_bytes;  // bytes per stored value
+    int compute_bytes;  // bytes per arithmetic value (8 for FP64, else 4)
+    // b = alpha [tr(G^2) + tr(G)^2] from q
+    cudaError_t (*source)(const Geom &, const Phys &, const Tiles &, const Inflow &,
+                          const void *q, void *b, cudaStream_t st);
+    // one Jacobi sweep s_out <- (b + beta sum c s_in) / (1/rho + beta sum c)
+    cudaError_t (*jacobi)(const Geom &, const Phys &, const Tiles &, const void *q,
+                          const void *b, const void *s_in, void *s_out, cudaStream_t st);
+    // flux divergence and RK stage (mode FLUX_STAGE*), or L(q; Sigma) into rhs (FLUX_RHS).
+    // Stage 3 also writes the per-block maximum wave speed of its output to blockmax.
+    cudaError_t (*flux)(const Geom &, const Phys &, const Tiles &, const Inflow &, int mode,
+                        const void *qs, const void *sig, const void *qn, void *out, void *rhs,
+                        const Scalars *sc, double *blockmax, int *err, cudaStream_t st);
+    // number of blocks of the flux launch (entries of blockmax it writes)
+    long long (*flux_blocks)(const Geom &, const Tiles &);
+    // per-block maximum wave speed of q; returns the block count in *nblocks
+    cudaError_t (*speed)(const Geom &, const Phys &, const void *q, double *blockmax,
+                         int *nblocks, cudaStream_t st);
+};
+
+extern const Ops ops_f64, ops_f32, ops_f16, ops_bf16;
+
+}  // namespace igr

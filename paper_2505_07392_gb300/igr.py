@@ -1,0 +1,268 @@
+"""ctypes binding of the C ABI in include/igr.h.
+
+Argument marshalling only: every step of the stage runs in libigr.so's CUDA
+kernels. PyTorch supplies device memory (its caching allocator backs the
+context's buffers through the igr_allocator callbacks) and the stream.
+Importing this module does not load the library; the first call does, and
+it raises if libigr.so has not been built (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libigr.so")
+
+# enums of igr.h
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
+F64, F32, F32_F16STORE, F32_BF16STORE = range(4)
+DT_F64, DT_F32, DT_F16, DT_BF16 = range(4)
+KC_SOURCE, KC_JACOBI, KC_FLUX, KC_OTHER = range(4)
+
+PRECISIONS = {"f64": F64, "f32": F32, "f16": F32_F16STORE, "bf16": F32_BF16STORE}
+STATUS = {0: "IGR_OK", 1: "IGR_ERR_INVALID_ARG", 2: "IGR_ERR_OOM", 3: "IGR_ERR_CUDA",
+          4: "IGR_ERR_NONFINITE", 5: "IGR_ERR_TIMEOUT", 6: "IGR_ERR_UNSUPPORTED"}
+
+
+class Jet(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("cx", "cy", "radius", "rho", "w", "p", "edge_width")]
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)),
+                ("free", C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)),
+                ("user", C.c_void_p)]
+
+
+class Config(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double),
+                ("gamma", C.c_double), ("alpha", C.c_double), ("cfl", C.c_double),
+                ("sweeps", C.c_int), ("prec", C.c_int), ("bc", C.c_int * 6),
+                ("jets", C.POINTER(Jet)), ("njets", C.c_int)]
+
+
+class IGRError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libigr.so with argument types set."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2505_07392_gb300.build` (nvcc, sm_103a)")
+        L = C.CDLL(LIB_PATH)
+        p, i, d = C.c_void_p, C.c_int, C.c_double
+        sigs = {
+            "igr_create": (i, [C.POINTER(Config), C.POINTER(Allocator), p, C.POINTER(p)]),
+            "igr_memory_bytes": (C.c_size_t, [C.POINTER(Config)]),
+            "igr_destroy": (i, [p]),
+            "igr_set_state": (i, [p, p, p, i, i]),
+            "igr_get_state": (i, [p, p, p, i, i]),
+            "igr_step": (i, [p, i, d, C.POINTER(d)]),
+            "igr_solve_sigma": (i, [p, p, p, i, i]),
+            "igr_rhs": (i, [p, p, p, p, i]),
+            "igr_get_dt": (i, [p, C.POINTER(d)]),
+            "igr_sync": (i, [p]),
+            "igr_profile_enable": (i, [p, i]),
+            "igr_profile_read": (i, [p, i, C.POINTER(C.c_longlong), C.POINTER(d)]),
+            "igr_last_error": (C.c_char_p, [p]),
+            "igr_version": (C.c_char_p, []),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(L, name)
+            f.restype, f.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+def make_config(case, precision: str = "f32"):
+    """Config struct (and the jet array it points to) from an inputs.Case."""
+    jets = (Jet * max(1, len(case.jets)))(*[Jet(*j) for j in case.jets])
+    cfg = Config(int(case.nx), int(case.ny), int(case.nz), float(case.dx), float(case.gamma),
+                 float(case.alpha), float(case.cfl), int(case.sweeps), PRECISIONS[precision],
+                 (C.c_int * 6)(*[int(b) for b in case.bc]), jets, len(case.jets))
+    return cfg, jets
+
+
+def memory_bytes(case, precision: str = "f32") -> int:
+    cfg, _jets = make_config(case, precision)
+    return int(lib().igr_memory_bytes(C.byref(cfg)))
+
+
+def storage_torch_dtype(precision: str):
+    import torch
+    return {"f64": torch.float64, "f32": torch.float32, "f16": torch.float16,
+            "bf16": torch.bfloat16}[precision]
+
+
+def compute_torch_dtype(precision: str):
+    import torch
+    return torch.float64 if precision == "f64" else torch.float32
+
+
+_TORCH_DT = None
+
+
+def _dt_code(t):
+    import torch
+    global _TORCH_DT
+    if _TORCH_DT is None:
+        _TORCH_DT = {torch.float64: DT_F64, torch.float32: DT_F32, torch.float16: DT_F16,
+                     torch.bfloat16: DT_BF16}
+    return _TORCH_DT[t]
+
+
+_NP_DT = {np.dtype(np.float64): DT_F64, np.dtype(np.float32): DT_F32, np.dtype(np.float16): DT_F16}
+
+
+class Solver:
+    """One IGR context on the current CUDA device and PyTorch's current stream."""
+
+    def __init__(self, case, precision: str = "f32", stream=None, torch_allocator: bool = True):
+        import torch
+        self.case = case
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        self.n = case.nx * case.ny * case.nz
+        self.shape = (case.nz, case.ny, case.nx)
+        self._cfg, self._jets = make_config(case, precision)
+        self._alloc = None
+        if torch_allocator:
+            dev, st = self.device.index, self.stream
+
+            @C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+            def _a(nbytes, user):
+                try:
+                    return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, st))
+                except Exception:
+                    return None
+
+            @C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+            def _f(ptr, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc = Allocator(_a, _f, None)
+        h = C.c_void_p()
+        s = lib().igr_create(C.byref(self._cfg), C.byref(self._alloc) if self._alloc else None,
+                             C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if s != OK:
+            raise IGRError(s, lib().igr_last_error(None).decode())
+        self.h = h
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "h", None):
+            lib().igr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, s):
+        if s != OK:
+            raise IGRError(s, lib().igr_last_error(self.h).decode())
+
+    # -- state
+    def set_state(self, q, sigma=None):
+        """q: (5, nz, ny, nx) torch CUDA tensor (any float dtype) or a numpy
+        array in the storage dtype (host); sigma likewise or None (zero)."""
+        import torch
+        if isinstance(q, torch.Tensor):
+            q = q.contiguous()
+            if sigma is not None:
+                sigma = sigma.to(q.dtype).contiguous()
+            self._check(lib().igr_set_state(self.h, C.c_void_p(q.data_ptr()),
+                                            C.c_void_p(sigma.data_ptr()) if sigma is not None else None,
+                                            _dt_code(q.dtype), 1))
+            # the copy is asynchronous on the solver's stream
+            if self.stream != torch.cuda.current_stream(self.device):
+                q.record_stream(self.stream)
+                if sigma is not None:
+                    sigma.record_stream(self.stream)
+        else:
+            q = np.ascontiguousarray(q)
+            sp = None
+            if sigma is not None:
+                sigma = np.ascontiguousarray(sigma, dtype=q.dtype)
+                sp = sigma.ctypes.data_as(C.c_void_p)
+            self._check(lib().igr_set_state(self.h, q.ctypes.data_as(C.c_void_p), sp,
+                                            _NP_DT[q.dtype], 0))
+
+    def get_state(self, dtype=None):
+        """(q, sigma) as new CUDA tensors (default: the storage dtype)."""
+        import torch
+        dtype = dtype or storage_torch_dtype(self.precision)
+        q = torch.empty((5,) + self.shape, dtype=dtype, device=self.device)
+        s = torch.empty(self.shape, dtype=dtype, device=self.device)
+        self._check(lib().igr_get_state(self.h, C.c_void_p(q.data_ptr()), C.c_void_p(s.data_ptr()),
+                                        _dt_code(dtype), 1))
+        return q, s
+
+    def get_state_host(self, q_out: np.ndarray, sigma_out: Optional[np.ndarray] = None):
+        """Copy the state into host arrays of the storage dtype."""
+        self._check(lib().igr_get_state(self.h, q_out.ctypes.data_as(C.c_void_p),
+                                        sigma_out.ctypes.data_as(C.c_void_p) if sigma_out is not None else None,
+                                        _NP_DT[q_out.dtype], 0))
+
+    # -- stepping
+    def step(self, nsteps: int = 1, fixed_dt: float = 0.0, sync: bool = True):
+        """Advance nsteps; returns the elapsed simulated time if sync."""
+        if sync:
+            t = C.c_double(0.0)
+            self._check(lib().igr_step(self.h, int(nsteps), float(fixed_dt), C.byref(t)))
+            return t.value
+        self._check(lib().igr_step(self.h, int(nsteps), float(fixed_dt), None))
+        return None
+
+    def dt(self) -> float:
+        d = C.c_double()
+        self._check(lib().igr_get_dt(self.h, C.byref(d)))
+        return d.value
+
+    def sync(self):
+        self._check(lib().igr_sync(self.h))
+
+    # -- stand-alone operators on caller buffers (storage dtype, CUDA)
+    def solve_sigma(self, q, sigma, sweeps: int):
+        """In place on sigma: b from q, then `sweeps` warm-started Jacobi sweeps."""
+        self._check(lib().igr_solve_sigma(self.h, C.c_void_p(q.data_ptr()), C.c_void_p(sigma.data_ptr()),
+                                          int(sweeps), _dt_code(q.dtype)))
+        return sigma
+
+    def rhs(self, q, sigma):
+        """L(q; Sigma) as a new (5, nz, ny, nx) tensor in the arithmetic dtype."""
+        import torch
+        out = torch.empty((5,) + self.shape, dtype=compute_torch_dtype(self.precision), device=self.device)
+        self._check(lib().igr_rhs(self.h, C.c_void_p(q.data_ptr()), C.c_void_p(sigma.data_ptr()),
+                                  C.c_void_p(out.data_ptr()), _dt_code(q.dtype)))
+        return out
+
+    # -- per-kernel timing
+    def profile(self, on: bool = True):
+        self._check(lib().igr_profile_enable(self.h, int(on)))
+
+    def profile_read(self, kernel_class: int):
+        n, ms = C.c_longlong(), C.c_double()
+        self._check(lib().igr_profile_read(self.h, int(kernel_class), C.byref(n), C.byref(ms)))
+        return int(n.value), float(ms.value)

@@ -1,0 +1,62 @@
+"""The C-ABI library loads and exports every function include/igr.h declares
+(no compute: this runs without a GPU)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "igr.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(igr_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_stage_calls():
+    names = declared_functions()
+    for fn in ("igr_create", "igr_set_state", "igr_step", "igr_solve_sigma", "igr_rhs",
+               "igr_get_state", "igr_destroy"):
+        assert fn in names
+
+
+@pytest.fixture(scope="module")
+def libigr():
+    from paper_2505_07392_gb300 import build, igr
+    if not os.path.exists(igr.LIB_PATH):
+        if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+            pytest.skip("nvcc is not available to build libigr.so")
+        build.build()
+    return ctypes.CDLL(igr.LIB_PATH)
+
+
+def test_library_exports_every_declared_function(libigr):
+    for name in declared_functions():
+        assert hasattr(libigr, name), name
+
+
+def test_host_only_calls(libigr):
+    """Calls that need no GPU: version, invalid-config rejection, memory sizing."""
+    from paper_2505_07392_gb300 import igr, inputs
+    L = igr.lib()
+    assert L.igr_version().decode().startswith("igr-gb300")
+    case = inputs.density_wave(32)
+    cfg, _ = igr.make_config(case, "f32")
+    # 3 states x 5 fields + 2 Sigma + b = 18 words per cell, plus small tables
+    n = case.ncells
+    assert L.igr_memory_bytes(ctypes.byref(cfg)) >= 18 * 4 * n
+    bad, _ = igr.make_config(inputs.density_wave(3), "f32")
+    assert L.igr_memory_bytes(ctypes.byref(bad)) == 0
+    h = ctypes.c_void_p()
+    assert L.igr_create(ctypes.byref(bad), None, None, ctypes.byref(h)) == igr.ERR_INVALID_ARG
+    assert b">= 4" in L.igr_last_error(None)
+    # inflow is only allowed on -z
+    c2 = inputs.blast(16)
+    c2.bc = (inputs.INFLOW,) + (inputs.OUTFLOW,) * 5
+    cfg2, _ = igr.make_config(c2, "f32")
+    assert L.igr_create(ctypes.byref(cfg2), None, None, ctypes.byref(h)) == igr.ERR_INVALID_ARG
+    assert b"-z face" in L.igr_last_error(None)

@@ -1,0 +1,279 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs. Tolerances (relative L2 per conserved field): FP64
+1e-12, FP32 1e-5, FP16 storage 2e-3; BF16 storage (7-bit mantissa, 8x the
+FP16 rounding step) is held to 8 x 2e-3."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from metrics import field_errors, max_error, sigma_error
+from paper_2505_07392_gb300 import inputs
+from paper_2505_07392_gb300.inputs import INFLOW, OUTFLOW, PERIODIC, Case
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 2e-3, "bf16": 1.6e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_07392_gb300 import build
+    build.build()
+    yield
+
+
+def gpu_run(case, q0, precision, nsteps, fixed_dt=0.0, sigma0=None):
+    import torch
+    from paper_2505_07392_gb300 import igr
+    with igr.Solver(case, precision) as s:
+        s.set_state(torch.from_numpy(np.ascontiguousarray(q0)).cuda(),
+                    None if sigma0 is None else torch.from_numpy(np.ascontiguousarray(sigma0)).cuda())
+        t = s.step(nsteps, fixed_dt)
+        q, sig = s.get_state(torch.float64)
+        return q.cpu().numpy(), sig.cpu().numpy(), t
+
+
+def smooth_state(case, seed=0, periodic=True):
+    """A smooth, non-trivial state (all fields vary, |u| ~ 0.3, p ~ 1)."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    ph = rng.uniform(0, 2 * np.pi, size=8)
+    L = np.array([case.nx, case.ny, case.nz]) * case.dx
+    z = (np.arange(case.nz) + 0.5) * case.dx / L[2]
+    y = (np.arange(case.ny) + 0.5) * case.dx / L[1]
+    x = (np.arange(case.nx) + 0.5) * case.dx / L[0]
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    tp = 2 * np.pi
+    rho = 1 + 0.2 * np.sin(tp * X + ph[0]) * np.cos(tp * Y + ph[1]) + 0.1 * np.sin(tp * Z + ph[2])
+    u = 0.3 * np.sin(tp * Y + ph[3]) * np.cos(tp * Z)
+    v = 0.25 * np.cos(tp * X + ph[4]) * np.sin(tp * Z + ph[5])
+    w = -0.3 * np.sin(tp * X + ph[6]) * np.cos(tp * Y)
+    p = 1 + 0.1 * np.cos(tp * (X + Y) + ph[7])
+    g = case.gamma
+    return np.stack([rho, rho * u, rho * v, rho * w, p / (g - 1) + 0.5 * rho * (u * u + v * v + w * w)])
+
+
+def small_jet_case(nx=40, ny=36, nz=20, sweeps=5):
+    dx = 1.0 / nx
+    w = 2.0 * math.sqrt(1.4 * 2.0)
+    jets = [(0.3, 0.45, 4 * dx, 1.0, w, 2.0, 1.0), (0.7, 0.55, 3 * dx, 1.0, 0.9 * w, 2.0, 1.0)]
+    bc = (OUTFLOW, OUTFLOW, OUTFLOW, OUTFLOW, INFLOW, OUTFLOW)
+    return Case("jets", nx, ny, nz, dx, alpha=dx * dx, sweeps=sweeps, bc=bc, jets=jets)
+
+
+# ------------------------------------------------------------------ steps
+
+def test_density_wave_fp64_100_steps():
+    """3D periodic 32^3 density wave with noise, 100 SSP-RK3 steps."""
+    c = inputs.density_wave(32)
+    q0 = inputs.initial_state(c)
+    qo, so, to = oracle.run(c, q0, None, nsteps=100)
+    qg, sg, tg = gpu_run(c, q0, "f64", 100)
+    assert max_error(qg, qo) <= TOL["f64"], field_errors(qg, qo)
+    assert math.isclose(tg, to, rel_tol=1e-13)
+    assert np.max(np.abs(sg - so)) <= 1e-20
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16", "bf16"])
+def test_blast(precision):
+    """Spherical blast (outflow faces, 10 sweeps), downsized to 40^3 for the oracle."""
+    c = inputs.blast(40, steps=30)
+    q0 = inputs.initial_state(c)
+    qo, so, to = oracle.run(c, q0, None, nsteps=30)
+    qg, sg, tg = gpu_run(c, q0, precision, 30)
+    err = field_errors(qg, qo)
+    assert max(err.values()) <= TOL[precision], err
+    assert sigma_error(sg, so, 0) <= 10 * TOL[precision]
+    assert math.isclose(tg, to, rel_tol=max(TOL[precision], 1e-13))
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16"])
+def test_jets_inflow(precision):
+    """Two inflow jets on -z with outflow elsewhere."""
+    c = small_jet_case()
+    q0 = inputs.jet_initial_state(c)
+    qo, so, to = oracle.run(c, q0, None, nsteps=20)
+    qg, sg, tg = gpu_run(c, q0, precision, 20)
+    err = field_errors(qg, qo)
+    assert max(err.values()) <= TOL[precision], err
+    assert sigma_error(sg, so, 0) <= 10 * TOL[precision]
+
+
+SHAPES = [
+    ((7, 13, 33), (PERIODIC,) * 6),
+    ((33, 7, 13), (OUTFLOW,) * 6),
+    ((13, 33, 7), (OUTFLOW, OUTFLOW, PERIODIC, PERIODIC, OUTFLOW, OUTFLOW)),
+    ((65, 9, 5), (PERIODIC, PERIODIC, OUTFLOW, OUTFLOW, PERIODIC, PERIODIC)),
+    ((4, 4, 4), (PERIODIC,) * 6),
+]
+
+
+@pytest.mark.parametrize("shape,bc", SHAPES)
+def test_odd_shapes(shape, bc):
+    """Grids that are no multiple of any tile, anisotropic, mixed faces."""
+    nx, ny, nz = shape
+    c = Case("odd", nx, ny, nz, 1.0 / max(shape), alpha=(1.0 / max(shape)) ** 2, sweeps=3, bc=bc)
+    q0 = smooth_state(c, seed=nx)
+    qo, so, to = oracle.run(c, q0, None, nsteps=4)
+    qg, sg, tg = gpu_run(c, q0, "f64", 4)
+    assert max_error(qg, qo) <= TOL["f64"], field_errors(qg, qo)
+    assert sigma_error(sg, so, 1e-300) <= 1e-11
+
+
+def test_uniform_state_bitwise_all_precisions():
+    import torch
+    c = Case("uniform", 20, 12, 9, 0.05, alpha=0.0025, bc=(OUTFLOW, OUTFLOW, PERIODIC, PERIODIC, OUTFLOW, OUTFLOW))
+    shape = (c.nz, c.ny, c.nx)
+    rho, u, v, w, p = 1.25, 0.5, -0.25, 0.75, 2.0
+    q0 = np.stack([np.full(shape, x) for x in (rho, rho * u, rho * v, rho * w,
+                                                p / 0.4 + 0.5 * rho * (u * u + v * v + w * w))])
+    from paper_2505_07392_gb300 import igr
+    for prec in ("f64", "f32", "f16", "bf16"):
+        dt = igr.storage_torch_dtype(prec)
+        qs = torch.from_numpy(q0).to(dt).cuda()
+        with igr.Solver(c, prec) as s:
+            s.set_state(qs)
+            s.step(10)
+            q1, s1 = s.get_state()
+        assert torch.equal(q1, qs), prec
+        assert torch.count_nonzero(s1) == 0
+
+
+def test_periodic_conservation_fp64():
+    c = Case("cons", 24, 20, 16, 1.0 / 24, alpha=1.0 / 24 ** 2, bc=(PERIODIC,) * 6)
+    q0 = smooth_state(c, seed=3)
+    qg, sg, _ = gpu_run(c, q0, "f64", 10)
+    tot0 = q0.reshape(5, -1).sum(axis=1)
+    tot1 = qg.reshape(5, -1).sum(axis=1)
+    scale = np.abs(q0).reshape(5, -1).sum(axis=1)
+    assert np.all(np.abs(tot1 - tot0) <= 1e-13 * scale)
+    assert np.abs(sg).max() > 1e-6
+
+
+# ------------------------------------------------------- stand-alone calls
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_rhs(precision):
+    import torch
+    from paper_2505_07392_gb300 import igr
+    c = Case("rhs", 36, 20, 24, 1.0 / 36, alpha=1.0 / 36 ** 2, bc=(PERIODIC, PERIODIC, OUTFLOW, OUTFLOW, OUTFLOW, OUTFLOW))
+    q0 = smooth_state(c, seed=5)
+    rng = np.random.Generator(np.random.Philox(9))
+    sig = 0.05 * smooth_state(c, seed=6)[0] + 0.01 * rng.uniform(-1, 1, size=(c.nz, c.ny, c.nx))
+    Lo = oracle.rhs(c, q0, sig)
+    dt = igr.storage_torch_dtype(precision)
+    with igr.Solver(c, precision) as s:
+        Lg = s.rhs(torch.from_numpy(q0).to(dt).cuda(), torch.from_numpy(sig).to(dt).cuda()).double().cpu().numpy()
+    rel = np.linalg.norm((Lg - Lo).reshape(5, -1), axis=1) / np.linalg.norm(Lo.reshape(5, -1), axis=1)
+    assert np.all(rel <= 10 * TOL[precision]), rel
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("sweeps", [1, 4, 5])
+def test_solve_sigma(precision, sweeps):
+    import torch
+    from paper_2505_07392_gb300 import igr
+    c = Case("sig", 28, 18, 22, 1.0 / 28, alpha=1.0 / 28 ** 2, bc=(OUTFLOW, OUTFLOW, PERIODIC, PERIODIC, OUTFLOW, OUTFLOW))
+    q0 = smooth_state(c, seed=7)
+    s0 = 0.1 * smooth_state(c, seed=8)[0]
+    so = oracle.jacobi(c, q0, oracle.source(c, q0), s0, sweeps)
+    dt = igr.storage_torch_dtype(precision)
+    with igr.Solver(c, precision) as s:
+        sg = torch.from_numpy(s0).to(dt).cuda()
+        s.solve_sigma(torch.from_numpy(q0).to(dt).cuda(), sg, sweeps)
+        sg = sg.double().cpu().numpy()
+    assert sigma_error(sg, so, 0) <= 10 * TOL[precision]
+
+
+def test_dt_rule():
+    import torch
+    from paper_2505_07392_gb300 import igr
+    c = inputs.blast(24)
+    q0 = inputs.initial_state(c)
+    with igr.Solver(c, "f64") as s:
+        s.set_state(torch.from_numpy(q0).cuda())
+        dt = s.dt()
+    assert math.isclose(dt, c.cfl * c.dx / oracle.max_speed(c, q0), rel_tol=1e-15)
+
+
+def test_nonfinite_flag():
+    """A state with negative pressure is flagged as IGR_ERR_NONFINITE at the
+    next synchronising call (host-side detection; nothing faults)."""
+    import torch
+    from paper_2505_07392_gb300 import igr
+    c = inputs.blast(16)
+    q0 = inputs.initial_state(c)
+    q0[4, 8, 8, 8] = -1.0  # negative energy -> negative pressure
+    with igr.Solver(c, "f32") as s:
+        s.set_state(torch.from_numpy(q0).cuda())
+        with pytest.raises(igr.IGRError) as e:
+            s.step(1, fixed_dt=1e-4)
+        assert e.value.status == igr.ERR_NONFINITE
+        # the context stays usable
+        s.set_state(torch.from_numpy(inputs.initial_state(c)).cuda())
+        s.step(1, fixed_dt=1e-4)
+
+
+# ------------------------------------------------- full-size sampled parity
+
+def _patch_case(full, i0, i1, j0, j1, k0, k1):
+    """Sub-box of a case: real boundary conditions where the patch touches the
+    domain boundary, zero-gradient at the cuts; jets shifted to patch coordinates."""
+    bc = list(full.bc)
+    if i0 > 0: bc[0] = OUTFLOW
+    if i1 < full.nx: bc[1] = OUTFLOW
+    if j0 > 0: bc[2] = OUTFLOW
+    if j1 < full.ny: bc[3] = OUTFLOW
+    if k0 > 0: bc[4] = OUTFLOW
+    if k1 < full.nz: bc[5] = OUTFLOW
+    jets = ([(j[0] - i0 * full.dx, j[1] - j0 * full.dx) + tuple(j[2:]) for j in full.jets]
+            if bc[4] == INFLOW else [])
+    return Case(full.name, i1 - i0, j1 - j0, k1 - k0, full.dx, alpha=full.alpha, cfl=full.cfl,
+                sweeps=full.sweeps, bc=tuple(bc), jets=jets)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+def test_plume_full_size_sampled(precision):
+    """The 1024 x 1024 x 2048 plume, one step at full size in the launch shape
+    the benchmark times; sampled sub-boxes recomputed by the oracle. One
+    stage reaches sweeps + 3 cells, so after a step only cells farther than
+    3 (sweeps + 3) from a cut face are compared."""
+    import torch
+    from paper_2505_07392_gb300 import igr
+    full = inputs.plume()
+    dt = 2.0e-5
+    R = 3 * (full.sweeps + 3) + 1
+    st = igr.storage_torch_dtype(precision)
+    with igr.Solver(full, precision) as s:
+        zc = 128
+        q = torch.empty((5, full.nz, full.ny, full.nx), dtype=st, device="cuda")
+        for k0 in range(0, full.nz, zc):
+            q[:, k0:k0 + zc] = inputs.jet_initial_state(full, (k0, min(full.nz, k0 + zc), 0, full.ny, 0, full.nx),
+                                                        xp=torch, device="cuda", dtype=st)
+        s.set_state(q)
+        del q
+        s.step(1, fixed_dt=dt)
+        qg, sg = s.get_state()
+        # inner-ring jet near (536, 512) on the inflow face, and the far corner
+        for (ic, jc, kc) in ((536, 512, 0), (1000, 20, 2040)):
+            H = R + 6
+            i0, i1 = max(0, ic - H), min(full.nx, ic + H)
+            j0, j1 = max(0, jc - H), min(full.ny, jc + H)
+            k0, k1 = max(0, kc - H), min(full.nz, kc + H)
+            pc = _patch_case(full, i0, i1, j0, j1, k0, k1)
+            q0 = inputs.jet_initial_state(full, (k0, k1, j0, j1, i0, i1))
+            qo, so, _ = oracle.run(pc, q0, None, nsteps=1, fixed_dt=dt)
+            # compare cells at least R from every cut face
+            lo = [R if a > 0 else 0 for a in (k0, j0, i0)]
+            hi = [(b - a) - R if b < n else (b - a) for a, b, n in
+                  ((k0, k1, full.nz), (j0, j1, full.ny), (i0, i1, full.nx))]
+            sl = tuple(slice(l, h) for l, h in zip(lo, hi))
+            got = qg[:, k0:k1, j0:j1, i0:i1].double().cpu().numpy()
+            err = field_errors(got[(slice(None),) + sl], qo[(slice(None),) + sl])
+            assert max(err.values()) <= TOL[precision], (ic, jc, kc, err)
