@@ -281,11 +281,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f16", choices=["f16", "bf16", "f32", "f64"])
-    ap.add_argument("--plain", default="f32", help="second form measured beside the headline ('' = none)")
+    ap.add_argument("--plain", default="f32", help="second form measured beside the headline ('none' = skip)")
     ap.add_argument("--size", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"))
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-size", type=int, nargs=3, default=(256, 256, 64))
+    ap.add_argument("--cpu-size", type=int, nargs=3, default=(256, 256, 128))
+    ap.add_argument("--cpu-steps", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -355,7 +356,7 @@ def main():
     roof, per_kernel = roofline_of(full, res, args.precision, peak, peak_kind)
 
     plain = None
-    if args.plain and args.plain != args.precision:
+    if args.plain not in ("", "none") and args.plain != args.precision:
         rp = run_form(full, args.plain, args.steps, args.warmup, sync_all)
         rp["prof_steps"] = args.steps
         roof_p, _ = roofline_of(full, rp, args.plain, peak, peak_kind)
@@ -391,7 +392,7 @@ def main():
                        "h2d_bytes_per_step": e["bytes"], "d2h_bytes_per_step": e["bytes"],
                        "steps": e["steps"]}
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(full, 1, tuple(args.cpu_size))
+        line["cpu_baseline"] = cpu_baseline(full, args.cpu_steps, tuple(args.cpu_size))
     print(json.dumps(line))
 
 

@@ -147,6 +147,16 @@ igr_status igr_solve_sigma(igr_ctx *ctx, const void *q, void *sigma_inout, int s
  * FP32 otherwise). */
 igr_status igr_rhs(igr_ctx *ctx, const void *q, const void *sigma, void *rhs, igr_dtype dtype);
 
+/* The SSP-RK3 stage combination alone, exactly as the stage kernel stores it:
+ *   out = qn + w [(qs - qn) + dt L],  w = 1, 1/4, 2/3 for stage = 1, 2, 3
+ * (Gottlieb-Shu SSP-RK3 in increment form). qn, qs, out: device buffers of
+ * count values in the storage dtype; L: device buffer in the arithmetic type
+ * (FP64 for IGR_F64, FP32 otherwise). In the 16-bit modes the stored value
+ * is the FP64 evaluation of the expression rounded to nearest-even. out may
+ * alias qn. For verification and tooling. */
+igr_status igr_rk_combine(igr_ctx *ctx, const void *qn, const void *qs, const void *L, void *out,
+                          long long count, int stage, double dt);
+
 /* Time step dt = cfl dx / max_d(|u_d| + c) of the current state.
  * Synchronises. */
 igr_status igr_get_dt(igr_ctx *ctx, double *dt);

@@ -613,6 +613,19 @@ igr_status igr_rhs(igr_ctx *c, const void *q, const void *sigma, void *rhs, igr_
     return IGR_OK;
 }
 
+igr_status igr_rk_combine(igr_ctx *c, const void *qn, const void *qs, const void *L, void *out,
+                          long long count, int stage, double dt)
+{
+    if (!c || !qn || !qs || !L || !out) return fail(c, IGR_ERR_INVALID_ARG, "null buffer");
+    if (count < 0 || stage < 1 || stage > 3) return fail(c, IGR_ERR_INVALID_ARG, "bad count or stage");
+    double w = stage == 1 ? 1.0 : stage == 2 ? 0.25 : 2.0 / 3.0;
+    if (count == 0) return IGR_OK;
+    prof_begin(c, KC_OTHER);
+    CU(c, c->ops->rk_combine(qn, qs, L, out, count, dt, w, c->st));
+    prof_end(c);
+    return IGR_OK;
+}
+
 igr_status igr_get_dt(igr_ctx *c, double *dt)
 {
     if (!c || !dt) return fail(c, IGR_ERR_INVALID_ARG, "ctx and dt are required");

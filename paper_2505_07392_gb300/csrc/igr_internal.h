@@ -69,6 +69,10 @@ struct Ops {
     // per-block maximum wave speed of q; returns the block count in *nblocks
     cudaError_t (*speed)(const Geom &, const Phys &, const void *q, double *blockmax,
                          int *nblocks, cudaStream_t st);
+    // out = qn + w ((qs - qn) + dt L) over n values, exactly as the flux
+    // kernel's epilogue stores it (L in the arithmetic type)
+    cudaError_t (*rk_combine)(const void *qn, const void *qs, const void *L, void *out,
+                              long long n, double dt, double w, cudaStream_t st);
 };
 
 extern const Ops ops_f64, ops_f32, ops_f16, ops_bf16;

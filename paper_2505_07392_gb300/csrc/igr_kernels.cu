@@ -26,6 +26,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <stdio.h>
+
 #include "igr_internal.h"
 
 #ifndef IGR_STORAGE
@@ -51,6 +53,15 @@ __device__ __forceinline__ double ldc(const double *p) { return __ldg(p); }
 __device__ __forceinline__ float ldc(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float ldc(const __half *p) { return __half2float(__ldg(p)); }
 __device__ __forceinline__ float ldc(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+
+// Raw loads for prefetching: the value stays in its storage type until it is
+// used, so no instruction waits on the load before then (a conversion right
+// after the load would stall there and hide nothing).
+__device__ __forceinline__ S ldr(const S *p) { return __ldg(p); }
+__device__ __forceinline__ double cv(double v) { return v; }
+__device__ __forceinline__ float cv(float v) { return v; }
+__device__ __forceinline__ float cv(__half v) { return __half2float(v); }
+__device__ __forceinline__ float cv(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 // store v rounded to nearest even; returns the stored value in type C
 __device__ __forceinline__ double stc(double *p, double v) { *p = v; return v; }
@@ -82,7 +93,12 @@ __device__ __forceinline__ float stc(__nv_bfloat16 *p, float v)
 
 // ------------------------------------------------------------ arithmetic
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float rcp(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double sqrt_c(double x) { return sqrt(x); }
 __device__ __forceinline__ float sqrt_c(float x)
 {
@@ -129,31 +145,34 @@ __device__ __forceinline__ C rec_right(C b, C c, C d, C e, C f)
            C(2.0 / 60.0) * f;
 }
 
-// Local Lax-Friedrichs flux along axis D from face states (rho, mx, my, mz,
-// E, Sigma) on the left and right: F_hat = (F_L + F_R)/2 - lam (q_R - q_L)/2,
-// F = (m_D, m u_D + (p + Sigma) e_D, (E + p + Sigma) u_D),
-// p = (gamma - 1)(E - |m|^2 / (2 rho)), lam = max(|u_D| + c) over both sides,
-// c = sqrt(gamma p / rho). Flags a non-positive face density or pressure.
+// Doubled local Lax-Friedrichs flux along axis D from face states (rho, mx,
+// my, mz, E, Sigma) on the left and right:
+//   G = 2 F_hat = (F_L + F_R) - lam (q_R - q_L),
+//   F = (m_D, m u_D + (p + Sigma) e_D, (E + p + Sigma) u_D),
+//   p = (gamma - 1)(E - |m|^2 / (2 rho)), lam = max(|u_D| + c) over both sides,
+//   c = sqrt(gamma p / rho).
+// (The factor 1/2 is applied once, in the divergence.) Flags a non-positive
+// face density or pressure.
 template <int D>
-__device__ __forceinline__ void lf_flux(const C *L, const C *R, C gamma, C gm1, C *F, bool &bad)
+__device__ __forceinline__ void lf_flux2(const C *L, const C *R, C gamma, C gm1, C *G, bool &bad)
 {
     C rL = rcp(L[0]), rR = rcp(R[0]);
     C uL = L[1 + D] * rL, uR = R[1 + D] * rR;
-    C pL = gm1 * (L[4] - C(0.5) * (L[1] * L[1] + L[2] * L[2] + L[3] * L[3]) * rL);
-    C pR = gm1 * (R[4] - C(0.5) * (R[1] * R[1] + R[2] * R[2] + R[3] * R[3]) * rR);
-    bad |= !(L[0] > C(0) && R[0] > C(0) && pL > C(0) && pR > C(0));
+    C pL = gm1 * (L[4] - C(0.5) * ((L[1] * L[1] + L[2] * L[2] + L[3] * L[3]) * rL));
+    C pR = gm1 * (R[4] - C(0.5) * ((R[1] * R[1] + R[2] * R[2] + R[3] * R[3]) * rR));
+    bad |= !(fmin(fmin(L[0], R[0]), fmin(pL, pR)) > C(0));
     C aL = fabs(uL) + sqrt_c(gamma * pL * rL);
     C aR = fabs(uR) + sqrt_c(gamma * pR * rR);
-    C h = C(0.5) * (aL > aR ? aL : aR);
+    C lam = aL > aR ? aL : aR;
     C PL = pL + L[5], PR = pR + R[5];
-    F[0] = C(0.5) * (L[1 + D] + R[1 + D]) - h * (R[0] - L[0]);
+    G[0] = (L[1 + D] + R[1 + D]) - lam * (R[0] - L[0]);
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        C f = C(0.5) * (L[1 + a] * uL + R[1 + a] * uR);
-        if (a == D) f += C(0.5) * (PL + PR);
-        F[1 + a] = f - h * (R[1 + a] - L[1 + a]);
+        C f = L[1 + a] * uL + R[1 + a] * uR;
+        if (a == D) f += PL + PR;
+        G[1 + a] = f - lam * (R[1 + a] - L[1 + a]);
     }
-    F[4] = C(0.5) * ((L[4] + PL) * uL + (R[4] + PR) * uR) - h * (R[4] - L[4]);
+    G[4] = ((L[4] + PL) * uL + (R[4] + PR) * uR) - lam * (R[4] - L[4]);
 }
 
 // wave speed max_d |u_d| + c at a cell
@@ -181,69 +200,193 @@ __device__ __forceinline__ double block_max(double v)
     return v;
 }
 
-constexpr int BX = 32, BY = 8;  // tile of the source and Jacobi kernels
+// ------------------------------------------------ 16-bit RK combination
+// The stage combination v = qn + w ((qs - qn) + dt L) is specified in FP64
+// and then rounded to the 16-bit storage format. FP64 runs at a small
+// fraction of the FP32 rate on this GPU, so it is evaluated in FP32 with a
+// rigorous bound e on |v32 - v64|:
+//   d = RN(qs - qn), p = RN(dt32 L + d), v = RN(w32 p + qn) with dt32, w32
+//   the FP32 roundings of dt, w (w <= 1) gives
+//   |v32 - v64| <= 2^-24 |v| + 2^-22 (|p| + |d|) <= 2^-22 (|v| + |p| + |d|).
+// If v32 sits farther than e from every rounding boundary of the storage
+// format, RN16(v32) = RN16(v64); otherwise (about one value in a thousand)
+// the combination is redone in FP64. The stored value therefore always
+// equals the FP64 evaluation rounded to nearest-even.
+template <typename T> struct Narrow;
+template <> struct Narrow<__half> {
+    static constexpr int M = 10;                 // stored mantissa bits
+    static constexpr float tiny = 0x1p-25f;      // half-ulp of the subnormals
+    static __device__ __forceinline__ __half rn(float v) { return __float2half_rn(v); }
+    static __device__ __forceinline__ __half rn(double v) { return __double2half(v); }
+    static __device__ __forceinline__ float f(__half h) { return __half2float(h); }
+};
+template <> struct Narrow<__nv_bfloat16> {
+    static constexpr int M = 7;
+    static constexpr float tiny = 0x1p-134f;
+    static __device__ __forceinline__ __nv_bfloat16 rn(float v) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ __nv_bfloat16 rn(double v) { return __double2bfloat16(v); }
+    static __device__ __forceinline__ float f(__nv_bfloat16 h) { return __bfloat162float(h); }
+};
+
+// FP64 evaluation, out of line so that only the rare lanes that need it run
+// FP64 instructions
+template <typename T>
+__device__ __noinline__ T rk_fp64(float qn, float qs, float L, double dt, double w)
+{
+    double vd = __dadd_rn(double(qn),
+                          __dmul_rn(w, __dadd_rn(__dsub_rn(double(qs), double(qn)),
+                                                 __dmul_rn(dt, double(L)))));
+    return Narrow<T>::rn(vd);
+}
+
+template <typename T>
+__device__ __forceinline__ float rk_store_narrow(T *p, float qn, float qs, float L, float dt32,
+                                                 double dt, float w32, double w)
+{
+    using NR = Narrow<T>;
+    float d = __fsub_rn(qs, qn);
+    float pp = __fmaf_rn(dt32, L, d);
+    float v = __fmaf_rn(w32, pp, qn);
+    float e = (fabsf(v) + fabsf(pp) + fabsf(d)) * 0x1p-22f;
+    T h = NR::rn(v);
+    float hv = NR::f(h);
+    float r = v - hv;  // exact: v and hv are within a factor 2
+    unsigned bits = __float_as_uint(hv);
+    // half the spacing of the format at hv (half of that below a power of two)
+    float hu = fmaxf(__uint_as_float((bits & 0x7F800000u) - (unsigned)((NR::M + 1) << 23)), NR::tiny);
+    bool pow2 = (bits & 0x7FFFFFu) == 0u;
+    float hb = (pow2 && r * hv < 0.f) ? 0.5f * hu : hu;
+    if (!(fabsf(r) + e < hb)) h = rk_fp64<T>(qn, qs, L, dt, w);
+    *p = h;
+    return NR::f(h);
+}
+
+constexpr bool kNarrow = sizeof(S) == 2;
+
+// stage combination for one value; returns the stored value in type C
+__device__ __forceinline__ C rk_store(S *p, C qn, C qs, C L, C dt32, double dt, C w32, double w)
+{
+    if constexpr (kNarrow) {
+        return rk_store_narrow<S>(p, qn, qs, L, dt32, dt, w32, w);
+    } else {
+        return stc(p, qn + w32 * ((qs - qn) + dt32 * L));
+    }
+}
+
+// --------------------------------------------- tiles of the 7-point kernels
+constexpr int BX = 32, BY = 8, BT = BX * BY;
+constexpr int HX = BX + 2, HY = BY + 2;   // plane tile with a halo of 1
+constexpr int NHALO1 = 2 * BX + 2 * BY;   // halo cells (corners are never read)
+
+// position of halo cell e (0 <= e < NHALO1) in the HX x HY tile
+__device__ __forceinline__ void halo1_cell(int e, int &lx, int &ly)
+{
+    if (e < BX) { lx = 1 + e; ly = 0; }
+    else if (e < 2 * BX) { lx = 1 + e - BX; ly = HY - 1; }
+    else if (e < 2 * BX + BY) { lx = 0; ly = 1 + e - 2 * BX; }
+    else { lx = HX - 1; ly = 1 + e - 2 * BX - BY; }
+}
 
 // --------------------------------------------------------------- source
-// u at column (i, j), plane kk (kk may leave the domain through -z/+z)
+// z-index of plane kk in [-1, nz]: periodic wrap or zero-gradient clamp
+__device__ __forceinline__ int zmap(int kk, const Geom &g)
+{
+    return kk < 0 ? (g.bc[4] == BC_PERIODIC ? kk + g.nz : 0)
+                  : (kk >= g.nz ? (g.bc[5] == BC_PERIODIC ? kk - g.nz : g.nz - 1) : kk);
+}
+
+// u = m / rho of the cell at in-plane offset c of plane kk (kk may leave the
+// domain through -z/+z: periodic wrap, zero-gradient clamp or the jet blend)
 __device__ __forceinline__ void col_u(const S *__restrict__ q, const Geom &g, const C *W,
-                                      const C *J, int i, int j, int kk, C u[3])
+                                      const C *J, int f, int kk, C u[3])
 {
     int km = map_axis(kk, g.nz, g.bc[4], g.bc[5]);
-    long long c = km * g.plane + (long long)j * g.nx + i;
+    long long c = km * g.plane + f;
     C rho = ldc(q + c), m0 = ldc(q + g.n + c), m1 = ldc(q + 2 * g.n + c), m2 = ldc(q + 3 * g.n + c);
     if (kk < 0 && g.bc[4] == BC_INFLOW) {
-        long long f = (long long)j * g.nx + i;
         C w = C(1) - W[f];
         rho = w * rho + J[f];
         m0 = w * m0 + J[g.plane + f];
         m1 = w * m1 + J[2 * g.plane + f];
         m2 = w * m2 + J[3 * g.plane + f];
     }
+    // products rounded before they are differenced: equal neighbours give an exact 0
     C r = rcp(rho);
     u[0] = mul_rn(m0, r);
     u[1] = mul_rn(m1, r);
     u[2] = mul_rn(m2, r);
 }
 
-__device__ __forceinline__ void plane_u(const S *__restrict__ q, const Geom &g, long long c, C u[3])
+// grad u by central differences from a shared plane tile U (x, y) and the
+// column's registers (z); b = alpha [tr(G^2) + tr(G)^2]
+__global__ void __launch_bounds__(BT) k_source(const S *__restrict__ q, S *__restrict__ b, Geom g,
+                                                C alpha, C inv2dx, const C *W, const C *J, int zc)
 {
-    C r = rcp(ldc(q + c));
-    u[0] = mul_rn(ldc(q + g.n + c), r);
-    u[1] = mul_rn(ldc(q + 2 * g.n + c), r);
-    u[2] = mul_rn(ldc(q + 3 * g.n + c), r);
-}
-
-__global__ void __launch_bounds__(BX *BY) k_source(const S *__restrict__ q, S *__restrict__ b,
-                                                    Geom g, C alpha, C inv2dx, const C *W,
-                                                    const C *J, int zc)
-{
-    int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return;
-    int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
-    int im = map_axis(i - 1, g.nx, g.bc[0], g.bc[1]), ip = map_axis(i + 1, g.nx, g.bc[0], g.bc[1]);
-    int jm = map_axis(j - 1, g.ny, g.bc[2], g.bc[3]), jp = map_axis(j + 1, g.ny, g.bc[2], g.bc[3]);
-    C um[3], u0[3], up[3];  // z-neighbours of the column
-    col_u(q, g, W, J, i, j, k0 - 1, um);
-    col_u(q, g, W, J, i, j, k0, u0);
+    __shared__ C U[3][HY][HX];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const int i = x0 + tx, j = y0 + ty;
+    const bool active = i < g.nx && j < g.ny;
+    const int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
+    // the own slot of the tile holds the mapped cell (it is a neighbour of
+    // active cells even when this thread is outside the domain)
+    const int f = map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx + map_axis(i, g.nx, g.bc[0], g.bc[1]);
+    const bool hv = tid < NHALO1;
+    int hs = 0, hf = 0;
+    if (hv) {
+        int lx, ly;
+        halo1_cell(tid, lx, ly);
+        hs = ly * HX + lx;
+        hf = map_axis(y0 + ly - 1, g.ny, g.bc[2], g.bc[3]) * g.nx +
+             map_axis(x0 + lx - 1, g.nx, g.bc[0], g.bc[1]);
+    }
+    C um[3], u0[3], up[3];
+    col_u(q, g, W, J, f, k0 - 1, um);
+    col_u(q, g, W, J, f, k0, u0);
+    // raw values one iteration ahead (loads overlap the previous plane's work):
+    // the column at k + 1 and the halo at k (planes >= 0 need no jet blend)
+    S nc[4], nh[4];
+    auto raw4 = [&](int off, int kk, S v[4]) {
+        long long c = zmap(kk, g) * g.plane + off;
+#pragma unroll
+        for (int a = 0; a < 4; a++) v[a] = ldr(q + a * g.n + c);
+    };
+    raw4(f, k0 + 1, nc);
+    if (hv) raw4(hf, k0, nh);
     for (int k = k0; k < k1; k++) {
-        col_u(q, g, W, J, i, j, k + 1, up);
-        long long pk = k * g.plane;
-        C uxm[3], uxp[3], uym[3], uyp[3];
-        plane_u(q, g, pk + (long long)j * g.nx + im, uxm);
-        plane_u(q, g, pk + (long long)j * g.nx + ip, uxp);
-        plane_u(q, g, pk + (long long)jm * g.nx + i, uym);
-        plane_u(q, g, pk + (long long)jp * g.nx + i, uyp);
-        C G[3][3];  // G[a][c] = d u_a / d x_c
+        C r = rcp(cv(nc[0]));
+#pragma unroll
+        for (int a = 0; a < 3; a++) up[a] = mul_rn(cv(nc[1 + a]), r);
+        C hu[3];
+        if (hv) {
+            C rh = rcp(cv(nh[0]));
+#pragma unroll
+            for (int a = 0; a < 3; a++) hu[a] = mul_rn(cv(nh[1 + a]), rh);
+        }
+        if (k + 1 < k1) {
+            raw4(f, k + 2, nc);
+            if (hv) raw4(hf, k + 1, nh);
+        }
+        __syncthreads();  // readers of the previous plane are done
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            G[a][0] = (uxp[a] - uxm[a]) * inv2dx;
-            G[a][1] = (uyp[a] - uym[a]) * inv2dx;
-            G[a][2] = (up[a] - um[a]) * inv2dx;
+            U[a][ty + 1][tx + 1] = u0[a];
+            if (hv) (&U[a][0][0])[hs] = hu[a];
         }
-        C tr = G[0][0] + G[1][1] + G[2][2];
-        C tr2 = G[0][0] * G[0][0] + G[1][1] * G[1][1] + G[2][2] * G[2][2] +
-                C(2) * (G[0][1] * G[1][0] + G[0][2] * G[2][0] + G[1][2] * G[2][1]);
-        stc(b + pk + (long long)j * g.nx + i, alpha * (tr2 + tr * tr));
+        __syncthreads();
+        if (active) {
+            C G[3][3];  // G[a][c] = d u_a / d x_c
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                G[a][0] = (U[a][ty + 1][tx + 2] - U[a][ty + 1][tx]) * inv2dx;
+                G[a][1] = (U[a][ty + 2][tx + 1] - U[a][ty][tx + 1]) * inv2dx;
+                G[a][2] = (up[a] - um[a]) * inv2dx;
+            }
+            C tr = G[0][0] + G[1][1] + G[2][2];
+            C tr2 = G[0][0] * G[0][0] + G[1][1] * G[1][1] + G[2][2] * G[2][2] +
+                    C(2) * (G[0][1] * G[1][0] + G[0][2] * G[2][0] + G[1][2] * G[2][1]);
+            stc(b + k * g.plane + (long long)j * g.nx + i, alpha * (tr2 + tr * tr));
+        }
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             um[a] = u0[a];
@@ -253,83 +396,401 @@ __global__ void __launch_bounds__(BX *BY) k_source(const S *__restrict__ q, S *_
 }
 
 // --------------------------------------------------------------- Jacobi
-__global__ void __launch_bounds__(BX *BY) k_jacobi(const S *__restrict__ q, const S *__restrict__ b,
-                                                    const S *__restrict__ sin, S *__restrict__ sout,
-                                                    Geom g, C beta, int zc)
+// One sweep s_out = (b + beta sum_f c_f s_nb) / (1/rho + beta sum_f c_f),
+// c_f = (1/rho_i + 1/rho_nb)/2; a face on a non-periodic boundary carries no
+// term. 1/rho and sigma of plane k sit in a shared tile with a halo of 1;
+// the z-neighbours stay in registers.
+
+__global__ void __launch_bounds__(BT) k_jacobi(const S *__restrict__ q, const S *__restrict__ b,
+                                                const S *__restrict__ sin, S *__restrict__ sout,
+                                                Geom g, C beta, int zc)
 {
-    int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return;
-    int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
-    // neighbour existence (a non-periodic boundary face carries no term)
-    bool hxm = i > 0 || g.bc[0] == BC_PERIODIC, hxp = i < g.nx - 1 || g.bc[1] == BC_PERIODIC;
-    bool hym = j > 0 || g.bc[2] == BC_PERIODIC, hyp = j < g.ny - 1 || g.bc[3] == BC_PERIODIC;
-    int im = wrap(i - 1, g.nx), ip = wrap(i + 1, g.nx), jm = wrap(j - 1, g.ny), jp = wrap(j + 1, g.ny);
-    long long col = (long long)j * g.nx + i;
-    // column values at k-1, k, k+1 (reciprocal density and sigma)
-    auto colv = [&](int kk, C &r, C &s) {
-        int km = wrap(kk, g.nz);
-        r = rcp(ldc(q + km * g.plane + col));
-        s = ldc(sin + km * g.plane + col);
-    };
+    __shared__ C R[HY][HX], SG[HY][HX];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const int i = x0 + tx, j = y0 + ty;
+    const bool active = i < g.nx && j < g.ny;
+    const int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
+    const int f = map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx + map_axis(i, g.nx, g.bc[0], g.bc[1]);
+    const bool hv = tid < NHALO1;
+    int hs = 0, hf = 0;
+    if (hv) {
+        int lx, ly;
+        halo1_cell(tid, lx, ly);
+        hs = ly * HX + lx;
+        hf = map_axis(y0 + ly - 1, g.ny, g.bc[2], g.bc[3]) * g.nx +
+             map_axis(x0 + lx - 1, g.nx, g.bc[0], g.bc[1]);
+    }
+    const C hb = C(0.5) * beta;
+    // a face term exists unless the face is a non-periodic domain boundary
+    const C exm = (i > 0 || g.bc[0] == BC_PERIODIC) ? hb : C(0);
+    const C exp_ = (i < g.nx - 1 || g.bc[1] == BC_PERIODIC) ? hb : C(0);
+    const C eym = (j > 0 || g.bc[2] == BC_PERIODIC) ? hb : C(0);
+    const C eyp = (j < g.ny - 1 || g.bc[3] == BC_PERIODIC) ? hb : C(0);
     C rm, sm, r0, s0, rp, sp;
-    colv(k0 - 1, rm, sm);
-    colv(k0, r0, s0);
-    C half_beta = C(0.5) * beta;
+    {
+        long long c = zmap(k0 - 1, g) * g.plane + f;
+        rm = rcp(ldc(q + c));
+        sm = ldc(sin + c);
+        c = (long long)k0 * g.plane + f;
+        r0 = rcp(ldc(q + c));
+        s0 = ldc(sin + c);
+    }
+    // raw values one iteration ahead: column at k + 1, halo and b at k
+    S ncr, ncs, nhr = S(1.0f), nhs = S(0.0f), nb;
+    auto pre = [&](int kk) {
+        long long c = zmap(kk + 1, g) * g.plane + f;
+        ncr = ldr(q + c);
+        ncs = ldr(sin + c);
+        if (hv) {
+            long long h = (long long)kk * g.plane + hf;
+            nhr = ldr(q + h);
+            nhs = ldr(sin + h);
+        }
+        nb = ldr(b + (long long)kk * g.plane + f);
+    };
+    pre(k0);
     for (int k = k0; k < k1; k++) {
-        colv(k + 1, rp, sp);
-        long long pk = k * g.plane;
-        C diag = r0, off = C(0);
-        // order of faces: -x, +x, -y, +y, -z, +z
-        auto face = [&](bool has, long long c) {
-            if (has) {
-                C cf = half_beta * (r0 + rcp(ldc(q + c)));
-                diag += cf;
-                off += cf * ldc(sin + c);
-            }
-        };
-        face(hxm, pk + (long long)j * g.nx + im);
-        face(hxp, pk + (long long)j * g.nx + ip);
-        face(hym, pk + (long long)jm * g.nx + i);
-        face(hyp, pk + (long long)jp * g.nx + i);
-        bool hzm = k > 0 || g.bc[4] == BC_PERIODIC, hzp = k < g.nz - 1 || g.bc[5] == BC_PERIODIC;
-        if (hzm) {
-            C cf = half_beta * (r0 + rm);
-            diag += cf;
-            off += cf * sm;
+        rp = rcp(cv(ncr));
+        sp = cv(ncs);
+        C hr = rcp(cv(nhr)), hsg = cv(nhs), bv = cv(nb);
+        if (k + 1 < k1) pre(k + 1);
+        __syncthreads();
+        R[ty + 1][tx + 1] = r0;
+        SG[ty + 1][tx + 1] = s0;
+        if (hv) {
+            (&R[0][0])[hs] = hr;
+            (&SG[0][0])[hs] = hsg;
         }
-        if (hzp) {
-            C cf = half_beta * (r0 + rp);
-            diag += cf;
-            off += cf * sp;
+        __syncthreads();
+        if (active) {
+            const C ezm = (k > 0 || g.bc[4] == BC_PERIODIC) ? hb : C(0);
+            const C ezp = (k < g.nz - 1 || g.bc[5] == BC_PERIODIC) ? hb : C(0);
+            // faces in the order -x, +x, -y, +y, -z, +z
+            C c0 = exm * (r0 + R[ty + 1][tx]);
+            C c1 = exp_ * (r0 + R[ty + 1][tx + 2]);
+            C c2 = eym * (r0 + R[ty][tx + 1]);
+            C c3 = eyp * (r0 + R[ty + 2][tx + 1]);
+            C c4 = ezm * (r0 + rm);
+            C c5 = ezp * (r0 + rp);
+            C diag = r0 + c0 + c1 + c2 + c3 + c4 + c5;
+            C off = c0 * SG[ty + 1][tx] + c1 * SG[ty + 1][tx + 2] + c2 * SG[ty][tx + 1] +
+                    c3 * SG[ty + 2][tx + 1] + c4 * sm + c5 * sp;
+            stc(sout + k * g.plane + (long long)j * g.nx + i, div_c(bv + off, diag));
         }
-        stc(sout + pk + col, div_c(ldc(b + pk + col) + off, diag));
         rm = r0; sm = s0;
         r0 = rp; s0 = sp;
     }
 }
 
+// Vector form of the sweep for rows whose length is a multiple of 4: each
+// thread owns 4 consecutive cells of a row (one 4-wide load/store per field),
+// takes x-neighbours from its own registers, y-neighbours as aligned 4-wide
+// shared loads. Same arithmetic per cell, in the same order, as k_jacobi.
+__device__ __forceinline__ void ld4(const double *p, double v[4])
+{
+    double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void ld4(const float *p, float v[4])
+{
+    float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void ld4(const __half *p, float v[4])
+{
+    uint2 a = __ldg(reinterpret_cast<const uint2 *>(p));
+    float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&a.x));
+    float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&a.y));
+    v[0] = lo.x; v[1] = lo.y; v[2] = hi.x; v[3] = hi.y;
+}
+__device__ __forceinline__ void ld4(const __nv_bfloat16 *p, float v[4])
+{
+    uint2 a = __ldg(reinterpret_cast<const uint2 *>(p));
+    float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&a.x));
+    float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&a.y));
+    v[0] = lo.x; v[1] = lo.y; v[2] = hi.x; v[3] = hi.y;
+}
+__device__ __forceinline__ void st4(double *p, const double v[4])
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void st4(float *p, const float v[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(__half *p, const float v[4])
+{
+    __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<unsigned *>(&a);
+    u.y = *reinterpret_cast<unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
+}
+__device__ __forceinline__ void st4(__nv_bfloat16 *p, const float v[4])
+{
+    __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<unsigned *>(&a);
+    u.y = *reinterpret_cast<unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
+}
+
+// four consecutive stored values kept raw after one vector load
+template <typename T> struct Vec4;
+template <> struct Vec4<double> { double2 a, b; };
+template <> struct Vec4<float> { float4 a; };
+template <> struct Vec4<__half> { uint2 a; };
+template <> struct Vec4<__nv_bfloat16> { uint2 a; };
+using V4 = Vec4<S>;
+
+__device__ __forceinline__ Vec4<double> ld4r(const double *p)
+{
+    return {__ldg(reinterpret_cast<const double2 *>(p)), __ldg(reinterpret_cast<const double2 *>(p) + 1)};
+}
+__device__ __forceinline__ Vec4<float> ld4r(const float *p) { return {__ldg(reinterpret_cast<const float4 *>(p))}; }
+__device__ __forceinline__ Vec4<__half> ld4r(const __half *p) { return {__ldg(reinterpret_cast<const uint2 *>(p))}; }
+__device__ __forceinline__ Vec4<__nv_bfloat16> ld4r(const __nv_bfloat16 *p)
+{
+    return {__ldg(reinterpret_cast<const uint2 *>(p))};
+}
+__device__ __forceinline__ void cv4(const Vec4<double> &v, double o[4])
+{
+    o[0] = v.a.x; o[1] = v.a.y; o[2] = v.b.x; o[3] = v.b.y;
+}
+__device__ __forceinline__ void cv4(const Vec4<float> &v, float o[4])
+{
+    o[0] = v.a.x; o[1] = v.a.y; o[2] = v.a.z; o[3] = v.a.w;
+}
+union H2U { unsigned u; __half2 h; };
+union B2U { unsigned u; __nv_bfloat162 h; };
+__device__ __forceinline__ void cv4(const Vec4<__half> &v, float o[4])
+{
+    H2U lo, hi;
+    lo.u = v.a.x;
+    hi.u = v.a.y;
+    float2 a = __half22float2(lo.h), b = __half22float2(hi.h);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void cv4(const Vec4<__nv_bfloat16> &v, float o[4])
+{
+    B2U lo, hi;
+    lo.u = v.a.x;
+    hi.u = v.a.y;
+    float2 a = __bfloat1622float2(lo.h), b = __bfloat1622float2(hi.h);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ Vec4<double> pack4(double a, double b, double c, double d)
+{
+    return {make_double2(a, b), make_double2(c, d)};
+}
+__device__ __forceinline__ Vec4<float> pack4(float a, float b, float c, float d) { return {make_float4(a, b, c, d)}; }
+__device__ __forceinline__ Vec4<__half> pack4(__half a, __half b, __half c, __half d)
+{
+    return {make_uint2(__half_as_ushort(a) | ((unsigned)__half_as_ushort(b) << 16),
+                       __half_as_ushort(c) | ((unsigned)__half_as_ushort(d) << 16))};
+}
+__device__ __forceinline__ Vec4<__nv_bfloat16> pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c,
+                                                      __nv_bfloat16 d)
+{
+    return {make_uint2(__bfloat16_as_ushort(a) | ((unsigned)__bfloat16_as_ushort(b) << 16),
+                       __bfloat16_as_ushort(c) | ((unsigned)__bfloat16_as_ushort(d) << 16))};
+}
+
+constexpr int VX = 4, TXV = BX * VX;        // 128 cells per tile row
+constexpr int HXV = TXV + 2 * VX;           // interior at column VX (16-byte aligned)
+constexpr int NYH = 2 * BX, NXH = 2 * BY;   // 4-wide y-halo tasks, scalar x-halo tasks
+
+// 4 raw values of field a at cells (x .. x+3) of row-plane offset rowoff:
+// one 4-wide load when the cells lie inside the row, mapped single loads otherwise
+__device__ __forceinline__ V4 ld4_mapped(const S *__restrict__ a, const Geom &g, long long rowoff, int x)
+{
+    if (x + VX <= g.nx) return ld4r(a + rowoff + x);
+    S v[VX];
+#pragma unroll
+    for (int c = 0; c < VX; c++) v[c] = ldr(a + rowoff + map_axis(x + c, g.nx, g.bc[0], g.bc[1]));
+    return pack4(v[0], v[1], v[2], v[3]);
+}
+
+__global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : 2) k_jacobi_v4(const S *__restrict__ q, const S *__restrict__ b,
+                                                   const S *__restrict__ sin, S *__restrict__ sout,
+                                                   Geom g, C beta, int zc)
+{
+    __shared__ __align__(16) C R[HY][HXV];
+    __shared__ __align__(16) C SG[HY][HXV];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    const int x0 = blockIdx.x * TXV, y0 = blockIdx.y * BY;
+    const int i0 = x0 + VX * tx, j = y0 + ty;
+    const bool active = i0 < g.nx && j < g.ny;
+    const int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
+    const long long rowj = (long long)map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx;
+    // halo tasks: 4-wide cells of the rows above/below the tile, then single
+    // cells left/right of each row
+    int htask = tid < NYH ? 0 : (tid < NYH + NXH ? 1 : 2);
+    int hsy = 0, hsx = 0, hx = 0;
+    long long hrow = 0;
+    if (htask == 0) {
+        int side = tid / BX, t = tid % BX;
+        hsy = side ? HY - 1 : 0;
+        hsx = VX + VX * t;
+        hx = x0 + VX * t;
+        hrow = (long long)map_axis(y0 + (side ? BY : -1), g.ny, g.bc[2], g.bc[3]) * g.nx;
+    } else if (htask == 1) {
+        int e = tid - NYH, side = e / BY, r = e % BY;
+        hsy = 1 + r;
+        hsx = side ? VX + TXV : VX - 1;
+        hx = map_axis(side ? x0 + TXV : x0 - 1, g.nx, g.bc[0], g.bc[1]);
+        hrow = (long long)map_axis(y0 + r, g.ny, g.bc[2], g.bc[3]) * g.nx;
+    }
+    const C hb = C(0.5) * beta;
+    const C exm = (i0 > 0 || g.bc[0] == BC_PERIODIC) ? hb : C(0);
+    const C exp_ = (i0 + VX - 1 < g.nx - 1 || g.bc[1] == BC_PERIODIC) ? hb : C(0);
+    const C eym = (j > 0 || g.bc[2] == BC_PERIODIC) ? hb : C(0);
+    const C eyp = (j < g.ny - 1 || g.bc[3] == BC_PERIODIC) ? hb : C(0);
+
+    C rm[VX], sm[VX], r0[VX], s0[VX], rp[VX], sp[VX];
+    {
+        C t[VX];
+        cv4(ld4_mapped(q, g, zmap(k0 - 1, g) * g.plane + rowj, i0), t);
+        cv4(ld4_mapped(sin, g, zmap(k0 - 1, g) * g.plane + rowj, i0), sm);
+#pragma unroll
+        for (int c = 0; c < VX; c++) rm[c] = rcp(t[c]);
+        cv4(ld4_mapped(q, g, (long long)k0 * g.plane + rowj, i0), t);
+        cv4(ld4_mapped(sin, g, (long long)k0 * g.plane + rowj, i0), s0);
+#pragma unroll
+        for (int c = 0; c < VX; c++) r0[c] = rcp(t[c]);
+    }
+    // raw values one iteration ahead: own cells at k + 1, halo and b at k
+    V4 ncr, ncs, nb, nhr, nhs;
+    S nxr = S(1.0f), nxs = S(0.0f);
+    auto pre = [&](int kk) {
+        long long pz = zmap(kk + 1, g) * g.plane + rowj;
+        ncr = ld4_mapped(q, g, pz, i0);
+        ncs = ld4_mapped(sin, g, pz, i0);
+        if (active) nb = ld4r(b + (long long)kk * g.plane + rowj + i0);
+        if (htask == 0) {
+            nhr = ld4_mapped(q, g, (long long)kk * g.plane + hrow, hx);
+            nhs = ld4_mapped(sin, g, (long long)kk * g.plane + hrow, hx);
+        } else if (htask == 1) {
+            nxr = ldr(q + (long long)kk * g.plane + hrow + hx);
+            nxs = ldr(sin + (long long)kk * g.plane + hrow + hx);
+        }
+    };
+    pre(k0);
+    for (int k = k0; k < k1; k++) {
+        C bv[VX], hr[VX], hsg[VX], t[VX];
+        cv4(ncr, t);
+        cv4(ncs, sp);
+#pragma unroll
+        for (int c = 0; c < VX; c++) rp[c] = rcp(t[c]);
+        if (active) cv4(nb, bv);
+        if (htask == 0) {
+            cv4(nhr, t);
+            cv4(nhs, hsg);
+#pragma unroll
+            for (int c = 0; c < VX; c++) hr[c] = rcp(t[c]);
+        } else if (htask == 1) {
+            hr[0] = rcp(cv(nxr));
+            hsg[0] = cv(nxs);
+        }
+        if (k + 1 < k1) pre(k + 1);
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < VX; c++) {
+            R[ty + 1][VX + VX * tx + c] = r0[c];
+            SG[ty + 1][VX + VX * tx + c] = s0[c];
+        }
+        if (htask == 0) {
+#pragma unroll
+            for (int c = 0; c < VX; c++) {
+                R[hsy][hsx + c] = hr[c];
+                SG[hsy][hsx + c] = hsg[c];
+            }
+        } else if (htask == 1) {
+            R[hsy][hsx] = hr[0];
+            SG[hsy][hsx] = hsg[0];
+        }
+        __syncthreads();
+        if (active) {
+            const C ezm = (k > 0 || g.bc[4] == BC_PERIODIC) ? hb : C(0);
+            const C ezp = (k < g.nz - 1 || g.bc[5] == BC_PERIODIC) ? hb : C(0);
+            const int col = VX + VX * tx;
+            C ry0[VX], ry1[VX], sy0[VX], sy1[VX], o[VX];
+#pragma unroll
+            for (int c = 0; c < VX; c++) {
+                ry0[c] = R[ty][col + c];
+                ry1[c] = R[ty + 2][col + c];
+                sy0[c] = SG[ty][col + c];
+                sy1[c] = SG[ty + 2][col + c];
+            }
+#pragma unroll
+            for (int c = 0; c < VX; c++) {
+                C rxm = c > 0 ? r0[c - 1] : R[ty + 1][col - 1];
+                C sxm = c > 0 ? s0[c - 1] : SG[ty + 1][col - 1];
+                C rxp = c < VX - 1 ? r0[c + 1] : R[ty + 1][col + VX];
+                C sxp = c < VX - 1 ? s0[c + 1] : SG[ty + 1][col + VX];
+                // faces in the order -x, +x, -y, +y, -z, +z
+                C c0 = (c > 0 ? hb : exm) * (r0[c] + rxm);
+                C c1 = (c < VX - 1 ? hb : exp_) * (r0[c] + rxp);
+                C c2 = eym * (r0[c] + ry0[c]);
+                C c3 = eyp * (r0[c] + ry1[c]);
+                C c4 = ezm * (r0[c] + rm[c]);
+                C c5 = ezp * (r0[c] + rp[c]);
+                C diag = r0[c] + c0 + c1 + c2 + c3 + c4 + c5;
+                C off = c0 * sxm + c1 * sxp + c2 * sy0[c] + c3 * sy1[c] + c4 * sm[c] + c5 * sp[c];
+                o[c] = div_c(bv[c] + off, diag);
+            }
+            st4(sout + (long long)k * g.plane + (long long)j * g.nx + i0, o);
+        }
+#pragma unroll
+        for (int c = 0; c < VX; c++) {
+            rm[c] = r0[c]; sm[c] = s0[c];
+            r0[c] = rp[c]; s0[c] = sp[c];
+        }
+    }
+}
+
 // ----------------------------------------------------------------- flux
-constexpr int TX = 32, TY = 8, NT = TX * TY;
-constexpr int PW = TX + 6, PH = TY + 6;  // plane tile with a halo of 3
+// Block of TY + 1 warps over a TX x TY tile of columns. Warps 0..TY-1 own a
+// row each: per plane a warp computes the x-face at the low side of each of
+// its cells, the y-face below its row and, from its register queue, the
+// z-face above; warp TY computes the y-faces above the last row and the
+// x-faces at the high end of every row. Every warp thus does three face
+// evaluations or fewer and the tile needs no face twice. The warp count is a
+// multiple of 4 so that the four SM sub-partitions (16K registers each) hold
+// equal shares: 16 warps of at most 128 registers in FP32 arithmetic, one
+// block per SM, keep the stencil queue in registers.
+constexpr int TX = 32, TY = sizeof(C) == 8 ? 7 : 15, NWARP = TY + 1, NT = 32 * NWARP;
+constexpr int PW = TX + 6, PH = TY + 6;          // plane tile with a halo of 3
+constexpr int NPLANE = TY * PW + 6 * TX;         // tile cells that are read (no corners)
+constexpr int LPT = (NPLANE + NT - 1) / NT;      // tile cells loaded per thread
 
 __host__ __device__ constexpr size_t flux_smem_elems()
 {
     return 6 * PH * PW + 5 * TY * (TX + 1) + 5 * (TY + 1) * TX;
 }
 
-// one column value set (rho, mx, my, mz, E, Sigma) at plane kk, with the
-// -z inflow blend for kk < 0
+// tile cell e (0 <= e < NPLANE) -> position (lx, ly) in the PW x PH tile
+__device__ __forceinline__ void plane_cell(int e, int &lx, int &ly)
+{
+    if (e < 3 * TX) { ly = e / TX; lx = 3 + e % TX; }
+    else if (e < 3 * TX + TY * PW) { e -= 3 * TX; ly = 3 + e / PW; lx = e % PW; }
+    else { e -= 3 * TX + TY * PW; ly = TY + 3 + e / TX; lx = 3 + e % TX; }
+}
+
+// one column value set (rho, mx, my, mz, E, Sigma) at in-plane offset f of
+// plane kk, with the -z jet blend for kk < 0
 __device__ __forceinline__ void col_load(const S *__restrict__ qs, const S *__restrict__ sig,
-                                         const Geom &g, const C *W, const C *J, int i, int j,
-                                         int kk, C v[6])
+                                         const Geom &g, const C *W, const C *J, int f, int kk,
+                                         C v[6])
 {
     int km = map_axis(kk, g.nz, g.bc[4], g.bc[5]);
-    long long c = km * g.plane + (long long)j * g.nx + i;
+    long long c = km * g.plane + f;
 #pragma unroll
     for (int u = 0; u < 5; u++) v[u] = ldc(qs + u * g.n + c);
     v[5] = ldc(sig + c);
     if (kk < 0 && g.bc[4] == BC_INFLOW) {
-        long long f = (long long)j * g.nx + i;
         C w = C(1) - W[f];
 #pragma unroll
         for (int u = 0; u < 5; u++) v[u] = w * v[u] + J[u * g.plane + f];
@@ -346,102 +807,164 @@ __device__ __forceinline__ void face_from_stencil(const C (&s)[6][6], C gamma, C
         L[u] = rec_left(s[0][u], s[1][u], s[2][u], s[3][u], s[4][u]);
         R[u] = rec_right(s[1][u], s[2][u], s[3][u], s[4][u], s[5][u]);
     }
-    lf_flux<D>(L, R, gamma, gm1, F, bad);
+    lf_flux2<D>(L, R, gamma, gm1, F, bad);
 }
 
-__global__ void __launch_bounds__(NT) k_flux(const S *__restrict__ qs, const S *__restrict__ sig,
-                                              const S *qn, S *out, C *rhs, Geom g, C gamma,
-                                              C inv_dx, int mode, const Scalars *sc,
-                                              double *blockmax, int *err, const C *W, const C *J,
-                                              int zc)
+// face along D from six consecutive tile cells starting at element `at`,
+// `step` elements apart, of every variable plane of P
+template <int D>
+__device__ __forceinline__ void tile_face(const C *P, int at, int step, C gamma, C gm1, C *F,
+                                          bool &bad)
+{
+    C s[6][6];
+#pragma unroll
+    for (int m = 0; m < 6; m++)
+#pragma unroll
+        for (int u = 0; u < 6; u++) s[m][u] = P[u * PH * PW + at + m * step];
+    face_from_stencil<D>(s, gamma, gm1, F, bad);
+}
+
+// registers per thread such that NWARP / 4 warps fit one sub-partition's 16K
+constexpr int FLUX_MAXREG = sizeof(C) == 8 ? 224 : 128;
+
+template <int mode>
+__global__ void __maxnreg__(FLUX_MAXREG)
+    k_flux(const S *__restrict__ qs, const S *__restrict__ sig, const S *qn, S *out, C *rhs,
+           Geom g, C gamma, C half_inv_dx, const Scalars *sc, double *blockmax, int *err,
+           const C *W, const C *J, int zc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *P = reinterpret_cast<C *>(smem_raw);  // [6][PH][PW]
     C *FX = P + 6 * PH * PW;                 // [5][TY][TX+1]
     C *FY = FX + 5 * TY * (TX + 1);          // [5][TY+1][TX]
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
-    const int i = x0 + tx, j = y0 + ty;
-    const bool active = i < g.nx && j < g.ny;
-    const int ic = min(i, g.nx - 1), jc = min(j, g.ny - 1);
+    const bool rowwarp = w < TY;  // warp-uniform
+    const int i = x0 + lane, j = y0 + (rowwarp ? w : 0);
+    const bool active = rowwarp && i < g.nx && j < g.ny;
+    const int fcol = map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx + map_axis(i, g.nx, g.bc[0], g.bc[1]);
     const C gm1 = gamma - C(1);
     bool bad = false;
 
-    A w = A(1), dt = A(0);
+    // tile cells this thread loads each plane: shared and in-plane offsets
+    int soff[LPT], goff[LPT];
+#pragma unroll
+    for (int r = 0; r < LPT; r++) {
+        int e = tid + r * NT;
+        soff[r] = -1;
+        goff[r] = 0;
+        if (e < NPLANE) {
+            int lx, ly;
+            plane_cell(e, lx, ly);
+            soff[r] = ly * PW + lx;
+            goff[r] = map_axis(y0 + ly - 3, g.ny, g.bc[2], g.bc[3]) * g.nx +
+                      map_axis(x0 + lx - 3, g.nx, g.bc[0], g.bc[1]);
+        }
+    }
+    S Rg[LPT][6];  // prefetched tile cells of the next plane (raw)
+    auto fetch = [&](int kk) {
+#pragma unroll
+        for (int r = 0; r < LPT; r++)
+            if (soff[r] >= 0) {
+                long long c = kk * g.plane + goff[r];
+#pragma unroll
+                for (int u = 0; u < 5; u++) Rg[r][u] = ldr(qs + u * g.n + c);
+                Rg[r][5] = ldr(sig + c);
+            }
+    };
+    auto commit = [&]() {
+#pragma unroll
+        for (int r = 0; r < LPT; r++)
+            if (soff[r] >= 0)
+#pragma unroll
+                for (int u = 0; u < 6; u++) P[u * PH * PW + soff[r]] = cv(Rg[r][u]);
+    };
+
+    C dt32 = C(0), w32 = C(1);
+    double dt = 0.0, wd = 1.0;
     if (mode != FLUX_RHS) {
-        dt = A(sc->dt);
-        w = mode == FLUX_STAGE1 ? A(1) : mode == FLUX_STAGE2 ? A(0.25) : A(2.0 / 3.0);
+        dt = sc->dt;
+        wd = mode == FLUX_STAGE1 ? 1.0 : mode == FLUX_STAGE2 ? 0.25 : 2.0 / 3.0;
+        dt32 = C(dt);
+        w32 = C(wd);
     }
     double smax = 0.0;
 
-    // Register queue of the column's z-stencil. At iteration k the slots hold
+    // Register queue of the column's z-stencil: at iteration k the slots hold
     // planes k-2..k+3 and give the z-face k + 1/2. The loop starts one plane
     // early so that the face k0 - 1/2 comes out of the same instructions as
     // every other z-face (bitwise equal to the neighbouring chunk's copy).
+    // Qn holds the column's next plane (loaded one iteration ahead; planes
+    // k0 + 2 and up never need the jet blend).
     C Q[6][6];
+    S Qn[6];
+    auto col_raw = [&](int kk) {
+        long long c = zmap(kk, g) * g.plane + fcol;
 #pragma unroll
-    for (int s = 1; s < 6; s++) col_load(qs, sig, g, W, J, ic, jc, k0 - 4 + s, Q[s]);
+        for (int u = 0; u < 5; u++) Qn[u] = ldr(qs + u * g.n + c);
+        Qn[5] = ldr(sig + c);
+    };
+    if (rowwarp) {
+#pragma unroll
+        for (int s = 1; s < 6; s++) col_load(qs, sig, g, W, J, fcol, k0 - 4 + s, Q[s]);
+        col_raw(k0 + 2);
+    }
+    fetch(k0);
     C Fzm[5];
     for (int k = k0 - 1; k < k1; k++) {
+        if (k >= k0 && k + 1 < k1) fetch(k + 1);
+        S qnv[5];
+        if (k >= k0 && active && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3)) {
+            long long c = k * g.plane + (long long)j * g.nx + i;
 #pragma unroll
-        for (int s = 0; s < 5; s++)
-#pragma unroll
-            for (int u = 0; u < 6; u++) Q[s][u] = Q[s + 1][u];
-        col_load(qs, sig, g, W, J, ic, jc, k + 3, Q[5]);
+            for (int u = 0; u < 5; u++) qnv[u] = ldr(qn + u * g.n + c);
+        }
         C Fzp[5];
-        face_from_stencil<2>(Q, gamma, gm1, Fzp, bad);  // z-face k + 1/2
+        if (rowwarp) {
+#pragma unroll
+            for (int s = 0; s < 5; s++)
+#pragma unroll
+                for (int u = 0; u < 6; u++) Q[s][u] = Q[s + 1][u];
+#pragma unroll
+            for (int u = 0; u < 6; u++) Q[5][u] = cv(Qn[u]);
+            if (k + 1 < k1) col_raw(k + 4);
+            face_from_stencil<2>(Q, gamma, gm1, Fzp, bad);  // z-face k + 1/2
+        }
         if (k >= k0) {
-            __syncthreads();  // readers of the previous plane are done
-            // plane k with an x/y halo of 3 (corners are never read)
-            for (int t = tid; t < PW * PH; t += NT) {
-                int lx = t % PW, ly = t / PW;
-                bool xin = lx >= 3 && lx < TX + 3, yin = ly >= 3 && ly < TY + 3;
-                if (!xin && !yin) continue;
-                int mx = map_axis(x0 + lx - 3, g.nx, g.bc[0], g.bc[1]);
-                int my = map_axis(y0 + ly - 3, g.ny, g.bc[2], g.bc[3]);
-                long long c = k * g.plane + (long long)my * g.nx + mx;
+            // P holds plane k
+            C F[5];
+            if (rowwarp) {
+                // x-face at the low side of cell `lane` of row w (tile cells lane-3..lane+2)
+                tile_face<0>(P, (w + 3) * PW + lane, 1, gamma, gm1, F, bad);
 #pragma unroll
-                for (int u = 0; u < 5; u++) P[(u * PH + ly) * PW + lx] = ldc(qs + u * g.n + c);
-                P[(5 * PH + ly) * PW + lx] = ldc(sig + c);
+                for (int u = 0; u < 5; u++) FX[(u * TY + w) * (TX + 1) + lane] = F[u];
+                // y-face below row w in column lane (tile rows w-3..w+2)
+                tile_face<1>(P, w * PW + lane + 3, PW, gamma, gm1, F, bad);
+#pragma unroll
+                for (int u = 0; u < 5; u++) FY[(u * (TY + 1) + w) * TX + lane] = F[u];
+            } else {
+                // y-face above the last row, column lane
+                tile_face<1>(P, TY * PW + lane + 3, PW, gamma, gm1, F, bad);
+#pragma unroll
+                for (int u = 0; u < 5; u++) FY[(u * (TY + 1) + TY) * TX + lane] = F[u];
+                if (lane < TY) {
+                    // x-face at the high end of row `lane`
+                    tile_face<0>(P, (lane + 3) * PW + TX, 1, gamma, gm1, F, bad);
+#pragma unroll
+                    for (int u = 0; u < 5; u++) FX[(u * TY + lane) * (TX + 1) + TX] = F[u];
+                }
             }
-            __syncthreads();
-            // x-faces: face f of row r sits between local cells f-1 and f
-            for (int t = tid; t < (TX + 1) * TY; t += NT) {
-                int f = t % (TX + 1), r = t / (TX + 1);
-                C s[6][6];
-#pragma unroll
-                for (int m = 0; m < 6; m++)
-#pragma unroll
-                    for (int u = 0; u < 6; u++) s[m][u] = P[(u * PH + r + 3) * PW + f + m];
-                C F[5];
-                face_from_stencil<0>(s, gamma, gm1, F, bad);
-#pragma unroll
-                for (int u = 0; u < 5; u++) FX[(u * TY + r) * (TX + 1) + f] = F[u];
-            }
-            // y-faces: face fr of column c sits between local rows fr-1 and fr
-            for (int t = tid; t < (TY + 1) * TX; t += NT) {
-                int c = t % TX, fr = t / TX;
-                C s[6][6];
-#pragma unroll
-                for (int m = 0; m < 6; m++)
-#pragma unroll
-                    for (int u = 0; u < 6; u++) s[m][u] = P[(u * PH + fr + m) * PW + c + 3];
-                C F[5];
-                face_from_stencil<1>(s, gamma, gm1, F, bad);
-#pragma unroll
-                for (int u = 0; u < 5; u++) FY[(u * (TY + 1) + fr) * TX + c] = F[u];
-            }
-            __syncthreads();
+            __syncthreads();  // faces complete; reads of P done
             if (active) {
                 long long c = k * g.plane + (long long)j * g.nx + i;
                 C Lv[5];
 #pragma unroll
                 for (int u = 0; u < 5; u++) {
-                    C dfx = FX[(u * TY + ty) * (TX + 1) + tx + 1] - FX[(u * TY + ty) * (TX + 1) + tx];
-                    C dfy = FY[(u * (TY + 1) + ty + 1) * TX + tx] - FY[(u * (TY + 1) + ty) * TX + tx];
+                    C dfx = FX[(u * TY + w) * (TX + 1) + lane + 1] - FX[(u * TY + w) * (TX + 1) + lane];
+                    C dfy = FY[(u * (TY + 1) + w + 1) * TX + lane] - FY[(u * (TY + 1) + w) * TX + lane];
                     C dfz = Fzp[u] - Fzm[u];
-                    Lv[u] = -((dfx + dfy) + dfz) * inv_dx;
+                    Lv[u] = -((dfx + dfy) + dfz) * half_inv_dx;
                 }
                 if (mode == FLUX_RHS) {
 #pragma unroll
@@ -450,10 +973,9 @@ __global__ void __launch_bounds__(NT) k_flux(const S *__restrict__ qs, const S *
                     C o[5];
 #pragma unroll
                     for (int u = 0; u < 5; u++) {
-                        A qsv = A(Q[2][u]);
-                        A qnv = mode == FLUX_STAGE1 ? qsv : A(ldc(qn + u * g.n + c));
-                        A v = qnv + w * ((qsv - qnv) + dt * A(Lv[u]));
-                        o[u] = stc(out + u * g.n + c, v);
+                        C qsv = Q[2][u];
+                        C qb = mode == FLUX_STAGE1 ? qsv : cv(qnv[u]);
+                        o[u] = rk_store(out + u * g.n + c, qb, qsv, Lv[u], dt32, dt, w32, wd);
                         bad |= !isfinite(o[u]);
                     }
                     if (mode == FLUX_STAGE3)
@@ -461,8 +983,12 @@ __global__ void __launch_bounds__(NT) k_flux(const S *__restrict__ qs, const S *
                 }
             }
         }
+        if (rowwarp) {
 #pragma unroll
-        for (int u = 0; u < 5; u++) Fzm[u] = Fzp[u];
+            for (int u = 0; u < 5; u++) Fzm[u] = Fzp[u];
+        }
+        if (k + 1 < k1) commit();  // P <- plane k + 1
+        __syncthreads();
     }
     if (bad) atomicOr(err, 1);
     if (mode == FLUX_STAGE3) {
@@ -470,6 +996,17 @@ __global__ void __launch_bounds__(NT) k_flux(const S *__restrict__ qs, const S *
         if (tid == 0)
             blockmax[(blockIdx.z * (long long)gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = m;
     }
+}
+
+// stand-alone stage combination (the flux kernel's epilogue) over n values
+__global__ void k_rk_combine(const S *__restrict__ qn, const S *__restrict__ qs,
+                             const C *__restrict__ L, S *__restrict__ out, long long n, double dt,
+                             double wd)
+{
+    C dt32 = C(dt), w32 = C(wd);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x)
+        rk_store(out + c, ldc(qn + c), ldc(qs + c), L[c], dt32, dt, w32, wd);
 }
 
 // ---------------------------------------------------------- wave speed
@@ -506,6 +1043,12 @@ cudaError_t launch_source(const Geom &g, const Phys &p, const Tiles &t, const In
 cudaError_t launch_jacobi(const Geom &g, const Phys &p, const Tiles &t, const void *q,
                           const void *b, const void *s_in, void *s_out, cudaStream_t st)
 {
+    if (g.nx % VX == 0) {
+        k_jacobi_v4<<<grid_of(g, TXV, BY, t.zc_jacobi), dim3(BX, BY), 0, st>>>(
+            (const S *)q, (const S *)b, (const S *)s_in, (S *)s_out, g, C(p.alpha / (p.dx * p.dx)),
+            t.zc_jacobi);
+        return cudaGetLastError();
+    }
     k_jacobi<<<grid_of(g, BX, BY, t.zc_jacobi), dim3(BX, BY), 0, st>>>(
         (const S *)q, (const S *)b, (const S *)s_in, (S *)s_out, g, C(p.alpha / (p.dx * p.dx)),
         t.zc_jacobi);
@@ -522,18 +1065,30 @@ cudaError_t launch_flux(const Geom &g, const Phys &p, const Tiles &t, const Infl
                         const void *qs, const void *sig, const void *qn, void *out, void *rhs,
                         const Scalars *sc, double *blockmax, int *err, cudaStream_t st)
 {
-    static bool attr_set = false;
     size_t smem = flux_smem_elems() * sizeof(C);
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_flux, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    auto go = [&](auto kern) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        kern<<<grid_of(g, TX, TY, t.zc_flux), NT, smem, st>>>(
+            (const S *)qs, (const S *)sig, (const S *)qn, (S *)out, (C *)rhs, g, C(p.gamma),
+            C(0.5 / p.dx), sc, blockmax, err, (const C *)in.W, (const C *)in.J, t.zc_flux);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            cudaFuncAttributes fa;
+            if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess)
+                fprintf(stderr, "igr: flux launch failed (%s): block %d, regs %d, max threads %d, "
+                                "static smem %zu, dynamic smem %zu, local %zu\n",
+                        cudaGetErrorString(e), NT, fa.numRegs, fa.maxThreadsPerBlock,
+                        fa.sharedSizeBytes, smem, fa.localSizeBytes);
+        }
+        return e;
+    };
+    switch (mode) {
+    case FLUX_RHS: return go(k_flux<FLUX_RHS>);
+    case FLUX_STAGE1: return go(k_flux<FLUX_STAGE1>);
+    case FLUX_STAGE2: return go(k_flux<FLUX_STAGE2>);
+    default: return go(k_flux<FLUX_STAGE3>);
     }
-    k_flux<<<grid_of(g, TX, TY, t.zc_flux), dim3(TX, TY), smem, st>>>(
-        (const S *)qs, (const S *)sig, (const S *)qn, (S *)out, (C *)rhs, g, C(p.gamma),
-        C(1.0 / p.dx), mode, sc, blockmax, err, (const C *)in.W, (const C *)in.J, t.zc_flux);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_speed(const Geom &g, const Phys &p, const void *q, double *blockmax,
@@ -546,11 +1101,20 @@ cudaError_t launch_speed(const Geom &g, const Phys &p, const void *q, double *bl
     return cudaGetLastError();
 }
 
+cudaError_t launch_rk_combine(const void *qn, const void *qs, const void *L, void *out,
+                              long long n, double dt, double w, cudaStream_t st)
+{
+    long long want = (n + 255) / 256;
+    int nb = (int)(want < 152 * 16 ? (want > 0 ? want : 1) : 152 * 16);
+    k_rk_combine<<<nb, 256, 0, st>>>((const S *)qn, (const S *)qs, (const C *)L, (S *)out, n, dt, w);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 extern const Ops IGR_OPS = {
     (int)sizeof(S), (int)sizeof(C), launch_source, launch_jacobi, launch_flux, flux_blocks,
-    launch_speed,
+    launch_speed, launch_rk_combine,
 };
 
 }  // namespace igr

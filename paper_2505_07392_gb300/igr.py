@@ -73,6 +73,7 @@ def lib():
             "igr_solve_sigma": (i, [p, p, p, i, i]),
             "igr_rhs": (i, [p, p, p, p, i]),
             "igr_get_dt": (i, [p, C.POINTER(d)]),
+            "igr_rk_combine": (i, [p, p, p, p, p, C.c_longlong, i, d]),
             "igr_sync": (i, [p]),
             "igr_profile_enable": (i, [p, i]),
             "igr_profile_read": (i, [p, i, C.POINTER(C.c_longlong), C.POINTER(d)]),
@@ -256,6 +257,16 @@ class Solver:
         out = torch.empty((5,) + self.shape, dtype=compute_torch_dtype(self.precision), device=self.device)
         self._check(lib().igr_rhs(self.h, C.c_void_p(q.data_ptr()), C.c_void_p(sigma.data_ptr()),
                                   C.c_void_p(out.data_ptr()), _dt_code(q.dtype)))
+        return out
+
+    def rk_combine(self, qn, qs, L, stage: int, dt: float):
+        """The stage kernel's RK combination on flat tensors (storage dtype; L in
+        the arithmetic dtype); returns a new tensor."""
+        import torch
+        out = torch.empty_like(qn)
+        self._check(lib().igr_rk_combine(self.h, C.c_void_p(qn.data_ptr()), C.c_void_p(qs.data_ptr()),
+                                         C.c_void_p(L.data_ptr()), C.c_void_p(out.data_ptr()),
+                                         int(qn.numel()), int(stage), float(dt)))
         return out
 
     # -- per-kernel timing

@@ -277,3 +277,53 @@ def test_plume_full_size_sampled(precision):
             got = qg[:, k0:k1, j0:j1, i0:i1].double().cpu().numpy()
             err = field_errors(got[(slice(None),) + sl], qo[(slice(None),) + sl])
             assert max(err.values()) <= TOL[precision], (ic, jc, kc, err)
+
+
+def _bf16_rn(x):
+    """float64 -> bfloat16 (round to nearest even, normal range), as float64."""
+    m, e = np.frexp(x)
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+@pytest.mark.parametrize("precision", ["f16", "bf16"])
+@pytest.mark.parametrize("stage", [1, 2, 3])
+def test_rk_combine_equals_fp64_rounding(precision, stage):
+    """16-bit storage: the stored stage combination qn + w((qs - qn) + dt L) is
+    the FP64 evaluation rounded to nearest-even, bit for bit, including values
+    built to sit within 1e-12 of a rounding midpoint."""
+    import torch
+    from paper_2505_07392_gb300 import igr
+    rng = np.random.Generator(np.random.Philox(40 + stage))
+    n = 1 << 20
+    w = {1: 1.0, 2: 0.25, 3: 2.0 / 3.0}[stage]
+    dt = 3.7e-4
+    st = igr.storage_torch_dtype(precision)
+    mag = 10.0 ** rng.uniform(-3, 2, size=n)
+    qn = torch.from_numpy(mag * rng.choice([-1.0, 1.0], size=n)).to(st)
+    qs = torch.from_numpy(qn.double().numpy() * (1 + rng.normal(0, 1e-2, size=n))).to(st)
+    if stage == 1:
+        qs = qn.clone()
+    L = rng.normal(0, 1, size=n) * mag * 30.0
+    # a quarter of the values: L chosen so that the exact result sits next to
+    # the midpoint between two neighbouring 16-bit values
+    k = n // 4
+    qn64 = qn.double().numpy()
+    qs64 = qs.double().numpy()
+    base = qn64[:k] + w * (qs64[:k] - qn64[:k])
+    hb = torch.from_numpy(base).to(st)
+    bits = hb.view(torch.int16).numpy().astype(np.int32)
+    nxt = torch.from_numpy(((bits + 1) & 0xFFFF).astype(np.uint16).astype(np.int16)).view(st).double().numpy()
+    mid = 0.5 * (hb.double().numpy() + nxt)
+    target = mid * (1 + rng.choice([-1.0, 1.0], size=k) * 10.0 ** rng.uniform(-15, -9, size=k))
+    L[:k] = (target - base) / (w * dt)
+    L32 = torch.from_numpy(L).float()
+    L64 = L32.double().numpy()
+    exact = qn64 + w * ((qs64 - qn64) + dt * L64)
+    ok = np.isfinite(exact) & (np.abs(exact) < 6e4)
+    expect = (torch.from_numpy(exact).to(torch.float16) if precision == "f16"
+              else torch.from_numpy(_bf16_rn(exact)).to(torch.bfloat16))
+    with igr.Solver(inputs.density_wave(4, noise=0.0), precision) as s:
+        got = s.rk_combine(qn.cuda(), qs.cuda(), L32.cuda(), stage, dt).cpu()
+    gb, eb = got.view(torch.int16).numpy(), expect.view(torch.int16).numpy()
+    bad = np.flatnonzero(ok & (gb != eb))
+    assert bad.size == 0, (bad.size, exact[bad[:5]], got[bad[:5]], expect[bad[:5]])
