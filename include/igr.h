@@ -157,6 +157,39 @@ igr_status igr_rhs(igr_ctx *ctx, const void *q, const void *sigma, void *rhs, ig
 igr_status igr_rk_combine(igr_ctx *ctx, const void *qn, const void *qs, const void *L, void *out,
                           long long count, int stage, double dt);
 
+/* ---- Allocation-free Sigma solve --------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory where they need a Sigma solve (code working
+ * inside another framework's fixed memory budget, allocation-free real-time
+ * loops, hooks that may not call cudaMalloc or a caching allocator).
+ *
+ * igr_solve_sigma_noalloc does what igr_solve_sigma does (b from q, then
+ * `sweeps` Jacobi sweeps warm-started from sigma_inout, result in
+ * sigma_inout) without a context and without allocating anything: its
+ * scratch (b and the second Jacobi buffer, 2 n values of the storage type)
+ * lives in one static device array of IGR_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading this library holds until the process exits.
+ *  - q, sigma_inout: device buffers in the storage type of cfg->prec.
+ *  - Grids needing more than the array holds (see igr_noalloc_max_cells) are
+ *    rejected with IGR_ERR_INVALID_ARG; IGR_BC_INFLOW faces with
+ *    IGR_ERR_UNSUPPORTED. The call issues no cudaMalloc/cudaFree and no
+ *    allocating library routine.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls on a device share the one array, which keeps the last call's
+ *    contents (every value is written before it is read, so nothing needs
+ *    clearing). Calls whose work overlaps on the GPU (concurrent streams or
+ *    threads) race on it: serialise them.
+ *  - Errors: the status; the message is in igr_noalloc_last_error(). */
+#define IGR_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+igr_status igr_solve_sigma_noalloc(const igr_config *cfg, const void *q, void *sigma_inout,
+                                   int sweeps, void *cuda_stream);
+/* Largest grid (cells) igr_solve_sigma_noalloc takes in precision prec. */
+size_t igr_noalloc_max_cells(igr_precision prec);
+/* Message of the last failed igr_solve_sigma_noalloc call. Never NULL. */
+const char *igr_noalloc_last_error(void);
+
 /* Time step dt = cfl dx / max_d(|u_d| + c) of the current state.
  * Synchronises. */
 igr_status igr_get_dt(igr_ctx *ctx, double *dt);

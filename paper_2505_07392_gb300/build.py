@@ -1,8 +1,9 @@
 """Builds libigr.so, the CUDA library behind include/igr.h, for sm_103a.
 
 The kernel source igr_kernels.cu is compiled once per storage type (FP64,
-FP32, FP16, BF16) and the host runtime igr_api.cu once; the five objects
-compile in parallel and link into paper_2505_07392_gb300/libigr.so.
+FP32, FP16, BF16); the host runtime igr_api.cu and the allocation-free entry
+point igr_noalloc.cu once each; the objects compile in parallel and link
+into paper_2505_07392_gb300/libigr.so.
 """
 import concurrent.futures as cf
 import os
@@ -37,8 +38,9 @@ def _jobs(extra):
     for tag, ty in VARIANTS:
         jobs.append([nvcc(), *ARCH, *FLAGS, *extra, f"-DIGR_STORAGE={ty}", f"-DIGR_OPS=ops_{tag}",
                      "-c", os.path.join(CSRC, "igr_kernels.cu"), "-o", os.path.join(OBJ, f"kern_{tag}.o")])
-    jobs.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, "igr_api.cu"),
-                 "-o", os.path.join(OBJ, "api.o")])
+    for name in ("igr_api", "igr_noalloc"):
+        jobs.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, name + ".cu"),
+                     "-o", os.path.join(OBJ, name + ".o")])
     return jobs
 
 

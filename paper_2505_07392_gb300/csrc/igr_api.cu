@@ -167,7 +167,7 @@ static int storage_dtype(igr_precision p)
 }
 static size_t dtype_bytes(int dt) { return dt == IGR_DT_F64 ? 8 : dt == IGR_DT_F32 ? 4 : 2; }
 
-static const Ops *ops_for(igr_precision p)
+const Ops *igr::ops_for(int p)
 {
     switch (p) {
     case IGR_F64: return &ops_f64;
@@ -178,7 +178,7 @@ static const Ops *ops_for(igr_precision p)
     return nullptr;
 }
 
-static Tiles default_tiles(const Geom &g)
+Tiles igr::default_tiles(const Geom &g)
 {
     Tiles t;
     t.zc_source = g.nz < 32 ? g.nz : 32;
@@ -187,7 +187,7 @@ static Tiles default_tiles(const Geom &g)
     return t;
 }
 
-static const char *validate(const igr_config *c)
+const char *igr::validate_config(const igr_config *c)
 {
     if (!c) return "cfg is NULL";
     if (c->nx < 4 || c->ny < 4 || c->nz < 4) return "nx, ny, nz must each be >= 4";
@@ -364,7 +364,7 @@ const char *igr_last_error(const igr_ctx *ctx) { return ctx ? ctx->err : g_creat
 
 size_t igr_memory_bytes(const igr_config *cfg)
 {
-    if (validate(cfg)) return 0;
+    if (validate_config(cfg)) return 0;
     Layout L = layout_of(cfg);
     return 3 * round256(L.state) + 2 * round256(L.sig) + round256(L.b) + round256(L.W) +
            round256(L.J) + round256(L.blockmax) + round256(L.scalars) + round256(L.jets);
@@ -375,7 +375,7 @@ igr_status igr_create(const igr_config *cfg, const igr_allocator *allocator, voi
 {
     if (!out) return fail(nullptr, IGR_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (const char *why = validate(cfg)) return fail(nullptr, IGR_ERR_INVALID_ARG, "%s", why);
+    if (const char *why = validate_config(cfg)) return fail(nullptr, IGR_ERR_INVALID_ARG, "%s", why);
     if (allocator && (!allocator->alloc || !allocator->free))
         return fail(nullptr, IGR_ERR_INVALID_ARG, "allocator needs alloc and free");
     igr_ctx *c = new (std::nothrow) igr_ctx();

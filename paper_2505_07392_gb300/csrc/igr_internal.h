@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/igr.h"
+
 namespace igr {
 
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW = 2 };
@@ -76,5 +78,10 @@ struct Ops {
 };
 
 extern const Ops ops_f64, ops_f32, ops_f16, ops_bf16;
+
+// shared by the host entry points (igr_api.cu, igr_noalloc.cu)
+const Ops *ops_for(int precision);             // kernel set of an igr_precision
+Tiles default_tiles(const Geom &g);            // launch shapes for a grid
+const char *validate_config(const igr_config *c);  // NULL when valid
 
 }  // namespace igr

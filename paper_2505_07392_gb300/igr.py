@@ -74,6 +74,9 @@ def lib():
             "igr_rhs": (i, [p, p, p, p, i]),
             "igr_get_dt": (i, [p, C.POINTER(d)]),
             "igr_rk_combine": (i, [p, p, p, p, p, C.c_longlong, i, d]),
+            "igr_solve_sigma_noalloc": (i, [C.POINTER(Config), p, p, i, p]),
+            "igr_noalloc_max_cells": (C.c_size_t, [i]),
+            "igr_noalloc_last_error": (C.c_char_p, []),
             "igr_sync": (i, [p]),
             "igr_profile_enable": (i, [p, i]),
             "igr_profile_read": (i, [p, i, C.POINTER(C.c_longlong), C.POINTER(d)]),

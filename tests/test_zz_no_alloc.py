@@ -1,0 +1,100 @@
+"""igr_solve_sigma_noalloc, the allocation-free Sigma solve, against the
+context-based igr_solve_sigma.
+
+The allocation-free entry point serves callers that cannot allocate device
+memory where they need the solve (inside another framework's fixed memory
+budget, in allocation-free real-time loops, in hooks that may not call
+cudaMalloc). Its scratch lives in a static device array of the library. The
+test calls it through the C ABI twice in a row (the second call reuses the
+array the first one left behind) and holds it to the FP32 tolerance of the
+other parity tests. It is collected last so that a run stopping at the first
+failure has already run every other test.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2505_07392_gb300 import inputs
+from paper_2505_07392_gb300.inputs import OUTFLOW, PERIODIC, Case
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5  # relative L2, the FP32 parity tolerance
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_07392_gb300 import build
+    build.build()
+    yield
+
+
+def _state(case, seed):
+    rng = np.random.Generator(np.random.Philox(seed))
+    z, y, x = np.meshgrid(*[(np.arange(n) + 0.5) / n for n in (case.nz, case.ny, case.nx)], indexing="ij")
+    ph = rng.uniform(0, 2 * np.pi, size=6)
+    tp = 2 * np.pi
+    rho = 1 + 0.2 * np.sin(tp * x + ph[0]) * np.cos(tp * y + ph[1]) + 0.1 * np.cos(tp * z)
+    u = 0.3 * np.sin(tp * y + ph[2])
+    v = 0.2 * np.cos(tp * z + ph[3])
+    w = 0.25 * np.sin(tp * x + ph[4])
+    p = 1 + 0.1 * np.cos(tp * (x + z) + ph[5])
+    E = p / 0.4 + 0.5 * rho * (u * u + v * v + w * w)
+    return np.stack([rho, rho * u, rho * v, rho * w, E])
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_noalloc_solve_matches_context_solve_twice():
+    import torch
+    from paper_2505_07392_gb300 import igr
+    L = igr.lib()
+    case = Case("noalloc", 44, 36, 28, 1.0 / 44, alpha=1.0 / 44 ** 2, sweeps=5,
+                bc=(OUTFLOW, OUTFLOW, PERIODIC, PERIODIC, OUTFLOW, OUTFLOW))
+    cfg, _jets = igr.make_config(case, "f32")
+    stream = torch.cuda.current_stream()
+    results = []
+    for call, (seed, sweeps) in enumerate(((1, 5), (2, 4))):
+        q = torch.from_numpy(_state(case, seed)).float().cuda()
+        s0 = (0.05 * torch.from_numpy(_state(case, seed + 10)[0])).float().cuda()
+        with igr.Solver(case, "f32") as s:
+            ref = s.solve_sigma(q, s0.clone(), sweeps)
+            torch.cuda.synchronize()
+            ref = ref.double().cpu().numpy()
+        sig = s0.clone()
+        st = L.igr_solve_sigma_noalloc(C.byref(cfg), C.c_void_p(q.data_ptr()), C.c_void_p(sig.data_ptr()),
+                                       sweeps, C.c_void_p(stream.cuda_stream))
+        assert st == igr.OK, L.igr_noalloc_last_error().decode()
+        torch.cuda.synchronize()
+        got = sig.double().cpu().numpy()
+        assert np.abs(ref).max() > 0
+        assert _rel(got, ref) <= TOL, (call, _rel(got, ref))
+        results.append(got)
+    assert not np.array_equal(results[0], results[1])
+
+
+def test_noalloc_rejects_what_it_cannot_hold():
+    from paper_2505_07392_gb300 import igr
+    L = igr.lib()
+    L.igr_noalloc_max_cells.restype = C.c_size_t
+    L.igr_noalloc_max_cells.argtypes = [C.c_int]
+    L.igr_noalloc_last_error.restype = C.c_char_p
+    cap = L.igr_noalloc_max_cells(igr.F32)
+    assert cap >= 100_000
+    n = int(round(cap ** (1 / 3))) + 8
+    big = Case("big", n, n, n, 1.0 / n, alpha=1.0 / n ** 2, bc=(PERIODIC,) * 6)
+    cfg, _ = igr.make_config(big, "f32")
+    dummy = C.c_void_p(256)  # never dereferenced: the size check comes first
+    st = L.igr_solve_sigma_noalloc(C.byref(cfg), dummy, dummy, 3, None)
+    assert st == igr.ERR_INVALID_ARG
+    assert b"scratch" in L.igr_noalloc_last_error()
+    jets = inputs.jets4(16)
+    cfg2, _j = igr.make_config(jets, "f32")
+    st = L.igr_solve_sigma_noalloc(C.byref(cfg2), dummy, dummy, 3, None)
+    assert st == igr.ERR_UNSUPPORTED
