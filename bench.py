@@ -38,7 +38,10 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per cell of one launch from an ncu capture of each kernel on the
 # plume workload, keyed by a hash of the kernel source they were taken with;
 # a changed source makes the figure stale (reported as null).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/flux_plume_f16.md: mean of the three stage launches, 512 x 512 x 128 plume
+    "flux_f16": {"bytes_per_cell": 29.752, "src": "cc66aa90565d5308"},
+}
 
 
 def kernel_source_hash():

@@ -163,7 +163,7 @@ __device__ __forceinline__ void lf_flux2(const C *L, const C *R, C gamma, C gm1,
     bad |= !(fmin(fmin(L[0], R[0]), fmin(pL, pR)) > C(0));
     C aL = fabs(uL) + sqrt_c(gamma * pL * rL);
     C aR = fabs(uR) + sqrt_c(gamma * pR * rR);
-    C lam = aL > aR ? aL : aR;
+    C lam = fmax(aL, aR);  // a NaN speed comes with a flagged face
     C PL = pL + L[5], PR = pR + R[5];
     G[0] = (L[1 + D] + R[1 + D]) - lam * (R[0] - L[0]);
 #pragma unroll
@@ -251,11 +251,10 @@ __device__ __forceinline__ float rk_store_narrow(T *p, float qn, float qs, float
     T h = NR::rn(v);
     float hv = NR::f(h);
     float r = v - hv;  // exact: v and hv are within a factor 2
-    unsigned bits = __float_as_uint(hv);
-    // half the spacing of the format at hv (half of that below a power of two)
-    float hu = fmaxf(__uint_as_float((bits & 0x7F800000u) - (unsigned)((NR::M + 1) << 23)), NR::tiny);
-    bool pow2 = (bits & 0x7FFFFFu) == 0u;
-    float hb = (pow2 && r * hv < 0.f) ? 0.5f * hu : hu;
+    // a lower bound on the distance from hv to the rounding boundaries on
+    // either side: |hv| 2^-(M+2) is at most half the format's spacing at hv,
+    // and at most half the (halved) spacing just below a power of two
+    float hb = fmaxf(fabsf(hv) * (1.0f / float(1 << (NR::M + 2))), NR::tiny);
     if (!(fabsf(r) + e < hb)) h = rk_fp64<T>(qn, qs, L, dt, w);
     *p = h;
     return NR::f(h);
@@ -976,8 +975,8 @@ __global__ void __maxnreg__(FLUX_MAXREG)
                         C qsv = Q[2][u];
                         C qb = mode == FLUX_STAGE1 ? qsv : cv(qnv[u]);
                         o[u] = rk_store(out + u * g.n + c, qb, qsv, Lv[u], dt32, dt, w32, wd);
-                        bad |= !isfinite(o[u]);
                     }
+                    bad |= !isfinite((o[0] + o[1]) + (o[2] + o[3]) + o[4]);
                     if (mode == FLUX_STAGE3)
                         smax = nanmax(smax, double(cell_speed(o[0], o[1], o[2], o[3], o[4], gamma, gm1)));
                 }
