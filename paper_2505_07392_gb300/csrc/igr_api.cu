@@ -192,6 +192,7 @@ const char *igr::validate_config(const igr_config *c)
     if (!c) return "cfg is NULL";
     if (c->nx < 4 || c->ny < 4 || c->nz < 4) return "nx, ny, nz must each be >= 4";
     if ((long long)c->nx * c->ny > (1ll << 31) - 1) return "nx*ny must fit in a 32-bit int";
+    if ((long long)c->nx * c->ny * c->nz >= (1ll << 32)) return "the grid must have fewer than 2^32 cells";
     if (!(c->dx > 0) || !(c->gamma > 1) || !(c->alpha >= 0) || !(c->cfl > 0) || isinf(c->dx))
         return "need dx > 0, gamma > 1, alpha >= 0, cfl > 0";
     if (c->sweeps < 1) return "sweeps must be >= 1";

@@ -48,6 +48,13 @@ template <> struct Num<__nv_bfloat16> { using C = float; using A = double; };
 using C = Num<S>::C;
 using A = Num<S>::A;
 
+// Offsets inside one field are 32-bit (grids hold fewer than 2^32 cells);
+// each field has its own base pointer, so an address is one 32x32->64 step.
+using idx = unsigned;
+template <int N> struct Fin { const S *p[N]; };   // fields read
+template <int N> struct Fout { S *p[N]; };        // fields written
+struct Frhs { C *p[5]; };
+
 // ------------------------------------------------------------ load/store
 __device__ __forceinline__ double ldc(const double *p) { return __ldg(p); }
 __device__ __forceinline__ float ldc(const float *p) { return __ldg(p); }
@@ -239,9 +246,10 @@ __device__ __noinline__ T rk_fp64(float qn, float qs, float L, double dt, double
     return Narrow<T>::rn(vd);
 }
 
+// FP32 evaluation and rounding; ok = false when the rounding could differ
+// from the FP64 evaluation's
 template <typename T>
-__device__ __forceinline__ float rk_store_narrow(T *p, float qn, float qs, float L, float dt32,
-                                                 double dt, float w32, double w)
+__device__ __forceinline__ T rk_narrow_fast(float qn, float qs, float L, float dt32, float w32, bool &ok)
 {
     using NR = Narrow<T>;
     float d = __fsub_rn(qs, qn);
@@ -255,20 +263,36 @@ __device__ __forceinline__ float rk_store_narrow(T *p, float qn, float qs, float
     // either side: |hv| 2^-(M+2) is at most half the format's spacing at hv,
     // and at most half the (halved) spacing just below a power of two
     float hb = fmaxf(fabsf(hv) * (1.0f / float(1 << (NR::M + 2))), NR::tiny);
-    if (!(fabsf(r) + e < hb)) h = rk_fp64<T>(qn, qs, L, dt, w);
-    *p = h;
-    return NR::f(h);
+    ok = fabsf(r) + e < hb;
+    return h;
 }
 
 constexpr bool kNarrow = sizeof(S) == 2;
 
-// stage combination for one value; returns the stored value in type C
-__device__ __forceinline__ C rk_store(S *p, C qn, C qs, C L, C dt32, double dt, C w32, double w)
+// Stage combination of the five conserved values of one cell, stored at
+// offset c of each output field; returns the stored values in type C. In the
+// 16-bit modes one branch per cell covers the rare FP64 re-evaluations.
+__device__ __forceinline__ void rk_store5(const Fout<5> &out, idx c, const C qn[5], const C qs[5],
+                                          const C L[5], C dt32, double dt, C w32, double w, C o[5])
 {
     if constexpr (kNarrow) {
-        return rk_store_narrow<S>(p, qn, qs, L, dt32, dt, w32, w);
+        S h[5];
+        bool ok[5];
+#pragma unroll
+        for (int u = 0; u < 5; u++) h[u] = rk_narrow_fast<S>(qn[u], qs[u], L[u], dt32, w32, ok[u]);
+        if (!(ok[0] && ok[1] && ok[2] && ok[3] && ok[4])) {
+#pragma unroll
+            for (int u = 0; u < 5; u++)
+                if (!ok[u]) h[u] = rk_fp64<S>(qn[u], qs[u], L[u], dt, w);
+        }
+#pragma unroll
+        for (int u = 0; u < 5; u++) {
+            out.p[u][c] = h[u];
+            o[u] = cv(h[u]);
+        }
     } else {
-        return stc(p, qn + w32 * ((qs - qn) + dt32 * L));
+#pragma unroll
+        for (int u = 0; u < 5; u++) o[u] = stc(out.p[u] + c, qn[u] + w32 * ((qs[u] - qn[u]) + dt32 * L[u]));
     }
 }
 
@@ -294,20 +318,20 @@ __device__ __forceinline__ int zmap(int kk, const Geom &g)
                   : (kk >= g.nz ? (g.bc[5] == BC_PERIODIC ? kk - g.nz : g.nz - 1) : kk);
 }
 
-// u = m / rho of the cell at in-plane offset c of plane kk (kk may leave the
+// u = m / rho of the cell at in-plane offset f of plane kk (kk may leave the
 // domain through -z/+z: periodic wrap, zero-gradient clamp or the jet blend)
-__device__ __forceinline__ void col_u(const S *__restrict__ q, const Geom &g, const C *W,
-                                      const C *J, int f, int kk, C u[3])
+__device__ __forceinline__ void col_u(const Fin<4> &q, const Geom &g, const C *W, const C *J, idx f,
+                                      int kk, C u[3])
 {
-    int km = map_axis(kk, g.nz, g.bc[4], g.bc[5]);
-    long long c = km * g.plane + f;
-    C rho = ldc(q + c), m0 = ldc(q + g.n + c), m1 = ldc(q + 2 * g.n + c), m2 = ldc(q + 3 * g.n + c);
+    idx c = (idx)map_axis(kk, g.nz, g.bc[4], g.bc[5]) * (idx)g.plane + f;
+    C rho = ldc(q.p[0] + c), m0 = ldc(q.p[1] + c), m1 = ldc(q.p[2] + c), m2 = ldc(q.p[3] + c);
     if (kk < 0 && g.bc[4] == BC_INFLOW) {
+        idx pl = (idx)g.plane;
         C w = C(1) - W[f];
         rho = w * rho + J[f];
-        m0 = w * m0 + J[g.plane + f];
-        m1 = w * m1 + J[2 * g.plane + f];
-        m2 = w * m2 + J[3 * g.plane + f];
+        m0 = w * m0 + J[pl + f];
+        m1 = w * m1 + J[2 * pl + f];
+        m2 = w * m2 + J[3 * pl + f];
     }
     // products rounded before they are differenced: equal neighbours give an exact 0
     C r = rcp(rho);
@@ -318,8 +342,8 @@ __device__ __forceinline__ void col_u(const S *__restrict__ q, const Geom &g, co
 
 // grad u by central differences from a shared plane tile U (x, y) and the
 // column's registers (z); b = alpha [tr(G^2) + tr(G)^2]
-__global__ void __launch_bounds__(BT) k_source(const S *__restrict__ q, S *__restrict__ b, Geom g,
-                                                C alpha, C inv2dx, const C *W, const C *J, int zc)
+__global__ void __launch_bounds__(BT) k_source(Fin<4> q, S *__restrict__ b, Geom g, C alpha,
+                                                C inv2dx, const C *W, const C *J, int zc)
 {
     __shared__ C U[3][HY][HX];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
@@ -327,17 +351,19 @@ __global__ void __launch_bounds__(BT) k_source(const S *__restrict__ q, S *__res
     const int i = x0 + tx, j = y0 + ty;
     const bool active = i < g.nx && j < g.ny;
     const int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
+    const idx pl = (idx)g.plane;
     // the own slot of the tile holds the mapped cell (it is a neighbour of
     // active cells even when this thread is outside the domain)
-    const int f = map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx + map_axis(i, g.nx, g.bc[0], g.bc[1]);
+    const idx f = (idx)(map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx + map_axis(i, g.nx, g.bc[0], g.bc[1]));
     const bool hv = tid < NHALO1;
-    int hs = 0, hf = 0;
+    int hs = 0;
+    idx hf = 0;
     if (hv) {
         int lx, ly;
         halo1_cell(tid, lx, ly);
         hs = ly * HX + lx;
-        hf = map_axis(y0 + ly - 1, g.ny, g.bc[2], g.bc[3]) * g.nx +
-             map_axis(x0 + lx - 1, g.nx, g.bc[0], g.bc[1]);
+        hf = (idx)(map_axis(y0 + ly - 1, g.ny, g.bc[2], g.bc[3]) * g.nx +
+                   map_axis(x0 + lx - 1, g.nx, g.bc[0], g.bc[1]));
     }
     C um[3], u0[3], up[3];
     col_u(q, g, W, J, f, k0 - 1, um);
@@ -345,10 +371,10 @@ __global__ void __launch_bounds__(BT) k_source(const S *__restrict__ q, S *__res
     // raw values one iteration ahead (loads overlap the previous plane's work):
     // the column at k + 1 and the halo at k (planes >= 0 need no jet blend)
     S nc[4], nh[4];
-    auto raw4 = [&](int off, int kk, S v[4]) {
-        long long c = zmap(kk, g) * g.plane + off;
+    auto raw4 = [&](idx off, int kk, S v[4]) {
+        idx c = (idx)zmap(kk, g) * pl + off;
 #pragma unroll
-        for (int a = 0; a < 4; a++) v[a] = ldr(q + a * g.n + c);
+        for (int a = 0; a < 4; a++) v[a] = ldr(q.p[a] + c);
     };
     raw4(f, k0 + 1, nc);
     if (hv) raw4(hf, k0, nh);
@@ -384,7 +410,7 @@ __global__ void __launch_bounds__(BT) k_source(const S *__restrict__ q, S *__res
             C tr = G[0][0] + G[1][1] + G[2][2];
             C tr2 = G[0][0] * G[0][0] + G[1][1] * G[1][1] + G[2][2] * G[2][2] +
                     C(2) * (G[0][1] * G[1][0] + G[0][2] * G[2][0] + G[1][2] * G[2][1]);
-            stc(b + k * g.plane + (long long)j * g.nx + i, alpha * (tr2 + tr * tr));
+            stc(b + (idx)k * pl + (idx)(j * g.nx + i), alpha * (tr2 + tr * tr));
         }
 #pragma unroll
         for (int a = 0; a < 3; a++) {
@@ -410,15 +436,17 @@ __global__ void __launch_bounds__(BT) k_jacobi(const S *__restrict__ q, const S 
     const int i = x0 + tx, j = y0 + ty;
     const bool active = i < g.nx && j < g.ny;
     const int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
-    const int f = map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx + map_axis(i, g.nx, g.bc[0], g.bc[1]);
+    const idx pl = (idx)g.plane;
+    const idx f = (idx)(map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx + map_axis(i, g.nx, g.bc[0], g.bc[1]));
     const bool hv = tid < NHALO1;
-    int hs = 0, hf = 0;
+    int hs = 0;
+    idx hf = 0;
     if (hv) {
         int lx, ly;
         halo1_cell(tid, lx, ly);
         hs = ly * HX + lx;
-        hf = map_axis(y0 + ly - 1, g.ny, g.bc[2], g.bc[3]) * g.nx +
-             map_axis(x0 + lx - 1, g.nx, g.bc[0], g.bc[1]);
+        hf = (idx)(map_axis(y0 + ly - 1, g.ny, g.bc[2], g.bc[3]) * g.nx +
+                   map_axis(x0 + lx - 1, g.nx, g.bc[0], g.bc[1]));
     }
     const C hb = C(0.5) * beta;
     // a face term exists unless the face is a non-periodic domain boundary
@@ -428,25 +456,25 @@ __global__ void __launch_bounds__(BT) k_jacobi(const S *__restrict__ q, const S 
     const C eyp = (j < g.ny - 1 || g.bc[3] == BC_PERIODIC) ? hb : C(0);
     C rm, sm, r0, s0, rp, sp;
     {
-        long long c = zmap(k0 - 1, g) * g.plane + f;
+        idx c = (idx)zmap(k0 - 1, g) * pl + f;
         rm = rcp(ldc(q + c));
         sm = ldc(sin + c);
-        c = (long long)k0 * g.plane + f;
+        c = (idx)k0 * pl + f;
         r0 = rcp(ldc(q + c));
         s0 = ldc(sin + c);
     }
     // raw values one iteration ahead: column at k + 1, halo and b at k
     S ncr, ncs, nhr = S(1.0f), nhs = S(0.0f), nb;
     auto pre = [&](int kk) {
-        long long c = zmap(kk + 1, g) * g.plane + f;
+        idx c = (idx)zmap(kk + 1, g) * pl + f;
         ncr = ldr(q + c);
         ncs = ldr(sin + c);
         if (hv) {
-            long long h = (long long)kk * g.plane + hf;
+            idx h = (idx)kk * pl + hf;
             nhr = ldr(q + h);
             nhs = ldr(sin + h);
         }
-        nb = ldr(b + (long long)kk * g.plane + f);
+        nb = ldr(b + (idx)kk * pl + f);
     };
     pre(k0);
     for (int k = k0; k < k1; k++) {
@@ -475,7 +503,7 @@ __global__ void __launch_bounds__(BT) k_jacobi(const S *__restrict__ q, const S 
             C diag = r0 + c0 + c1 + c2 + c3 + c4 + c5;
             C off = c0 * SG[ty + 1][tx] + c1 * SG[ty + 1][tx + 2] + c2 * SG[ty][tx + 1] +
                     c3 * SG[ty + 2][tx + 1] + c4 * sm + c5 * sp;
-            stc(sout + k * g.plane + (long long)j * g.nx + i, div_c(bv + off, diag));
+            stc(sout + (idx)k * pl + (idx)(j * g.nx + i), div_c(bv + off, diag));
         }
         rm = r0; sm = s0;
         r0 = rp; s0 = sp;
@@ -598,17 +626,39 @@ __device__ __forceinline__ Vec4<__nv_bfloat16> pack4(__nv_bfloat16 a, __nv_bfloa
 }
 
 constexpr int VX = 4, TXV = BX * VX;        // 128 cells per tile row
+
+// 4 consecutive values of a 16-byte aligned shared row (one 128-bit access
+// for FP32, two for FP64; scalar accesses at stride 4 would conflict 4-way)
+__device__ __forceinline__ void sh_st4(float *p, const float v[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void sh_st4(double *p, const double v[4])
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void sh_ld4(const float *p, float v[4])
+{
+    float4 a = *reinterpret_cast<const float4 *>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void sh_ld4(const double *p, double v[4])
+{
+    double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
 constexpr int HXV = TXV + 2 * VX;           // interior at column VX (16-byte aligned)
 constexpr int NYH = 2 * BX, NXH = 2 * BY;   // 4-wide y-halo tasks, scalar x-halo tasks
 
 // 4 raw values of field a at cells (x .. x+3) of row-plane offset rowoff:
 // one 4-wide load when the cells lie inside the row, mapped single loads otherwise
-__device__ __forceinline__ V4 ld4_mapped(const S *__restrict__ a, const Geom &g, long long rowoff, int x)
+__device__ __forceinline__ V4 ld4_mapped(const S *__restrict__ a, const Geom &g, idx rowoff, int x)
 {
     if (x + VX <= g.nx) return ld4r(a + rowoff + x);
     S v[VX];
 #pragma unroll
-    for (int c = 0; c < VX; c++) v[c] = ldr(a + rowoff + map_axis(x + c, g.nx, g.bc[0], g.bc[1]));
+    for (int c = 0; c < VX; c++) v[c] = ldr(a + rowoff + (idx)map_axis(x + c, g.nx, g.bc[0], g.bc[1]));
     return pack4(v[0], v[1], v[2], v[3]);
 }
 
@@ -623,24 +673,25 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : 2) k_jacobi_v4(const 
     const int i0 = x0 + VX * tx, j = y0 + ty;
     const bool active = i0 < g.nx && j < g.ny;
     const int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
-    const long long rowj = (long long)map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx;
+    const idx pl = (idx)g.plane;
+    const idx rowj = (idx)(map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx);
     // halo tasks: 4-wide cells of the rows above/below the tile, then single
     // cells left/right of each row
     int htask = tid < NYH ? 0 : (tid < NYH + NXH ? 1 : 2);
     int hsy = 0, hsx = 0, hx = 0;
-    long long hrow = 0;
+    idx hrow = 0;
     if (htask == 0) {
         int side = tid / BX, t = tid % BX;
         hsy = side ? HY - 1 : 0;
         hsx = VX + VX * t;
         hx = x0 + VX * t;
-        hrow = (long long)map_axis(y0 + (side ? BY : -1), g.ny, g.bc[2], g.bc[3]) * g.nx;
+        hrow = (idx)(map_axis(y0 + (side ? BY : -1), g.ny, g.bc[2], g.bc[3]) * g.nx);
     } else if (htask == 1) {
         int e = tid - NYH, side = e / BY, r = e % BY;
         hsy = 1 + r;
         hsx = side ? VX + TXV : VX - 1;
         hx = map_axis(side ? x0 + TXV : x0 - 1, g.nx, g.bc[0], g.bc[1]);
-        hrow = (long long)map_axis(y0 + r, g.ny, g.bc[2], g.bc[3]) * g.nx;
+        hrow = (idx)(map_axis(y0 + r, g.ny, g.bc[2], g.bc[3]) * g.nx);
     }
     const C hb = C(0.5) * beta;
     const C exm = (i0 > 0 || g.bc[0] == BC_PERIODIC) ? hb : C(0);
@@ -651,12 +702,12 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : 2) k_jacobi_v4(const 
     C rm[VX], sm[VX], r0[VX], s0[VX], rp[VX], sp[VX];
     {
         C t[VX];
-        cv4(ld4_mapped(q, g, zmap(k0 - 1, g) * g.plane + rowj, i0), t);
-        cv4(ld4_mapped(sin, g, zmap(k0 - 1, g) * g.plane + rowj, i0), sm);
+        cv4(ld4_mapped(q, g, (idx)zmap(k0 - 1, g) * pl + rowj, i0), t);
+        cv4(ld4_mapped(sin, g, (idx)zmap(k0 - 1, g) * pl + rowj, i0), sm);
 #pragma unroll
         for (int c = 0; c < VX; c++) rm[c] = rcp(t[c]);
-        cv4(ld4_mapped(q, g, (long long)k0 * g.plane + rowj, i0), t);
-        cv4(ld4_mapped(sin, g, (long long)k0 * g.plane + rowj, i0), s0);
+        cv4(ld4_mapped(q, g, (idx)k0 * pl + rowj, i0), t);
+        cv4(ld4_mapped(sin, g, (idx)k0 * pl + rowj, i0), s0);
 #pragma unroll
         for (int c = 0; c < VX; c++) r0[c] = rcp(t[c]);
     }
@@ -664,16 +715,16 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : 2) k_jacobi_v4(const 
     V4 ncr, ncs, nb, nhr, nhs;
     S nxr = S(1.0f), nxs = S(0.0f);
     auto pre = [&](int kk) {
-        long long pz = zmap(kk + 1, g) * g.plane + rowj;
+        idx pz = (idx)zmap(kk + 1, g) * pl + rowj;
         ncr = ld4_mapped(q, g, pz, i0);
         ncs = ld4_mapped(sin, g, pz, i0);
-        if (active) nb = ld4r(b + (long long)kk * g.plane + rowj + i0);
+        if (active) nb = ld4r(b + (idx)kk * pl + rowj + (idx)i0);
         if (htask == 0) {
-            nhr = ld4_mapped(q, g, (long long)kk * g.plane + hrow, hx);
-            nhs = ld4_mapped(sin, g, (long long)kk * g.plane + hrow, hx);
+            nhr = ld4_mapped(q, g, (idx)kk * pl + hrow, hx);
+            nhs = ld4_mapped(sin, g, (idx)kk * pl + hrow, hx);
         } else if (htask == 1) {
-            nxr = ldr(q + (long long)kk * g.plane + hrow + hx);
-            nxs = ldr(sin + (long long)kk * g.plane + hrow + hx);
+            nxr = ldr(q + (idx)kk * pl + hrow + hx);
+            nxs = ldr(sin + (idx)kk * pl + hrow + hx);
         }
     };
     pre(k0);
@@ -695,17 +746,11 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : 2) k_jacobi_v4(const 
         }
         if (k + 1 < k1) pre(k + 1);
         __syncthreads();
-#pragma unroll
-        for (int c = 0; c < VX; c++) {
-            R[ty + 1][VX + VX * tx + c] = r0[c];
-            SG[ty + 1][VX + VX * tx + c] = s0[c];
-        }
+        sh_st4(&R[ty + 1][VX + VX * tx], r0);
+        sh_st4(&SG[ty + 1][VX + VX * tx], s0);
         if (htask == 0) {
-#pragma unroll
-            for (int c = 0; c < VX; c++) {
-                R[hsy][hsx + c] = hr[c];
-                SG[hsy][hsx + c] = hsg[c];
-            }
+            sh_st4(&R[hsy][hsx], hr);
+            sh_st4(&SG[hsy][hsx], hsg);
         } else if (htask == 1) {
             R[hsy][hsx] = hr[0];
             SG[hsy][hsx] = hsg[0];
@@ -716,13 +761,10 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : 2) k_jacobi_v4(const 
             const C ezp = (k < g.nz - 1 || g.bc[5] == BC_PERIODIC) ? hb : C(0);
             const int col = VX + VX * tx;
             C ry0[VX], ry1[VX], sy0[VX], sy1[VX], o[VX];
-#pragma unroll
-            for (int c = 0; c < VX; c++) {
-                ry0[c] = R[ty][col + c];
-                ry1[c] = R[ty + 2][col + c];
-                sy0[c] = SG[ty][col + c];
-                sy1[c] = SG[ty + 2][col + c];
-            }
+            sh_ld4(&R[ty][col], ry0);
+            sh_ld4(&R[ty + 2][col], ry1);
+            sh_ld4(&SG[ty][col], sy0);
+            sh_ld4(&SG[ty + 2][col], sy1);
 #pragma unroll
             for (int c = 0; c < VX; c++) {
                 C rxm = c > 0 ? r0[c - 1] : R[ty + 1][col - 1];
@@ -740,7 +782,7 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : 2) k_jacobi_v4(const 
                 C off = c0 * sxm + c1 * sxp + c2 * sy0[c] + c3 * sy1[c] + c4 * sm[c] + c5 * sp[c];
                 o[c] = div_c(bv[c] + off, diag);
             }
-            st4(sout + (long long)k * g.plane + (long long)j * g.nx + i0, o);
+            st4(sout + (idx)k * pl + (idx)(j * g.nx + i0), o);
         }
 #pragma unroll
         for (int c = 0; c < VX; c++) {
@@ -780,19 +822,16 @@ __device__ __forceinline__ void plane_cell(int e, int &lx, int &ly)
 
 // one column value set (rho, mx, my, mz, E, Sigma) at in-plane offset f of
 // plane kk, with the -z jet blend for kk < 0
-__device__ __forceinline__ void col_load(const S *__restrict__ qs, const S *__restrict__ sig,
-                                         const Geom &g, const C *W, const C *J, int f, int kk,
-                                         C v[6])
+__device__ __forceinline__ void col_load(const Fin<6> &in, const Geom &g, const C *W, const C *J,
+                                         idx f, int kk, C v[6])
 {
-    int km = map_axis(kk, g.nz, g.bc[4], g.bc[5]);
-    long long c = km * g.plane + f;
+    idx c = (idx)map_axis(kk, g.nz, g.bc[4], g.bc[5]) * (idx)g.plane + f;
 #pragma unroll
-    for (int u = 0; u < 5; u++) v[u] = ldc(qs + u * g.n + c);
-    v[5] = ldc(sig + c);
+    for (int u = 0; u < 6; u++) v[u] = ldc(in.p[u] + c);
     if (kk < 0 && g.bc[4] == BC_INFLOW) {
         C w = C(1) - W[f];
 #pragma unroll
-        for (int u = 0; u < 5; u++) v[u] = w * v[u] + J[u * g.plane + f];
+        for (int u = 0; u < 5; u++) v[u] = w * v[u] + J[(idx)u * (idx)g.plane + f];
     }
 }
 
@@ -828,9 +867,8 @@ constexpr int FLUX_MAXREG = sizeof(C) == 8 ? 224 : 128;
 
 template <int mode>
 __global__ void __maxnreg__(FLUX_MAXREG)
-    k_flux(const S *__restrict__ qs, const S *__restrict__ sig, const S *qn, S *out, C *rhs,
-           Geom g, C gamma, C half_inv_dx, const Scalars *sc, double *blockmax, int *err,
-           const C *W, const C *J, int zc)
+    k_flux(Fin<6> in, Fin<5> qn, Fout<5> out, Frhs rhs, Geom g, C gamma, C half_inv_dx,
+           const Scalars *sc, double *blockmax, int *err, const C *W, const C *J, int zc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *P = reinterpret_cast<C *>(smem_raw);  // [6][PH][PW]
@@ -842,12 +880,14 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     const bool rowwarp = w < TY;  // warp-uniform
     const int i = x0 + lane, j = y0 + (rowwarp ? w : 0);
     const bool active = rowwarp && i < g.nx && j < g.ny;
-    const int fcol = map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx + map_axis(i, g.nx, g.bc[0], g.bc[1]);
+    const idx pl = (idx)g.plane;
+    const idx fcol = (idx)(map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx + map_axis(i, g.nx, g.bc[0], g.bc[1]));
     const C gm1 = gamma - C(1);
     bool bad = false;
 
     // tile cells this thread loads each plane: shared and in-plane offsets
-    int soff[LPT], goff[LPT];
+    int soff[LPT];
+    idx goff[LPT];
 #pragma unroll
     for (int r = 0; r < LPT; r++) {
         int e = tid + r * NT;
@@ -857,8 +897,8 @@ __global__ void __maxnreg__(FLUX_MAXREG)
             int lx, ly;
             plane_cell(e, lx, ly);
             soff[r] = ly * PW + lx;
-            goff[r] = map_axis(y0 + ly - 3, g.ny, g.bc[2], g.bc[3]) * g.nx +
-                      map_axis(x0 + lx - 3, g.nx, g.bc[0], g.bc[1]);
+            goff[r] = (idx)(map_axis(y0 + ly - 3, g.ny, g.bc[2], g.bc[3]) * g.nx +
+                            map_axis(x0 + lx - 3, g.nx, g.bc[0], g.bc[1]));
         }
     }
     S Rg[LPT][6];  // prefetched tile cells of the next plane (raw)
@@ -866,10 +906,9 @@ __global__ void __maxnreg__(FLUX_MAXREG)
 #pragma unroll
         for (int r = 0; r < LPT; r++)
             if (soff[r] >= 0) {
-                long long c = kk * g.plane + goff[r];
+                idx c = (idx)kk * pl + goff[r];
 #pragma unroll
-                for (int u = 0; u < 5; u++) Rg[r][u] = ldr(qs + u * g.n + c);
-                Rg[r][5] = ldr(sig + c);
+                for (int u = 0; u < 6; u++) Rg[r][u] = ldr(in.p[u] + c);
             }
     };
     auto commit = [&]() {
@@ -888,7 +927,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
         dt32 = C(dt);
         w32 = C(wd);
     }
-    double smax = 0.0;
+    C smax = C(0);  // running wave-speed maximum (FP32 here: FP64 is slow on this GPU)
 
     // Register queue of the column's z-stencil: at iteration k the slots hold
     // planes k-2..k+3 and give the z-face k + 1/2. The loop starts one plane
@@ -899,14 +938,13 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     C Q[6][6];
     S Qn[6];
     auto col_raw = [&](int kk) {
-        long long c = zmap(kk, g) * g.plane + fcol;
+        idx c = (idx)zmap(kk, g) * pl + fcol;
 #pragma unroll
-        for (int u = 0; u < 5; u++) Qn[u] = ldr(qs + u * g.n + c);
-        Qn[5] = ldr(sig + c);
+        for (int u = 0; u < 6; u++) Qn[u] = ldr(in.p[u] + c);
     };
     if (rowwarp) {
 #pragma unroll
-        for (int s = 1; s < 6; s++) col_load(qs, sig, g, W, J, fcol, k0 - 4 + s, Q[s]);
+        for (int s = 1; s < 6; s++) col_load(in, g, W, J, fcol, k0 - 4 + s, Q[s]);
         col_raw(k0 + 2);
     }
     fetch(k0);
@@ -915,9 +953,9 @@ __global__ void __maxnreg__(FLUX_MAXREG)
         if (k >= k0 && k + 1 < k1) fetch(k + 1);
         S qnv[5];
         if (k >= k0 && active && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3)) {
-            long long c = k * g.plane + (long long)j * g.nx + i;
+            idx c = (idx)k * pl + (idx)(j * g.nx + i);
 #pragma unroll
-            for (int u = 0; u < 5; u++) qnv[u] = ldr(qn + u * g.n + c);
+            for (int u = 0; u < 5; u++) qnv[u] = ldr(qn.p[u] + c);
         }
         C Fzp[5];
         if (rowwarp) {
@@ -956,7 +994,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
             }
             __syncthreads();  // faces complete; reads of P done
             if (active) {
-                long long c = k * g.plane + (long long)j * g.nx + i;
+                idx c = (idx)k * pl + (idx)(j * g.nx + i);
                 C Lv[5];
 #pragma unroll
                 for (int u = 0; u < 5; u++) {
@@ -967,18 +1005,20 @@ __global__ void __maxnreg__(FLUX_MAXREG)
                 }
                 if (mode == FLUX_RHS) {
 #pragma unroll
-                    for (int u = 0; u < 5; u++) rhs[u * g.n + c] = Lv[u];
+                    for (int u = 0; u < 5; u++) rhs.p[u][c] = Lv[u];
                 } else {
-                    C o[5];
+                    C o[5], qb[5], qsv[5];
 #pragma unroll
                     for (int u = 0; u < 5; u++) {
-                        C qsv = Q[2][u];
-                        C qb = mode == FLUX_STAGE1 ? qsv : cv(qnv[u]);
-                        o[u] = rk_store(out + u * g.n + c, qb, qsv, Lv[u], dt32, dt, w32, wd);
+                        qsv[u] = Q[2][u];
+                        qb[u] = mode == FLUX_STAGE1 ? qsv[u] : cv(qnv[u]);
                     }
+                    rk_store5(out, c, qb, qsv, Lv, dt32, dt, w32, wd, o);
                     bad |= !isfinite((o[0] + o[1]) + (o[2] + o[3]) + o[4]);
-                    if (mode == FLUX_STAGE3)
-                        smax = nanmax(smax, double(cell_speed(o[0], o[1], o[2], o[3], o[4], gamma, gm1)));
+                    if (mode == FLUX_STAGE3) {
+                        C sp = cell_speed(o[0], o[1], o[2], o[3], o[4], gamma, gm1);
+                        smax = (sp > smax || sp != sp) ? sp : smax;
+                    }
                 }
             }
         }
@@ -991,7 +1031,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     }
     if (bad) atomicOr(err, 1);
     if (mode == FLUX_STAGE3) {
-        double m = block_max<NT>(smax);
+        double m = block_max<NT>(double(smax));
         if (tid == 0)
             blockmax[(blockIdx.z * (long long)gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = m;
     }
@@ -1004,8 +1044,17 @@ __global__ void k_rk_combine(const S *__restrict__ qn, const S *__restrict__ qs,
 {
     C dt32 = C(dt), w32 = C(wd);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-         c += (long long)gridDim.x * blockDim.x)
-        rk_store(out + c, ldc(qn + c), ldc(qs + c), L[c], dt32, dt, w32, wd);
+         c += (long long)gridDim.x * blockDim.x) {
+        C a = ldc(qn + c), b = ldc(qs + c), l = L[c];
+        if constexpr (kNarrow) {
+            bool ok;
+            S h = rk_narrow_fast<S>(a, b, l, dt32, w32, ok);
+            if (!ok) h = rk_fp64<S>(a, b, l, dt, wd);
+            out[c] = h;
+        } else {
+            out[c] = a + w32 * ((b - a) + dt32 * l);
+        }
+    }
 }
 
 // ---------------------------------------------------------- wave speed
@@ -1030,12 +1079,19 @@ dim3 grid_of(const Geom &g, int bx, int by, int zc)
     return dim3((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, (g.nz + zc - 1) / zc);
 }
 
+template <int N> Fin<N> fields_in(const void *base, long long n)
+{
+    Fin<N> f;
+    for (int u = 0; u < N; u++) f.p[u] = base ? (const S *)base + u * n : nullptr;
+    return f;
+}
+
 cudaError_t launch_source(const Geom &g, const Phys &p, const Tiles &t, const Inflow &in,
                           const void *q, void *b, cudaStream_t st)
 {
     k_source<<<grid_of(g, BX, BY, t.zc_source), dim3(BX, BY), 0, st>>>(
-        (const S *)q, (S *)b, g, C(p.alpha), C(0.5 / p.dx), (const C *)in.W, (const C *)in.J,
-        t.zc_source);
+        fields_in<4>(q, g.n), (S *)b, g, C(p.alpha), C(0.5 / p.dx), (const C *)in.W,
+        (const C *)in.J, t.zc_source);
     return cudaGetLastError();
 }
 
@@ -1068,9 +1124,17 @@ cudaError_t launch_flux(const Geom &g, const Phys &p, const Tiles &t, const Infl
     auto go = [&](auto kern) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        Fin<6> fi = fields_in<6>(qs, g.n);
+        fi.p[5] = (const S *)sig;
+        Fout<5> fo;
+        Frhs fr;
+        for (int u = 0; u < 5; u++) {
+            fo.p[u] = out ? (S *)out + u * g.n : nullptr;
+            fr.p[u] = rhs ? (C *)rhs + u * g.n : nullptr;
+        }
         kern<<<grid_of(g, TX, TY, t.zc_flux), NT, smem, st>>>(
-            (const S *)qs, (const S *)sig, (const S *)qn, (S *)out, (C *)rhs, g, C(p.gamma),
-            C(0.5 / p.dx), sc, blockmax, err, (const C *)in.W, (const C *)in.J, t.zc_flux);
+            fi, fields_in<5>(qn, g.n), fo, fr, g, C(p.gamma), C(0.5 / p.dx), sc, blockmax, err,
+            (const C *)in.W, (const C *)in.J, t.zc_flux);
         e = cudaGetLastError();
         if (e != cudaSuccess) {
             cudaFuncAttributes fa;
