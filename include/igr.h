@@ -204,6 +204,39 @@ igr_status igr_sync(igr_ctx *ctx);
 igr_status igr_profile_enable(igr_ctx *ctx, int on);
 igr_status igr_profile_read(igr_ctx *ctx, int kernel_class, long long *launches, double *total_ms);
 
+/* ---- Launch shapes and the autotuner ----------------------------------
+ * Each kernel class marches blocks up chunks of z-planes; the chunk length
+ * is the tunable launch shape (>= 4 planes, at most nz). Results do not
+ * depend on it: every face flux comes out of the same instructions whatever
+ * the chunking, and there are no atomics, so outputs are bitwise identical
+ * for every choice. igr_autotune times each class on the current state for
+ * the candidate lengths 4..128 (reps launches each, on the context stream;
+ * only scratch buffers are written) and keeps the fastest; call it after
+ * igr_set_state. It synchronises. */
+igr_status igr_set_tiles(igr_ctx *ctx, int zc_source, int zc_jacobi, int zc_flux);
+igr_status igr_get_tiles(igr_ctx *ctx, int *zc_source, int *zc_jacobi, int *zc_flux);
+igr_status igr_autotune(igr_ctx *ctx, int reps);
+
+/* ---- Batches of independent instances -----------------------------------
+ * n independent contexts (any sizes and configurations) advanced together.
+ * igr_create_batch creates one context per config, each on its own stream
+ * forked from and joined into cuda_stream. igr_batch_instance(b, i) gives
+ * instance i's context for igr_set_state / igr_get_state / igr_autotune /
+ * igr_get_dt (not for igr_step: step the batch). igr_step_batch advances
+ * every instance by nsteps SSP-RK3 steps, each with its own CFL dt; a step
+ * is captured once as a CUDA graph (one branch per instance, so instances
+ * progress independently) and replayed, except the first step after a
+ * set_state, which launches directly. Asynchronous on cuda_stream;
+ * igr_sync_batch synchronises and reports any instance's error. */
+typedef struct igr_batch igr_batch;
+igr_status igr_create_batch(const igr_config *cfgs, int n, const igr_allocator *allocator,
+                            void *cuda_stream, igr_batch **out);
+igr_ctx *igr_batch_instance(igr_batch *b, int i);
+igr_status igr_step_batch(igr_batch *b, int nsteps);
+igr_status igr_sync_batch(igr_batch *b);
+const char *igr_batch_last_error(const igr_batch *b);
+igr_status igr_destroy_batch(igr_batch *b);
+
 /* Message of the last failure on ctx (or of the last failed igr_create when
  * ctx is NULL). Never NULL. */
 const char *igr_last_error(const igr_ctx *ctx);

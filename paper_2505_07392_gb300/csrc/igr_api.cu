@@ -58,6 +58,9 @@ struct igr_ctx {
 
 static char g_create_err[512] = "";
 
+// smallest z-chunk (planes per block) a launch may use
+static constexpr int kMinZChunk = 4;
+
 static igr_status fail(igr_ctx *c, igr_status s, const char *fmt, ...)
 {
     char *buf = c ? c->err : g_create_err;
@@ -232,6 +235,7 @@ static Layout layout_of(const igr_config *c)
     L.b = L.sig;
     L.W = (size_t)g.plane * o->compute_bytes;
     L.J = 5 * L.W;
+    t.zc_flux = kMinZChunk;  // the tuner may pick chunks down to kMinZChunk planes
     long long fb = o->flux_blocks(g, t);
     L.blockmax = (size_t)(fb > 4096 ? fb : 4096) * sizeof(double);
     L.scalars = 2 * sizeof(Scalars);  // [0] stepping, [1] igr_get_dt
@@ -671,6 +675,272 @@ igr_status igr_profile_read(igr_ctx *c, int kc, long long *launches, double *tot
     prof_collect(c);
     *launches = c->prof_launches[kc];
     *total_ms = c->prof_ms[kc];
+    return IGR_OK;
+}
+
+
+// ------------------------------------------------------------ launch shapes
+
+static int clamp_zc(int zc, int nz) { return zc < kMinZChunk ? kMinZChunk : (zc > nz ? nz : zc); }
+
+igr_status igr_set_tiles(igr_ctx *c, int zc_source, int zc_jacobi, int zc_flux)
+{
+    if (!c || zc_source < 1 || zc_jacobi < 1 || zc_flux < 1)
+        return fail(c, IGR_ERR_INVALID_ARG, "z-chunks must be >= 1");
+    c->tiles.zc_source = clamp_zc(zc_source, c->g.nz);
+    c->tiles.zc_jacobi = clamp_zc(zc_jacobi, c->g.nz);
+    c->tiles.zc_flux = clamp_zc(zc_flux, c->g.nz);
+    return IGR_OK;
+}
+
+igr_status igr_get_tiles(igr_ctx *c, int *zc_source, int *zc_jacobi, int *zc_flux)
+{
+    if (!c || !zc_source || !zc_jacobi || !zc_flux) return fail(c, IGR_ERR_INVALID_ARG, "null argument");
+    *zc_source = c->tiles.zc_source;
+    *zc_jacobi = c->tiles.zc_jacobi;
+    *zc_flux = c->tiles.zc_flux;
+    return IGR_OK;
+}
+
+}  // extern "C"
+
+// mean milliseconds of `reps` launches of fn() on the context stream
+template <typename F> static igr_status time_launches(igr_ctx *c, int reps, F fn, float *ms)
+{
+    cudaEvent_t a, b;
+    CU(c, cudaEventCreate(&a));
+    CU(c, cudaEventCreate(&b));
+    CU(c, fn());  // warm-up
+    CU(c, cudaEventRecord(a, c->st));
+    for (int r = 0; r < reps; r++) CU(c, fn());
+    CU(c, cudaEventRecord(b, c->st));
+    CU(c, cudaEventSynchronize(b));
+    CU(c, cudaEventElapsedTime(ms, a, b));
+    *ms /= reps;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return IGR_OK;
+}
+
+extern "C" {
+
+igr_status igr_autotune(igr_ctx *c, int reps)
+{
+    if (!c || reps < 1) return fail(c, IGR_ERR_INVALID_ARG, "ctx and reps >= 1 are required");
+    if (c->profiling) return fail(c, IGR_ERR_INVALID_ARG, "disable profiling before tuning");
+    const int cand[] = {4, 8, 16, 32, 64, 128};
+    Tiles best = c->tiles;
+    float tbest[3] = {1e30f, 1e30f, 1e30f};
+    void *sig = c->sig[c->cur], *scratch = c->sig[1 - c->cur];
+    for (int zc : cand) {
+        if (zc > c->g.nz && zc != cand[0]) continue;
+        Tiles t = c->tiles;
+        t.zc_source = t.zc_jacobi = t.zc_flux = clamp_zc(zc, c->g.nz);
+        float ms;
+        igr_status s;
+        // each kernel class writes only scratch: b, the other Sigma buffer, the stage-1 output
+        s = time_launches(c, reps, [&] { return c->ops->source(c->g, c->p, t, inflow_of(c), c->q[0], c->b, c->st); }, &ms);
+        if (s != IGR_OK) return s;
+        if (ms < tbest[0]) { tbest[0] = ms; best.zc_source = t.zc_source; }
+        s = time_launches(c, reps, [&] { return c->ops->jacobi(c->g, c->p, t, c->q[0], c->b, sig, scratch, c->st); }, &ms);
+        if (s != IGR_OK) return s;
+        if (ms < tbest[1]) { tbest[1] = ms; best.zc_jacobi = t.zc_jacobi; }
+        s = time_launches(c, reps, [&] {
+            return c->ops->flux(c->g, c->p, t, inflow_of(c), FLUX_STAGE1, c->q[0], sig, c->q[0], c->q[1],
+                                nullptr, c->sc, c->blockmax, &c->sc->err, c->st);
+        }, &ms);
+        if (s != IGR_OK) return s;
+        if (ms < tbest[2]) { tbest[2] = ms; best.zc_flux = t.zc_flux; }
+    }
+    c->tiles = best;
+    return IGR_OK;
+}
+
+// ------------------------------------------------------------ batches
+
+struct igr_batch {
+    std::vector<igr_ctx *> inst;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> join;
+    cudaStream_t user;  // the caller's stream (may be the legacy stream, which cannot be captured)
+    cudaStream_t main;  // the batch's own stream, ordered after `user` at entry and before it at exit
+    cudaEvent_t fork, enter, leave;
+    struct Host {  // host-side stepping state of one instance
+        int cur, speed_nblocks;
+        Tiles tiles;
+        bool operator==(const Host &o) const
+        {
+            return cur == o.cur && speed_nblocks == o.speed_nblocks && tiles.zc_source == o.tiles.zc_source &&
+                   tiles.zc_jacobi == o.tiles.zc_jacobi && tiles.zc_flux == o.tiles.zc_flux;
+        }
+    };
+    struct Graph {
+        std::vector<Host> before, after;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
+    char err[512];
+};
+
+static igr_status bfail(igr_batch *b, igr_status s, const char *msg)
+{
+    snprintf(b->err, sizeof b->err, "%s", msg);
+    return s;
+}
+
+static std::vector<igr_batch::Host> host_state(const igr_batch *b)
+{
+    std::vector<igr_batch::Host> h(b->inst.size());
+    for (size_t i = 0; i < h.size(); i++) h[i] = {b->inst[i]->cur, b->inst[i]->speed_nblocks, b->inst[i]->tiles};
+    return h;
+}
+
+static void set_host_state(igr_batch *b, const std::vector<igr_batch::Host> &h)
+{
+    for (size_t i = 0; i < h.size(); i++) {
+        b->inst[i]->cur = h[i].cur;
+        b->inst[i]->speed_nblocks = h[i].speed_nblocks;
+    }
+}
+
+// one step of every instance, each on its own stream, forked from and joined
+// back into the batch's stream
+static igr_status step_forkjoin(igr_batch *b)
+{
+    if (cudaEventRecord(b->fork, b->main) != cudaSuccess) return bfail(b, IGR_ERR_CUDA, "fork record");
+    for (size_t i = 0; i < b->inst.size(); i++) {
+        if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) return bfail(b, IGR_ERR_CUDA, "fork wait");
+        igr_status s = igr_step(b->inst[i], 1, 0.0, nullptr);
+        if (s != IGR_OK) return bfail(b, s, igr_last_error(b->inst[i]));
+        if (cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess) return bfail(b, IGR_ERR_CUDA, "join record");
+        if (cudaStreamWaitEvent(b->main, b->join[i], 0) != cudaSuccess) return bfail(b, IGR_ERR_CUDA, "join wait");
+    }
+    return IGR_OK;
+}
+
+static igr_status step_batch_steps(igr_batch *b, int nsteps);
+
+igr_status igr_create_batch(const igr_config *cfgs, int n, const igr_allocator *allocator,
+                            void *cuda_stream, igr_batch **out)
+{
+    if (!out || !cfgs || n < 1) return fail(nullptr, IGR_ERR_INVALID_ARG, "cfgs, n >= 1 and out are required");
+    *out = nullptr;
+    igr_batch *b = new (std::nothrow) igr_batch();
+    if (!b) return fail(nullptr, IGR_ERR_OOM, "host allocation failed");
+    b->user = (cudaStream_t)cuda_stream;
+    igr_status s = IGR_OK;
+    if (cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->enter, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->leave, cudaEventDisableTiming) != cudaSuccess)
+        s = fail(nullptr, IGR_ERR_CUDA, "stream/event creation failed");
+    for (int i = 0; i < n && s == IGR_OK; i++) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            s = fail(nullptr, IGR_ERR_CUDA, "stream/event creation failed");
+            break;
+        }
+        b->streams.push_back(st);
+        b->join.push_back(ev);
+        igr_ctx *c = nullptr;
+        s = igr_create(&cfgs[i], allocator, st, &c);
+        if (s == IGR_OK) b->inst.push_back(c);
+    }
+    if (s != IGR_OK) {
+        char msg[512];
+        snprintf(msg, sizeof msg, "%s", g_create_err);
+        igr_destroy_batch(b);
+        snprintf(g_create_err, sizeof g_create_err, "%s", msg);
+        return s;
+    }
+    *out = b;
+    return IGR_OK;
+}
+
+igr_ctx *igr_batch_instance(igr_batch *b, int i)
+{
+    return (b && i >= 0 && i < (int)b->inst.size()) ? b->inst[i] : nullptr;
+}
+
+igr_status igr_step_batch(igr_batch *b, int nsteps)
+{
+    if (!b || nsteps < 0) return IGR_ERR_INVALID_ARG;
+    if (cudaEventRecord(b->enter, b->user) != cudaSuccess || cudaStreamWaitEvent(b->main, b->enter, 0) != cudaSuccess)
+        return bfail(b, IGR_ERR_CUDA, "ordering after the caller's stream");
+    igr_status st = step_batch_steps(b, nsteps);
+    if (cudaEventRecord(b->leave, b->main) != cudaSuccess || cudaStreamWaitEvent(b->user, b->leave, 0) != cudaSuccess)
+        return bfail(b, IGR_ERR_CUDA, "ordering the caller's stream after the batch");
+    return st;
+}
+
+static igr_status step_batch_steps(igr_batch *b, int nsteps)
+{
+    for (int n = 0; n < nsteps; n++) {
+        bool steady = true;
+        for (igr_ctx *c : b->inst)
+            steady = steady && !c->profiling && c->speed_nblocks == (int)c->ops->flux_blocks(c->g, c->tiles);
+        if (!steady) {  // first step after set_state (the dt needs a stand-alone reduction)
+            igr_status s = step_forkjoin(b);
+            if (s != IGR_OK) return s;
+            continue;
+        }
+        std::vector<igr_batch::Host> now = host_state(b);
+        igr_batch::Graph *gr = nullptr;
+        for (auto &g : b->graphs)
+            if (g.before == now) gr = &g;
+        if (!gr) {
+            igr_batch::Graph g;
+            g.before = now;
+            cudaGraph_t graph;
+            if (cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return bfail(b, IGR_ERR_CUDA, "begin capture");
+            igr_status s = step_forkjoin(b);
+            cudaError_t e = cudaStreamEndCapture(b->main, &graph);
+            if (s != IGR_OK) return s;
+            if (e != cudaSuccess) return bfail(b, IGR_ERR_CUDA, cudaGetErrorString(e));
+            g.after = host_state(b);
+            e = cudaGraphInstantiate(&g.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return bfail(b, IGR_ERR_CUDA, cudaGetErrorString(e));
+            set_host_state(b, g.before);
+            b->graphs.push_back(g);
+            gr = &b->graphs.back();
+        }
+        if (cudaGraphLaunch(gr->exec, b->main) != cudaSuccess) return bfail(b, IGR_ERR_CUDA, "graph launch");
+        set_host_state(b, gr->after);
+    }
+    return IGR_OK;
+}
+
+igr_status igr_sync_batch(igr_batch *b)
+{
+    if (!b) return IGR_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(b->main) != cudaSuccess || cudaStreamSynchronize(b->user) != cudaSuccess)
+        return bfail(b, IGR_ERR_CUDA, "synchronize");
+    for (igr_ctx *c : b->inst) {
+        igr_status s = igr_sync(c);
+        if (s != IGR_OK) return bfail(b, s, igr_last_error(c));
+    }
+    return IGR_OK;
+}
+
+const char *igr_batch_last_error(const igr_batch *b) { return b ? b->err : g_create_err; }
+
+igr_status igr_destroy_batch(igr_batch *b)
+{
+    if (!b) return IGR_OK;
+    if (b->main) cudaStreamSynchronize(b->main);
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+    for (igr_ctx *c : b->inst) igr_destroy(c);
+    for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->enter) cudaEventDestroy(b->enter);
+    if (b->leave) cudaEventDestroy(b->leave);
+    if (b->main) cudaStreamDestroy(b->main);
+    delete b;
     return IGR_OK;
 }
 

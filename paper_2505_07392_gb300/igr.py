@@ -77,6 +77,15 @@ def lib():
             "igr_solve_sigma_noalloc": (i, [C.POINTER(Config), p, p, i, p]),
             "igr_noalloc_max_cells": (C.c_size_t, [i]),
             "igr_noalloc_last_error": (C.c_char_p, []),
+            "igr_set_tiles": (i, [p, i, i, i]),
+            "igr_get_tiles": (i, [p, C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
+            "igr_autotune": (i, [p, i]),
+            "igr_create_batch": (i, [C.POINTER(Config), i, C.POINTER(Allocator), p, C.POINTER(p)]),
+            "igr_batch_instance": (p, [p, i]),
+            "igr_step_batch": (i, [p, i]),
+            "igr_sync_batch": (i, [p]),
+            "igr_batch_last_error": (C.c_char_p, [p]),
+            "igr_destroy_batch": (i, [p]),
             "igr_sync": (i, [p]),
             "igr_profile_enable": (i, [p, i]),
             "igr_profile_read": (i, [p, i, C.POINTER(C.c_longlong), C.POINTER(d)]),
@@ -272,6 +281,19 @@ class Solver:
                                          int(qn.numel()), int(stage), float(dt)))
         return out
 
+    # -- launch shapes
+    def set_tiles(self, zc_source: int, zc_jacobi: int, zc_flux: int):
+        self._check(lib().igr_set_tiles(self.h, int(zc_source), int(zc_jacobi), int(zc_flux)))
+
+    def tiles(self):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        self._check(lib().igr_get_tiles(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def autotune(self, reps: int = 3):
+        self._check(lib().igr_autotune(self.h, int(reps)))
+        return self.tiles()
+
     # -- per-kernel timing
     def profile(self, on: bool = True):
         self._check(lib().igr_profile_enable(self.h, int(on)))
@@ -280,3 +302,91 @@ class Solver:
         n, ms = C.c_longlong(), C.c_double()
         self._check(lib().igr_profile_read(self.h, int(kernel_class), C.byref(n), C.byref(ms)))
         return int(n.value), float(ms.value)
+
+
+class _Instance(Solver):
+    """A context owned by a Batch (not destroyed on its own)."""
+
+    def __init__(self, case, precision, handle, stream):
+        import torch
+        self.case = case
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream
+        self.n = case.nx * case.ny * case.nz
+        self.shape = (case.nz, case.ny, case.nx)
+        self.h = handle
+
+    def close(self):
+        self.h = None
+
+
+class Batch:
+    """Independent instances advanced together (igr_create_batch): one CUDA
+    graph per step with a branch per instance, replayed."""
+
+    def __init__(self, cases, precision: str = "f16", stream=None, torch_allocator: bool = True):
+        import torch
+        self.cases = list(cases)
+        self.precision = precision
+        self.stream = stream or torch.cuda.current_stream()
+        made = [make_config(c, precision) for c in self.cases]
+        self._jets = [m[1] for m in made]
+        cfgs = (Config * len(made))(*[m[0] for m in made])
+        self._cfgs = cfgs
+        helper = Solver.__new__(Solver)
+        self._alloc = None
+        if torch_allocator:
+            dev = torch.cuda.current_device()
+
+            @C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+            def _a(nbytes, user):
+                try:
+                    return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, self.stream))
+                except Exception:
+                    return None
+
+            @C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+            def _f(ptr, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc = Allocator(_a, _f, None)
+        h = C.c_void_p()
+        s = lib().igr_create_batch(cfgs, len(made), C.byref(self._alloc) if self._alloc else None,
+                                   C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if s != OK:
+            raise IGRError(s, lib().igr_last_error(None).decode())
+        self.h = h
+        self.instances = [_Instance(c, precision, lib().igr_batch_instance(h, i), self.stream)
+                          for i, c in enumerate(self.cases)]
+
+    def step(self, nsteps: int = 1, sync: bool = False):
+        s = lib().igr_step_batch(self.h, int(nsteps))
+        if s != OK:
+            raise IGRError(s, lib().igr_batch_last_error(self.h).decode())
+        if sync:
+            self.sync()
+
+    def sync(self):
+        s = lib().igr_sync_batch(self.h)
+        if s != OK:
+            raise IGRError(s, lib().igr_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            for inst in self.instances:
+                inst.h = None
+            lib().igr_destroy_batch(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

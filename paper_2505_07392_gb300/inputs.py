@@ -20,6 +20,8 @@ Workloads:
   plume         1024 x 1024 x 2048 box, 33 Mach-3 inflow jets on z = 0, outflow elsewhere
   jets4         128^3 box, 4 Mach-2 inflow jets on z = 0
   sod           quasi-1D shock tube along x
+  tgv           periodic Taylor-Green vortex at Mach 0.5 with density noise
+                (tgv_batch: 64 of them with edges drawn from {48,64,80,96,128})
 """
 from __future__ import annotations
 
@@ -50,6 +52,7 @@ class Case:
     steps: int = 1
     seed: int = 0
     noise: float = 0.0
+    mach: float = 0.0           # Mach number of the Taylor-Green initial state
 
     @property
     def ncells(self) -> int:
@@ -147,6 +150,22 @@ def sod(n: int, transverse: int = 4, sweeps: int = 5) -> Case:
     return Case("sod", n, transverse, transverse, dx, alpha=dx * dx, sweeps=sweeps, bc=bc)
 
 
+def tgv(n: int, seed: int = 4, instance: int = 0, steps: int = 200, sweeps: int = 5,
+        mach: float = 0.5, noise: float = 0.05) -> Case:
+    """Periodic cube of side 1 with a Taylor-Green vortex (k = 2 pi, V0 = 1,
+    rho0 = 1, p0 = 1 / (gamma M^2)) and density noise U(-noise, noise)."""
+    dx = 1.0 / n
+    return Case("tgv", n, n, n, dx, alpha=dx * dx, sweeps=sweeps, bc=(PERIODIC,) * 6, steps=steps,
+                seed=seed * 1000 + instance, noise=noise, mach=mach)
+
+
+def tgv_batch(count: int = 64, seed: int = 4, steps: int = 200):
+    """count Taylor-Green instances whose edges are drawn from {48,64,80,96,128}."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    edges = rng.choice([48, 64, 80, 96, 128], size=count)
+    return [tgv(int(e), seed=seed, instance=i, steps=steps) for i, e in enumerate(edges)]
+
+
 # --------------------------------------------------------- initial states
 
 def initial_state(case: Case, window=None, cell_average: bool = False) -> np.ndarray:
@@ -187,6 +206,17 @@ def initial_state(case: Case, window=None, cell_average: bool = False) -> np.nda
         return np.stack([rho, 0 * ones, 0 * ones, 0 * ones, _e(p, rho, 0.0, g)])
     if case.name in ("plume", "jets4"):
         return jet_initial_state(case, window, np)
+    if case.name == "tgv":
+        k = 2.0 * math.pi
+        m = case.mach
+        p0 = 1.0 / (g * m * m)
+        u = np.sin(k * x) * np.cos(k * y) * np.cos(k * z)
+        v = -np.cos(k * x) * np.sin(k * y) * np.cos(k * z)
+        p = p0 + (1.0 / 16.0) * (np.cos(2 * k * x) + np.cos(2 * k * y)) * (np.cos(2 * k * z) + 2.0)
+        if window != _full(case) and case.noise:
+            raise ValueError("noisy cases are generated whole")
+        rho = 1.0 + _noise(case, shape)
+        return np.stack([rho * ones, rho * u, rho * v, 0 * ones, _e(p, rho, u * u + v * v, g)])
     raise ValueError(f"no initial state for case {case.name!r}")
 
 

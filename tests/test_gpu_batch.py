@@ -1,0 +1,84 @@
+"""Batches and launch shapes on the GPU.
+
+A batch of independent instances (igr_create_batch / igr_step_batch) must
+give, instance by instance, the bits a lone context gives: the kernels are
+the same and nothing is shared between instances. The z-chunk length of
+every kernel class (igr_set_tiles / igr_autotune) must not change a bit
+either: no atomics, and every face flux comes out of the same instructions
+whatever the chunking.
+"""
+import numpy as np
+import pytest
+
+from paper_2505_07392_gb300 import inputs
+from paper_2505_07392_gb300.inputs import INFLOW, OUTFLOW, Case
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_07392_gb300 import build
+    build.build()
+    yield
+
+
+def _alone(case, q0, precision, steps, tiles=None):
+    import torch
+    from paper_2505_07392_gb300 import igr
+    with igr.Solver(case, precision) as s:
+        s.set_state(q0)
+        if tiles:
+            s.set_tiles(*tiles)
+        s.step(steps)
+        q, sig = s.get_state()
+    return q, sig
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+def test_batch_equals_single_bitwise(precision):
+    import torch
+    from paper_2505_07392_gb300 import igr
+    cases = [inputs.tgv(16, instance=0), inputs.tgv(24, instance=1), inputs.tgv(20, instance=2),
+             inputs.blast(12, sweeps=4)]
+    dt = igr.storage_torch_dtype(precision)
+    q0 = [torch.from_numpy(inputs.initial_state(c)).to(dt).cuda() for c in cases]
+    torch.cuda.synchronize()
+    steps = 5  # first step direct, then two captured graphs (Sigma parity) replayed
+    with igr.Batch(cases, precision) as b:
+        for inst, q in zip(b.instances, q0):
+            inst.set_state(q)
+        b.step(2)
+        b.step(steps - 2, sync=True)
+        got = [inst.get_state() for inst in b.instances]
+    for c, q, (qb, sb) in zip(cases, q0, got):
+        qa, sa = _alone(c, q, precision, steps)
+        assert torch.equal(qa, qb), c.name
+        assert torch.equal(sa, sb), c.name
+        assert torch.isfinite(qb.float()).all()
+
+
+def test_results_do_not_depend_on_z_chunks():
+    import torch
+    from paper_2505_07392_gb300 import igr
+    dx = 1.0 / 40
+    w = 2.0 * np.sqrt(1.4 * 2.0)
+    case = Case("jets", 40, 36, 44, dx, alpha=dx * dx, sweeps=5,
+                bc=(OUTFLOW, OUTFLOW, OUTFLOW, OUTFLOW, INFLOW, OUTFLOW),
+                jets=[(0.3, 0.45, 4 * dx, 1.0, w, 2.0, 1.0), (0.7, 0.55, 3 * dx, 1.0, 0.9 * w, 2.0, 1.0)])
+    q0 = torch.from_numpy(inputs.jet_initial_state(case)).float().cuda()
+    ref = _alone(case, q0, "f32", 4, tiles=(44, 44, 44))
+    for tiles in ((4, 4, 4), (8, 16, 32), (32, 8, 5), (7, 13, 11)):
+        q, s = _alone(case, q0, "f32", 4, tiles=tiles)
+        assert torch.equal(q, ref[0]), tiles
+        assert torch.equal(s, ref[1]), tiles
+    with igr.Solver(case, "f32") as s:
+        s.set_state(q0)
+        tiles = s.autotune(reps=2)
+        assert all(4 <= t <= case.nz for t in tiles)
+        s.step(4)
+        q, sig = s.get_state()
+    assert torch.equal(q, ref[0])
