@@ -42,6 +42,10 @@ def lib():
             "orc_stage": (None, [g, p, p, p, p, d, d]),
             "orc_step": (d, [g, p, p, d]),
             "orc_run": (d, [g, p, p, C.c_int, d]),
+            "orc_adjoint_step": (None, [g, p, p, d, p, p, p, p, p]),
+            "orc_rhs_vjp": (None, [g, p, p, p, p, p]),
+            "orc_source_vjp": (None, [g, p, p, p]),
+            "orc_jacobi_vjp": (None, [g, p, p, p, C.c_int, p, p, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -158,3 +162,53 @@ def run(cfg, q, sigma=None, nsteps=1, fixed_dt=0.0):
          else np.array(_f64(sigma, (g.n,)), copy=True).reshape(g.nz, g.ny, g.nx))
     t = lib().orc_run(g.ptr, _p(q), _p(s), int(nsteps), float(fixed_dt))
     return q, s, float(t)
+
+
+def adjoint_step(cfg, q, sigma, dt, lq, ls):
+    """Adjoint of one SSP-RK3 step with fixed dt: given the adjoints (lq, ls)
+    of the step's outputs (q', Sigma'), returns (lq_in, ls_in, gw) — the
+    adjoints of (q, Sigma) and the gradient with respect to the jet
+    velocities w_n of <lq, q'> + <ls, Sigma'>."""
+    g = _grid(cfg)
+    if g.s.sweeps > 63:
+        raise ValueError("at most 63 sweeps")
+    q = _f64(q, (5, g.n))
+    sig = _f64(sigma, (g.n,))
+    lq = _f64(lq, (5, g.n))
+    ls = _f64(ls, (g.n,))
+    lq_out = np.empty((5, g.nz, g.ny, g.nx))
+    ls_out = np.empty((g.nz, g.ny, g.nx))
+    gw = np.zeros(max(1, g.s.njets))
+    lib().orc_adjoint_step(g.ptr, _p(q), _p(sig), float(dt), _p(lq), _p(ls), _p(lq_out), _p(ls_out), _p(gw))
+    return lq_out, ls_out, gw[:g.s.njets]
+
+
+def rhs_vjp(cfg, q, sigma, Lb):
+    """(dL/dq)^T Lb and (dL/dSigma)^T Lb of the spatial operator."""
+    g = _grid(cfg)
+    qb = np.zeros((5, g.nz, g.ny, g.nx))
+    sb = np.zeros((g.nz, g.ny, g.nx))
+    lib().orc_rhs_vjp(g.ptr, _p(_f64(q, (5, g.n))), _p(_f64(sigma, (g.n,))), _p(_f64(Lb, (5, g.n))),
+                      _p(qb), _p(sb))
+    return qb, sb
+
+
+def source_vjp(cfg, q, bb):
+    """(db/dq)^T bb of the IGR source."""
+    g = _grid(cfg)
+    qb = np.zeros((5, g.nz, g.ny, g.nx))
+    lib().orc_source_vjp(g.ptr, _p(_f64(q, (5, g.n))), _p(_f64(bb, (g.n,))), _p(qb))
+    return qb
+
+
+def jacobi_vjp(cfg, q, b, sigma0, sweeps, sb):
+    """Adjoints of (sigma0, b, rho) of `sweeps` Jacobi sweeps given the
+    adjoint sb of their result."""
+    g = _grid(cfg)
+    s = np.array(_f64(sb, (g.n,)), copy=True)
+    bb = np.zeros(g.n)
+    rb = np.zeros(g.n)
+    lib().orc_jacobi_vjp(g.ptr, _p(_f64(q, (5, g.n))), _p(_f64(b, (g.n,))), _p(_f64(sigma0, (g.n,))),
+                         int(sweeps), _p(s), _p(bb), _p(rb))
+    shp = (g.nz, g.ny, g.nx)
+    return s.reshape(shp), bb.reshape(shp), rb.reshape(shp)

@@ -464,3 +464,436 @@ double orc_run(const orc_grid *g, double *q, double *sigma, int nsteps, double f
     for (int n = 0; n < nsteps; n++) t += orc_step(g, q, sigma, fixed_dt);
     return t;
 }
+
+/* ======================================================================
+ * Discrete adjoint of one SSP-RK3 step (fixed dt), in FP64.
+ *
+ * With dt frozen, one step maps (q, Sigma; jet velocities w) to
+ * (q', Sigma'). Given the adjoints (lq, ls) of (q', Sigma'), the functions
+ * below return the adjoints of (q, Sigma) and add d<lq,q'> + <ls,Sigma'>/dw
+ * to gw. Each routine is the hand-written reverse of the forward routine
+ * of the same name: the forward step is recomputed and stored (stage
+ * inputs, Sigma iterates of every sweep), then the stages are reversed.
+ * Non-smooth points take one-sided branches matching the forward: the LF
+ * speed max(aL, aR) sends its adjoint to the side the forward selected,
+ * |u| takes sign(u) with sign(0) = 0.
+ * ====================================================================== */
+
+/* reverse of fill_axis_x/y/z: the adjoint of each ghost cell goes back to the
+ * cell it was copied from (times 1 - sum s for an inflow ghost, whose jet part
+ * goes to lamJ[var][j][i]); the ghost's adjoint is consumed */
+static void fill_axis_x_rev(const orc_grid *g, double *fb)
+{
+    int nx = g->nx;
+    for (int k = g->nz + G - 1; k >= -G; k--)
+        for (int j = g->ny + G - 1; j >= -G; j--)
+            for (int s = G; s >= 1; s--) {
+                int lo = -s, hi = nx - 1 + s;
+                int slo = g->bc[0] == BC_PERIODIC ? ((lo % nx) + nx) % nx : 0;
+                int shi = g->bc[1] == BC_PERIODIC ? hi % nx : nx - 1;
+                fb[GI(g, shi, j, k)] += fb[GI(g, hi, j, k)];
+                fb[GI(g, hi, j, k)] = 0.0;
+                fb[GI(g, slo, j, k)] += fb[GI(g, lo, j, k)];
+                fb[GI(g, lo, j, k)] = 0.0;
+            }
+}
+static void fill_axis_y_rev(const orc_grid *g, double *fb)
+{
+    int ny = g->ny;
+    for (int k = g->nz + G - 1; k >= -G; k--)
+        for (int s = G; s >= 1; s--)
+            for (int i = g->nx + G - 1; i >= -G; i--) {
+                int lo = -s, hi = ny - 1 + s;
+                int slo = g->bc[2] == BC_PERIODIC ? ((lo % ny) + ny) % ny : 0;
+                int shi = g->bc[3] == BC_PERIODIC ? hi % ny : ny - 1;
+                fb[GI(g, i, shi, k)] += fb[GI(g, i, hi, k)];
+                fb[GI(g, i, hi, k)] = 0.0;
+                fb[GI(g, i, slo, k)] += fb[GI(g, i, lo, k)];
+                fb[GI(g, i, lo, k)] = 0.0;
+            }
+}
+static void fill_axis_z_rev(const orc_grid *g, double *fb, int var, double *lamJ)
+{
+    int nz = g->nz;
+    for (int s = G; s >= 1; s--)
+        for (int j = g->ny + G - 1; j >= -G; j--)
+            for (int i = g->nx + G - 1; i >= -G; i--) {
+                int lo = -s, hi = nz - 1 + s;
+                int slo = g->bc[4] == BC_PERIODIC ? ((lo % nz) + nz) % nz : 0;
+                int shi = g->bc[5] == BC_PERIODIC ? hi % nz : nz - 1;
+                fb[GI(g, i, j, shi)] += fb[GI(g, i, j, hi)];
+                fb[GI(g, i, j, hi)] = 0.0;
+                double a = fb[GI(g, i, j, lo)];
+                fb[GI(g, i, j, lo)] = 0.0;
+                if (g->bc[4] == BC_INFLOW && var >= 0) {
+                    double x = (i + 0.5) * g->dx, y = (j + 0.5) * g->dx;
+                    double wsum = 0.0;
+                    for (int n = 0; n < g->njets; n++) {
+                        const double *J = g->jets + 7 * n;
+                        double r = sqrt((x - J[0]) * (x - J[0]) + (y - J[1]) * (y - J[1]));
+                        wsum += 0.5 * (1.0 - tanh((r - J[2]) / (J[6] * g->dx)));
+                    }
+                    fb[GI(g, i, j, slo)] += (1.0 - wsum) * a;
+                    if (i >= 0 && i < g->nx && j >= 0 && j < g->ny)
+                        lamJ[((long)var * g->ny + j) * g->nx + i] += a;
+                } else {
+                    fb[GI(g, i, j, slo)] += a;
+                }
+            }
+}
+
+/* reverse of orc_fill_ghosts: qgb (ghost-array adjoints, consumed) is added
+ * to qb (interior adjoints); lamJ (5 x ny x nx) collects the jet-table part */
+static void fill_ghosts_rev(const orc_grid *g, double *qgb, double *qb, double *lamJ)
+{
+    long N = ncell(g), NG = nghost(g);
+    for (int v = 0; v < NV; v++) {
+        double *fb = qgb + v * NG;
+        fill_axis_z_rev(g, fb, v, lamJ);
+        fill_axis_y_rev(g, fb);
+        fill_axis_x_rev(g, fb);
+        for (int k = 0; k < g->nz; k++)
+            for (int j = 0; j < g->ny; j++)
+                for (int i = 0; i < g->nx; i++) qb[v * N + I(g, i, j, k)] += fb[GI(g, i, j, k)];
+    }
+}
+
+static void fill_sigma_ghosts_rev(const orc_grid *g, double *sgb, double *sb)
+{
+    fill_axis_z_rev(g, sgb, -1, NULL);
+    fill_axis_y_rev(g, sgb);
+    fill_axis_x_rev(g, sgb);
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++) sb[I(g, i, j, k)] += sgb[GI(g, i, j, k)];
+}
+
+/* reverse of source_from_ghosts: bb (adjoint of b) added into qgb.
+ * d b / d G[a][c] = alpha (2 G[c][a] + 2 tr(G) delta_ac). */
+static void source_rev(const orc_grid *g, const double *qg, const double *bb, double *qgb)
+{
+    long NG = nghost(g);
+    const double *rho = qg, *m[3] = {qg + NG, qg + 2 * NG, qg + 3 * NG};
+    double *rhob = qgb, *mb[3] = {qgb + NG, qgb + 2 * NG, qgb + 3 * NG};
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++) {
+                int off[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+                double Gm[3][3];
+                long ip[3], im[3];
+                for (int c = 0; c < 3; c++) {
+                    ip[c] = GI(g, i + off[c][0], j + off[c][1], k + off[c][2]);
+                    im[c] = GI(g, i - off[c][0], j - off[c][1], k - off[c][2]);
+                    for (int a = 0; a < 3; a++)
+                        Gm[a][c] = (m[a][ip[c]] / rho[ip[c]] - m[a][im[c]] / rho[im[c]]) / (2.0 * g->dx);
+                }
+                double trG = Gm[0][0] + Gm[1][1] + Gm[2][2];
+                double b_bar = bb[I(g, i, j, k)];
+                for (int c = 0; c < 3; c++)
+                    for (int a = 0; a < 3; a++) {
+                        double Gb = g->alpha * (2.0 * Gm[c][a] + (a == c ? 2.0 * trG : 0.0)) * b_bar;
+                        double ub = Gb / (2.0 * g->dx); /* + at ip, - at im */
+                        long p = ip[c], q = im[c];
+                        mb[a][p] += ub / rho[p];
+                        rhob[p] -= ub * m[a][p] / (rho[p] * rho[p]);
+                        mb[a][q] -= ub / rho[q];
+                        rhob[q] += ub * m[a][q] / (rho[q] * rho[q]);
+                    }
+            }
+}
+
+/* reverse of `sweeps` Jacobi sweeps. it[0..sweeps] are the iterates of the
+ * forward solve (it[0] the warm start). sb: in, the adjoint of it[sweeps];
+ * out, the adjoint of it[0]. bb and rhob accumulate. With D_i the diagonal
+ * and mu = lambda / D, the adjoint of a sweep is the same 7-point stencil
+ * applied to mu (the operator is symmetric). */
+static void jacobi_rev(const orc_grid *g, const double *q, double *const *it, int sweeps, double *sb,
+                       double *bb, double *rhob)
+{
+    long N = ncell(g);
+    const double *rho = q;
+    double beta = g->alpha / (g->dx * g->dx);
+    double *mu = malloc(sizeof(double) * N), *rb = calloc(N, sizeof(double)), *nl = malloc(sizeof(double) * N);
+    for (int it_k = sweeps - 1; it_k >= 0; it_k--) {
+        const double *s0 = it[it_k], *F = it[it_k + 1];
+        for (long c = 0; c < N; c++) nl[c] = 0.0;
+        for (int k = 0; k < g->nz; k++)
+            for (int j = 0; j < g->ny; j++)
+                for (int i = 0; i < g->nx; i++) {
+                    long c = I(g, i, j, k), nb;
+                    double ri = 1.0 / rho[c], diag = ri;
+                    for (int d = 0; d < 6; d++)
+                        if (neighbour(g, i, j, k, d, &nb)) diag += beta * 0.5 * (ri + 1.0 / rho[nb]);
+                    mu[c] = sb[c] / diag;
+                }
+        for (int k = 0; k < g->nz; k++)
+            for (int j = 0; j < g->ny; j++)
+                for (int i = 0; i < g->nx; i++) {
+                    long c = I(g, i, j, k), nb;
+                    double ri = 1.0 / rho[c];
+                    double ssum = 0.0;
+                    int nf = 0;
+                    bb[c] += mu[c];
+                    for (int d = 0; d < 6; d++) {
+                        if (!neighbour(g, i, j, k, d, &nb)) continue;
+                        double cf = 0.5 * (ri + 1.0 / rho[nb]);
+                        nl[nb] += beta * cf * mu[c];
+                        ssum += s0[nb];
+                        nf++;
+                        rb[nb] += mu[c] * 0.5 * beta * (s0[nb] - F[c]);
+                    }
+                    rb[c] += mu[c] * (0.5 * beta * ssum - F[c] * (1.0 + 0.5 * beta * nf));
+                }
+        for (long c = 0; c < N; c++) sb[c] = nl[c];
+    }
+    for (long c = 0; c < N; c++) rhob[c] -= rb[c] / (rho[c] * rho[c]);
+    free(mu);
+    free(rb);
+    free(nl);
+}
+
+/* reverse of phys_flux: Fb (5) and ab (adjoint of |u_d| + c) into qvb (5), sigb */
+static void phys_flux_rev(const orc_grid *g, const double qv[NV], double sig, int d, const double Fb[NV],
+                          double ab, double qvb[NV], double *sigb)
+{
+    double gm = g->gamma;
+    double rho = qv[0], E = qv[4];
+    double u[3] = {qv[1] / rho, qv[2] / rho, qv[3] / rho};
+    double ke = 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    double p = (gm - 1.0) * (E - ke);
+    double P = p + sig;
+    double c = sqrt(gm * p / rho);
+    double ub[3] = {0, 0, 0}, rhob = 0, Eb = 0, Pb = 0, pb = 0;
+    /* F0 = rho u_d, F[1+a] = m_a u_d + P delta_ad, F4 = (E + P) u_d */
+    rhob += Fb[0] * u[d];
+    ub[d] += Fb[0] * rho;
+    for (int a = 0; a < 3; a++) {
+        qvb[1 + a] += Fb[1 + a] * u[d];
+        ub[d] += Fb[1 + a] * qv[1 + a];
+    }
+    Pb += Fb[1 + d];
+    Eb += Fb[4] * u[d];
+    Pb += Fb[4] * u[d];
+    ub[d] += Fb[4] * (E + P);
+    /* a = |u_d| + sqrt(gamma p / rho) */
+    ub[d] += ab * (u[d] > 0 ? 1.0 : (u[d] < 0 ? -1.0 : 0.0));
+    pb += ab * gm / (2.0 * c * rho);
+    rhob += -ab * c / (2.0 * rho);
+    /* P = p + Sigma; p = (gamma-1)(E - ke); ke = rho |u|^2 / 2 */
+    pb += Pb;
+    *sigb += Pb;
+    Eb += (gm - 1.0) * pb;
+    double keb = -(gm - 1.0) * pb;
+    rhob += keb * 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    for (int a = 0; a < 3; a++) ub[a] += keb * rho * u[a];
+    /* u_a = m_a / rho */
+    for (int a = 0; a < 3; a++) {
+        qvb[1 + a] += ub[a] / rho;
+        rhob -= ub[a] * u[a] / rho;
+    }
+    qvb[0] += rhob;
+    qvb[4] += Eb;
+}
+
+/* reverse of rhs_from_ghosts: Lb (adjoint of L, interior) into qgb, sgb */
+static void rhs_rev(const orc_grid *g, const double *qg, const double *sg, const double *Lb, double *qgb,
+                    double *sgb)
+{
+    static const double cl[6] = {2.0 / 60, -13.0 / 60, 47.0 / 60, 27.0 / 60, -3.0 / 60, 0.0};
+    static const double cr[6] = {0.0, -3.0 / 60, 27.0 / 60, 47.0 / 60, -13.0 / 60, 2.0 / 60};
+    long N = ncell(g), NG = nghost(g);
+    int n3[3] = {g->nx, g->ny, g->nz};
+    for (int d = 0; d < 3; d++) {
+        int fx = g->nx + (d == 0), fy = g->ny + (d == 1), fz = g->nz + (d == 2);
+        for (int k = 0; k < fz; k++)
+            for (int j = 0; j < fy; j++)
+                for (int i = 0; i < fx; i++) {
+                    int c3[3] = {i, j, k};
+                    int f = c3[d];
+                    /* F_hat at face f is -1/dx in L of cell f-1 and +1/dx in L of cell f */
+                    double Fh_b[NV];
+                    for (int v = 0; v < NV; v++) {
+                        double lo = 0.0, hi = 0.0;
+                        if (f >= 1) {
+                            int cc[3] = {i, j, k};
+                            cc[d] = f - 1;
+                            lo = Lb[v * N + I(g, cc[0], cc[1], cc[2])];
+                        }
+                        if (f < n3[d]) hi = Lb[v * N + I(g, i, j, k)];
+                        Fh_b[v] = (hi - lo) / g->dx;
+                    }
+                    long pos[6];
+                    double vq[NV + 1][6];
+                    for (int s = 0; s < 6; s++) {
+                        int cc[3] = {i, j, k};
+                        cc[d] += s - 3;
+                        pos[s] = GI(g, cc[0], cc[1], cc[2]);
+                        for (int v = 0; v < NV; v++) vq[v][s] = qg[v * NG + pos[s]];
+                        vq[NV][s] = sg[pos[s]];
+                    }
+                    double qL[NV], qR[NV], FL[NV], FR[NV];
+                    for (int v = 0; v < NV; v++) {
+                        qL[v] = recon_left(vq[v]);
+                        qR[v] = recon_right(vq[v]);
+                    }
+                    double sL = recon_left(vq[NV]), sR = recon_right(vq[NV]);
+                    double aL = phys_flux(g, qL, sL, d, FL);
+                    double aR = phys_flux(g, qR, sR, d, FR);
+                    double lam = aL > aR ? aL : aR;
+                    double FLb[NV], FRb[NV], qLb[NV] = {0}, qRb[NV] = {0}, sLb = 0, sRb = 0, lamb = 0;
+                    for (int v = 0; v < NV; v++) {
+                        FLb[v] = 0.5 * Fh_b[v];
+                        FRb[v] = 0.5 * Fh_b[v];
+                        qLb[v] += 0.5 * lam * Fh_b[v];
+                        qRb[v] -= 0.5 * lam * Fh_b[v];
+                        lamb -= 0.5 * (qR[v] - qL[v]) * Fh_b[v];
+                    }
+                    double aLb = aL > aR ? lamb : 0.0, aRb = aL > aR ? 0.0 : lamb;
+                    phys_flux_rev(g, qL, sL, d, FLb, aLb, qLb, &sLb);
+                    phys_flux_rev(g, qR, sR, d, FRb, aRb, qRb, &sRb);
+                    for (int s = 0; s < 6; s++) {
+                        for (int v = 0; v < NV; v++) qgb[v * NG + pos[s]] += cl[s] * qLb[v] + cr[s] * qRb[v];
+                        sgb[pos[s]] += cl[s] * sLb + cr[s] * sRb;
+                    }
+                }
+    }
+}
+
+/* Adjoint of one SSP-RK3 step with fixed dt > 0 from (q, sigma):
+ * lq, ls: adjoints of q', Sigma' (inputs); lq_out, ls_out: adjoints of q,
+ * Sigma (outputs, overwritten); gw (njets) accumulates the jet-velocity
+ * gradient. */
+void orc_adjoint_step(const orc_grid *g, const double *q, const double *sigma, double dt,
+                      const double *lq, const double *ls, double *lq_out, double *ls_out, double *gw)
+{
+    long N = ncell(g), NG = nghost(g);
+    int S = g->sweeps;
+    const double wst[3] = {1.0, 0.25, 2.0 / 3.0};
+    /* forward recompute with storage */
+    double *qs[3], *its[3][64];
+    double *qg = malloc(sizeof(double) * NV * NG), *sg = malloc(sizeof(double) * NG);
+    double *b = malloc(sizeof(double) * N), *L = malloc(sizeof(double) * NV * N);
+    for (int st = 0; st < 3; st++) {
+        qs[st] = malloc(sizeof(double) * NV * N);
+        for (int s = 0; s <= S; s++) its[st][s] = malloc(sizeof(double) * N);
+    }
+    memcpy(qs[0], q, sizeof(double) * NV * N);
+    memcpy(its[0][0], sigma, sizeof(double) * N);
+    for (int st = 0; st < 3; st++) {
+        orc_fill_ghosts(g, qs[st], qg);
+        source_from_ghosts(g, qg, b);
+        for (int s = 0; s < S; s++) {
+            memcpy(its[st][s + 1], its[st][s], sizeof(double) * N);
+            orc_jacobi(g, qs[st], b, its[st][s + 1], 1);
+        }
+        if (st < 2) {
+            fill_sigma_ghosts(g, its[st][S], sg);
+            rhs_from_ghosts(g, qg, sg, L);
+            for (long n = 0; n < NV * N; n++)
+                qs[st + 1][n] = q[n] + wst[st] * ((qs[st][n] - q[n]) + dt * L[n]);
+            memcpy(its[st + 1][0], its[st][S], sizeof(double) * N);
+        }
+    }
+    /* reverse */
+    double *lqs = calloc(NV * N, sizeof(double)), *lq0 = calloc(NV * N, sizeof(double));
+    double *lsig = malloc(sizeof(double) * N), *lb = malloc(sizeof(double) * N);
+    double *qgb = malloc(sizeof(double) * NV * NG), *sgb = malloc(sizeof(double) * NG);
+    double *Lb = calloc(NV * N, sizeof(double));
+    double *lamJ = calloc((long)NV * g->ny * g->nx, sizeof(double));
+    double *lout = malloc(sizeof(double) * NV * N);
+    memcpy(lout, lq, sizeof(double) * NV * N);
+    memcpy(lsig, ls, sizeof(double) * N);
+    for (int st = 2; st >= 0; st--) {
+        double w = wst[st];
+        /* out = q + w ((qs - q) + dt L(qs, Sigma^S)) */
+        for (long n = 0; n < NV * N; n++) {
+            lq0[n] += (1.0 - w) * lout[n];
+            lqs[n] = w * lout[n];
+            Lb[n] = w * dt * lout[n];
+        }
+        orc_fill_ghosts(g, qs[st], qg);
+        fill_sigma_ghosts(g, its[st][S], sg);
+        memset(qgb, 0, sizeof(double) * NV * NG);
+        memset(sgb, 0, sizeof(double) * NG);
+        rhs_rev(g, qg, sg, Lb, qgb, sgb);
+        fill_sigma_ghosts_rev(g, sgb, lsig); /* lsig: adjoint of Sigma^S */
+        memset(lb, 0, sizeof(double) * N);
+        jacobi_rev(g, qs[st], its[st], S, lsig, lb, lqs); /* rho adjoint into lqs[0..N) */
+        source_rev(g, qg, lb, qgb);
+        fill_ghosts_rev(g, qgb, lqs, lamJ);
+        /* the stage input is q (stage 1) or the previous stage's output */
+        if (st == 0)
+            for (long n = 0; n < NV * N; n++) lq0[n] += lqs[n];
+        else
+            memcpy(lout, lqs, sizeof(double) * NV * N);
+    }
+    memcpy(lq_out, lq0, sizeof(double) * NV * N);
+    memcpy(ls_out, lsig, sizeof(double) * N);
+    /* jet tables: J[v](x, y) = sum_n s_n q_jet_n[v]; d q_jet_n / d w_n = (0,0,0,rho_n, rho_n w_n) */
+    for (int n = 0; n < g->njets; n++) {
+        const double *Jt = g->jets + 7 * n;
+        double acc = 0.0;
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++) {
+                double x = (i + 0.5) * g->dx, y = (j + 0.5) * g->dx;
+                double r = sqrt((x - Jt[0]) * (x - Jt[0]) + (y - Jt[1]) * (y - Jt[1]));
+                double sn = 0.5 * (1.0 - tanh((r - Jt[2]) / (Jt[6] * g->dx)));
+                long f = (long)j * g->nx + i;
+                acc += sn * (Jt[3] * lamJ[3L * g->ny * g->nx + f] + Jt[3] * Jt[4] * lamJ[4L * g->ny * g->nx + f]);
+            }
+        gw[n] += acc;
+    }
+    for (int st = 0; st < 3; st++) {
+        free(qs[st]);
+        for (int s = 0; s <= S; s++) free(its[st][s]);
+    }
+    free(qg); free(sg); free(b); free(L); free(lqs); free(lq0); free(lsig); free(lb);
+    free(qgb); free(sgb); free(Lb); free(lamJ); free(lout);
+}
+
+/* ---------------- vector-Jacobian products of the parts (for pinning) */
+
+/* qb (5N) += (dL/dq)^T Lb, sb (N) += (dL/dSigma)^T Lb, lamJ ignored */
+void orc_rhs_vjp(const orc_grid *g, const double *q, const double *sigma, const double *Lb, double *qb,
+                 double *sb)
+{
+    long NG = nghost(g);
+    double *qg = malloc(sizeof(double) * NV * NG), *sg = malloc(sizeof(double) * NG);
+    double *qgb = calloc(NV * NG, sizeof(double)), *sgb = calloc(NG, sizeof(double));
+    double *lamJ = calloc((long)NV * g->ny * g->nx, sizeof(double));
+    orc_fill_ghosts(g, q, qg);
+    fill_sigma_ghosts(g, sigma, sg);
+    rhs_rev(g, qg, sg, Lb, qgb, sgb);
+    fill_sigma_ghosts_rev(g, sgb, sb);
+    fill_ghosts_rev(g, qgb, qb, lamJ);
+    free(qg); free(sg); free(qgb); free(sgb); free(lamJ);
+}
+
+/* qb (5N) += (db/dq)^T bb */
+void orc_source_vjp(const orc_grid *g, const double *q, const double *bb, double *qb)
+{
+    long NG = nghost(g);
+    double *qg = malloc(sizeof(double) * NV * NG), *qgb = calloc(NV * NG, sizeof(double));
+    double *lamJ = calloc((long)NV * g->ny * g->nx, sizeof(double));
+    orc_fill_ghosts(g, q, qg);
+    source_rev(g, qg, bb, qgb);
+    fill_ghosts_rev(g, qgb, qb, lamJ);
+    free(qg); free(qgb); free(lamJ);
+}
+
+/* Jacobi sweeps from sigma0: sb in = adjoint of the result, out = adjoint of
+ * sigma0; bb (N) and rhob (N) accumulate */
+void orc_jacobi_vjp(const orc_grid *g, const double *q, const double *b, const double *sigma0, int sweeps,
+                    double *sb, double *bb, double *rhob)
+{
+    long N = ncell(g);
+    double *it[64] = {0};
+    for (int s = 0; s <= sweeps; s++) it[s] = malloc(sizeof(double) * N);
+    memcpy(it[0], sigma0, sizeof(double) * N);
+    for (int s = 0; s < sweeps; s++) {
+        memcpy(it[s + 1], it[s], sizeof(double) * N);
+        orc_jacobi(g, q, b, it[s + 1], 1);
+    }
+    jacobi_rev(g, q, it, sweeps, sb, bb, rhob);
+    for (int s = 0; s <= sweeps; s++) free(it[s]);
+}

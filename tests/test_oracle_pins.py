@@ -365,3 +365,121 @@ def test_blast_mirror_symmetry():
         assert np.allclose(q1[4], flip(q1[4]), rtol=0, atol=1e-13)
         assert np.allclose(q1[mv], -flip(q1[mv]), rtol=0, atol=1e-13)
         assert np.allclose(s1, np.flip(s1, axis=ax - 1), rtol=0, atol=1e-13)
+
+
+# ------------------------------------------------------------- adjoint
+
+def _offset_state(c, seed):
+    """Smooth state whose velocity components stay away from zero (|u| has a
+    kink at 0 that central differences would straddle)."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    z, y, x = centres(c)
+    ph = rng.uniform(0, 2 * np.pi, size=8)
+    tp = 2 * np.pi
+    rho = 1 + 0.2 * np.sin(tp * x + ph[0]) * np.cos(tp * y + ph[1]) + 0.1 * np.sin(tp * z + ph[2])
+    u = 0.45 + 0.2 * np.sin(tp * y + ph[3])
+    v = -0.4 + 0.15 * np.cos(tp * x + ph[4]) * np.sin(tp * z)
+    w = 0.42 + 0.2 * np.sin(tp * x + ph[5])
+    p = 1 + 0.1 * np.cos(tp * (x + y) + ph[6])
+    return cons(rho, u, v, w, p)
+
+
+def _fd_agrees(fd_at, ad, hs=(1e-6, 3e-7), tol=1e-6):
+    """The adjoint against central differences: the LF speed max(aL, aR) is
+    only piecewise smooth, so take the better of two small steps."""
+    errs = [abs(fd_at(h) - ad) / abs(ad) for h in hs]
+    return min(errs) <= tol, errs
+
+
+@pytest.mark.parametrize("bc", [(PERIODIC,) * 6, (OUTFLOW,) * 6])
+def test_adjoint_parts_match_finite_differences(bc):
+    """Vector-Jacobian products of the spatial operator, the source and the
+    Jacobi sweeps against central differences of the pinned forward maps."""
+    c = box(8, bc, nx=8, ny=7, nz=6, sweeps=3)
+    rng = np.random.Generator(np.random.Philox(7))
+    q = _offset_state(c, 2)
+    s = 0.05 * np.sin(2 * np.pi * centres(c)[2] * 3)
+    vq, vs = rng.normal(size=q.shape), rng.normal(size=s.shape)
+    Lb = rng.normal(size=q.shape)
+    qb, sb = oracle.rhs_vjp(c, q, s, Lb)
+    ok, errs = _fd_agrees(lambda h: np.sum(Lb * (oracle.rhs(c, q + h * vq, s + h * vs)
+                                                 - oracle.rhs(c, q - h * vq, s - h * vs))) / (2 * h),
+                          np.sum(qb * vq) + np.sum(sb * vs))
+    assert ok, ("rhs", errs)
+    bb = rng.normal(size=s.shape)
+    qb = oracle.source_vjp(c, q, bb)
+    ok, errs = _fd_agrees(lambda h: np.sum(bb * (oracle.source(c, q + h * vq) - oracle.source(c, q - h * vq))) / (2 * h),
+                          np.sum(qb * vq))
+    assert ok, ("source", errs)
+    b = oracle.source(c, q)
+    vb, vr = rng.normal(size=s.shape), rng.normal(size=s.shape)
+    sbar = rng.normal(size=s.shape)
+    s0b, bbar, rbar = oracle.jacobi_vjp(c, q, b, s, 3, sbar)
+    qv = np.zeros_like(q)
+    qv[0] = vr
+    J = lambda h: oracle.jacobi(c, q + h * qv, b + h * vb, s + h * vs, 3)
+    ok, errs = _fd_agrees(lambda h: np.sum(sbar * (J(h) - J(-h))) / (2 * h),
+                          np.sum(s0b * vs) + np.sum(bbar * vb) + np.sum(rbar * vr))
+    assert ok, ("jacobi", errs)
+
+
+def test_jacobi_adjoint_is_the_transposed_sweep():
+    """With uniform density the sweep is linear and symmetric: its adjoint with
+    respect to the warm start applied to e_m equals the forward sweep of e_m."""
+    c = box(6, (PERIODIC,) * 6)
+    q = cons(1.3 + 0 * centres(c)[0], 0 * centres(c)[0], 0 * centres(c)[0], 0 * centres(c)[0],
+             1 + 0 * centres(c)[0])
+    rng = np.random.Generator(np.random.Philox(12))
+    a, bvec = rng.normal(size=c.ncells), rng.normal(size=c.ncells)
+    zero = np.zeros(c.ncells)
+    fa = oracle.jacobi(c, q, zero, a, 1).ravel()
+    s0b, _, _ = oracle.jacobi_vjp(c, q, zero, zero, 1, bvec)
+    assert np.isclose(np.dot(fa, bvec), np.dot(a, s0b.ravel()), rtol=1e-13)
+
+
+@pytest.mark.parametrize("bc", [(PERIODIC,) * 6, (OUTFLOW,) * 6])
+def test_adjoint_step_matches_finite_differences(bc):
+    """The adjoint of a full SSP-RK3 step (fixed dt) in the state and Sigma."""
+    c = box(8, bc, nx=8, ny=7, nz=6, sweeps=3)
+    rng = np.random.Generator(np.random.Philox(3))
+    q = _offset_state(c, 4)
+    s = 0.05 * np.cos(2 * np.pi * centres(c)[1] * 2)
+    dt = 0.01
+    lq, ls = rng.normal(size=q.shape), rng.normal(size=s.shape)
+    aq, a_s, _ = oracle.adjoint_step(c, q, s, dt, lq, ls)
+    vq, vs = rng.normal(size=q.shape), rng.normal(size=s.shape)
+
+    def fd(h):
+        qp, sp, _ = oracle.run(c, q + h * vq, s + h * vs, 1, dt)
+        qm, sm, _ = oracle.run(c, q - h * vq, s - h * vs, 1, dt)
+        return (np.sum(lq * (qp - qm)) + np.sum(ls * (sp - sm))) / (2 * h)
+
+    ok, errs = _fd_agrees(fd, np.sum(aq * vq) + np.sum(a_s * vs))
+    assert ok, errs
+
+
+def test_adjoint_jet_velocity_gradient():
+    """d/dw of <lq, q'> + <ls, Sigma'> through the inflow ghosts, per jet."""
+    dx = 1.0 / 16
+    w = 2 * math.sqrt(2.8)
+    c = Case("jets", 16, 14, 10, dx, alpha=dx * dx, sweeps=3,
+             bc=(OUTFLOW,) * 4 + (INFLOW, OUTFLOW),
+             jets=[(0.3, 0.45, 3 * dx, 1.0, w, 2.0, 1.0), (0.65, 0.5, 2.5 * dx, 1.0, 0.8 * w, 2.0, 1.0)])
+    q0 = inputs.jet_initial_state(c)
+    q, s, _ = oracle.run(c, q0, None, 3, 1e-3)
+    dt = 1e-3
+    rng = np.random.Generator(np.random.Philox(8))
+    lq, ls = rng.normal(size=q.shape), rng.normal(size=s.shape)
+    _, _, gw = oracle.adjoint_step(c, q, s, dt, lq, ls)
+    for n in range(2):
+        def fd(h):
+            vals = []
+            for sgn in (1, -1):
+                jets = [list(j) for j in c.jets]
+                jets[n][4] += sgn * h
+                cc = replace(c, jets=[tuple(j) for j in jets])
+                q1, s1, _ = oracle.run(cc, q, s, 1, dt)
+                vals.append(np.sum(lq * q1) + np.sum(ls * s1))
+            return (vals[0] - vals[1]) / (2 * h)
+        ok, errs = _fd_agrees(fd, gw[n], hs=(1e-5, 1e-6), tol=1e-6)
+        assert ok, (n, errs)
