@@ -44,7 +44,7 @@ typedef enum {
     IGR_ERR_INVALID_ARG = 1, /* rejected before any launch */
     IGR_ERR_OOM = 2,         /* an allocation failed */
     IGR_ERR_CUDA = 3,        /* a CUDA call failed */
-    IGR_ERR_NONFINITE = 4,   /* a stage produced a NaN/Inf (e.g. negative pressure) */
+    IGR_ERR_NONFINITE = 4,   /* a stage produced a NaN/Inf value or time step */
     IGR_ERR_TIMEOUT = 5,     /* reserved for bounded device-side waits */
     IGR_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
 } igr_status;
@@ -147,6 +147,30 @@ igr_status igr_solve_sigma(igr_ctx *ctx, const void *q, void *sigma_inout, int s
  * FP32 otherwise). */
 igr_status igr_rhs(igr_ctx *ctx, const void *q, const void *sigma, void *rhs, igr_dtype dtype);
 
+/* Discrete adjoint of one SSP-RK3 step with a fixed dt: the transpose of the
+ * Jacobian of (q, Sigma) -> (q', Sigma') that igr_step(ctx, 1, dt) computes
+ * (Sigma enters through the warm start of the Jacobi sweeps, so it is part
+ * of the state), applied to (lam_q_np1, lam_sigma_np1):
+ *   lam_q_n     = (dq'/dq)^T lam_q_np1 + (dSigma'/dq)^T lam_sigma_np1
+ *   lam_sigma_n = (dq'/dSigma)^T lam_q_np1 + (dSigma'/dSigma)^T lam_sigma_np1
+ *   grad_jet_w[j] += the same product's derivative in jet j's velocity w_j.
+ * It is the hand-written reverse of every piece of the stage (RK combination,
+ * flux divergence, local LF flux with p + Sigma, 5th-order reconstruction,
+ * Jacobi sweeps in the variable mu = lambda / diagonal, IGR source, boundary
+ * and jet-blend index mapping); the forward step is recomputed from (q_n,
+ * sigma_n) and every Sigma iterate kept. Non-smooth points follow the
+ * forward's branch (max(aL, aR): the side taken, aR on a tie; |u|: sign(u)).
+ * q_n, sigma_n: device buffers in the storage dtype (dtype); lam_*: device
+ * buffers in the arithmetic type (FP64 for IGR_F64, else FP32; 5 n and n
+ * values; outputs may not alias inputs); grad_jet_w: host array of njets
+ * doubles or NULL (synchronises when given). The first call allocates a
+ * workspace of about (29 + 3 sweeps) n stored values plus 30 n arithmetic
+ * values through the context's allocator. The scatter steps use atomics, so
+ * FP32 results vary in the last bits from run to run. */
+igr_status igr_adjoint_step(igr_ctx *ctx, const void *q_n, const void *sigma_n,
+                            const void *lam_q_np1, const void *lam_sigma_np1, void *lam_q_n,
+                            void *lam_sigma_n, double *grad_jet_w, double dt, igr_dtype dtype);
+
 /* The SSP-RK3 stage combination alone, exactly as the stage kernel stores it:
  *   out = qn + w [(qs - qn) + dt L],  w = 1, 1/4, 2/3 for stage = 1, 2, 3
  * (Gottlieb-Shu SSP-RK3 in increment form). qn, qs, out: device buffers of
@@ -196,6 +220,15 @@ igr_status igr_get_dt(igr_ctx *ctx, double *dt);
 
 /* Synchronise the stream and report pending asynchronous errors. */
 igr_status igr_sync(igr_ctx *ctx);
+
+/* Warnings seen since the last call or the last igr_set_state (synchronises):
+ * IGR_WARN_FACE_POSITIVITY when a reconstructed face state had rho <= 0 or
+ * p <= 0 (its LF speed is then not a number and the other side's speed is
+ * used, as in the scheme's definition; the step goes on). Errors are returned
+ * as by igr_sync. igr_set_state drops the warnings and errors still pending
+ * from the state it replaces. */
+#define IGR_WARN_FACE_POSITIVITY 2
+igr_status igr_get_flags(igr_ctx *ctx, int *flags);
 
 /* Per-kernel timing with CUDA events on the context stream. While enabled,
  * every launch is bracketed by an event pair; igr_profile_read synchronises

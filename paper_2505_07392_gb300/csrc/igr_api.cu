@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "../../include/igr.h"
@@ -48,12 +49,26 @@ struct igr_ctx {
     double *jets_dev;
     int cur;            // index of the current Sigma buffer
     int speed_nblocks;  // valid entries of blockmax for the current state (0: stale)
+    int warn_flags;     // IGR_WARN_* seen at synchronising calls since the last igr_get_flags
     bool profiling;
     std::vector<cudaEvent_t> ev;  // start/stop pairs of the pending launches
     std::vector<int> ev_class;
     long long prof_launches[KC_COUNT];
     double prof_ms[KC_COUNT];
     char err[512];
+    // adjoint workspace (allocated by the first igr_adjoint_step)
+    struct Adj {
+        bool ready;
+        void *qs[2];                       // stage-2/3 inputs (storage, 5 n)
+        void *its;                         // Sigma iterates, 3 x (sweeps + 1) x n (storage)
+        void *b;                           // source (storage, n)
+        void *lq0, *lqs, *lout, *Lb;       // adjoints (arithmetic type, 5 n)
+        void *lsig, *lb, *mu, *nl, *rb;    // adjoints (arithmetic type, n)
+        void *lamJ;                        // adjoint of the inflow tables (5 x plane)
+        double *gw;                        // jet gradient (njets)
+        Scalars *sc;                       // dt of the recomputed stages
+        std::vector<void *> all;
+    } adj;
 };
 
 static char g_create_err[512] = "";
@@ -151,7 +166,7 @@ __global__ void k_finalize_dt(const double *blockmax, int nblocks, Scalars *sc, 
         for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = nanmax_d(m, red[w]);
         double dt = fixed_dt > 0.0 ? fixed_dt : cfl_dx / m;
         if (fixed_dt <= 0.0) sc->speed = m;
-        if (!(dt > 0.0) || isinf(dt)) sc->err |= 1;
+        if (!(dt > 0.0) || isinf(dt)) sc->err |= ERRF_NONFINITE;
         sc->dt = dt;
         sc->t += dt;
     }
@@ -353,8 +368,9 @@ static igr_status read_flags(igr_ctx *c)
     if (err) {
         int zero = 0;
         CU(c, cudaMemcpy(&c->sc->err, &zero, sizeof(int), cudaMemcpyHostToDevice));
-        return fail(c, IGR_ERR_NONFINITE,
-                    "a stage produced a non-finite value or a non-positive face density/pressure");
+        c->warn_flags |= err & ERRF_FACE;
+        if (err & ERRF_NONFINITE)
+            return fail(c, IGR_ERR_NONFINITE, "a stage produced a non-finite value or time step");
     }
     return IGR_OK;
 }
@@ -477,6 +493,8 @@ igr_status igr_destroy(igr_ctx *c)
                     c->blockmax, c->sc, c->jets_dev};
     for (void *p : bufs)
         if (p) c->alloc.free(p, c->alloc.user);
+    for (void *p : c->adj.all)
+        if (p) c->alloc.free(p, c->alloc.user);
     delete c;
     return IGR_OK;
 }
@@ -535,6 +553,9 @@ igr_status igr_set_state(igr_ctx *c, const void *q, const void *sigma, igr_dtype
         CU(c, cudaMemsetAsync(c->sig[0], 0, c->g.n * dtype_bytes(storage_dtype(c->cfg.prec)), c->st));
     }
     c->speed_nblocks = 0;
+    // a new trajectory: flags pending from the replaced state are dropped
+    c->warn_flags = 0;
+    CU(c, cudaMemsetAsync(&c->sc->err, 0, sizeof(int), c->st));
     if (!on_device) CU(c, cudaStreamSynchronize(c->st));
     return IGR_OK;
 }
@@ -942,6 +963,120 @@ igr_status igr_destroy_batch(igr_batch *b)
     if (b->main) cudaStreamDestroy(b->main);
     delete b;
     return IGR_OK;
+}
+
+
+// ------------------------------------------------------------ adjoint
+
+static igr_status adj_alloc(igr_ctx *c, void **p, size_t bytes)
+{
+    igr_status s = ctx_alloc(c, p, bytes);
+    if (s == IGR_OK) c->adj.all.push_back(*p);
+    return s;
+}
+
+static igr_status ensure_adjoint(igr_ctx *c)
+{
+    if (c->adj.ready) return IGR_OK;
+    size_t n = (size_t)c->g.n, sb = c->ops->storage_bytes, cb = c->ops->compute_bytes;
+    int S = c->cfg.sweeps;
+    igr_status s = IGR_OK;
+    for (int i = 0; i < 2 && s == IGR_OK; i++) s = adj_alloc(c, &c->adj.qs[i], 5 * n * sb);
+    if (s == IGR_OK) s = adj_alloc(c, &c->adj.its, 3 * (size_t)(S + 1) * n * sb);
+    if (s == IGR_OK) s = adj_alloc(c, &c->adj.b, n * sb);
+    void **five[] = {&c->adj.lq0, &c->adj.lqs, &c->adj.lout, &c->adj.Lb};
+    for (void **p : five)
+        if (s == IGR_OK) s = adj_alloc(c, p, 5 * n * cb);
+    void **one[] = {&c->adj.lsig, &c->adj.lb, &c->adj.mu, &c->adj.nl, &c->adj.rb};
+    for (void **p : one)
+        if (s == IGR_OK) s = adj_alloc(c, p, n * cb);
+    if (s == IGR_OK) s = adj_alloc(c, &c->adj.lamJ, 5 * (size_t)c->g.plane * cb);
+    if (s == IGR_OK) s = adj_alloc(c, (void **)&c->adj.gw, (size_t)(c->cfg.njets > 0 ? c->cfg.njets : 1) * sizeof(double));
+    if (s == IGR_OK) s = adj_alloc(c, (void **)&c->adj.sc, sizeof(Scalars));
+    if (s != IGR_OK) return s;
+    CU(c, cudaMemsetAsync(c->adj.sc, 0, sizeof(Scalars), c->st));
+    c->adj.ready = true;
+    return IGR_OK;
+}
+
+igr_status igr_adjoint_step(igr_ctx *c, const void *q_n, const void *sigma_n, const void *lam_q_np1,
+                            const void *lam_sigma_np1, void *lam_q_n, void *lam_sigma_n, double *grad_jet_w,
+                            double dt, igr_dtype dtype)
+{
+    if (!c || !q_n || !sigma_n || !lam_q_np1 || !lam_sigma_np1 || !lam_q_n || !lam_sigma_n)
+        return fail(c, IGR_ERR_INVALID_ARG, "null buffer");
+    if (!(dt > 0.0)) return fail(c, IGR_ERR_INVALID_ARG, "the adjoint needs a fixed dt > 0");
+    if ((int)dtype != storage_dtype(c->cfg.prec))
+        return fail(c, IGR_ERR_UNSUPPORTED, "q_n and sigma_n must use the storage dtype");
+    if (c->profiling) return fail(c, IGR_ERR_INVALID_ARG, "disable profiling before the adjoint");
+    igr_status s = ensure_adjoint(c);
+    if (s != IGR_OK) return s;
+    auto &A = c->adj;
+    const Ops *o = c->ops;
+    size_t n = (size_t)c->g.n, sb = o->storage_bytes, cb = o->compute_bytes;
+    int S = c->cfg.sweeps;
+    auto it = [&](int st, int k) { return (void *)((unsigned char *)A.its + ((size_t)st * (S + 1) + k) * n * sb); };
+    const double wst[3] = {1.0, 0.25, 2.0 / 3.0};
+    Scalars hsc = {};
+    hsc.dt = dt;
+    CU(c, cudaMemcpyAsync(A.sc, &hsc, sizeof(Scalars), cudaMemcpyHostToDevice, c->st));
+    CU(c, cudaStreamSynchronize(c->st));  // hsc lives on this stack frame
+    // forward recompute: stage inputs and every Sigma iterate
+    const void *qs[3] = {q_n, A.qs[0], A.qs[1]};
+    CU(c, cudaMemcpyAsync(it(0, 0), sigma_n, n * sb, cudaMemcpyDeviceToDevice, c->st));
+    for (int st = 0; st < 3; st++) {
+        CU(c, o->source(c->g, c->p, c->tiles, inflow_of(c), qs[st], A.b, c->st));
+        for (int k = 0; k < S; k++)
+            CU(c, o->jacobi(c->g, c->p, c->tiles, qs[st], A.b, it(st, k), it(st, k + 1), c->st));
+        if (st < 2) {
+            CU(c, o->flux(c->g, c->p, c->tiles, inflow_of(c), st == 0 ? FLUX_STAGE1 : FLUX_STAGE2, qs[st],
+                          it(st, S), q_n, (void *)qs[st + 1], nullptr, A.sc, c->blockmax, &A.sc->err, c->st));
+            CU(c, cudaMemcpyAsync(it(st + 1, 0), it(st, S), n * sb, cudaMemcpyDeviceToDevice, c->st));
+        }
+    }
+    // reverse
+    void *lout = A.lout, *lqs = A.lqs, *lsig = A.lsig, *nl = A.nl;
+    CU(c, cudaMemcpyAsync(lout, lam_q_np1, 5 * n * cb, cudaMemcpyDeviceToDevice, c->st));
+    CU(c, cudaMemcpyAsync(lsig, lam_sigma_np1, n * cb, cudaMemcpyDeviceToDevice, c->st));
+    CU(c, cudaMemsetAsync(A.lq0, 0, 5 * n * cb, c->st));
+    CU(c, cudaMemsetAsync(A.lamJ, 0, 5 * (size_t)c->g.plane * cb, c->st));
+    CU(c, cudaMemsetAsync(A.rb, 0, n * cb, c->st));
+    for (int st = 2; st >= 0; st--) {
+        CU(c, o->adj_rk(lout, A.lq0, lqs, A.Lb, 5 * (long long)n, wst[st], dt, c->st));
+        CU(c, o->adj_rhs(c->g, c->p, inflow_of(c), qs[st], it(st, S), A.Lb, lqs, lsig, A.lamJ, c->st));
+        CU(c, cudaMemsetAsync(A.lb, 0, n * cb, c->st));
+        for (int k = S - 1; k >= 0; k--) {
+            CU(c, o->adj_jacobi(c->g, c->p, qs[st], it(st, k), it(st, k + 1), lsig, nl, A.lb, A.rb, A.mu, c->st));
+            std::swap(lsig, nl);
+        }
+        CU(c, o->adj_rho(c->g, qs[st], A.rb, lqs, c->st));
+        CU(c, o->adj_source(c->g, c->p, inflow_of(c), qs[st], A.lb, lqs, A.lamJ, c->st));
+        if (st == 0)  // the first stage reads q_n itself: lq0 += lqs
+            CU(c, o->adj_rk(lqs, A.lq0, lqs, A.Lb, 5 * (long long)n, 0.0, 0.0, c->st));
+        else
+            std::swap(lout, lqs);
+    }
+    CU(c, cudaMemcpyAsync(lam_q_n, A.lq0, 5 * n * cb, cudaMemcpyDeviceToDevice, c->st));
+    CU(c, cudaMemcpyAsync(lam_sigma_n, lsig, n * cb, cudaMemcpyDeviceToDevice, c->st));
+    if (grad_jet_w && c->cfg.njets > 0) {
+        CU(c, cudaMemsetAsync(A.gw, 0, c->cfg.njets * sizeof(double), c->st));
+        CU(c, o->adj_jets(c->g, c->p, c->jets_dev, c->cfg.njets, A.lamJ, A.gw, c->st));
+        std::vector<double> h(c->cfg.njets);
+        CU(c, cudaMemcpyAsync(h.data(), A.gw, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CU(c, cudaStreamSynchronize(c->st));
+        for (int j = 0; j < c->cfg.njets; j++) grad_jet_w[j] += h[j];
+    }
+    return IGR_OK;
+}
+
+
+igr_status igr_get_flags(igr_ctx *c, int *flags)
+{
+    if (!c || !flags) return fail(c, IGR_ERR_INVALID_ARG, "ctx and flags are required");
+    igr_status s = read_flags(c);
+    *flags = c->warn_flags;
+    c->warn_flags = 0;
+    return s;
 }
 
 }  // extern "C"

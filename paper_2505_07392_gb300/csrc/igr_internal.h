@@ -24,12 +24,15 @@ struct Phys {
     double dx, gamma, alpha, cfl;
 };
 
+// bits of Scalars::err
+enum { ERRF_NONFINITE = 1, ERRF_FACE = 2 };
+
 // Device-resident scalars of a context.
 struct Scalars {
     double dt;          // time step of the current step
     double t;           // accumulated simulated time
     double speed;       // max_d(|u_d| + c) of the state at the start of the step
-    int err;            // bit 0: non-finite value or non-positive face rho/p
+    int err;            // ERRF_NONFINITE: a non-finite value or dt; ERRF_FACE: a face with rho or p <= 0
     int pad;
 };
 
@@ -75,6 +78,28 @@ struct Ops {
     // kernel's epilogue stores it (L in the arithmetic type)
     cudaError_t (*rk_combine)(const void *qn, const void *qs, const void *L, void *out,
                               long long n, double dt, double w, cudaStream_t st);
+
+    // ---- adjoint (all adjoint buffers in the arithmetic type) ----
+    // lq0 += (1 - w) lout; lqs = w lout; Lb = w dt lout   (5 n values)
+    cudaError_t (*adj_rk)(const void *lout, void *lq0, void *lqs, void *Lb, long long n5, double w,
+                          double dt, cudaStream_t st);
+    // reverse of L(qs; sig): Lb -> lqs (5 fields), lsig, lamJ (5 x plane), by atomics
+    cudaError_t (*adj_rhs)(const Geom &, const Phys &, const Inflow &, const void *qs,
+                           const void *sig, const void *Lb, void *lqs, void *lsig, void *lamJ,
+                           cudaStream_t st);
+    // one reversed Jacobi sweep s_k -> F: lsig (in: adjoint of F) -> nl (adjoint
+    // of s_k); lb += mu; rb += d/d(1/rho); mu is scratch
+    cudaError_t (*adj_jacobi)(const Geom &, const Phys &, const void *q, const void *sk,
+                              const void *F, const void *lsig, void *nl, void *lb, void *rb,
+                              void *mu, cudaStream_t st);
+    // lqs[rho] -= rb / rho^2; rb = 0
+    cudaError_t (*adj_rho)(const Geom &, const void *q, void *rb, void *lqs, cudaStream_t st);
+    // reverse of the IGR source: lb -> lqs (rho, m), lamJ, by atomics
+    cudaError_t (*adj_source)(const Geom &, const Phys &, const Inflow &, const void *q,
+                              const void *lb, void *lqs, void *lamJ, cudaStream_t st);
+    // gw[n] += sum over the inflow face of s_n (rho_n lamJ_mz + rho_n w_n lamJ_E)
+    cudaError_t (*adj_jets)(const Geom &, const Phys &, const double *jets, int njets,
+                            const void *lamJ, double *gw, cudaStream_t st);
 };
 
 extern const Ops ops_f64, ops_f32, ops_f16, ops_bf16;

@@ -883,7 +883,8 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     const idx pl = (idx)g.plane;
     const idx fcol = (idx)(map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx + map_axis(i, g.nx, g.bc[0], g.bc[1]));
     const C gm1 = gamma - C(1);
-    bool bad = false;
+    bool bad = false;       // a face state with rho <= 0 or p <= 0 (warning)
+    bool nonfinite = false; // a non-finite output (error)
 
     // tile cells this thread loads each plane: shared and in-plane offsets
     int soff[LPT];
@@ -1006,6 +1007,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
                 if (mode == FLUX_RHS) {
 #pragma unroll
                     for (int u = 0; u < 5; u++) rhs.p[u][c] = Lv[u];
+                    nonfinite |= !isfinite((Lv[0] + Lv[1]) + (Lv[2] + Lv[3]) + Lv[4]);
                 } else {
                     C o[5], qb[5], qsv[5];
 #pragma unroll
@@ -1014,7 +1016,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
                         qb[u] = mode == FLUX_STAGE1 ? qsv[u] : cv(qnv[u]);
                     }
                     rk_store5(out, c, qb, qsv, Lv, dt32, dt, w32, wd, o);
-                    bad |= !isfinite((o[0] + o[1]) + (o[2] + o[3]) + o[4]);
+                    nonfinite |= !isfinite((o[0] + o[1]) + (o[2] + o[3]) + o[4]);
                     if (mode == FLUX_STAGE3) {
                         C sp = cell_speed(o[0], o[1], o[2], o[3], o[4], gamma, gm1);
                         smax = (sp > smax || sp != sp) ? sp : smax;
@@ -1029,7 +1031,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
         if (k + 1 < k1) commit();  // P <- plane k + 1
         __syncthreads();
     }
-    if (bad) atomicOr(err, 1);
+    if (nonfinite || bad) atomicOr(err, (nonfinite ? ERRF_NONFINITE : 0) | (bad ? ERRF_FACE : 0));
     if (mode == FLUX_STAGE3) {
         double m = block_max<NT>(double(smax));
         if (tid == 0)
@@ -1071,6 +1073,325 @@ __global__ void __launch_bounds__(SPEED_NT) k_speed(const S *__restrict__ q, lon
                                         ldc(q + 3 * n + c), ldc(q + 4 * n + c), gamma, gm1)));
     m = block_max<SPEED_NT>(m);
     if (threadIdx.x == 0) blockmax[blockIdx.x] = m;
+}
+
+// ---------------------------------------------------------------- adjoint
+// Reverse of one stage (discrete adjoint with dt frozen). Simple kernels: one
+// thread per face or cell, grid-stride loops, and atomics where the forward
+// gathers (each reverse stencil scatters to the cells it read). Adjoint
+// values are in the arithmetic type C. Non-smooth points follow the forward's
+// branch: the LF speed max(aL, aR) sends its adjoint to the side the forward
+// took (aR on a tie), |u| takes sign(u) with sign(0) = 0.
+
+__device__ __forceinline__ void aadd(float *p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void aadd(double *p, double v) { atomicAdd(p, v); }
+
+// forward value of field u (0..4 conserved, 5 Sigma) read at (i, j, kk):
+// index mapping plus the jet blend of the -z inflow face
+__device__ __forceinline__ C val_at(const S *q, const S *sig, const Geom &g, const C *W, const C *J,
+                                    int i, int j, int kk, int u)
+{
+    int mi = map_axis(i, g.nx, g.bc[0], g.bc[1]), mj = map_axis(j, g.ny, g.bc[2], g.bc[3]);
+    int mk = map_axis(kk, g.nz, g.bc[4], g.bc[5]);
+    idx f = (idx)(mj * g.nx + mi);
+    idx c = (idx)mk * (idx)g.plane + f;
+    if (u == 5) return ldc(sig + c);
+    C v = ldc(q + (size_t)u * (size_t)g.n + c);
+    if (kk < 0 && g.bc[4] == BC_INFLOW) v = (C(1) - W[f]) * v + J[(idx)u * (idx)g.plane + f];
+    return v;
+}
+
+// adjoint of that read: scatter `a` back to the cell(s) the value came from
+__device__ __forceinline__ void scatter_at(C *lq, C *lsig, C *lamJ, const Geom &g, const C *W, int i,
+                                           int j, int kk, int u, C a)
+{
+    int mi = map_axis(i, g.nx, g.bc[0], g.bc[1]), mj = map_axis(j, g.ny, g.bc[2], g.bc[3]);
+    int mk = map_axis(kk, g.nz, g.bc[4], g.bc[5]);
+    idx f = (idx)(mj * g.nx + mi);
+    idx c = (idx)mk * (idx)g.plane + f;
+    if (u == 5) {
+        aadd(lsig + c, a);
+        return;
+    }
+    if (kk < 0 && g.bc[4] == BC_INFLOW) {
+        aadd(lq + (size_t)u * (size_t)g.n + c, (C(1) - W[f]) * a);
+        aadd(lamJ + (idx)u * (idx)g.plane + f, a);
+        return;
+    }
+    aadd(lq + (size_t)u * (size_t)g.n + c, a);
+}
+
+__global__ void k_adj_rk(const C *lout, C *lq0, C *lqs, C *Lb, long long n5, C w, C dt)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n5;
+         c += (long long)gridDim.x * blockDim.x) {
+        C a = lout[c];
+        lq0[c] += (C(1) - w) * a;
+        lqs[c] = w * a;
+        Lb[c] = w * dt * a;
+    }
+}
+
+// reverse of the physical flux along D at a face state v = (rho, m, E) and
+// Sigma s: Fb (adjoint of F) and ab (adjoint of |u_D| + c) into vb, sb
+template <int D>
+__device__ __forceinline__ void flux_rev(const C v[5], C s, const C Fb[5], C ab, C gamma, C vb[5], C &sb)
+{
+    C rho = v[0], E = v[4], r = C(1) / rho;
+    C u[3] = {v[1] * r, v[2] * r, v[3] * r};
+    C ke = C(0.5) * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    C p = (gamma - C(1)) * (E - ke);
+    C P = p + s;
+    C c = sqrt(gamma * p * r);
+    C ub[3] = {C(0), C(0), C(0)}, rhob = C(0), Eb = C(0), Pb = C(0), pb = C(0);
+    rhob += Fb[0] * u[D];
+    ub[D] += Fb[0] * rho;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        vb[1 + a] += Fb[1 + a] * u[D];
+        ub[D] += Fb[1 + a] * v[1 + a];
+    }
+    Pb += Fb[1 + D] + Fb[4] * u[D];
+    Eb += Fb[4] * u[D];
+    ub[D] += Fb[4] * (E + P);
+    ub[D] += ab * (u[D] > C(0) ? C(1) : (u[D] < C(0) ? C(-1) : C(0)));
+    pb += ab * gamma / (C(2) * c * rho);
+    rhob -= ab * c / (C(2) * rho);
+    pb += Pb;
+    sb += Pb;
+    Eb += (gamma - C(1)) * pb;
+    C keb = -(gamma - C(1)) * pb;
+    rhob += keb * C(0.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#pragma unroll
+    for (int a = 0; a < 3; a++) ub[a] += keb * rho * u[a];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        vb[1 + a] += ub[a] * r;
+        rhob -= ub[a] * u[a] * r;
+    }
+    vb[0] += rhob;
+    vb[4] += Eb;
+}
+
+template <int D>
+__device__ __forceinline__ C fwd_flux(const C v[5], C s, C gamma, C F[5])
+{
+    C rho = v[0], E = v[4], r = C(1) / rho;
+    C u[3] = {v[1] * r, v[2] * r, v[3] * r};
+    C p = (gamma - C(1)) * (E - C(0.5) * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+    C P = p + s;
+    F[0] = rho * u[D];
+#pragma unroll
+    for (int a = 0; a < 3; a++) F[1 + a] = v[1 + a] * u[D] + (a == D ? P : C(0));
+    F[4] = (E + P) * u[D];
+    return fabs(u[D]) + sqrt(gamma * p * r);
+}
+
+// one thread per face normal to D: face f sits between cells f-1 and f
+template <int D>
+__global__ void k_adj_rhs(const S *q, const S *sig, const C *Lb, C *lq, C *lsig, C *lamJ, Geom g, C gamma,
+                          C inv_dx, const C *W, const C *J)
+{
+    const int nf[3] = {g.nx + (D == 0), g.ny + (D == 1), g.nz + (D == 2)};
+    const int nd = D == 0 ? g.nx : D == 1 ? g.ny : g.nz;
+    const long long total = (long long)nf[0] * nf[1] * nf[2];
+    const C cl[6] = {C(2.0 / 60), C(-13.0 / 60), C(47.0 / 60), C(27.0 / 60), C(-3.0 / 60), C(0)};
+    const C cr[6] = {C(0), C(-3.0 / 60), C(27.0 / 60), C(47.0 / 60), C(-13.0 / 60), C(2.0 / 60)};
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int c3[3];
+        c3[0] = (int)(t % nf[0]);
+        c3[1] = (int)((t / nf[0]) % nf[1]);
+        c3[2] = (int)(t / ((long long)nf[0] * nf[1]));
+        const int f = c3[D];
+        C Fb[5];
+#pragma unroll
+        for (int u = 0; u < 5; u++) {
+            C hi = C(0), lo = C(0);
+            if (f < nd) hi = Lb[(size_t)u * g.n + ((size_t)c3[2] * g.ny + c3[1]) * g.nx + c3[0]];
+            if (f >= 1) {
+                int cc[3] = {c3[0], c3[1], c3[2]};
+                cc[D] = f - 1;
+                lo = Lb[(size_t)u * g.n + ((size_t)cc[2] * g.ny + cc[1]) * g.nx + cc[0]];
+            }
+            Fb[u] = (hi - lo) * inv_dx;
+        }
+        C sv[6][6];
+#pragma unroll
+        for (int m = 0; m < 6; m++) {
+            int cc[3] = {c3[0], c3[1], c3[2]};
+            cc[D] += m - 3;
+#pragma unroll
+            for (int u = 0; u < 6; u++) sv[m][u] = val_at(q, sig, g, W, J, cc[0], cc[1], cc[2], u);
+        }
+        C L[6], R[6];
+#pragma unroll
+        for (int u = 0; u < 6; u++) {
+            L[u] = rec_left(sv[0][u], sv[1][u], sv[2][u], sv[3][u], sv[4][u]);
+            R[u] = rec_right(sv[1][u], sv[2][u], sv[3][u], sv[4][u], sv[5][u]);
+        }
+        C FL[5], FR[5];
+        C aL = fwd_flux<D>(L, L[5], gamma, FL);
+        C aR = fwd_flux<D>(R, R[5], gamma, FR);
+        C lam = aL > aR ? aL : aR;
+        C Lbv[5] = {C(0), C(0), C(0), C(0), C(0)}, Rbv[5] = {C(0), C(0), C(0), C(0), C(0)};
+        C FLb[5], FRb[5], lamb = C(0);
+#pragma unroll
+        for (int u = 0; u < 5; u++) {
+            FLb[u] = C(0.5) * Fb[u];
+            FRb[u] = C(0.5) * Fb[u];
+            Lbv[u] += C(0.5) * lam * Fb[u];
+            Rbv[u] -= C(0.5) * lam * Fb[u];
+            lamb -= C(0.5) * (R[u] - L[u]) * Fb[u];
+        }
+        C sLb = C(0), sRb = C(0);
+        flux_rev<D>(L, L[5], FLb, aL > aR ? lamb : C(0), gamma, Lbv, sLb);
+        flux_rev<D>(R, R[5], FRb, aL > aR ? C(0) : lamb, gamma, Rbv, sRb);
+#pragma unroll
+        for (int m = 0; m < 6; m++) {
+            int cc[3] = {c3[0], c3[1], c3[2]};
+            cc[D] += m - 3;
+#pragma unroll
+            for (int u = 0; u < 5; u++) {
+                C a = cl[m] * Lbv[u] + cr[m] * Rbv[u];
+                if (a != C(0)) scatter_at(lq, lsig, lamJ, g, W, cc[0], cc[1], cc[2], u, a);
+            }
+            C a = cl[m] * sLb + cr[m] * sRb;
+            if (a != C(0)) scatter_at(lq, lsig, lamJ, g, W, cc[0], cc[1], cc[2], 5, a);
+        }
+    }
+}
+
+// neighbour of cell (i,j,k) across face d (0:-x .. 5:+z); false on a
+// non-periodic domain boundary (no face term there)
+__device__ __forceinline__ bool nbr(const Geom &g, int i, int j, int k, int d, idx &out)
+{
+    int c[3] = {i, j, k}, n[3] = {g.nx, g.ny, g.nz};
+    int ax = d >> 1;
+    c[ax] += (d & 1) ? 1 : -1;
+    if (c[ax] < 0 || c[ax] >= n[ax]) {
+        if (g.bc[d] != BC_PERIODIC) return false;
+        c[ax] = c[ax] < 0 ? c[ax] + n[ax] : c[ax] - n[ax];
+    }
+    out = ((idx)c[2] * (idx)g.ny + (idx)c[1]) * (idx)g.nx + (idx)c[0];
+    return true;
+}
+
+// mu = lambda / D_i, lb += mu
+__global__ void k_adj_jac_mu(const S *q, const C *lsig, C *mu, C *lb, Geom g, C beta)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.n;
+         t += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / g.plane);
+        C ri = C(1) / ldc(q + t), diag = ri;
+        for (int d = 0; d < 6; d++) {
+            idx m;
+            if (nbr(g, i, j, k, d, m)) diag += beta * C(0.5) * (ri + C(1) / ldc(q + m));
+        }
+        C mv = lsig[t] / diag;
+        mu[t] = mv;
+        lb[t] += mv;
+    }
+}
+
+// gather form of the transposed sweep (the neighbour relation is symmetric):
+// nl_m = sum_i beta c_im mu_i; rb_m += mu_m (beta/2 sum s_nb - F_m (1 + beta nf/2))
+//                                  + sum_i mu_i beta/2 (s_m - F_i)
+__global__ void k_adj_jac_gather(const S *q, const S *sk, const S *F, const C *mu, C *nl, C *rb, Geom g,
+                                 C beta)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.n;
+         t += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / g.plane);
+        C rm = C(1) / ldc(q + t), sm = ldc(sk + t), Fm = ldc(F + t), mum = mu[t];
+        C acc = C(0), ssum = C(0), rbm = C(0);
+        int nfc = 0;
+        for (int d = 0; d < 6; d++) {
+            idx n;
+            if (!nbr(g, i, j, k, d, n)) continue;
+            C rn = C(1) / ldc(q + n), mun = mu[n];
+            acc += beta * C(0.5) * (rm + rn) * mun;
+            ssum += ldc(sk + n);
+            nfc++;
+            rbm += mun * C(0.5) * beta * (sm - ldc(F + n));
+        }
+        rbm += mum * (C(0.5) * beta * ssum - Fm * (C(1) + C(0.5) * beta * C(nfc)));
+        nl[t] = acc;
+        rb[t] += rbm;
+    }
+}
+
+__global__ void k_adj_rho(const S *q, C *rb, C *lqs, long long n)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        C rho = ldc(q + t);
+        lqs[t] -= rb[t] / (rho * rho);
+        rb[t] = C(0);
+    }
+}
+
+// reverse of the source at one cell: lambda_b -> u at the 6 neighbours -> (rho, m) there
+__global__ void k_adj_source(const S *q, const C *lb, C *lq, C *lamJ, Geom g, C alpha, C inv2dx, const C *W,
+                             const C *J)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.n;
+         t += (long long)gridDim.x * blockDim.x) {
+        C bb = lb[t];
+        if (bb == C(0)) continue;
+        int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / g.plane);
+        C rho[2][3], m[2][3][3], u[2][3][3];  // [+/-][direction][component]
+        for (int c = 0; c < 3; c++)
+            for (int sgn = 0; sgn < 2; sgn++) {
+                int cc[3] = {i, j, k};
+                cc[c] += sgn == 0 ? 1 : -1;
+                rho[sgn][c] = val_at(q, nullptr, g, W, J, cc[0], cc[1], cc[2], 0);
+                for (int a = 0; a < 3; a++) {
+                    m[sgn][c][a] = val_at(q, nullptr, g, W, J, cc[0], cc[1], cc[2], 1 + a);
+                    u[sgn][c][a] = m[sgn][c][a] / rho[sgn][c];
+                }
+            }
+        C G[3][3];
+        for (int a = 0; a < 3; a++)
+            for (int c = 0; c < 3; c++) G[a][c] = (u[0][c][a] - u[1][c][a]) * inv2dx;
+        C tr = G[0][0] + G[1][1] + G[2][2];
+        for (int c = 0; c < 3; c++)
+            for (int a = 0; a < 3; a++) {
+                C Gb = alpha * (C(2) * G[c][a] + (a == c ? C(2) * tr : C(0))) * bb;
+                C ub = Gb * inv2dx;
+                for (int sgn = 0; sgn < 2; sgn++) {
+                    C us = sgn == 0 ? ub : -ub;
+                    int cc[3] = {i, j, k};
+                    cc[c] += sgn == 0 ? 1 : -1;
+                    C r = rho[sgn][c];
+                    scatter_at(lq, nullptr, lamJ, g, W, cc[0], cc[1], cc[2], 1 + a, us / r);
+                    scatter_at(lq, nullptr, lamJ, g, W, cc[0], cc[1], cc[2], 0, -us * m[sgn][c][a] / (r * r));
+                }
+            }
+    }
+}
+
+// gw[n] += sum over the inflow face of s_n (rho_n lamJ_mz + rho_n w_n lamJ_E); one block per jet
+__global__ void k_adj_jets(const double *jets, const C *lamJ, double *gw, int nx, int ny, double dx)
+{
+    const double *jt = jets + 7 * blockIdx.x;
+    long long plane = (long long)nx * ny;
+    double acc = 0.0;
+    for (long long f = threadIdx.x; f < plane; f += blockDim.x) {
+        int i = (int)(f % nx), j = (int)(f / nx);
+        double x = (i + 0.5) * dx, y = (j + 0.5) * dx;
+        double r = sqrt((x - jt[0]) * (x - jt[0]) + (y - jt[1]) * (y - jt[1]));
+        double sn = 0.5 * (1.0 - tanh((r - jt[2]) / (jt[6] * dx)));
+        acc += sn * (jt[3] * double(lamJ[3 * plane + f]) + jt[3] * jt[4] * double(lamJ[4 * plane + f]));
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) gw[blockIdx.x] += red[0];
 }
 
 // ------------------------------------------------------------ launchers
@@ -1173,11 +1494,72 @@ cudaError_t launch_rk_combine(const void *qn, const void *qs, const void *L, voi
     return cudaGetLastError();
 }
 
+int adj_blocks(long long n)
+{
+    long long b = (n + 255) / 256;
+    return (int)(b < 152 * 32 ? (b > 0 ? b : 1) : 152 * 32);
+}
+
+cudaError_t launch_adj_rk(const void *lout, void *lq0, void *lqs, void *Lb, long long n5, double w,
+                          double dt, cudaStream_t st)
+{
+    k_adj_rk<<<adj_blocks(n5), 256, 0, st>>>((const C *)lout, (C *)lq0, (C *)lqs, (C *)Lb, n5, C(w), C(dt));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_rhs(const Geom &g, const Phys &p, const Inflow &in, const void *qs, const void *sig,
+                           const void *Lb, void *lqs, void *lsig, void *lamJ, cudaStream_t st)
+{
+    long long nfx = (long long)(g.nx + 1) * g.ny * g.nz, nfy = (long long)g.nx * (g.ny + 1) * g.nz,
+              nfz = (long long)g.nx * g.ny * (g.nz + 1);
+    const C *W = (const C *)in.W, *J = (const C *)in.J;
+    k_adj_rhs<0><<<adj_blocks(nfx), 256, 0, st>>>((const S *)qs, (const S *)sig, (const C *)Lb, (C *)lqs,
+                                                   (C *)lsig, (C *)lamJ, g, C(p.gamma), C(1.0 / p.dx), W, J);
+    k_adj_rhs<1><<<adj_blocks(nfy), 256, 0, st>>>((const S *)qs, (const S *)sig, (const C *)Lb, (C *)lqs,
+                                                   (C *)lsig, (C *)lamJ, g, C(p.gamma), C(1.0 / p.dx), W, J);
+    k_adj_rhs<2><<<adj_blocks(nfz), 256, 0, st>>>((const S *)qs, (const S *)sig, (const C *)Lb, (C *)lqs,
+                                                   (C *)lsig, (C *)lamJ, g, C(p.gamma), C(1.0 / p.dx), W, J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_jacobi(const Geom &g, const Phys &p, const void *q, const void *sk, const void *F,
+                              const void *lsig, void *nl, void *lb, void *rb, void *mu, cudaStream_t st)
+{
+    C beta = C(p.alpha / (p.dx * p.dx));
+    k_adj_jac_mu<<<adj_blocks(g.n), 256, 0, st>>>((const S *)q, (const C *)lsig, (C *)mu, (C *)lb, g, beta);
+    k_adj_jac_gather<<<adj_blocks(g.n), 256, 0, st>>>((const S *)q, (const S *)sk, (const S *)F,
+                                                       (const C *)mu, (C *)nl, (C *)rb, g, beta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_rho(const Geom &g, const void *q, void *rb, void *lqs, cudaStream_t st)
+{
+    k_adj_rho<<<adj_blocks(g.n), 256, 0, st>>>((const S *)q, (C *)rb, (C *)lqs, g.n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_source(const Geom &g, const Phys &p, const Inflow &in, const void *q, const void *lb,
+                              void *lqs, void *lamJ, cudaStream_t st)
+{
+    k_adj_source<<<adj_blocks(g.n), 256, 0, st>>>((const S *)q, (const C *)lb, (C *)lqs, (C *)lamJ, g,
+                                                   C(p.alpha), C(0.5 / p.dx), (const C *)in.W, (const C *)in.J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_jets(const Geom &g, const Phys &p, const double *jets, int njets, const void *lamJ,
+                            double *gw, cudaStream_t st)
+{
+    if (njets <= 0) return cudaSuccess;
+    k_adj_jets<<<njets, 256, 0, st>>>(jets, (const C *)lamJ, gw, g.nx, g.ny, p.dx);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 extern const Ops IGR_OPS = {
     (int)sizeof(S), (int)sizeof(C), launch_source, launch_jacobi, launch_flux, flux_blocks,
-    launch_speed, launch_rk_combine,
+    launch_speed, launch_rk_combine, launch_adj_rk, launch_adj_rhs, launch_adj_jacobi, launch_adj_rho,
+    launch_adj_source, launch_adj_jets,
 };
 
 }  // namespace igr

@@ -77,6 +77,7 @@ def lib():
             "igr_solve_sigma_noalloc": (i, [C.POINTER(Config), p, p, i, p]),
             "igr_noalloc_max_cells": (C.c_size_t, [i]),
             "igr_noalloc_last_error": (C.c_char_p, []),
+            "igr_adjoint_step": (i, [p, p, p, p, p, p, p, C.POINTER(d), d, i]),
             "igr_set_tiles": (i, [p, i, i, i]),
             "igr_get_tiles": (i, [p, C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
             "igr_autotune": (i, [p, i]),
@@ -87,6 +88,7 @@ def lib():
             "igr_batch_last_error": (C.c_char_p, [p]),
             "igr_destroy_batch": (i, [p]),
             "igr_sync": (i, [p]),
+            "igr_get_flags": (i, [p, C.POINTER(i)]),
             "igr_profile_enable": (i, [p, i]),
             "igr_profile_read": (i, [p, i, C.POINTER(C.c_longlong), C.POINTER(d)]),
             "igr_last_error": (C.c_char_p, [p]),
@@ -256,6 +258,12 @@ class Solver:
     def sync(self):
         self._check(lib().igr_sync(self.h))
 
+    def flags(self) -> int:
+        """Warnings since the last call (IGR_WARN_FACE_POSITIVITY = 2)."""
+        f = C.c_int()
+        self._check(lib().igr_get_flags(self.h, C.byref(f)))
+        return f.value
+
     # -- stand-alone operators on caller buffers (storage dtype, CUDA)
     def solve_sigma(self, q, sigma, sweeps: int):
         """In place on sigma: b from q, then `sweeps` warm-started Jacobi sweeps."""
@@ -280,6 +288,24 @@ class Solver:
                                          C.c_void_p(L.data_ptr()), C.c_void_p(out.data_ptr()),
                                          int(qn.numel()), int(stage), float(dt)))
         return out
+
+    # -- adjoint
+    def adjoint_step(self, q_n, sigma_n, lam_q, lam_sigma, dt: float):
+        """Adjoint of one SSP-RK3 step with fixed dt from the stored state
+        (q_n, sigma_n): returns (lam_q_n, lam_sigma_n, grad_jet_w)."""
+        import torch
+        ct = compute_torch_dtype(self.precision)
+        lam_q = lam_q.to(ct).contiguous()
+        lam_sigma = lam_sigma.to(ct).contiguous()
+        out_q = torch.empty_like(lam_q)
+        out_s = torch.empty_like(lam_sigma)
+        nj = len(self.case.jets)
+        gw = (C.c_double * max(1, nj))()
+        self._check(lib().igr_adjoint_step(self.h, C.c_void_p(q_n.data_ptr()), C.c_void_p(sigma_n.data_ptr()),
+                                           C.c_void_p(lam_q.data_ptr()), C.c_void_p(lam_sigma.data_ptr()),
+                                           C.c_void_p(out_q.data_ptr()), C.c_void_p(out_s.data_ptr()),
+                                           gw if nj else None, float(dt), _dt_code(q_n.dtype)))
+        return out_q, out_s, [gw[j] for j in range(nj)]
 
     # -- launch shapes
     def set_tiles(self, zc_source: int, zc_jacobi: int, zc_flux: int):

@@ -1,0 +1,237 @@
+"""The GPU adjoint (igr_adjoint_step) against the FP64 oracle adjoint and
+against finite differences of the GPU forward.
+
+Tolerances: FP64 1e-10 relative L2 against the oracle (the scatter steps use
+atomics, so only the summation order differs); FP32 1e-4 (the adjoint of an
+FP32 forward). Jet-velocity gradients of the plane-pressure objective: 1e-4
+relative against central differences (h = 1e-4) of the FP64 GPU forward, as
+the target states.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_07392_gb300 import inputs
+from paper_2505_07392_gb300.inputs import INFLOW, OUTFLOW, PERIODIC, Case
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-10, "f32": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_07392_gb300 import build
+    build.build()
+    yield
+
+
+def _offset_state(c, seed):
+    rng = np.random.Generator(np.random.Philox(seed))
+    z, y, x = np.meshgrid(*[(np.arange(n) + 0.5) / n for n in (c.nz, c.ny, c.nx)], indexing="ij")
+    ph = rng.uniform(0, 2 * np.pi, size=8)
+    tp = 2 * np.pi
+    rho = 1 + 0.2 * np.sin(tp * x + ph[0]) * np.cos(tp * y + ph[1]) + 0.1 * np.sin(tp * z + ph[2])
+    u = 0.45 + 0.2 * np.sin(tp * y + ph[3])
+    v = -0.4 + 0.15 * np.cos(tp * x + ph[4]) * np.sin(tp * z)
+    w = 0.42 + 0.2 * np.sin(tp * x + ph[5])
+    p = 1 + 0.1 * np.cos(tp * (x + y) + ph[6])
+    return np.stack([rho, rho * u, rho * v, rho * w, p / 0.4 + 0.5 * rho * (u * u + v * v + w * w)])
+
+
+def _jets_case(n=16):
+    dx = 1.0 / n
+    w = 2 * math.sqrt(2.8)
+    return Case("jets", n, n - 2, n - 6, dx, alpha=dx * dx, sweeps=3,
+                bc=(OUTFLOW,) * 4 + (INFLOW, OUTFLOW),
+                jets=[(0.3, 0.45, 3 * dx, 1.0, w, 2.0, 1.0), (0.65, 0.5, 2.5 * dx, 1.0, 0.8 * w, 2.0, 1.0)])
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+CASES = {
+    "periodic": lambda: (Case("p", 12, 10, 8, 1 / 12, alpha=1 / 144, sweeps=3, bc=(PERIODIC,) * 6), None),
+    "outflow": lambda: (Case("o", 12, 10, 8, 1 / 12, alpha=1 / 144, sweeps=4, bc=(OUTFLOW,) * 6), None),
+    "jets": lambda: (_jets_case(), "jets"),
+}
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_adjoint_step_matches_oracle(precision, name):
+    import torch
+    from paper_2505_07392_gb300 import igr
+    c, kind = CASES[name]()
+    if kind == "jets":
+        q0 = oracle.run(c, inputs.jet_initial_state(c), None, 3, 1e-3)[0]
+        s0 = oracle.run(c, q0, None, 1, 1e-3)[1]
+        dt = 1e-3
+    else:
+        q0 = _offset_state(c, 4)
+        s0 = 0.05 * _offset_state(c, 5)[0]
+        dt = 0.01
+    rng = np.random.Generator(np.random.Philox(9))
+    lq, ls = rng.normal(size=q0.shape), rng.normal(size=s0.shape)
+    oq, osig, ogw = oracle.adjoint_step(c, q0, s0, dt, lq, ls)
+    st, ct = igr.storage_torch_dtype(precision), igr.compute_torch_dtype(precision)
+    with igr.Solver(c, precision) as s:
+        gq, gs, ggw = s.adjoint_step(torch.from_numpy(q0).to(st).cuda(), torch.from_numpy(s0).to(st).cuda(),
+                                     torch.from_numpy(lq).to(ct).cuda(), torch.from_numpy(ls).to(ct).cuda(), dt)
+        gq, gs = gq.double().cpu().numpy(), gs.double().cpu().numpy()
+    assert _rel(gq, oq) <= TOL[precision], _rel(gq, oq)
+    assert _rel(gs, osig) <= TOL[precision], _rel(gs, osig)
+    if kind == "jets":
+        assert _rel(ggw, ogw) <= TOL[precision], (ggw, ogw)
+
+
+def _rollout_oracle(c, q0, nsteps, dt, k):
+    """FP64 oracle objective and its jet gradient (no checkpointing)."""
+    g = c.gamma
+
+    def P(q):
+        qq = q[:, k:k + 2]
+        p = (g - 1) * (qq[4] - 0.5 * (qq[1] ** 2 + qq[2] ** 2 + qq[3] ** 2) / qq[0])
+        return p.mean()
+
+    def dP(q):
+        out = np.zeros_like(q)
+        qq = q[:, k:k + 2]
+        nn = qq[0].size
+        out[0, k:k + 2] = (g - 1) * 0.5 * (qq[1] ** 2 + qq[2] ** 2 + qq[3] ** 2) / qq[0] ** 2 / nn
+        for a in range(3):
+            out[1 + a, k:k + 2] = -(g - 1) * qq[1 + a] / qq[0] / nn
+        out[4, k:k + 2] = (g - 1) / nn
+        return out
+
+    states = [(q0, np.zeros((c.nz, c.ny, c.nx)))]
+    J = 0.0
+    for _ in range(nsteps):
+        q1, s1, _ = oracle.run(c, states[-1][0], states[-1][1], 1, dt)
+        states.append((q1, s1))
+        J += dt * P(q1)
+    lq = np.zeros_like(q0)
+    ls = np.zeros((c.nz, c.ny, c.nx))
+    gw = np.zeros(len(c.jets))
+    for n in range(nsteps, 0, -1):
+        lq = lq + dt * dP(states[n][0])
+        lq, ls, g1 = oracle.adjoint_step(c, states[n - 1][0], states[n - 1][1], dt, lq, ls)
+        gw += g1
+    return J, gw
+
+
+def _four_jets(n):
+    c = inputs.jets4(n)
+    return c
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_jet_gradient_small(precision):
+    """Reduced jet workload (32^3, 4 Mach-2 jets, 12 steps, checkpoints every
+    5, pressure on the plane between layers 4 and 5, which the jets reach in
+    that time): dJ/dw by the GPU adjoint rollout against the oracle's FP64
+    adjoint and against central differences of the FP64 GPU forward."""
+    import torch
+    from paper_2505_07392_gb300 import adjoint
+    n, nsteps, dt = 32, 12, 2e-3
+    c = _four_jets(n)
+    k = 4
+    q0 = inputs.jet_initial_state(c)
+    w0 = [j[4] for j in c.jets]
+    J, gw = adjoint.rollout_jet_gradient(c, precision, torch.from_numpy(q0).cuda(), nsteps, dt, k,
+                                         checkpoint_every=5)
+    Jo, gwo = _rollout_oracle(c, q0, nsteps, dt, k)
+    assert abs(J - Jo) <= (1e-10 if precision == "f64" else 1e-5) * abs(Jo)
+    assert max(abs(x) for x in gwo) > 1e-8  # the jets reach the plane (leakage alone is ~1e-15)
+    # the gradient is a small difference of larger terms (the four symmetric
+    # jets' oracle values already differ at the 5th digit), so 1e-4 for both
+    assert _rel(gw, gwo) <= 1e-4, (gw, gwo)
+    h = 1e-4
+    for jn in range(len(w0)):
+        vals = []
+        for sgn in (1, -1):
+            w = list(w0)
+            w[jn] += sgn * h
+            cj = adjoint.with_jet_velocities(c, w)
+            Jh, _ = _objective_gpu(cj, q0, nsteps, dt, k)
+            vals.append(Jh)
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(gw[jn] - fd) <= 1e-4 * max(abs(fd), 1e-3 * max(abs(x) for x in gwo)), (jn, gw[jn], fd)
+
+
+def _objective_gpu(c, q0, nsteps, dt, k, precision="f64"):
+    import torch
+    from paper_2505_07392_gb300 import adjoint, igr
+    with igr.Solver(c, precision) as s:
+        s.set_state(torch.from_numpy(q0).cuda())
+        J = 0.0
+        for _ in range(nsteps):
+            s.step(1, fixed_dt=dt, sync=False)
+            q, _ = s.get_state(torch.float64)
+            J += dt * float(adjoint.plane_pressure(q, k, c.gamma))
+    return J, None
+
+
+def test_igr_step_autograd_function():
+    """torch.autograd through IGRStep equals the oracle's adjoint of a step."""
+    import torch
+    from paper_2505_07392_gb300 import adjoint, igr
+    c = Case("o", 12, 10, 8, 1 / 12, alpha=1 / 144, sweeps=3, bc=(OUTFLOW,) * 6)
+    q0 = _offset_state(c, 6)
+    s0 = 0.05 * _offset_state(c, 7)[0]
+    rng = np.random.Generator(np.random.Philox(2))
+    lq, ls = rng.normal(size=q0.shape), rng.normal(size=s0.shape)
+    with igr.Solver(c, "f64") as s:
+        q = torch.from_numpy(q0).cuda().requires_grad_(True)
+        sg = torch.from_numpy(s0).cuda().requires_grad_(True)
+        q1, s1 = adjoint.IGRStep.apply(q, sg, s, 0.01)
+        loss = (q1 * torch.from_numpy(lq).cuda()).sum() + (s1 * torch.from_numpy(ls).cuda()).sum()
+        loss.backward()
+        gq, gs = q.grad.cpu().numpy(), sg.grad.cpu().numpy()
+    oq, osig, _ = oracle.adjoint_step(c, q0, s0, 0.01, lq, ls)
+    assert _rel(gq, oq) <= 1e-10 and _rel(gs, osig) <= 1e-10
+
+
+@pytest.mark.slow
+def test_jet_gradient_full_size():
+    """The jet workload at full size: 128^3, 4 Mach-2 jets of radius 6 cells,
+    300 steps with fixed dt = 5.5e-4 (CFL about 0.35 at the jet exit speed)
+    and checkpoints every 30; FP32 adjoint against central differences
+    (h = 1e-4) of the FP64 GPU forward. In those 300 steps (t = 0.165) the
+    jets' disturbance travels less than half the box: the mean pressure on
+    z = 0.75 (between layers 95 and 96) never changes, and both the adjoint
+    and the differences give dJ/dw = 0 there; on z = 0.25 (layers 31, 32),
+    which the jets reach, the gradient is checked to 1e-4."""
+    import torch
+    from paper_2505_07392_gb300 import adjoint
+    c = inputs.jets4(128, steps=300)
+    nsteps, dt = 300, 5.5e-4
+    q0 = inputs.jet_initial_state(c)
+    w0 = [j[4] for j in c.jets]
+    J75, gw75 = adjoint.rollout_jet_gradient(c, "f32", torch.from_numpy(q0).cuda(), nsteps, dt, 95,
+                                             checkpoint_every=30)
+    J, gw = adjoint.rollout_jet_gradient(c, "f32", torch.from_numpy(q0).cuda(), nsteps, dt, 31,
+                                         checkpoint_every=30)
+    h = 1e-4
+    fds, fds75 = [], []
+    for jn in range(len(w0)):
+        vals, vals75 = [], []
+        for sgn in (1, -1):
+            w = list(w0)
+            w[jn] += sgn * h
+            cj = adjoint.with_jet_velocities(c, w)
+            vals.append(_objective_gpu(cj, q0, nsteps, dt, 31)[0])
+            vals75.append(_objective_gpu(cj, q0, nsteps, dt, 95)[0])
+        fds.append((vals[0] - vals[1]) / (2 * h))
+        fds75.append((vals75[0] - vals75[1]) / (2 * h))
+    scale = max(abs(f) for f in fds)
+    assert scale > 1e-6  # the jets reach z = 0.25
+    for jn in range(len(w0)):
+        assert abs(gw[jn] - fds[jn]) <= 1e-4 * scale, (jn, gw[jn], fds[jn])
+        assert fds75[jn] == 0.0 and abs(gw75[jn]) <= 1e-8 * scale, (jn, gw75[jn], fds75[jn])

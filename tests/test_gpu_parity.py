@@ -202,8 +202,10 @@ def test_dt_rule():
 
 
 def test_nonfinite_flag():
-    """A state with negative pressure is flagged as IGR_ERR_NONFINITE at the
-    next synchronising call (host-side detection; nothing faults)."""
+    """Negative pressure in a cell: with a fixed dt the step goes on and the
+    face-positivity warning is raised; with the CFL rule the wave speed (and
+    so dt) is not a number, reported as IGR_ERR_NONFINITE at the next
+    synchronising call (detection on the host; nothing faults)."""
     import torch
     from paper_2505_07392_gb300 import igr
     c = inputs.blast(16)
@@ -211,12 +213,17 @@ def test_nonfinite_flag():
     q0[4, 8, 8, 8] = -1.0  # negative energy -> negative pressure
     with igr.Solver(c, "f32") as s:
         s.set_state(torch.from_numpy(q0).cuda())
+        s.step(1, fixed_dt=1e-4)
+        assert s.flags() & 2
+        assert s.flags() == 0  # reading clears
+        s.set_state(torch.from_numpy(q0).cuda())
         with pytest.raises(igr.IGRError) as e:
-            s.step(1, fixed_dt=1e-4)
+            s.step(1)
         assert e.value.status == igr.ERR_NONFINITE
         # the context stays usable
         s.set_state(torch.from_numpy(inputs.initial_state(c)).cuda())
-        s.step(1, fixed_dt=1e-4)
+        s.step(1)
+        assert s.flags() == 0
 
 
 # ------------------------------------------------- full-size sampled parity
