@@ -198,6 +198,23 @@ def test_igr_step_autograd_function():
     assert _rel(gq, oq) <= 1e-10 and _rel(gs, osig) <= 1e-10
 
 
+def test_jet_rollout_autograd_function():
+    """torch.autograd through JetRollout: J and dJ/dw equal the oracle's
+    (16^3, 4 jets, 6 steps, checkpoints every 4)."""
+    import torch
+    from paper_2505_07392_gb300 import adjoint
+    c = _four_jets(16)
+    nsteps, dt, k = 6, 4e-3, 2
+    q0 = inputs.jet_initial_state(c)
+    w = torch.tensor([j[4] for j in c.jets], dtype=torch.float64, requires_grad=True)
+    J = adjoint.JetRollout.apply(w, c, "f64", torch.from_numpy(q0).cuda(), nsteps, dt, k, 4)
+    (3.0 * J).backward()
+    Jo, gwo = _rollout_oracle(c, q0, nsteps, dt, k)
+    assert abs(float(J) - Jo) <= 1e-10 * abs(Jo)
+    assert max(abs(x) for x in gwo) > 1e-8
+    assert _rel(w.grad.numpy(), 3.0 * np.asarray(gwo)) <= 1e-8
+
+
 @pytest.mark.slow
 def test_jet_gradient_full_size():
     """The jet workload at full size: 128^3, 4 Mach-2 jets of radius 6 cells,
