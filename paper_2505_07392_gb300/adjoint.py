@@ -34,8 +34,10 @@ def plane_pressure(q: torch.Tensor, k: int, gamma: float) -> torch.Tensor:
 
 
 def _dP(q: torch.Tensor, k: int, gamma: float) -> torch.Tensor:
-    x = q.detach().to(torch.float64).requires_grad_(True)
-    (g,) = torch.autograd.grad(plane_pressure(x, k, gamma), x)
+    # grad mode is off inside an autograd.Function's forward
+    with torch.enable_grad():
+        x = q.detach().to(torch.float64).requires_grad_(True)
+        (g,) = torch.autograd.grad(plane_pressure(x, k, gamma), x)
     return g
 
 

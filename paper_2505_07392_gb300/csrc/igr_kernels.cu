@@ -807,9 +807,74 @@ constexpr int PW = TX + 6, PH = TY + 6;          // plane tile with a halo of 3
 constexpr int NPLANE = TY * PW + 6 * TX;         // tile cells that are read (no corners)
 constexpr int LPT = (NPLANE + NT - 1) / NT;      // tile cells loaded per thread
 
-__host__ __device__ constexpr size_t flux_smem_elems()
+// The plane tile and the z-queue keep the six face variables as three pairs,
+// (rho, m_x), (m_y, m_z), (E, Sigma): a stencil point of a pair is one 8-byte
+// (16-byte in FP64) shared load, and the reconstruction of a pair is one
+// packed FP32x2 multiply-add per term (fma.rn.f32x2 on sm_100 and later;
+// each lane rounds exactly like the scalar fma.rn.f32).
+template <typename T> struct PairOf;
+template <> struct PairOf<float> { using T = float2; };
+template <> struct PairOf<double> { using T = double2; };
+using C2 = typename PairOf<C>::T;
+
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b)
 {
-    return 6 * PH * PW + 5 * TY * (TX + 1) + 5 * (TY + 1) * TX;
+    return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c)
+{
+    return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
+}
+__device__ __forceinline__ C2 pset(C x, C y)
+{
+    C2 r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+__device__ __forceinline__ C2 bcast(C v) { return pset(v, v); }
+
+// 5th-order face values of a pair (weights as in rec_left / rec_right)
+__device__ __forceinline__ C2 rec_left2(C2 a, C2 b, C2 c, C2 d, C2 e)
+{
+    C2 t = pmul(bcast(C(2.0 / 60.0)), a);
+    t = pfma(bcast(C(-13.0 / 60.0)), b, t);
+    t = pfma(bcast(C(47.0 / 60.0)), c, t);
+    t = pfma(bcast(C(27.0 / 60.0)), d, t);
+    return pfma(bcast(C(-3.0 / 60.0)), e, t);
+}
+__device__ __forceinline__ C2 rec_right2(C2 b, C2 c, C2 d, C2 e, C2 f)
+{
+    C2 t = pmul(bcast(C(-3.0 / 60.0)), b);
+    t = pfma(bcast(C(27.0 / 60.0)), c, t);
+    t = pfma(bcast(C(47.0 / 60.0)), d, t);
+    t = pfma(bcast(C(-13.0 / 60.0)), e, t);
+    return pfma(bcast(C(2.0 / 60.0)), f, t);
+}
+
+constexpr int TILE2 = 3 * PH * PW;  // pairs in one plane tile
+constexpr int RING = 7;             // plane tiles resident: k-2..k+3 and k+4 in flight
+
+// Storage equal to the arithmetic type: plane tiles are copied global ->
+// shared with cp.async (4- or 8-byte elements), which holds no registers.
+constexpr bool kAsyncTile = sizeof(S) == sizeof(C);
+__device__ __forceinline__ void cp_async_elem(C *dst, const S *src)
+{
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(C) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// shared bytes: the ring of plane tiles (pairs), two sets of x- and y-face fluxes
+__host__ __device__ constexpr size_t flux_smem_bytes()
+{
+    return RING * TILE2 * sizeof(C2) + 2 * (5 * TY * (TX + 1) + 5 * (TY + 1) * TX) * sizeof(C);
 }
 
 // tile cell e (0 <= e < NPLANE) -> position (lx, ly) in the PW x PH tile
@@ -820,60 +885,63 @@ __device__ __forceinline__ void plane_cell(int e, int &lx, int &ly)
     else { e -= 3 * TX + TY * PW; ly = TY + 3 + e / TX; lx = 3 + e % TX; }
 }
 
-// one column value set (rho, mx, my, mz, E, Sigma) at in-plane offset f of
-// plane kk, with the -z jet blend for kk < 0
-__device__ __forceinline__ void col_load(const Fin<6> &in, const Geom &g, const C *W, const C *J,
-                                         idx f, int kk, C v[6])
-{
-    idx c = (idx)map_axis(kk, g.nz, g.bc[4], g.bc[5]) * (idx)g.plane + f;
-#pragma unroll
-    for (int u = 0; u < 6; u++) v[u] = ldc(in.p[u] + c);
-    if (kk < 0 && g.bc[4] == BC_INFLOW) {
-        C w = C(1) - W[f];
-#pragma unroll
-        for (int u = 0; u < 5; u++) v[u] = w * v[u] + J[(idx)u * (idx)g.plane + f];
-    }
-}
-
 template <int D>
-__device__ __forceinline__ void face_from_stencil(const C (&s)[6][6], C gamma, C gm1, C *F,
+__device__ __forceinline__ void face_from_stencil(const C2 (&s)[6][3], C gamma, C gm1, C *F,
                                                   bool &bad)
 {
     C L[6], R[6];
 #pragma unroll
-    for (int u = 0; u < 6; u++) {
-        L[u] = rec_left(s[0][u], s[1][u], s[2][u], s[3][u], s[4][u]);
-        R[u] = rec_right(s[1][u], s[2][u], s[3][u], s[4][u], s[5][u]);
+    for (int p = 0; p < 3; p++) {
+        C2 l = rec_left2(s[0][p], s[1][p], s[2][p], s[3][p], s[4][p]);
+        C2 r = rec_right2(s[1][p], s[2][p], s[3][p], s[4][p], s[5][p]);
+        L[2 * p] = l.x;
+        L[2 * p + 1] = l.y;
+        R[2 * p] = r.x;
+        R[2 * p + 1] = r.y;
     }
     lf_flux2<D>(L, R, gamma, gm1, F, bad);
 }
 
-// face along D from six consecutive tile cells starting at element `at`,
-// `step` elements apart, of every variable plane of P
+// face along D (0, 1) from six consecutive cells of one plane tile starting
+// at element `at`, `step` elements apart
 template <int D>
-__device__ __forceinline__ void tile_face(const C *P, int at, int step, C gamma, C gm1, C *F,
+__device__ __forceinline__ void tile_face(const C2 *T, int at, int step, C gamma, C gm1, C *F,
                                           bool &bad)
 {
-    C s[6][6];
+    C2 s[6][3];
 #pragma unroll
     for (int m = 0; m < 6; m++)
 #pragma unroll
-        for (int u = 0; u < 6; u++) s[m][u] = P[u * PH * PW + at + m * step];
+        for (int p = 0; p < 3; p++) s[m][p] = T[p * PH * PW + at + m * step];
     face_from_stencil<D>(s, gamma, gm1, F, bad);
 }
 
 // registers per thread such that NWARP / 4 warps fit one sub-partition's 16K
 constexpr int FLUX_MAXREG = sizeof(C) == 8 ? 224 : 128;
 
+// The block keeps a ring of RING plane tiles (halo 3 in x and y) in shared
+// memory: plane kk lives in slot (kk - k0 + 3) mod RING. Iteration k (from
+// k0 - 1 to k1 - 1), one barrier each:
+//   - start the copy of plane k + 4 into the slot of plane k - 3 (read for
+//     the last time before the previous barrier);
+//   - row warps: divergence and stage combination of plane k - 1 (face
+//     buffers of parity k - 1), then the z-face k + 1/2 from planes
+//     k - 2..k + 3 of the ring at the warp's own cells;
+//   - all warps (k >= k0): the x- and y-faces of plane k into the face
+//     buffers of parity k;
+//   - complete the copy of plane k + 4, barrier.
+// Planes k0 - 3..k0 + 2 are filled before the loop (with the boundary index
+// mapping and, below an inflow face, the jet blend). Every plane is read from
+// global memory once per block; nothing relies on the L1 cache.
 template <int mode>
 __global__ void __maxnreg__(FLUX_MAXREG)
     k_flux(Fin<6> in, Fin<5> qn, Fout<5> out, Frhs rhs, Geom g, C gamma, C half_inv_dx,
            const Scalars *sc, double *blockmax, int *err, const C *W, const C *J, int zc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *P = reinterpret_cast<C *>(smem_raw);  // [6][PH][PW]
-    C *FX = P + 6 * PH * PW;                 // [5][TY][TX+1]
-    C *FY = FX + 5 * TY * (TX + 1);          // [5][TY+1][TX]
+    C2 *P = reinterpret_cast<C2 *>(smem_raw);        // [RING][3][PH][PW]
+    C *FXb = reinterpret_cast<C *>(P + RING * TILE2); // [2][5][TY][TX+1]
+    C *FYb = FXb + 2 * 5 * TY * (TX + 1);            // [2][5][TY+1][TX]
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
@@ -881,10 +949,12 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     const int i = x0 + lane, j = y0 + (rowwarp ? w : 0);
     const bool active = rowwarp && i < g.nx && j < g.ny;
     const idx pl = (idx)g.plane;
-    const idx fcol = (idx)(map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx + map_axis(i, g.nx, g.bc[0], g.bc[1]));
+    const idx own = (idx)(j * g.nx + i);
+    const int tcell = (w + 3) * PW + lane + 3;  // this row-warp lane's cell in a tile
     const C gm1 = gamma - C(1);
     bool bad = false;       // a face state with rho <= 0 or p <= 0 (warning)
     bool nonfinite = false; // a non-finite output (error)
+    auto tile = [&](int kk) { return P + ((kk - k0 + 3) % RING) * TILE2; };
 
     // tile cells this thread loads each plane: shared and in-plane offsets
     int soff[LPT];
@@ -902,23 +972,64 @@ __global__ void __maxnreg__(FLUX_MAXREG)
                             map_axis(x0 + lx - 3, g.nx, g.bc[0], g.bc[1]));
         }
     }
-    S Rg[LPT][6];  // prefetched tile cells of the next plane (raw)
-    auto fetch = [&](int kk) {
+
+    // planes k0 - 3..k0 + 2, loaded and stored directly (index mapping in z,
+    // jet blend below an inflow face)
+#pragma unroll 1
+    for (int kk = k0 - 3; kk < k0 + 3; kk++) {
+        C2 *T = tile(kk);
+        const idx zb = (idx)zmap(kk, g) * pl;
+        const bool blend = kk < 0 && g.bc[4] == BC_INFLOW;
 #pragma unroll
         for (int r = 0; r < LPT; r++)
             if (soff[r] >= 0) {
-                idx c = (idx)kk * pl + goff[r];
+                C v[6];
 #pragma unroll
-                for (int u = 0; u < 6; u++) Rg[r][u] = ldr(in.p[u] + c);
+                for (int u = 0; u < 6; u++) v[u] = ldc(in.p[u] + zb + goff[r]);
+                if (blend) {
+                    C wf = C(1) - W[goff[r]];
+#pragma unroll
+                    for (int u = 0; u < 5; u++) v[u] = wf * v[u] + J[(idx)u * pl + goff[r]];
+                }
+#pragma unroll
+                for (int p = 0; p < 3; p++) T[p * PH * PW + soff[r]] = pset(v[2 * p], v[2 * p + 1]);
             }
-    };
-    auto commit = [&]() {
+    }
+
+    // plane kk >= k0 + 3 of the pipeline: FP32/FP64 storage copies with
+    // cp.async; 16-bit storage loads raw values into registers at `fetch`
+    // and converts and stores them at `land`
+    S Rg[LPT][6];  // (unused with cp.async)
+    auto fetch = [&](int kk) {
+        C2 *T = tile(kk);
+        const idx zb = (idx)zmap(kk, g) * pl;
 #pragma unroll
         for (int r = 0; r < LPT; r++)
-            if (soff[r] >= 0)
+            if (soff[r] >= 0) {
 #pragma unroll
-                for (int u = 0; u < 6; u++) P[u * PH * PW + soff[r]] = cv(Rg[r][u]);
+                for (int u = 0; u < 6; u++) {
+                    if constexpr (kAsyncTile)
+                        cp_async_elem(&T[(u >> 1) * PH * PW + soff[r]].x + (u & 1), in.p[u] + zb + goff[r]);
+                    else
+                        Rg[r][u] = ldr(in.p[u] + zb + goff[r]);
+                }
+            }
+        if constexpr (kAsyncTile) cp_async_commit();
     };
+    auto land = [&](int kk) {
+        if constexpr (kAsyncTile) {
+            cp_async_wait_all();
+        } else {
+            C2 *T = tile(kk);
+#pragma unroll
+            for (int r = 0; r < LPT; r++)
+                if (soff[r] >= 0)
+#pragma unroll
+                    for (int p = 0; p < 3; p++)
+                        T[p * PH * PW + soff[r]] = pset(cv(Rg[r][2 * p]), cv(Rg[r][2 * p + 1]));
+        }
+    };
+    __syncthreads();
 
     C dt32 = C(0), w32 = C(1);
     double dt = 0.0, wd = 1.0;
@@ -930,107 +1041,94 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     }
     C smax = C(0);  // running wave-speed maximum (FP32 here: FP64 is slow on this GPU)
 
-    // Register queue of the column's z-stencil: at iteration k the slots hold
-    // planes k-2..k+3 and give the z-face k + 1/2. The loop starts one plane
-    // early so that the face k0 - 1/2 comes out of the same instructions as
-    // every other z-face (bitwise equal to the neighbouring chunk's copy).
-    // Qn holds the column's next plane (loaded one iteration ahead; planes
-    // k0 + 2 and up never need the jet blend).
-    C Q[6][6];
-    S Qn[6];
-    auto col_raw = [&](int kk) {
-        idx c = (idx)zmap(kk, g) * pl + fcol;
+    C Fzm[5], Fzp[5];
+    S qnv[5];  // q^n of plane k - 1 (stages 2 and 3), loaded one iteration ahead
+
+    // divergence and stage combination of plane kk (face buffers of parity kk)
+    auto finish = [&](int kk) {
+        const C *FX = FXb + (kk & 1) * 5 * TY * (TX + 1);
+        const C *FY = FYb + (kk & 1) * 5 * (TY + 1) * TX;
+        idx c = (idx)kk * pl + own;
+        C Lv[5];
 #pragma unroll
-        for (int u = 0; u < 6; u++) Qn[u] = ldr(in.p[u] + c);
-    };
-    if (rowwarp) {
-#pragma unroll
-        for (int s = 1; s < 6; s++) col_load(in, g, W, J, fcol, k0 - 4 + s, Q[s]);
-        col_raw(k0 + 2);
-    }
-    fetch(k0);
-    C Fzm[5];
-    for (int k = k0 - 1; k < k1; k++) {
-        if (k >= k0 && k + 1 < k1) fetch(k + 1);
-        S qnv[5];
-        if (k >= k0 && active && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3)) {
-            idx c = (idx)k * pl + (idx)(j * g.nx + i);
-#pragma unroll
-            for (int u = 0; u < 5; u++) qnv[u] = ldr(qn.p[u] + c);
+        for (int u = 0; u < 5; u++) {
+            C dfx = FX[(u * TY + w) * (TX + 1) + lane + 1] - FX[(u * TY + w) * (TX + 1) + lane];
+            C dfy = FY[(u * (TY + 1) + w + 1) * TX + lane] - FY[(u * (TY + 1) + w) * TX + lane];
+            C dfz = Fzp[u] - Fzm[u];
+            Lv[u] = -((dfx + dfy) + dfz) * half_inv_dx;
         }
-        C Fzp[5];
+        if (mode == FLUX_RHS) {
+#pragma unroll
+            for (int u = 0; u < 5; u++) rhs.p[u][c] = Lv[u];
+            nonfinite |= !isfinite((Lv[0] + Lv[1]) + (Lv[2] + Lv[3]) + Lv[4]);
+        } else {
+            const C2 *T = tile(kk);
+            C2 a = T[tcell], b = T[PH * PW + tcell], e = T[2 * PH * PW + tcell];
+            const C qsv[5] = {a.x, a.y, b.x, b.y, e.x};
+            C o[5], qb[5];
+#pragma unroll
+            for (int u = 0; u < 5; u++) qb[u] = mode == FLUX_STAGE1 ? qsv[u] : cv(qnv[u]);
+            rk_store5(out, c, qb, qsv, Lv, dt32, dt, w32, wd, o);
+            nonfinite |= !isfinite((o[0] + o[1]) + (o[2] + o[3]) + o[4]);
+            if (mode == FLUX_STAGE3) {
+                C sp = cell_speed(o[0], o[1], o[2], o[3], o[4], gamma, gm1);
+                smax = (sp > smax || sp != sp) ? sp : smax;
+            }
+        }
+    };
+
+    for (int k = k0 - 1; k < k1; k++) {
+        const bool more = k + 4 <= k1 + 2;  // plane k + 4 feeds the z-faces
+        if (more) fetch(k + 4);
         if (rowwarp) {
+            if (k > k0 && active) finish(k - 1);
 #pragma unroll
-            for (int s = 0; s < 5; s++)
+            for (int u = 0; u < 5; u++) Fzm[u] = Fzp[u];
+            if (k >= k0 && active && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3)) {
+                idx c = (idx)k * pl + own;
 #pragma unroll
-                for (int u = 0; u < 6; u++) Q[s][u] = Q[s + 1][u];
+                for (int u = 0; u < 5; u++) qnv[u] = ldr(qn.p[u] + c);
+            }
+            C2 sz[6][3];  // z-stencil: planes k - 2..k + 3 at this cell
 #pragma unroll
-            for (int u = 0; u < 6; u++) Q[5][u] = cv(Qn[u]);
-            if (k + 1 < k1) col_raw(k + 4);
-            face_from_stencil<2>(Q, gamma, gm1, Fzp, bad);  // z-face k + 1/2
+            for (int m = 0; m < 6; m++) {
+                const C2 *T = tile(k - 2 + m);
+#pragma unroll
+                for (int p = 0; p < 3; p++) sz[m][p] = T[p * PH * PW + tcell];
+            }
+            face_from_stencil<2>(sz, gamma, gm1, Fzp, bad);  // z-face k + 1/2
         }
         if (k >= k0) {
-            // P holds plane k
+            const C2 *T = tile(k);
+            C *FX = FXb + (k & 1) * 5 * TY * (TX + 1);
+            C *FY = FYb + (k & 1) * 5 * (TY + 1) * TX;
             C F[5];
             if (rowwarp) {
                 // x-face at the low side of cell `lane` of row w (tile cells lane-3..lane+2)
-                tile_face<0>(P, (w + 3) * PW + lane, 1, gamma, gm1, F, bad);
+                tile_face<0>(T, (w + 3) * PW + lane, 1, gamma, gm1, F, bad);
 #pragma unroll
                 for (int u = 0; u < 5; u++) FX[(u * TY + w) * (TX + 1) + lane] = F[u];
                 // y-face below row w in column lane (tile rows w-3..w+2)
-                tile_face<1>(P, w * PW + lane + 3, PW, gamma, gm1, F, bad);
+                tile_face<1>(T, w * PW + lane + 3, PW, gamma, gm1, F, bad);
 #pragma unroll
                 for (int u = 0; u < 5; u++) FY[(u * (TY + 1) + w) * TX + lane] = F[u];
             } else {
                 // y-face above the last row, column lane
-                tile_face<1>(P, TY * PW + lane + 3, PW, gamma, gm1, F, bad);
+                tile_face<1>(T, TY * PW + lane + 3, PW, gamma, gm1, F, bad);
 #pragma unroll
                 for (int u = 0; u < 5; u++) FY[(u * (TY + 1) + TY) * TX + lane] = F[u];
                 if (lane < TY) {
                     // x-face at the high end of row `lane`
-                    tile_face<0>(P, (lane + 3) * PW + TX, 1, gamma, gm1, F, bad);
+                    tile_face<0>(T, (lane + 3) * PW + TX, 1, gamma, gm1, F, bad);
 #pragma unroll
                     for (int u = 0; u < 5; u++) FX[(u * TY + lane) * (TX + 1) + TX] = F[u];
                 }
             }
-            __syncthreads();  // faces complete; reads of P done
-            if (active) {
-                idx c = (idx)k * pl + (idx)(j * g.nx + i);
-                C Lv[5];
-#pragma unroll
-                for (int u = 0; u < 5; u++) {
-                    C dfx = FX[(u * TY + w) * (TX + 1) + lane + 1] - FX[(u * TY + w) * (TX + 1) + lane];
-                    C dfy = FY[(u * (TY + 1) + w + 1) * TX + lane] - FY[(u * (TY + 1) + w) * TX + lane];
-                    C dfz = Fzp[u] - Fzm[u];
-                    Lv[u] = -((dfx + dfy) + dfz) * half_inv_dx;
-                }
-                if (mode == FLUX_RHS) {
-#pragma unroll
-                    for (int u = 0; u < 5; u++) rhs.p[u][c] = Lv[u];
-                    nonfinite |= !isfinite((Lv[0] + Lv[1]) + (Lv[2] + Lv[3]) + Lv[4]);
-                } else {
-                    C o[5], qb[5], qsv[5];
-#pragma unroll
-                    for (int u = 0; u < 5; u++) {
-                        qsv[u] = Q[2][u];
-                        qb[u] = mode == FLUX_STAGE1 ? qsv[u] : cv(qnv[u]);
-                    }
-                    rk_store5(out, c, qb, qsv, Lv, dt32, dt, w32, wd, o);
-                    nonfinite |= !isfinite((o[0] + o[1]) + (o[2] + o[3]) + o[4]);
-                    if (mode == FLUX_STAGE3) {
-                        C sp = cell_speed(o[0], o[1], o[2], o[3], o[4], gamma, gm1);
-                        smax = (sp > smax || sp != sp) ? sp : smax;
-                    }
-                }
-            }
         }
-        if (rowwarp) {
-#pragma unroll
-            for (int u = 0; u < 5; u++) Fzm[u] = Fzp[u];
-        }
-        if (k + 1 < k1) commit();  // P <- plane k + 1
+        if (more) land(k + 4);
         __syncthreads();
     }
+    if (active) finish(k1 - 1);  // the last plane (its faces are behind the final barrier)
     if (nonfinite || bad) atomicOr(err, (nonfinite ? ERRF_NONFINITE : 0) | (bad ? ERRF_FACE : 0));
     if (mode == FLUX_STAGE3) {
         double m = block_max<NT>(double(smax));
@@ -1441,7 +1539,7 @@ cudaError_t launch_flux(const Geom &g, const Phys &p, const Tiles &t, const Infl
                         const void *qs, const void *sig, const void *qn, void *out, void *rhs,
                         const Scalars *sc, double *blockmax, int *err, cudaStream_t st)
 {
-    size_t smem = flux_smem_elems() * sizeof(C);
+    size_t smem = flux_smem_bytes();
     auto go = [&](auto kern) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
