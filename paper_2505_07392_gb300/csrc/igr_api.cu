@@ -196,24 +196,25 @@ const Ops *igr::ops_for(int p)
     return nullptr;
 }
 
-// Longest z-chunk (at most 128 planes) that still gives the kernel at least
-// six waves of blocks on 152 SMs: every block starts by loading the planes
-// below its chunk, so longer chunks amortise that prologue, while too few
-// blocks leave SMs idle in the last wave. (tx, ty): columns per block.
-static int default_zc(const Geom &g, int tx, int ty)
+// Longest z-chunk (at most 128 planes, at least 16) that still gives the
+// kernel six waves of blocks on 152 SMs holding `resident` blocks each: every
+// block starts by loading the planes below its chunk, so longer chunks
+// amortise that prologue, while too few blocks leave SMs idle in the last
+// wave. (tx, ty): columns per block.
+static int default_zc(const Geom &g, int tx, int ty, int resident)
 {
     long long cols = (long long)((g.nx + tx - 1) / tx) * ((g.ny + ty - 1) / ty);
     int zc = 128;
-    while (zc > 16 && cols * ((g.nz + zc - 1) / zc) < 6 * 152) zc /= 2;
+    while (zc > 16 && cols * ((g.nz + zc - 1) / zc) < 6LL * 152 * resident) zc /= 2;
     return zc > g.nz ? g.nz : zc;
 }
 
 Tiles igr::default_tiles(const Geom &g)
 {
     Tiles t;
-    t.zc_source = default_zc(g, 32, 8);
-    t.zc_jacobi = default_zc(g, 128, 8);
-    t.zc_flux = default_zc(g, 32, 15);
+    t.zc_source = default_zc(g, 32, 8, 5);
+    t.zc_jacobi = default_zc(g, 128, 8, 3);
+    t.zc_flux = default_zc(g, 32, 15, 1);
     return t;
 }
 
