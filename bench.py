@@ -173,6 +173,10 @@ def run_form(case, precision, steps, warmup, sync_all, e2e_steps=0):
                  ("other", igr.KC_OTHER))}
         s.profile(False)
         s.sync()
+        # FP64 diagnostics of the final state (outside the timed region)
+        d = s.diagnose()
+        res["diag"] = {"sigma_residual": d["sigma_residual"], "rho_min": d["rho_min"],
+                       "p_min": d["p_min"], "sigma_absmax": d["sigma_absmax"]}
         res.update(ms=ms, prof=prof, clocks=clocks)
         if e2e_steps:
             res["e2e"] = run_e2e(s, case, precision, e2e_steps, sync_all)
@@ -432,6 +436,7 @@ def main():
         "kernels": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in v.items()}
                     for k, v in per_kernel.items()},
         "clocks": res["clocks"],
+        "diagnostics_fp64": res["diag"],
     }
     if plain:
         line["plain"] = plain

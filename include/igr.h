@@ -230,6 +230,29 @@ igr_status igr_sync(igr_ctx *ctx);
 #define IGR_WARN_FACE_POSITIVITY 2
 igr_status igr_get_flags(igr_ctx *ctx, int *flags);
 
+/* Diagnostics of the current state, evaluated in FP64 on the device from the
+ * stored values (every stored value converts to double exactly):
+ *  - totals over cells of rho, m and E times dx^3 (conserved exactly up to
+ *    round-off under periodic boundaries);
+ *  - minima of rho and p = (gamma - 1)(E - |m|^2 / (2 rho)), maximum |Sigma|;
+ *  - the residual of the elliptic equation for Sigma (Eq. igrelliptic):
+ *    ||A Sigma - b||_2 / ||b||_2 over cells (||A Sigma||_2 when b = 0), with
+ *    A the operator the Jacobi sweeps relax (face coefficients
+ *    (1/rho_i + 1/rho_nb)/2, faces on non-periodic boundaries dropped) and b
+ *    the IGR source of the current state. After igr_step, Sigma is the last
+ *    stage's solve and the state has advanced since, so this measures how
+ *    well Sigma solves the equation for the state it is paired with.
+ * Per-block partial sums are reduced in a fixed order (deterministic). The
+ * first call allocates (10 x 1216 doubles) through the context allocator.
+ * Synchronises; errors as igr_sync. */
+typedef struct {
+    double mass, momentum[3], energy;
+    double rho_min, p_min, sigma_absmax;
+    double b_norm;          /* ||b||_2 over cells */
+    double sigma_residual;  /* ||A Sigma - b||_2 / ||b||_2 */
+} igr_diagnostics;
+igr_status igr_diagnose(igr_ctx *ctx, igr_diagnostics *out);
+
 /* Per-kernel timing with CUDA events on the context stream. While enabled,
  * every launch is bracketed by an event pair; igr_profile_read synchronises
  * and returns, for kernel class k (0 source, 1 jacobi, 2 flux, 3 other),

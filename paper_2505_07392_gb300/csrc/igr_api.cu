@@ -45,6 +45,7 @@ struct igr_ctx {
     void *W, *J;
     double *blockmax;
     long long blockmax_len;
+    double *diag_part;  // per-block diagnostics partials (allocated by the first igr_diagnose)
     Scalars *sc;
     double *jets_dev;
     int cur;            // index of the current Sigma buffer
@@ -503,7 +504,7 @@ igr_status igr_destroy(igr_ctx *c)
     cudaStreamSynchronize(c->st);
     if (c->profiling) prof_collect(c);
     void *bufs[] = {c->q[0], c->q[1], c->q[2], c->sig[0], c->sig[1], c->b, c->W, c->J,
-                    c->blockmax, c->sc, c->jets_dev};
+                    c->blockmax, c->sc, c->jets_dev, c->diag_part};
     for (void *p : bufs)
         if (p) c->alloc.free(p, c->alloc.user);
     for (void *p : c->adj.all)
@@ -1082,6 +1083,43 @@ igr_status igr_adjoint_step(igr_ctx *c, const void *q_n, const void *sigma_n, co
     return IGR_OK;
 }
 
+
+igr_status igr_diagnose(igr_ctx *c, igr_diagnostics *out)
+{
+    if (!c || !out) return fail(c, IGR_ERR_INVALID_ARG, "ctx and out are required");
+    if (!c->diag_part) {
+        igr_status s = ctx_alloc(c, (void **)&c->diag_part, sizeof(double) * DIAG_PARTS * DIAG_BLOCKS_MAX);
+        if (s != IGR_OK) return s;
+    }
+    int nb = 0;
+    Inflow in{c->W, c->J};
+    prof_begin(c, KC_OTHER);
+    CU(c, c->ops->diag(c->g, c->p, in, c->q[0], c->sig[c->cur], c->diag_part, &nb, c->st));
+    prof_end(c);
+    std::vector<double> part((size_t)nb * DIAG_PARTS);
+    CU(c, cudaMemcpyAsync(part.data(), c->diag_part, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->st));
+    igr_status s = read_flags(c);  // synchronises
+    if (s != IGR_OK) return s;
+    double acc[DIAG_PARTS] = {0, 0, 0, 0, 0, 0, 0, INFINITY, INFINITY, 0};
+    for (int b = 0; b < nb; b++) {  // fixed order: deterministic
+        const double *x = part.data() + (size_t)b * DIAG_PARTS;
+        for (int t = 0; t < 7; t++) acc[t] += x[t];
+        acc[7] = fmin(acc[7], x[7]);
+        acc[8] = fmin(acc[8], x[8]);
+        acc[9] = fmax(acc[9], x[9]);
+    }
+    double vol = c->p.dx * c->p.dx * c->p.dx;
+    out->mass = acc[0] * vol;
+    for (int a = 0; a < 3; a++) out->momentum[a] = acc[1 + a] * vol;
+    out->energy = acc[4] * vol;
+    out->rho_min = acc[7];
+    out->p_min = acc[8];
+    out->sigma_absmax = acc[9];
+    out->b_norm = sqrt(acc[6]);
+    out->sigma_residual = acc[6] > 0 ? sqrt(acc[5] / acc[6]) : sqrt(acc[5]);
+    return IGR_OK;
+}
 
 igr_status igr_get_flags(igr_ctx *c, int *flags)
 {

@@ -100,7 +100,17 @@ struct Ops {
     // gw[n] += sum over the inflow face of s_n (rho_n lamJ_mz + rho_n w_n lamJ_E)
     cudaError_t (*adj_jets)(const Geom &, const Phys &, const double *jets, int njets,
                             const void *lamJ, double *gw, cudaStream_t st);
+
+    // ---- diagnostics (FP64) ----
+    // per-block partials (DIAG_PARTS doubles each) of the state's totals,
+    // extrema and the elliptic residual; *nblocks <= DIAG_MAXBLOCKS blocks
+    cudaError_t (*diag)(const Geom &, const Phys &, const Inflow &, const void *q, const void *sig,
+                        double *part, int *nblocks, cudaStream_t st);
 };
+
+// layout of one block's diagnostics partials: sums of rho, mx, my, mz, E,
+// (A Sigma - b)^2, b^2; minima of rho and p; maximum |Sigma|
+enum { DIAG_PARTS = 10, DIAG_BLOCKS_MAX = 152 * 8 };
 
 extern const Ops ops_f64, ops_f32, ops_f16, ops_bf16;
 

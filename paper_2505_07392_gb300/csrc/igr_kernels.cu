@@ -1173,6 +1173,122 @@ __global__ void __launch_bounds__(SPEED_NT) k_speed(const S *__restrict__ q, lon
     if (threadIdx.x == 0) blockmax[blockIdx.x] = m;
 }
 
+// ------------------------------------------------------------ diagnostics
+// FP64 evaluation of the state's totals, extrema and the residual of the
+// elliptic equation (Eq. igrelliptic) for the stored Sigma:
+//   (A s)_i = s_i (1/rho_i + beta sum_f c_f) - beta sum_f c_f s_nb,
+//   c_f = (1/rho_i + 1/rho_nb) / 2, beta = alpha / dx^2, faces on a
+//   non-periodic boundary dropped (the operator the Jacobi sweeps relax);
+//   b_i = alpha [sum_ab G_ab G_ba + (sum_a G_aa)^2], G_ab the central
+//   difference of u_a = m_a / rho along b (the source kernel's definition,
+//   with the same boundary mapping and jet blend).
+// Every stored value converts to double exactly, so the result is the FP64
+// evaluation on the stored state. One thread per cell (grid-stride), per-block
+// partial results in a fixed reduction order: deterministic.
+constexpr int DIAG_NT = 256, DIAG_NV = DIAG_PARTS;
+
+// conserved value u at (i, j, kk) through the boundary mapping, in FP64
+__device__ __forceinline__ double dval(const S *q, const Geom &g, const C *W, const C *J, int i,
+                                       int j, int kk, int u)
+{
+    int mi = map_axis(i, g.nx, g.bc[0], g.bc[1]), mj = map_axis(j, g.ny, g.bc[2], g.bc[3]);
+    int mk = map_axis(kk, g.nz, g.bc[4], g.bc[5]);
+    idx f = (idx)(mj * g.nx + mi);
+    double v = (double)cv(q[(size_t)u * (size_t)g.n + (size_t)mk * (size_t)g.plane + f]);
+    if (kk < 0 && g.bc[4] == BC_INFLOW)
+        v = (1.0 - (double)W[f]) * v + (double)J[(size_t)u * (size_t)g.plane + f];
+    return v;
+}
+
+// velocity u_a at (i, j, kk), FP64
+__device__ __forceinline__ void dvel(const S *q, const Geom &g, const C *W, const C *J, int i, int j,
+                                     int kk, double u[3])
+{
+    double rho = dval(q, g, W, J, i, j, kk, 0);
+#pragma unroll
+    for (int a = 0; a < 3; a++) u[a] = dval(q, g, W, J, i, j, kk, 1 + a) / rho;
+}
+
+__global__ void __launch_bounds__(DIAG_NT) k_diag(const S *__restrict__ q, const S *__restrict__ sig,
+                                                  Geom g, double gamma, double alpha, double dx,
+                                                  const C *W, const C *J, double *part)
+{
+    // acc: sums of rho, mx, my, mz, E, (A s - b)^2, b^2; minima of rho, p; max |Sigma|
+    double acc[DIAG_NV] = {0, 0, 0, 0, 0, 0, 0, INFINITY, INFINITY, 0};
+    const double beta = alpha / (dx * dx), inv2dx = 0.5 / dx;
+    for (long long c = blockIdx.x * (long long)DIAG_NT + threadIdx.x; c < g.n;
+         c += (long long)gridDim.x * DIAG_NT) {
+        int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / g.plane);
+        double v[5];
+#pragma unroll
+        for (int u = 0; u < 5; u++) v[u] = (double)cv(q[(size_t)u * (size_t)g.n + (size_t)c]);
+        double s0 = (double)cv(sig[c]);
+#pragma unroll
+        for (int u = 0; u < 5; u++) acc[u] += v[u];
+        double p = (gamma - 1.0) * (v[4] - 0.5 * (v[1] * v[1] + v[2] * v[2] + v[3] * v[3]) / v[0]);
+        acc[7] = fmin(acc[7], v[0]);
+        acc[8] = fmin(acc[8], p);
+        acc[9] = fmax(acc[9], fabs(s0));
+        // b from central differences of u
+        double G[3][3];
+        const int di[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            double up[3], um[3];
+            dvel(q, g, W, J, i + di[b][0], j + di[b][1], k + di[b][2], up);
+            dvel(q, g, W, J, i - di[b][0], j - di[b][1], k - di[b][2], um);
+#pragma unroll
+            for (int a = 0; a < 3; a++) G[a][b] = (up[a] - um[a]) * inv2dx;
+        }
+        double tr = G[0][0] + G[1][1] + G[2][2], t2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = 0; b < 3; b++) t2 += G[a][b] * G[b][a];
+        double bv = alpha * (t2 + tr * tr);
+        // A Sigma with the boundary faces of non-periodic sides dropped
+        double r0 = 1.0 / v[0], diag = r0, off = 0.0;
+        const int dir[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+        const int ext[3] = {g.nx, g.ny, g.nz}, pos[3] = {i, j, k};
+#pragma unroll
+        for (int f = 0; f < 6; f++) {
+            int ax = f >> 1;
+            int pn = pos[ax] + ((f & 1) ? 1 : -1);
+            if ((pn < 0 || pn >= ext[ax]) && g.bc[f] != BC_PERIODIC) continue;
+            int ni = map_axis(i + dir[f][0], g.nx, g.bc[0], g.bc[1]);
+            int nj = map_axis(j + dir[f][1], g.ny, g.bc[2], g.bc[3]);
+            int nk = map_axis(k + dir[f][2], g.nz, g.bc[4], g.bc[5]);
+            size_t nc = (size_t)nk * (size_t)g.plane + (size_t)nj * g.nx + ni;
+            double cf = 0.5 * beta * (r0 + 1.0 / (double)cv(q[nc]));
+            diag += cf;
+            off += cf * (double)cv(sig[nc]);
+        }
+        double res = diag * s0 - off - bv;
+        acc[5] += res * res;
+        acc[6] += bv * bv;
+    }
+    // block reduction in a fixed order
+    __shared__ double red[DIAG_NT / 32][DIAG_NV];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int t = 0; t < DIAG_NV; t++) {
+        double x = acc[t];
+        for (int o = 16; o > 0; o >>= 1) {
+            double y = __shfl_down_sync(0xffffffffu, x, o);
+            x = t < 7 ? x + y : (t < 9 ? fmin(x, y) : fmax(x, y));
+        }
+        if (lane == 0) red[w][t] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < DIAG_NV) {
+        int t = threadIdx.x;
+        double x = red[0][t];
+        for (int ww = 1; ww < DIAG_NT / 32; ww++)
+            x = t < 7 ? x + red[ww][t] : (t < 9 ? fmin(x, red[ww][t]) : fmax(x, red[ww][t]));
+        part[blockIdx.x * DIAG_NV + t] = x;
+    }
+}
+
 // ---------------------------------------------------------------- adjoint
 // Reverse of one stage (discrete adjoint with dt frozen). Simple kernels: one
 // thread per face or cell, grid-stride loops, and atomics where the forward
@@ -1652,12 +1768,23 @@ cudaError_t launch_adj_jets(const Geom &g, const Phys &p, const double *jets, in
     return cudaGetLastError();
 }
 
+cudaError_t launch_diag(const Geom &g, const Phys &p, const Inflow &in, const void *q, const void *sig,
+                        double *part, int *nblocks, cudaStream_t st)
+{
+    long long nb = (g.n + DIAG_NT - 1) / DIAG_NT;
+    int blocks = (int)(nb < DIAG_BLOCKS_MAX ? nb : DIAG_BLOCKS_MAX);
+    *nblocks = blocks;
+    k_diag<<<blocks, DIAG_NT, 0, st>>>((const S *)q, (const S *)sig, g, p.gamma, p.alpha, p.dx,
+                                        (const C *)in.W, (const C *)in.J, part);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 extern const Ops IGR_OPS = {
     (int)sizeof(S), (int)sizeof(C), launch_source, launch_jacobi, launch_flux, flux_blocks,
     launch_speed, launch_rk_combine, launch_adj_rk, launch_adj_rhs, launch_adj_jacobi, launch_adj_rho,
-    launch_adj_source, launch_adj_jets,
+    launch_adj_source, launch_adj_jets, launch_diag,
 };
 
 }  // namespace igr

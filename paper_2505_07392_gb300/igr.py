@@ -54,6 +54,13 @@ class IGRError(RuntimeError):
 _lib = None
 
 
+class Diagnostics(C.Structure):
+    """igr_diagnostics."""
+    _fields_ = [("mass", C.c_double), ("momentum", C.c_double * 3), ("energy", C.c_double),
+                ("rho_min", C.c_double), ("p_min", C.c_double), ("sigma_absmax", C.c_double),
+                ("b_norm", C.c_double), ("sigma_residual", C.c_double)]
+
+
 def lib():
     """The loaded libigr.so with argument types set."""
     global _lib
@@ -89,6 +96,7 @@ def lib():
             "igr_destroy_batch": (i, [p]),
             "igr_sync": (i, [p]),
             "igr_get_flags": (i, [p, C.POINTER(i)]),
+            "igr_diagnose": (i, [p, C.POINTER(Diagnostics)]),
             "igr_profile_enable": (i, [p, i]),
             "igr_profile_read": (i, [p, i, C.POINTER(C.c_longlong), C.POINTER(d)]),
             "igr_last_error": (C.c_char_p, [p]),
@@ -257,6 +265,15 @@ class Solver:
 
     def sync(self):
         self._check(lib().igr_sync(self.h))
+
+    def diagnose(self) -> dict:
+        """FP64 totals, extrema and the Sigma residual of the current state
+        (igr_diagnose)."""
+        d = Diagnostics()
+        self._check(lib().igr_diagnose(self.h, C.byref(d)))
+        return {"mass": d.mass, "momentum": tuple(d.momentum), "energy": d.energy,
+                "rho_min": d.rho_min, "p_min": d.p_min, "sigma_absmax": d.sigma_absmax,
+                "b_norm": d.b_norm, "sigma_residual": d.sigma_residual}
 
     def flags(self) -> int:
         """Warnings since the last call (IGR_WARN_FACE_POSITIVITY = 2)."""
