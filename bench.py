@@ -120,8 +120,23 @@ def plume_case(args):
     return inputs.plume(steps=args.steps)
 
 
+def make_case(args):
+    """(case, workload description) of --workload (the plume by default)."""
+    if args.workload == "blast":
+        n = args.size[0] if args.size else 256
+        c = inputs.blast(n)
+        return c, f"spherical blast {n}^3, outflow, S={c.sweeps}"
+    if args.workload == "density_wave":
+        c = inputs.density_wave(args.size[0] if args.size else 32)
+        return c, f"periodic density wave {c.nx}^3, S={c.sweeps}"
+    c = plume_case(args)
+    return c, f"plume {c.nx}x{c.ny}x{c.nz}, 33 Mach-3 jets, S={c.sweeps}"
+
+
 def fill_initial_state(case, dtype, device):
     import torch
+    if not case.jets:
+        return torch.from_numpy(inputs.initial_state(case)).to(dtype).to(device)
     q = torch.empty((5, case.nz, case.ny, case.nx), dtype=dtype, device=device)
     zc = max(1, (1 << 27) // (case.nx * case.ny))
     for k0 in range(0, case.nz, zc):
@@ -298,6 +313,16 @@ def oracle_sample_case(full, size):
 
 def cpu_baseline(full, steps=1, size=(256, 256, 64)):
     import oracle
+    if not full.jets:  # the whole (small) grid
+        q0 = inputs.initial_state(full)
+        oracle.lib()
+        t0 = time.perf_counter()
+        oracle.run(full, q0, None, nsteps=steps)
+        sec = time.perf_counter() - t0
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        return {"value": full.ncells * steps / sec, "unit": "cell-updates/s", "cores": cores,
+                "kind": "oracle", "sample": f"the whole {full.nx}x{full.ny}x{full.nz} grid, "
+                                            f"{steps} SSP-RK3 step(s) in FP64, {sec:.1f} s"}
     c, window = oracle_sample_case(full, size)
     q0 = inputs.jet_initial_state(full, window)
     oracle.lib()
@@ -333,23 +358,27 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-size", type=int, nargs=3, default=(256, 256, 128))
     ap.add_argument("--cpu-steps", type=int, default=2)
-    ap.add_argument("--workload", default="plume", choices=["plume", "tgv_batch"])
+    ap.add_argument("--workload", default="plume", choices=["plume", "tgv_batch", "blast", "density_wave"])
     ap.add_argument("--batch-count", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
 
     world, rank, local = dist_setup(args)
-    full = plume_case(args)
-    workload = f"plume {full.nx}x{full.ny}x{full.nz}, 33 Mach-3 jets, S={full.sweeps}"
+    full, workload = make_case(args)
 
     if args.impl == "reference":
         if rank != 0:
             return
         # W warm-up steps are accepted for the contract; the oracle keeps no state to warm
         import oracle
-        c, window = oracle_sample_case(full, tuple(args.cpu_size))
-        q = inputs.jet_initial_state(full, window)
+        if full.jets:
+            c, window = oracle_sample_case(full, tuple(args.cpu_size))
+            q = inputs.jet_initial_state(full, window)
+            where = f"{c.nx}x{c.ny}x{c.nz} crop of the plume at the inflow face (all 33 jets)"
+        else:
+            c, q = full, inputs.initial_state(full)
+            where = f"the whole {c.nx}x{c.ny}x{c.nz} grid"
         sig = None
         oracle.lib()
         secs = 0.0
@@ -360,14 +389,13 @@ def main():
         value = c.ncells * args.steps / secs
         cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
         cb = {"value": value, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
-              "sample": f"{c.nx}x{c.ny}x{c.nz} crop of the plume at the inflow face (all 33 jets), "
-                        f"{args.steps} SSP-RK3 step(s) in FP64, {secs:.1f} s"}
+              "sample": f"{where}, {args.steps} SSP-RK3 step(s) in FP64, {secs:.1f} s"}
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * secs / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": workload + " (oracle on a crop)",
-                                                "crop": list(args.cpu_size)},
+                "data": "synthetic", "config": {"workload": workload + (" (oracle on a crop)" if full.jets else ""),
+                                                "crop": list(args.cpu_size) if full.jets else None},
                 "cpu_baseline": cb,
                 "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}

@@ -213,12 +213,16 @@ __device__ __forceinline__ double block_max(double v)
 // fraction of the FP32 rate on this GPU, so it is evaluated in FP32 with a
 // rigorous bound e on |v32 - v64|:
 //   d = RN(qs - qn), p = RN(dt32 L + d), v = RN(w32 p + qn) with dt32, w32
-//   the FP32 roundings of dt, w (w <= 1) gives
-//   |v32 - v64| <= 2^-24 |v| + 2^-22 (|p| + |d|) <= 2^-22 (|v| + |p| + |d|).
+//   the FP32 roundings of dt, w (w <= 1) gives, to first order,
+//   |v32 - v64| <= 2^-24 (|v| + 3 |p| + 2 |d|) <= 2^-22 (|v| + |p| + |d|),
+//   the slack covering the FP64 evaluation's own rounding and the FP32
+//   evaluation of e; where a rounding result is an FP32 subnormal its error
+//   is absolute (at most 2^-150), so e adds 2^-148 for the three roundings.
 // If v32 sits farther than e from every rounding boundary of the storage
-// format, RN16(v32) = RN16(v64); otherwise (about one value in a thousand)
-// the combination is redone in FP64. The stored value therefore always
-// equals the FP64 evaluation rounded to nearest-even.
+// format, RN16(v32) = RN16(v64); otherwise (for smooth data, about e / spacing
+// of the values, well under one in a thousand) the combination is redone in
+// FP64. The stored value therefore always equals the FP64 evaluation rounded
+// to nearest-even, the sign of a zero included.
 template <typename T> struct Narrow;
 template <> struct Narrow<__half> {
     static constexpr int M = 10;                 // stored mantissa bits
@@ -255,15 +259,27 @@ __device__ __forceinline__ T rk_narrow_fast(float qn, float qs, float L, float d
     float d = __fsub_rn(qs, qn);
     float pp = __fmaf_rn(dt32, L, d);
     float v = __fmaf_rn(w32, pp, qn);
-    float e = (fabsf(v) + fabsf(pp) + fabsf(d)) * 0x1p-22f;
+    // relative rounding errors, plus 2^-148 for the three roundings whose
+    // results may be FP32 subnormals (absolute error up to 2^-150 each)
+    float e = __fmaf_rn(fabsf(v) + fabsf(pp) + fabsf(d), 0x1p-22f, 0x1p-148f);
     T h = NR::rn(v);
     float hv = NR::f(h);
     float r = v - hv;  // exact: v and hv are within a factor 2
-    // a lower bound on the distance from hv to the rounding boundaries on
-    // either side: |hv| 2^-(M+2) is at most half the format's spacing at hv,
-    // and at most half the (halved) spacing just below a power of two
-    float hb = fmaxf(fabsf(hv) * (1.0f / float(1 << (NR::M + 2))), NR::tiny);
-    ok = fabsf(r) + e < hb;
+    // Distance from hv to the rounding boundaries of the storage format on
+    // either side: half the spacing of hv's binade (p2 2^-M with p2 the power
+    // of two at or below |hv|); a quarter of it when |hv| is itself a power of
+    // two (the spacing below is half as wide); half the subnormal spacing
+    // (tiny) at the bottom of the range and at zero.
+    float ah = fabsf(hv);
+    float p2 = __int_as_float(__float_as_int(ah) & 0x7f800000);
+    float hb = p2 * (ah == p2 ? 1.0f / float(1 << (NR::M + 2)) : 1.0f / float(1 << (NR::M + 1)));
+    hb = fmaxf(hb, NR::tiny);
+    // v64 lies within e of v, so it rounds to hv when |r| + e < hb; at hv = 0
+    // its sign (that of the stored zero) must also be v's: certain when
+    // |v| > e, or when qn, d and L are all zeros (both evaluations then
+    // combine the same signed zeros by the same IEEE rules)
+    ok = fabsf(r) + e < hb &&
+         (ah != 0.0f || fabsf(v) > e || (qn == 0.0f && d == 0.0f && L == 0.0f));
     return h;
 }
 

@@ -287,17 +287,21 @@ def test_plume_full_size_sampled(precision):
 
 
 def _bf16_rn(x):
-    """float64 -> bfloat16 (round to nearest even, normal range), as float64."""
+    """float64 -> bfloat16 (round to nearest even), as float64: 8 significant
+    bits in the normal range, the fixed grid of 2^-133 below 2^-126."""
     m, e = np.frexp(x)
-    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+    normal = np.ldexp(np.rint(m * 256.0) / 256.0, e)
+    return np.where(np.abs(x) < 2.0 ** -126, np.rint(x * 2.0 ** 133) * 2.0 ** -133, normal)
 
 
 @pytest.mark.parametrize("precision", ["f16", "bf16"])
 @pytest.mark.parametrize("stage", [1, 2, 3])
 def test_rk_combine_equals_fp64_rounding(precision, stage):
     """16-bit storage: the stored stage combination qn + w((qs - qn) + dt L) is
-    the FP64 evaluation rounded to nearest-even, bit for bit, including values
-    built to sit within 1e-12 of a rounding midpoint."""
+    the FP64 evaluation rounded to nearest-even, bit for bit (sign of zero
+    included), including values built to sit within 1e-9..1e-15 (relative) of
+    a rounding midpoint on either side, around exact powers of two, among the
+    format's subnormals, and within 1e-9 of zero."""
     import torch
     from paper_2505_07392_gb300 import igr
     rng = np.random.Generator(np.random.Philox(40 + stage))
@@ -307,22 +311,42 @@ def test_rk_combine_equals_fp64_rounding(precision, stage):
     st = igr.storage_torch_dtype(precision)
     mag = 10.0 ** rng.uniform(-3, 2, size=n)
     qn = torch.from_numpy(mag * rng.choice([-1.0, 1.0], size=n)).to(st)
-    qs = torch.from_numpy(qn.double().numpy() * (1 + rng.normal(0, 1e-2, size=n))).to(st)
-    if stage == 1:
-        qs = qn.clone()
     L = rng.normal(0, 1, size=n) * mag * 30.0
-    # a quarter of the values: L chosen so that the exact result sits next to
-    # the midpoint between two neighbouring 16-bit values
-    k = n // 4
+    # Slices of the values get L chosen so that the exact result sits next to
+    # a rounding boundary: [0, k) the midpoint above (in magnitude) the
+    # rounded base, [k, 2k) the midpoint below it, [2k, 3k) the same around
+    # exact powers of two (where the spacing below is half as wide), [3k, 4k)
+    # around subnormals of the format, [4k, 5k) results within 1e-9 of zero.
+    k = n // 8
+    sub = 1e-6 if precision == "f16" else 1e-38  # inside the subnormal range
+    qn64 = qn.double().numpy().copy()
+    p2 = np.ldexp(1.0, rng.integers(-12, 8, size=k)) * rng.choice([-1.0, 1.0], size=k)
+    qn64[2 * k:3 * k] = p2
+    qn64[3 * k:4 * k] = sub * rng.uniform(0.05, 20, size=k) * rng.choice([-1.0, 1.0], size=k)
+    qn64[4 * k:5 * k] *= 1e-3
+    qn = torch.from_numpy(qn64).to(st)
     qn64 = qn.double().numpy()
+    qs = qn.clone() if stage == 1 else torch.from_numpy(
+        qn64 * (1 + rng.normal(0, 1e-2, size=n))).to(st)
     qs64 = qs.double().numpy()
-    base = qn64[:k] + w * (qs64[:k] - qn64[:k])
-    hb = torch.from_numpy(base).to(st)
-    bits = hb.view(torch.int16).numpy().astype(np.int32)
-    nxt = torch.from_numpy(((bits + 1) & 0xFFFF).astype(np.uint16).astype(np.int16)).view(st).double().numpy()
-    mid = 0.5 * (hb.double().numpy() + nxt)
-    target = mid * (1 + rng.choice([-1.0, 1.0], size=k) * 10.0 ** rng.uniform(-15, -9, size=k))
-    L[:k] = (target - base) / (w * dt)
+
+    def neighbour(h, step):
+        bits = h.view(torch.int16).numpy().astype(np.int32)
+        return torch.from_numpy(((bits + step) & 0xFFFF).astype(np.uint16).astype(np.int16)).view(st).double().numpy()
+
+    def near(x):
+        return x * (1 + rng.choice([-1.0, 1.0], size=x.size) * 10.0 ** rng.uniform(-15, -9, size=x.size))
+
+    for lo, step in ((0, 1), (k, -1), (2 * k, -1), (3 * k, 1)):
+        sl = slice(lo, lo + k)
+        base = qn64[sl] + w * (qs64[sl] - qn64[sl])
+        hb = torch.from_numpy(base).to(st)
+        mid = 0.5 * (hb.double().numpy() + neighbour(hb, step))
+        L[sl] = (near(mid) - base) / (w * dt)
+    sl = slice(4 * k, 5 * k)
+    base = qn64[sl] + w * (qs64[sl] - qn64[sl])
+    target = rng.choice([-1.0, 1.0], size=k) * 10.0 ** rng.uniform(-13, -9, size=k)
+    L[sl] = (target - base) / (w * dt)
     L32 = torch.from_numpy(L).float()
     L64 = L32.double().numpy()
     exact = qn64 + w * ((qs64 - qn64) + dt * L64)
