@@ -222,7 +222,7 @@ __device__ __forceinline__ double block_max(double v)
 // format, RN16(v32) = RN16(v64); otherwise (for smooth data, about e / spacing
 // of the values, well under one in a thousand) the combination is redone in
 // FP64. The stored value therefore always equals the FP64 evaluation rounded
-// to nearest-even, the sign of a zero included.
+// to nearest-even, with zeros stored as +0.
 template <typename T> struct Narrow;
 template <> struct Narrow<__half> {
     static constexpr int M = 10;                 // stored mantissa bits
@@ -230,6 +230,8 @@ template <> struct Narrow<__half> {
     static __device__ __forceinline__ __half rn(float v) { return __float2half_rn(v); }
     static __device__ __forceinline__ __half rn(double v) { return __double2half(v); }
     static __device__ __forceinline__ float f(__half h) { return __half2float(h); }
+    // zeros are stored as +0 (-0 + +0 = +0 under round-to-nearest)
+    static __device__ __forceinline__ __half canon(__half h) { return __hadd(h, __ushort_as_half(0)); }
 };
 template <> struct Narrow<__nv_bfloat16> {
     static constexpr int M = 7;
@@ -237,6 +239,10 @@ template <> struct Narrow<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 rn(float v) { return __float2bfloat16_rn(v); }
     static __device__ __forceinline__ __nv_bfloat16 rn(double v) { return __double2bfloat16(v); }
     static __device__ __forceinline__ float f(__nv_bfloat16 h) { return __bfloat162float(h); }
+    static __device__ __forceinline__ __nv_bfloat16 canon(__nv_bfloat16 h)
+    {
+        return __hadd(h, __ushort_as_bfloat16(0));
+    }
 };
 
 // FP64 evaluation, out of line so that only the rare lanes that need it run
@@ -247,7 +253,7 @@ __device__ __noinline__ T rk_fp64(float qn, float qs, float L, double dt, double
     double vd = __dadd_rn(double(qn),
                           __dmul_rn(w, __dadd_rn(__dsub_rn(double(qs), double(qn)),
                                                  __dmul_rn(dt, double(L)))));
-    return Narrow<T>::rn(vd);
+    return Narrow<T>::canon(Narrow<T>::rn(vd));
 }
 
 // FP32 evaluation and rounding; ok = false when the rounding could differ
@@ -262,7 +268,7 @@ __device__ __forceinline__ T rk_narrow_fast(float qn, float qs, float L, float d
     // relative rounding errors, plus 2^-148 for the three roundings whose
     // results may be FP32 subnormals (absolute error up to 2^-150 each)
     float e = __fmaf_rn(fabsf(v) + fabsf(pp) + fabsf(d), 0x1p-22f, 0x1p-148f);
-    T h = NR::rn(v);
+    T h = NR::canon(NR::rn(v));
     float hv = NR::f(h);
     float r = v - hv;  // exact: v and hv are within a factor 2
     // Distance from hv to the rounding boundaries of the storage format on
@@ -274,12 +280,9 @@ __device__ __forceinline__ T rk_narrow_fast(float qn, float qs, float L, float d
     float p2 = __int_as_float(__float_as_int(ah) & 0x7f800000);
     float hb = p2 * (ah == p2 ? 1.0f / float(1 << (NR::M + 2)) : 1.0f / float(1 << (NR::M + 1)));
     hb = fmaxf(hb, NR::tiny);
-    // v64 lies within e of v, so it rounds to hv when |r| + e < hb; at hv = 0
-    // its sign (that of the stored zero) must also be v's: certain when
-    // |v| > e, or when qn, d and L are all zeros (both evaluations then
-    // combine the same signed zeros by the same IEEE rules)
-    ok = fabsf(r) + e < hb &&
-         (ah != 0.0f || fabsf(v) > e || (qn == 0.0f && d == 0.0f && L == 0.0f));
+    // v64 lies within e of v, so it rounds to hv when |r| + e < hb (a zero
+    // result is stored as +0 on both paths, whatever the sign of v)
+    ok = fabsf(r) + e < hb;
     return h;
 }
 
