@@ -154,14 +154,14 @@ def words_per_cell(sweeps):
     return {"source": 3 * 5, "jacobi": 3 * sweeps * 4, "flux": 11 + 16 + 16}
 
 
-def run_form(case, precision, steps, warmup, sync_all, e2e_steps=0):
+def run_form(case, precision, steps, warmup, sync_all, e2e_steps=0, host_rk_base=False):
     """Time `steps` steps of one precision form; returns a result dict."""
     import torch
     from paper_2505_07392_gb300 import igr
     dev = torch.device("cuda", torch.cuda.current_device())
     st_dtype = igr.storage_torch_dtype(precision)
     res = {}
-    with igr.Solver(case, precision) as s:
+    with igr.Solver(case, precision, host_rk_base=host_rk_base) as s:
         q = fill_initial_state(case, st_dtype, dev)
         s.set_state(q)
         del q
@@ -360,6 +360,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--workload", default="plume", choices=["plume", "tgv_batch", "blast", "density_wave"])
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--host-rk-base", action="store_true",
+                    help="keep the RK base q^n in host memory (read over NVLink-C2C)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -424,7 +426,7 @@ def main():
         return
 
     res = run_form(full, args.precision, args.steps, args.warmup, sync_all,
-                   e2e_steps=args.e2e_steps if rank == 0 else 0)
+                   e2e_steps=args.e2e_steps if rank == 0 else 0, host_rk_base=args.host_rk_base)
     res["prof_steps"] = args.steps
     ms = res["ms"]
     if world > 1:
@@ -439,7 +441,7 @@ def main():
 
     plain = None
     if args.plain not in ("", "none") and args.plain != args.precision:
-        rp = run_form(full, args.plain, args.steps, args.warmup, sync_all)
+        rp = run_form(full, args.plain, args.steps, args.warmup, sync_all, host_rk_base=args.host_rk_base)
         rp["prof_steps"] = args.steps
         roof_p, _ = roofline_of(full, rp, args.plain, peak, peak_kind)
         plain = {"precision": args.plain, "value": full.ncells * args.steps * world / (rp["ms"] * 1e-3),
@@ -458,6 +460,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": workload, "cells": full.ncells, "precision": args.precision,
                    "sweeps": full.sweeps, "parallelism": f"replicas x{world}",
+                   "rk_base": "host memory (NVLink-C2C)" if args.host_rk_base else "device",
                    "l2": "inputs larger than L2 (state %.1f GB)" % (6 * full.ncells * wb / 1e9)},
         "gpu_launches": launches,
         "roofline": roof,

@@ -96,12 +96,20 @@ typedef struct {
     igr_bc bc[6];       /* faces -x, +x, -y, +y, -z, +z */
     const igr_jet *jets;/* njets jets on an IGR_BC_INFLOW -z face (copied) */
     int njets;
+    int host_rk_base;   /* 0: in-core. 1: keep the RK base q^n (5 n values) in pinned,
+                           device-mapped host memory (cudaHostAlloc) instead of a third
+                           device state buffer: stage 1 writes it while it reads its
+                           input, stages 2 and 3 read it over the CPU-GPU link (NVLink-C2C
+                           on Grace systems). Device memory drops from 18 to 13 values
+                           per cell; results are bitwise those of the in-core mode. Not
+                           available in batches. Ignored by igr_solve_sigma_noalloc. */
 } igr_config;
 
 typedef struct igr_ctx igr_ctx; /* opaque */
 
 /* Validate cfg and allocate the context on the current CUDA device:
- * three state buffers (5 fields each), two Sigma buffers, the source b,
+ * three state buffers (5 fields each; two with host_rk_base, plus the host
+ * buffer of the RK base), two Sigma buffers, the source b,
  * the inflow tables and a few scalars, all in the storage type of
  * cfg->prec. allocator may be NULL (cudaMalloc). cuda_stream is a
  * cudaStream_t (NULL = legacy default stream). The state and Sigma start
@@ -109,7 +117,8 @@ typedef struct igr_ctx igr_ctx; /* opaque */
 igr_status igr_create(const igr_config *cfg, const igr_allocator *allocator, void *cuda_stream,
                       igr_ctx **out);
 
-/* Device bytes igr_create allocates for cfg (0 if cfg is invalid). */
+/* Device bytes igr_create allocates for cfg (0 if cfg is invalid); with
+ * host_rk_base the pinned host buffer (5 n stored values) is not counted. */
 size_t igr_memory_bytes(const igr_config *cfg);
 
 /* Synchronise the stream, free every buffer, destroy the context. NULL is a no-op. */

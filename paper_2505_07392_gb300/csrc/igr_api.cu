@@ -39,7 +39,9 @@ struct igr_ctx {
     bool own_alloc;
     cudaStream_t st;
     int device;
-    void *q[3];
+    void *q[3];         // q^n, q^1, q^2 (q[2] unused with host_rk_base)
+    void *hbase;        // host_rk_base: pinned host buffer of the RK base (5 n values)
+    void *hbase_dev;    // its device-mapped address
     void *sig[2];
     void *b;
     void *W, *J;
@@ -237,6 +239,7 @@ const char *igr::validate_config(const igr_config *c)
     for (int f = 0; f < 6; f++)
         if (c->bc[f] == IGR_BC_INFLOW && f != 4) return "IGR_BC_INFLOW is supported on the -z face only";
     if (c->njets < 0 || (c->njets > 0 && !c->jets)) return "jets is NULL with njets > 0";
+    if (c->host_rk_base != 0 && c->host_rk_base != 1) return "host_rk_base must be 0 or 1";
     if (c->njets > 0 && c->bc[4] != IGR_BC_INFLOW) return "jets need an IGR_BC_INFLOW -z face";
     for (int n = 0; n < c->njets; n++) {
         const igr_jet &j = c->jets[n];
@@ -346,7 +349,8 @@ static igr_status launch_sweeps(igr_ctx *c, const void *q, const void *b, void *
     return IGR_OK;
 }
 
-static igr_status run_stage(igr_ctx *c, int mode, const void *qs, const void *qn, void *out)
+static igr_status run_stage(igr_ctx *c, int mode, const void *qs, const void *qn, void *out,
+                            void *base_out = nullptr)
 {
     prof_begin(c, KC_SOURCE);
     CU(c, c->ops->source(c->g, c->p, c->tiles, inflow_of(c), qs, c->b, c->st));
@@ -357,7 +361,7 @@ static igr_status run_stage(igr_ctx *c, int mode, const void *qs, const void *qn
     c->cur = res == c->sig[0] ? 0 : 1;
     prof_begin(c, KC_FLUX);
     CU(c, c->ops->flux(c->g, c->p, c->tiles, inflow_of(c), mode, qs, c->sig[c->cur], qn, out,
-                       nullptr, c->sc, c->blockmax, &c->sc->err, c->st));
+                       nullptr, base_out, c->sc, c->blockmax, &c->sc->err, c->st));
     prof_end(c);
     return IGR_OK;
 }
@@ -401,8 +405,8 @@ size_t igr_memory_bytes(const igr_config *cfg)
 {
     if (validate_config(cfg)) return 0;
     Layout L = layout_of(cfg);
-    return 3 * round256(L.state) + 2 * round256(L.sig) + round256(L.b) + round256(L.W) +
-           round256(L.J) + round256(L.blockmax) + round256(L.scalars) + round256(L.jets);
+    return (cfg->host_rk_base ? 2 : 3) * round256(L.state) + 2 * round256(L.sig) + round256(L.b) +
+           round256(L.W) + round256(L.J) + round256(L.blockmax) + round256(L.scalars) + round256(L.jets);
 }
 
 igr_status igr_create(const igr_config *cfg, const igr_allocator *allocator, void *cuda_stream,
@@ -442,7 +446,18 @@ igr_status igr_create(const igr_config *cfg, const igr_allocator *allocator, voi
 
     Layout L = layout_of(cfg);
     igr_status s = IGR_OK;
-    for (int n = 0; n < 3 && s == IGR_OK; n++) s = ctx_alloc(c, &c->q[n], L.state);
+    const int nstate = cfg->host_rk_base ? 2 : 3;
+    for (int n = 0; n < nstate && s == IGR_OK; n++) s = ctx_alloc(c, &c->q[n], L.state);
+    if (s == IGR_OK && cfg->host_rk_base) {
+        if (cudaHostAlloc(&c->hbase, L.state, cudaHostAllocMapped) != cudaSuccess) {
+            c->hbase = nullptr;
+            s = fail(c, IGR_ERR_OOM, "pinned host allocation of %zu bytes failed", L.state);
+        } else if (cudaHostGetDevicePointer(&c->hbase_dev, c->hbase, 0) != cudaSuccess) {
+            s = fail(c, IGR_ERR_UNSUPPORTED, "the device cannot map host memory");
+        } else {
+            memset(c->hbase, 0, L.state);
+        }
+    }
     for (int n = 0; n < 2 && s == IGR_OK; n++) s = ctx_alloc(c, &c->sig[n], L.sig);
     if (s == IGR_OK) s = ctx_alloc(c, &c->b, L.b);
     if (s == IGR_OK) s = ctx_alloc(c, &c->W, L.W);
@@ -458,7 +473,7 @@ igr_status igr_create(const igr_config *cfg, const igr_allocator *allocator, voi
     }
     // zero state, Sigma, scalars; build the inflow tables
     cudaError_t e = cudaSuccess;
-    for (int n = 0; n < 3 && e == cudaSuccess; n++) e = cudaMemsetAsync(c->q[n], 0, L.state, c->st);
+    for (int n = 0; n < nstate && e == cudaSuccess; n++) e = cudaMemsetAsync(c->q[n], 0, L.state, c->st);
     for (int n = 0; n < 2 && e == cudaSuccess; n++) e = cudaMemsetAsync(c->sig[n], 0, L.sig, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->b, 0, L.b, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->sc, 0, L.scalars, c->st);
@@ -509,6 +524,7 @@ igr_status igr_destroy(igr_ctx *c)
         if (p) c->alloc.free(p, c->alloc.user);
     for (void *p : c->adj.all)
         if (p) c->alloc.free(p, c->alloc.user);
+    if (c->hbase) cudaFreeHost(c->hbase);
     delete c;
     return IGR_OK;
 }
@@ -604,9 +620,19 @@ igr_status igr_step(igr_ctx *c, int nsteps, double fixed_dt, double *t_inout)
                                             c->cfg.cfl * c->cfg.dx, fixed_dt);
         CU(c, cudaGetLastError());
         prof_end(c);
-        igr_status s = run_stage(c, FLUX_STAGE1, c->q[0], c->q[0], c->q[1]);
-        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE2, c->q[1], c->q[0], c->q[2]);
-        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE3, c->q[2], c->q[0], c->q[0]);
+        igr_status s;
+        if (c->hbase) {
+            // RK base in host memory: stage 1 copies q^n there while it reads it,
+            // stages 2 and 3 read it back; the two device buffers alternate
+            s = run_stage(c, FLUX_STAGE1, c->q[0], c->q[0], c->q[1], c->hbase_dev);
+            if (s == IGR_OK) s = run_stage(c, FLUX_STAGE2, c->q[1], c->hbase_dev, c->q[0]);
+            if (s == IGR_OK) s = run_stage(c, FLUX_STAGE3, c->q[0], c->hbase_dev, c->q[1]);
+            std::swap(c->q[0], c->q[1]);
+        } else {
+            s = run_stage(c, FLUX_STAGE1, c->q[0], c->q[0], c->q[1]);
+            if (s == IGR_OK) s = run_stage(c, FLUX_STAGE2, c->q[1], c->q[0], c->q[2]);
+            if (s == IGR_OK) s = run_stage(c, FLUX_STAGE3, c->q[2], c->q[0], c->q[0]);
+        }
         if (s != IGR_OK) return s;
         c->speed_nblocks = (int)c->ops->flux_blocks(c->g, c->tiles);
     }
@@ -648,7 +674,7 @@ igr_status igr_rhs(igr_ctx *c, const void *q, const void *sigma, void *rhs, igr_
         return fail(c, IGR_ERR_UNSUPPORTED, "dtype must be the storage dtype");
     prof_begin(c, KC_FLUX);
     CU(c, c->ops->flux(c->g, c->p, c->tiles, inflow_of(c), FLUX_RHS, q, sigma, nullptr, nullptr,
-                       rhs, c->sc, c->blockmax, &c->sc->err, c->st));
+                       rhs, nullptr, c->sc, c->blockmax, &c->sc->err, c->st));
     prof_end(c);
     return IGR_OK;
 }
@@ -782,7 +808,7 @@ igr_status igr_autotune(igr_ctx *c, int reps)
         if (ms < tbest[1]) { tbest[1] = ms; best.zc_jacobi = t.zc_jacobi; }
         s = time_launches(c, reps, [&] {
             return c->ops->flux(c->g, c->p, t, inflow_of(c), FLUX_STAGE1, c->q[0], sig, c->q[0], c->q[1],
-                                nullptr, c->sc, c->blockmax, &c->sc->err, c->st);
+                                nullptr, nullptr, c->sc, c->blockmax, &c->sc->err, c->st);
         }, &ms);
         if (s != IGR_OK) return s;
         if (ms < tbest[2]) { tbest[2] = ms; best.zc_flux = t.zc_flux; }
@@ -860,6 +886,9 @@ igr_status igr_create_batch(const igr_config *cfgs, int n, const igr_allocator *
 {
     if (!out || !cfgs || n < 1) return fail(nullptr, IGR_ERR_INVALID_ARG, "cfgs, n >= 1 and out are required");
     *out = nullptr;
+    for (int i = 0; i < n; i++)
+        if (cfgs[i].host_rk_base)  // captured graphs hold fixed state pointers
+            return fail(nullptr, IGR_ERR_UNSUPPORTED, "host_rk_base is not available in batches");
     igr_batch *b = new (std::nothrow) igr_batch();
     if (!b) return fail(nullptr, IGR_ERR_OOM, "host allocation failed");
     b->user = (cudaStream_t)cuda_stream;
@@ -1044,7 +1073,8 @@ igr_status igr_adjoint_step(igr_ctx *c, const void *q_n, const void *sigma_n, co
             CU(c, o->jacobi(c->g, c->p, c->tiles, qs[st], A.b, it(st, k), it(st, k + 1), c->st));
         if (st < 2) {
             CU(c, o->flux(c->g, c->p, c->tiles, inflow_of(c), st == 0 ? FLUX_STAGE1 : FLUX_STAGE2, qs[st],
-                          it(st, S), q_n, (void *)qs[st + 1], nullptr, A.sc, c->blockmax, &A.sc->err, c->st));
+                          it(st, S), q_n, (void *)qs[st + 1], nullptr, nullptr, A.sc, c->blockmax, &A.sc->err,
+                          c->st));
             CU(c, cudaMemcpyAsync(it(st + 1, 0), it(st, S), n * sb, cudaMemcpyDeviceToDevice, c->st));
         }
     }

@@ -66,9 +66,12 @@ struct Ops {
                           const void *b, const void *s_in, void *s_out, cudaStream_t st);
     // flux divergence and RK stage (mode FLUX_STAGE*), or L(q; Sigma) into rhs (FLUX_RHS).
     // Stage 3 also writes the per-block maximum wave speed of its output to blockmax.
+    // Stage 1 with base_out != NULL also copies its input qs there (the RK base of
+    // stages 2 and 3 when it lives in host memory).
     cudaError_t (*flux)(const Geom &, const Phys &, const Tiles &, const Inflow &, int mode,
                         const void *qs, const void *sig, const void *qn, void *out, void *rhs,
-                        const Scalars *sc, double *blockmax, int *err, cudaStream_t st);
+                        void *base_out, const Scalars *sc, double *blockmax, int *err,
+                        cudaStream_t st);
     // number of blocks of the flux launch (entries of blockmax it writes)
     long long (*flux_blocks)(const Geom &, const Tiles &);
     // per-block maximum wave speed of q; returns the block count in *nblocks

@@ -954,8 +954,9 @@ constexpr int FLUX_MAXREG = sizeof(C) == 8 ? 224 : 128;
 // global memory once per block; nothing relies on the L1 cache.
 template <int mode>
 __global__ void __maxnreg__(FLUX_MAXREG)
-    k_flux(Fin<6> in, Fin<5> qn, Fout<5> out, Frhs rhs, Geom g, C gamma, C half_inv_dx,
-           const Scalars *sc, double *blockmax, int *err, const C *W, const C *J, int zc)
+    k_flux(Fin<6> in, Fin<5> qn, Fout<5> out, Frhs rhs, Fout<5> base_out, Geom g, C gamma,
+           C half_inv_dx, const Scalars *sc, double *blockmax, int *err, const C *W, const C *J,
+           int zc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *P = reinterpret_cast<C2 *>(smem_raw);        // [RING][3][PH][PW]
@@ -1084,6 +1085,11 @@ __global__ void __maxnreg__(FLUX_MAXREG)
             const C2 *T = tile(kk);
             C2 a = T[tcell], b = T[PH * PW + tcell], e = T[2 * PH * PW + tcell];
             const C qsv[5] = {a.x, a.y, b.x, b.y, e.x};
+            if (mode == FLUX_STAGE1 && base_out.p[0]) {
+                // the RK base q^n for stages 2 and 3 (exact: qsv holds stored values)
+#pragma unroll
+                for (int u = 0; u < 5; u++) stc(base_out.p[u] + c, qsv[u]);
+            }
             C o[5], qb[5];
 #pragma unroll
             for (int u = 0; u < 5; u++) qb[u] = mode == FLUX_STAGE1 ? qsv[u] : cv(qnv[u]);
@@ -1672,7 +1678,7 @@ long long flux_blocks(const Geom &g, const Tiles &t)
 
 cudaError_t launch_flux(const Geom &g, const Phys &p, const Tiles &t, const Inflow &in, int mode,
                         const void *qs, const void *sig, const void *qn, void *out, void *rhs,
-                        const Scalars *sc, double *blockmax, int *err, cudaStream_t st)
+                        void *base_out, const Scalars *sc, double *blockmax, int *err, cudaStream_t st)
 {
     size_t smem = flux_smem_bytes();
     auto go = [&](auto kern) {
@@ -1680,14 +1686,15 @@ cudaError_t launch_flux(const Geom &g, const Phys &p, const Tiles &t, const Infl
         if (e != cudaSuccess) return e;
         Fin<6> fi = fields_in<6>(qs, g.n);
         fi.p[5] = (const S *)sig;
-        Fout<5> fo;
+        Fout<5> fo, fb;
         Frhs fr;
         for (int u = 0; u < 5; u++) {
             fo.p[u] = out ? (S *)out + u * g.n : nullptr;
+            fb.p[u] = base_out ? (S *)base_out + u * g.n : nullptr;
             fr.p[u] = rhs ? (C *)rhs + u * g.n : nullptr;
         }
         kern<<<grid_of(g, TX, TY, t.zc_flux), NT, smem, st>>>(
-            fi, fields_in<5>(qn, g.n), fo, fr, g, C(p.gamma), C(0.5 / p.dx), sc, blockmax, err,
+            fi, fields_in<5>(qn, g.n), fo, fr, fb, g, C(p.gamma), C(0.5 / p.dx), sc, blockmax, err,
             (const C *)in.W, (const C *)in.J, t.zc_flux);
         e = cudaGetLastError();
         if (e != cudaSuccess) {

@@ -42,7 +42,7 @@ class Config(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double),
                 ("gamma", C.c_double), ("alpha", C.c_double), ("cfl", C.c_double),
                 ("sweeps", C.c_int), ("prec", C.c_int), ("bc", C.c_int * 6),
-                ("jets", C.POINTER(Jet)), ("njets", C.c_int)]
+                ("jets", C.POINTER(Jet)), ("njets", C.c_int), ("host_rk_base", C.c_int)]
 
 
 class IGRError(RuntimeError):
@@ -109,17 +109,17 @@ def lib():
     return _lib
 
 
-def make_config(case, precision: str = "f32"):
+def make_config(case, precision: str = "f32", host_rk_base: bool = False):
     """Config struct (and the jet array it points to) from an inputs.Case."""
     jets = (Jet * max(1, len(case.jets)))(*[Jet(*j) for j in case.jets])
     cfg = Config(int(case.nx), int(case.ny), int(case.nz), float(case.dx), float(case.gamma),
                  float(case.alpha), float(case.cfl), int(case.sweeps), PRECISIONS[precision],
-                 (C.c_int * 6)(*[int(b) for b in case.bc]), jets, len(case.jets))
+                 (C.c_int * 6)(*[int(b) for b in case.bc]), jets, len(case.jets), int(host_rk_base))
     return cfg, jets
 
 
-def memory_bytes(case, precision: str = "f32") -> int:
-    cfg, _jets = make_config(case, precision)
+def memory_bytes(case, precision: str = "f32", host_rk_base: bool = False) -> int:
+    cfg, _jets = make_config(case, precision, host_rk_base)
     return int(lib().igr_memory_bytes(C.byref(cfg)))
 
 
@@ -152,15 +152,18 @@ _NP_DT = {np.dtype(np.float64): DT_F64, np.dtype(np.float32): DT_F32, np.dtype(n
 class Solver:
     """One IGR context on the current CUDA device and PyTorch's current stream."""
 
-    def __init__(self, case, precision: str = "f32", stream=None, torch_allocator: bool = True):
+    def __init__(self, case, precision: str = "f32", stream=None, torch_allocator: bool = True,
+                 host_rk_base: bool = False):
+        """host_rk_base keeps the RK base q^n in pinned host memory (igr_config)."""
         import torch
         self.case = case
         self.precision = precision
+        self.host_rk_base = bool(host_rk_base)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream or torch.cuda.current_stream(self.device)
         self.n = case.nx * case.ny * case.nz
         self.shape = (case.nz, case.ny, case.nx)
-        self._cfg, self._jets = make_config(case, precision)
+        self._cfg, self._jets = make_config(case, precision, host_rk_base)
         self._alloc = None
         if torch_allocator:
             dev, st = self.device.index, self.stream

@@ -60,3 +60,11 @@ def test_host_only_calls(libigr):
     cfg2, _ = igr.make_config(c2, "f32")
     assert L.igr_create(ctypes.byref(cfg2), None, None, ctypes.byref(h)) == igr.ERR_INVALID_ARG
     assert b"-z face" in L.igr_last_error(None)
+    # host_rk_base: one 5-field state buffer fewer on the device (13 words per cell)
+    cfgh, _ = igr.make_config(case, "f16", host_rk_base=True)
+    cfgd, _ = igr.make_config(case, "f16")
+    state = -(-5 * 2 * n // 256) * 256
+    assert L.igr_memory_bytes(ctypes.byref(cfgd)) - L.igr_memory_bytes(ctypes.byref(cfgh)) == state
+    cfgh.host_rk_base = 2
+    assert L.igr_create(ctypes.byref(cfgh), None, None, ctypes.byref(h)) == igr.ERR_INVALID_ARG
+    assert b"host_rk_base" in L.igr_last_error(None)

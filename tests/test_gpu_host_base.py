@@ -1,0 +1,68 @@
+"""RK base in host memory (igr_config.host_rk_base): the same kernels read
+q^n over the CPU-GPU link instead of from a third device buffer, so every
+result must equal the in-core run's bit for bit."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2505_07392_gb300 import inputs
+from paper_2505_07392_gb300.inputs import INFLOW, OUTFLOW, Case
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_07392_gb300 import build
+    build.build()
+    yield
+
+
+def _jets(n=24):
+    dx = 1.0 / n
+    w = 2 * math.sqrt(2.8)
+    return Case("jets", n, n - 4, n + 8, dx, alpha=dx * dx, sweeps=4,
+                bc=(OUTFLOW,) * 4 + (INFLOW, OUTFLOW),
+                jets=[(0.3, 0.45, 3 * dx, 1.0, w, 2.0, 1.0), (0.65, 0.5, 2.5 * dx, 1.0, 0.8 * w, 2.0, 1.0)])
+
+
+def _run(case, q0, precision, steps, host):
+    import torch
+    from paper_2505_07392_gb300 import igr
+    with igr.Solver(case, precision, host_rk_base=host) as s:
+        s.set_state(torch.from_numpy(q0).to(igr.storage_torch_dtype(precision)).cuda())
+        t = s.step(steps)
+        q, sig = s.get_state()
+        d = s.diagnose()
+    return q, sig, t, d
+
+
+@pytest.mark.parametrize("name,make,precision", [
+    ("blast-f32", lambda: inputs.blast(24, sweeps=6), "f32"),
+    ("blast-f16", lambda: inputs.blast(24, sweeps=6), "f16"),
+    ("jets-f64", _jets, "f64"),
+    ("jets-bf16", _jets, "bf16"),
+])
+def test_host_rk_base_bitwise(name, make, precision):
+    import torch
+    c = make()
+    q0 = inputs.jet_initial_state(c) if c.jets else inputs.initial_state(c)
+    a = _run(c, q0, precision, 7, False)
+    b = _run(c, q0, precision, 7, True)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    assert a[2] == b[2]  # the same dt sequence
+    assert a[3] == b[3]
+
+
+def test_batches_refuse_host_rk_base():
+    from paper_2505_07392_gb300 import igr
+    cases = [inputs.tgv(12), inputs.tgv(16)]
+    cfgs = [igr.make_config(c, "f32", host_rk_base=(i == 1)) for i, c in enumerate(cases)]
+    import ctypes
+    arr = (igr.Config * 2)(*[cf for cf, _ in cfgs])
+    h = ctypes.c_void_p()
+    assert igr.lib().igr_create_batch(arr, 2, None, None, ctypes.byref(h)) == igr.ERR_UNSUPPORTED
