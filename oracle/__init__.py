@@ -9,7 +9,8 @@ arrays, double precision, no contraction). This module only marshals numpy
 arrays through ctypes. A grid description is any object with the attributes
 ``nx, ny, nz, dx, gamma, alpha, cfl, sweeps, bc`` (6 ints: 0 periodic,
 1 outflow, 2 inflow, faces -x,+x,-y,+y,-z,+z) and ``jets`` (list of
-``(cx, cy, radius, rho, w, p, edge_width)``).
+``(cx, cy, radius, rho, w, p, edge_width)``), and optionally ``order`` (5 or 3)
+and ``sigma_solver`` (0 Jacobi, 1 red-black Gauss-Seidel).
 """
 import ctypes as C
 
@@ -24,7 +25,8 @@ class _Grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("dx", C.c_double), ("gamma", C.c_double), ("alpha", C.c_double),
                 ("cfl", C.c_double), ("sweeps", C.c_int), ("bc", C.c_int * 6),
-                ("njets", C.c_int), ("jets", C.POINTER(C.c_double))]
+                ("njets", C.c_int), ("jets", C.POINTER(C.c_double)),
+                ("order", C.c_int), ("sigma_solver", C.c_int)]
 
 
 def lib():
@@ -64,7 +66,8 @@ class Grid:
         self.s = _Grid(self.nx, self.ny, self.nz, float(cfg.dx), float(cfg.gamma),
                        float(cfg.alpha), float(cfg.cfl), int(cfg.sweeps),
                        (C.c_int * 6)(*[int(b) for b in cfg.bc]), int(jets.shape[0]),
-                       jets.ctypes.data_as(C.POINTER(C.c_double)))
+                       jets.ctypes.data_as(C.POINTER(C.c_double)),
+                       int(getattr(cfg, "order", 5)), int(getattr(cfg, "sigma_solver", 0)))
 
     @property
     def n(self):
@@ -164,11 +167,18 @@ def run(cfg, q, sigma=None, nsteps=1, fixed_dt=0.0):
     return q, s, float(t)
 
 
+def _jacobi5(cfg):
+    """The adjoint is written for the default scheme: 5th-order faces, Jacobi."""
+    if getattr(cfg, "order", 5) != 5 or getattr(cfg, "sigma_solver", 0) != 0:
+        raise ValueError("the adjoint covers 5th-order faces with Jacobi sweeps only")
+
+
 def adjoint_step(cfg, q, sigma, dt, lq, ls):
     """Adjoint of one SSP-RK3 step with fixed dt: given the adjoints (lq, ls)
     of the step's outputs (q', Sigma'), returns (lq_in, ls_in, gw) — the
     adjoints of (q, Sigma) and the gradient with respect to the jet
     velocities w_n of <lq, q'> + <ls, Sigma'>."""
+    _jacobi5(cfg)
     g = _grid(cfg)
     if g.s.sweeps > 63:
         raise ValueError("at most 63 sweeps")
@@ -185,6 +195,7 @@ def adjoint_step(cfg, q, sigma, dt, lq, ls):
 
 def rhs_vjp(cfg, q, sigma, Lb):
     """(dL/dq)^T Lb and (dL/dSigma)^T Lb of the spatial operator."""
+    _jacobi5(cfg)
     g = _grid(cfg)
     qb = np.zeros((5, g.nz, g.ny, g.nx))
     sb = np.zeros((g.nz, g.ny, g.nx))
@@ -195,6 +206,7 @@ def rhs_vjp(cfg, q, sigma, Lb):
 
 def source_vjp(cfg, q, bb):
     """(db/dq)^T bb of the IGR source."""
+    _jacobi5(cfg)
     g = _grid(cfg)
     qb = np.zeros((5, g.nz, g.ny, g.nx))
     lib().orc_source_vjp(g.ptr, _p(_f64(q, (5, g.n))), _p(_f64(bb, (g.n,))), _p(qb))
@@ -204,6 +216,7 @@ def source_vjp(cfg, q, bb):
 def jacobi_vjp(cfg, q, b, sigma0, sweeps, sb):
     """Adjoints of (sigma0, b, rho) of `sweeps` Jacobi sweeps given the
     adjoint sb of their result."""
+    _jacobi5(cfg)
     g = _grid(cfg)
     s = np.array(_f64(sb, (g.n,)), copy=True)
     bb = np.zeros(g.n)

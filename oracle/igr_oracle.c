@@ -17,7 +17,10 @@
  *     7-point elliptic stencil, warm-started Jacobi sweeps, 3rd-order SSP
  *     Runge-Kutta (Gottlieb-Shu);
  *   - Algorithm 1 (flux of p+Sigma in every direction, Sigma reconstructed
- *     like the conserved variables).
+ *     like the conserved variables);
+ *   - the alternatives the same section names: 3rd-order face values and
+ *     (red-black) Gauss-Seidel sweeps, selected by orc_grid.order and
+ *     orc_grid.sigma_solver (the adjoint covers the default scheme only).
  * Readings where the paper is silent (face coefficient of the elliptic
  * operator, local LF speed, boundary treatment of Sigma, dt rule, jet
  * inflow ghosts) are listed next to the code that takes them.
@@ -41,6 +44,8 @@ typedef struct {
     int bc[6];          /* faces -x,+x,-y,+y,-z,+z */
     int njets;
     const double *jets; /* njets x 7: cx, cy, radius, rho, w, p, edge_width */
+    int order;          /* face reconstruction: 5 or 3 (Sec. "Discretization") */
+    int sigma_solver;   /* Sigma sweeps: 0 Jacobi, 1 red-black Gauss-Seidel */
 } orc_grid;
 
 /* ---------------------------------------------------------------- indexing */
@@ -253,13 +258,49 @@ void orc_apply_A(const orc_grid *g, const double *q, const double *s, double *ou
             }
 }
 
+/* Red-black Gauss-Seidel sweeps on A sigma = b (Sec. "Discretization":
+ * Jacobi or Gauss-Seidel, warm-started): each sweep updates the red cells
+ * (i + j + k even), then the black cells (odd), in place, each from the
+ * current values of its neighbours, which are all of the other colour
+ * (periodic axes have even length):
+ *   sigma_i <- (b_i + beta sum_f c_f sigma_nb) / (r_i + beta sum_f c_f). */
+static void rbgs(const orc_grid *g, const double *q, const double *b, double *sigma, int sweeps)
+{
+    const double *rho = q;
+    double beta = g->alpha / (g->dx * g->dx);
+    for (int it = 0; it < sweeps; it++)
+        for (int colour = 0; colour < 2; colour++) {
+#pragma omp parallel for
+            for (int k = 0; k < g->nz; k++)
+                for (int j = 0; j < g->ny; j++)
+                    for (int i = 0; i < g->nx; i++) {
+                        if (((i + j + k) & 1) != colour) continue;
+                        long c = I(g, i, j, k), nb;
+                        double ri = 1.0 / rho[c];
+                        double diag = ri, off = 0.0;
+                        for (int d = 0; d < 6; d++) {
+                            if (!neighbour(g, i, j, k, d, &nb)) continue;
+                            double cf = 0.5 * (ri + 1.0 / rho[nb]);
+                            diag += beta * cf;
+                            off += beta * cf * sigma[nb];
+                        }
+                        sigma[c] = (b[c] + off) / diag;
+                    }
+        }
+}
+
 /* `sweeps` Jacobi sweeps on A sigma = b, warm-started from the incoming
  * sigma (Sec. "Discretization": the previous Sigma is the initial guess):
  *   sigma_i <- (b_i + beta sum_f c_f sigma_nb) / (r_i + beta sum_f c_f),
- * every cell updated from the previous iterate only (two buffers). */
+ * every cell updated from the previous iterate only (two buffers); with
+ * g->sigma_solver = 1 red-black Gauss-Seidel sweeps instead. */
 void orc_jacobi(const orc_grid *g, const double *q, const double *b, double *sigma,
                 int sweeps)
 {
+    if (g->sigma_solver == 1) {
+        rbgs(g, q, b, sigma, sweeps);
+        return;
+    }
     long N = ncell(g);
     const double *rho = q;
     double beta = g->alpha / (g->dx * g->dx);
@@ -299,6 +340,21 @@ static double recon_left(const double v[6])
 static double recon_right(const double v[6])
 {
     return (-3.0 * v[1] + 27.0 * v[2] + 47.0 * v[3] - 13.0 * v[4] + 2.0 * v[5]) / 60.0;
+}
+
+/* 3rd-order alternative (Sec. "Discretization": third- or fifth-order finite
+ * volumes): the quadratic through the three cell averages of the biased
+ * stencil i-1..i+1 (left) or i..i+2 (right), evaluated at face i+1/2. */
+static double recon3_left(const double v[6]) { return (-v[1] + 5.0 * v[2] + 2.0 * v[3]) / 6.0; }
+static double recon3_right(const double v[6]) { return (2.0 * v[2] + 5.0 * v[3] - v[4]) / 6.0; }
+
+static double face_left(const orc_grid *g, const double v[6])
+{
+    return g->order == 3 ? recon3_left(v) : recon_left(v);
+}
+static double face_right(const orc_grid *g, const double v[6])
+{
+    return g->order == 3 ? recon3_right(v) : recon_right(v);
 }
 
 /* Physical flux of the IGR-modified Euler system along axis d,
@@ -355,10 +411,10 @@ static void rhs_from_ghosts(const orc_grid *g, const double *qg, const double *s
                     }
                     double qL[NV], qR[NV], FL[NV], FR[NV];
                     for (int v = 0; v < NV; v++) {
-                        qL[v] = recon_left(vq[v]);
-                        qR[v] = recon_right(vq[v]);
+                        qL[v] = face_left(g, vq[v]);
+                        qR[v] = face_right(g, vq[v]);
                     }
-                    double sL = recon_left(vq[NV]), sR = recon_right(vq[NV]);
+                    double sL = face_left(g, vq[NV]), sR = face_right(g, vq[NV]);
                     double aL = phys_flux(g, qL, sL, d, FL);
                     double aR = phys_flux(g, qR, sR, d, FR);
                     double lam = aL > aR ? aL : aR;
@@ -733,10 +789,10 @@ static void rhs_rev(const orc_grid *g, const double *qg, const double *sg, const
                     }
                     double qL[NV], qR[NV], FL[NV], FR[NV];
                     for (int v = 0; v < NV; v++) {
-                        qL[v] = recon_left(vq[v]);
-                        qR[v] = recon_right(vq[v]);
+                        qL[v] = face_left(g, vq[v]);
+                        qR[v] = face_right(g, vq[v]);
                     }
-                    double sL = recon_left(vq[NV]), sR = recon_right(vq[NV]);
+                    double sL = face_left(g, vq[NV]), sR = face_right(g, vq[NV]);
                     double aL = phys_flux(g, qL, sL, d, FL);
                     double aR = phys_flux(g, qR, sR, d, FR);
                     double lam = aL > aR ? aL : aR;

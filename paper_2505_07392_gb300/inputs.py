@@ -53,6 +53,8 @@ class Case:
     seed: int = 0
     noise: float = 0.0
     mach: float = 0.0           # Mach number of the Taylor-Green initial state
+    order: int = 5              # face reconstruction: 5th (default) or 3rd order
+    sigma_solver: int = 0       # Sigma sweeps: 0 Jacobi, 1 red-black Gauss-Seidel
 
     @property
     def ncells(self) -> int:

@@ -254,6 +254,79 @@ def test_face_states_exact_for_quartic_density(axis):
     assert np.max(np.abs(L[(slice(None),) + tuple(sl)])) <= 1e-12
 
 
+@pytest.mark.parametrize("axis", [0, 2])
+def test_third_order_faces_exact_for_quadratic_only(axis):
+    """3rd-order faces (Sec. "Discretization": third- or fifth-order finite
+    volumes): rho = cell averages of a quadratic along one axis gives equal
+    left/right face values at every face, hence L = 0 away from the boundary;
+    a quartic does not (the 5th-order weights would still be exact there)."""
+    n = 16
+    dims = [3, 3, 3]
+    dims[axis] = n
+    bc = [PERIODIC] * 6
+    bc[2 * axis] = bc[2 * axis + 1] = OUTFLOW
+    c = Case("pin", dims[0], dims[1], dims[2], 1.0 / n, alpha=1.0 / n ** 2, bc=tuple(bc), order=3)
+    xf = np.arange(n + 1) * c.dx
+    shape = (c.nz, c.ny, c.nx)
+    bshape = [1, 1, 1]
+    bshape[2 - axis] = n
+    sl = [slice(None)] * 3
+    sl[2 - axis] = slice(3, n - 3)
+    out = []
+    for coef in ([1.0, 0.4, -0.3], [1.0, 0.4, -0.3, 0.2, 0.9]):
+        row = np.array([_quartic_avg(coef, xf[i], xf[i + 1]) for i in range(n)])
+        rho = np.broadcast_to(row.reshape(bshape), shape).copy()
+        q = cons(rho, 0 * rho, 0 * rho, 0 * rho, 1 + 0 * rho)
+        L = oracle.rhs(c, q, np.zeros(shape))
+        out.append(np.max(np.abs(L[(slice(None),) + tuple(sl)])))
+    assert out[0] <= 1e-12, out
+    assert out[1] > 1e-6, out
+
+
+def test_red_black_gauss_seidel_closed_form():
+    """Red-black Gauss-Seidel (Sec. "Discretization": Jacobi or Gauss-Seidel)
+    on a periodic box of even size with rho = 1, b = 0, Sigma = 1: every red
+    update multiplies the (uniform) black values by l = 6 beta / (1 + 6 beta)
+    and every black update the red ones, so after n sweeps red cells hold
+    l^(2n-1) and black cells l^(2n) (Jacobi gives l^n everywhere)."""
+    c = box(8, (PERIODIC,) * 6, nx=8, ny=6, nz=4)
+    c = replace(c, sigma_solver=1)
+    beta = c.alpha / c.dx ** 2
+    lam = 6 * beta / (1 + 6 * beta)
+    shape = (c.nz, c.ny, c.nx)
+    q = cons(np.ones(shape), np.zeros(shape), np.zeros(shape), np.zeros(shape), np.ones(shape))
+    z, y, x = np.meshgrid(*[np.arange(m) for m in shape], indexing="ij")
+    red = (x + y + z) % 2 == 0
+    for n in (1, 2, 3):
+        s = oracle.jacobi(c, q, np.zeros(shape), np.ones(shape), n)
+        assert np.allclose(s[red], lam ** (2 * n - 1), rtol=1e-14, atol=0)
+        assert np.allclose(s[~red], lam ** (2 * n), rtol=1e-14, atol=0)
+    sj = oracle.jacobi(replace(c, sigma_solver=0), q, np.zeros(shape), np.ones(shape), 3)
+    assert np.allclose(sj, lam ** 3, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("bc", [(OUTFLOW,) * 6, (PERIODIC,) * 4 + (OUTFLOW,) * 2])
+def test_red_black_gauss_seidel_converges_to_direct_solve(bc):
+    """Red-black sweeps reach the dense direct solve of A Sigma = b (A
+    assembled from the oracle's operator), and faster than Jacobi."""
+    c = box(6, bc, nx=6, ny=4, nz=6)
+    rng = np.random.Generator(np.random.Philox(5))
+    shape = (c.nz, c.ny, c.nx)
+    rho = 1 + 0.3 * rng.uniform(-1, 1, shape)
+    q = cons(rho, np.zeros(shape), np.zeros(shape), np.zeros(shape), np.ones(shape))
+    n = rho.size
+    A = np.stack([oracle.apply_A(c, q, np.eye(n)[k]).ravel() for k in range(n)], 1)
+    b = rng.normal(size=n)
+    exact = np.linalg.solve(A, b).reshape(shape)
+    gs = replace(c, sigma_solver=1)
+    s = oracle.jacobi(gs, q, b.reshape(shape), np.zeros(shape), 400)
+    assert np.max(np.abs(s - exact)) <= 1e-12 * np.max(np.abs(exact))
+    for sweeps in (2, 5, 10):
+        e_gs = np.linalg.norm(oracle.jacobi(gs, q, b.reshape(shape), np.zeros(shape), sweeps) - exact)
+        e_j = np.linalg.norm(oracle.jacobi(c, q, b.reshape(shape), np.zeros(shape), sweeps) - exact)
+        assert e_gs < e_j, (sweeps, e_gs, e_j)
+
+
 def test_time_step_rule():
     """dt = cfl dx / max_d(|u_d| + c): rho = 1.4, p = 1 gives c = 1; with
     u = (0.5, -2, 1) the maximum is 3."""
@@ -315,6 +388,21 @@ def test_density_wave_design_order():
         errs.append(np.mean(np.abs(q1[0] - q0[0])))
     orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(orders > 4.5), (errs, orders)
+
+
+@pytest.mark.slow
+def test_density_wave_design_order_third_order_faces():
+    """The same wave with 3rd-order faces and dt ~ dx: both the spatial and
+    the temporal error are 3rd order, so the L1 error falls at order ~3."""
+    errs = []
+    for n in (16, 32, 64):
+        c = replace(inputs.density_wave(n, noise=0.0, ny=3, nz=3), order=3)
+        q0 = inputs.initial_state(c, cell_average=True)
+        steps = int(math.ceil(1.0 / (0.3 * c.dx)))
+        q1, s1, t = oracle.run(c, q0, None, nsteps=steps, fixed_dt=1.0 / steps)
+        errs.append(np.mean(np.abs(q1[0] - q0[0])))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 2.7) and np.all(orders < 3.5), (errs, orders)
 
 
 @pytest.mark.slow
