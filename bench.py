@@ -18,6 +18,7 @@ benchmark) on the host cores, on a bounded crop of the same workload.
 """
 import argparse
 import hashlib
+from dataclasses import replace
 import json
 import math
 import os
@@ -121,7 +122,20 @@ def plume_case(args):
 
 
 def make_case(args):
-    """(case, workload description) of --workload (the plume by default)."""
+    """(case, workload description) of --workload (the plume by default),
+    with the scheme options --order and --sigma-solver."""
+    c, desc = _base_case(args)
+    opts = {}
+    if args.order != 5:
+        opts["order"] = args.order
+        desc += f", {args.order}rd-order faces"
+    if args.sigma_solver == "rbgs":
+        opts["sigma_solver"] = 1
+        desc += ", red-black Gauss-Seidel sweeps"
+    return (replace(c, **opts) if opts else c), desc
+
+
+def _base_case(args):
     if args.workload == "blast":
         n = args.size[0] if args.size else 256
         c = inputs.blast(n)
@@ -360,6 +374,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--workload", default="plume", choices=["plume", "tgv_batch", "blast", "density_wave"])
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--order", type=int, default=5, choices=[3, 5], help="face reconstruction order")
+    ap.add_argument("--sigma-solver", default="jacobi", choices=["jacobi", "rbgs"])
     ap.add_argument("--host-rk-base", action="store_true",
                     help="keep the RK base q^n in host memory (read over NVLink-C2C)")
     args = ap.parse_args()

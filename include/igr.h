@@ -103,7 +103,20 @@ typedef struct {
                            on Grace systems). Device memory drops from 18 to 13 values
                            per cell; results are bitwise those of the in-core mode. Not
                            available in batches. Ignored by igr_solve_sigma_noalloc. */
+    int order;          /* face reconstruction (Sec. "Discretization": third- or
+                           fifth-order finite volumes): 5 (0 means 5) or 3, the
+                           quadratic through three cell averages of each biased
+                           stencil */
+    int sigma_solver;   /* Sigma sweeps (Sec. "Discretization": Jacobi or Gauss-Seidel):
+                           IGR_SOLVER_JACOBI (two Sigma buffers) or IGR_SOLVER_RBGS,
+                           red-black Gauss-Seidel in place (red cells, i + j + k even,
+                           then black; one Sigma buffer; every periodic axis must
+                           have even length). igr_adjoint_step covers order 5 with
+                           Jacobi only. */
 } igr_config;
+
+#define IGR_SOLVER_JACOBI 0
+#define IGR_SOLVER_RBGS 1
 
 typedef struct igr_ctx igr_ctx; /* opaque */
 

@@ -240,6 +240,14 @@ const char *igr::validate_config(const igr_config *c)
         if (c->bc[f] == IGR_BC_INFLOW && f != 4) return "IGR_BC_INFLOW is supported on the -z face only";
     if (c->njets < 0 || (c->njets > 0 && !c->jets)) return "jets is NULL with njets > 0";
     if (c->host_rk_base != 0 && c->host_rk_base != 1) return "host_rk_base must be 0 or 1";
+    if (c->order != 0 && c->order != 3 && c->order != 5) return "order must be 3 or 5 (0 means 5)";
+    if (c->sigma_solver != SOLVER_JACOBI && c->sigma_solver != SOLVER_RBGS) return "unknown sigma_solver";
+    if (c->sigma_solver == SOLVER_RBGS) {
+        const int len[3] = {c->nx, c->ny, c->nz};
+        for (int a = 0; a < 3; a++)
+            if (c->bc[2 * a] == IGR_BC_PERIODIC && len[a] % 2)
+                return "red-black sweeps need an even number of cells along every periodic axis";
+    }
     if (c->njets > 0 && c->bc[4] != IGR_BC_INFLOW) return "jets need an IGR_BC_INFLOW -z face";
     for (int n = 0; n < c->njets; n++) {
         const igr_jet &j = c->jets[n];
@@ -333,13 +341,26 @@ static Inflow inflow_of(igr_ctx *c)
     return in;
 }
 
+// `sweeps` sweeps warm-started from s_first: Jacobi ping-pongs between
+// s_first and s_other; red-black Gauss-Seidel updates s_first in place (two
+// half-sweeps each). *result is the buffer holding the solution.
 static igr_status launch_sweeps(igr_ctx *c, const void *q, const void *b, void *s_first,
                                 void *s_other, int sweeps, void **result)
 {
+    if (c->cfg.sigma_solver == SOLVER_RBGS) {
+        for (int it = 0; it < sweeps; it++)
+            for (int colour = 0; colour < 2; colour++) {
+                prof_begin(c, KC_JACOBI);
+                CU(c, c->ops->jacobi(c->g, c->p, c->tiles, q, b, s_first, s_first, colour, c->st));
+                prof_end(c);
+            }
+        *result = s_first;
+        return IGR_OK;
+    }
     void *src = s_first, *dst = s_other;
     for (int it = 0; it < sweeps; it++) {
         prof_begin(c, KC_JACOBI);
-        CU(c, c->ops->jacobi(c->g, c->p, c->tiles, q, b, src, dst, c->st));
+        CU(c, c->ops->jacobi(c->g, c->p, c->tiles, q, b, src, dst, -1, c->st));
         prof_end(c);
         void *t = src;
         src = dst;
@@ -405,7 +426,8 @@ size_t igr_memory_bytes(const igr_config *cfg)
 {
     if (validate_config(cfg)) return 0;
     Layout L = layout_of(cfg);
-    return (cfg->host_rk_base ? 2 : 3) * round256(L.state) + 2 * round256(L.sig) + round256(L.b) +
+    return (cfg->host_rk_base ? 2 : 3) * round256(L.state) +
+           (cfg->sigma_solver == SOLVER_RBGS ? 1 : 2) * round256(L.sig) + round256(L.b) +
            round256(L.W) + round256(L.J) + round256(L.blockmax) + round256(L.scalars) + round256(L.jets);
 }
 
@@ -432,6 +454,7 @@ igr_status igr_create(const igr_config *cfg, const igr_allocator *allocator, voi
     c->p.gamma = cfg->gamma;
     c->p.alpha = cfg->alpha;
     c->p.cfl = cfg->cfl;
+    c->p.order = cfg->order == 3 ? 3 : 5;
     c->tiles = default_tiles(c->g);
     c->ops = ops_for(cfg->prec);
     if (allocator) {
@@ -458,7 +481,8 @@ igr_status igr_create(const igr_config *cfg, const igr_allocator *allocator, voi
             memset(c->hbase, 0, L.state);
         }
     }
-    for (int n = 0; n < 2 && s == IGR_OK; n++) s = ctx_alloc(c, &c->sig[n], L.sig);
+    const int nsig = cfg->sigma_solver == SOLVER_RBGS ? 1 : 2;  // red-black sweeps work in place
+    for (int n = 0; n < nsig && s == IGR_OK; n++) s = ctx_alloc(c, &c->sig[n], L.sig);
     if (s == IGR_OK) s = ctx_alloc(c, &c->b, L.b);
     if (s == IGR_OK) s = ctx_alloc(c, &c->W, L.W);
     if (s == IGR_OK) s = ctx_alloc(c, &c->J, L.J);
@@ -474,7 +498,7 @@ igr_status igr_create(const igr_config *cfg, const igr_allocator *allocator, voi
     // zero state, Sigma, scalars; build the inflow tables
     cudaError_t e = cudaSuccess;
     for (int n = 0; n < nstate && e == cudaSuccess; n++) e = cudaMemsetAsync(c->q[n], 0, L.state, c->st);
-    for (int n = 0; n < 2 && e == cudaSuccess; n++) e = cudaMemsetAsync(c->sig[n], 0, L.sig, c->st);
+    for (int n = 0; n < nsig && e == cudaSuccess; n++) e = cudaMemsetAsync(c->sig[n], 0, L.sig, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->b, 0, L.b, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->sc, 0, L.scalars, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->W, 0, L.W, c->st);
@@ -793,6 +817,9 @@ igr_status igr_autotune(igr_ctx *c, int reps)
     Tiles best = c->tiles;
     float tbest[3] = {1e30f, 1e30f, 1e30f};
     void *sig = c->sig[c->cur], *scratch = c->sig[1 - c->cur];
+    if (c->cfg.sigma_solver == SOLVER_RBGS)
+        CU(c, cudaMemcpyAsync(c->q[1], sig, c->g.n * (size_t)c->ops->storage_bytes, cudaMemcpyDeviceToDevice,
+                              c->st));
     for (int zc : cand) {
         if (zc > c->g.nz && zc != cand[0]) continue;
         Tiles t = c->tiles;
@@ -803,7 +830,12 @@ igr_status igr_autotune(igr_ctx *c, int reps)
         s = time_launches(c, reps, [&] { return c->ops->source(c->g, c->p, t, inflow_of(c), c->q[0], c->b, c->st); }, &ms);
         if (s != IGR_OK) return s;
         if (ms < tbest[0]) { tbest[0] = ms; best.zc_source = t.zc_source; }
-        s = time_launches(c, reps, [&] { return c->ops->jacobi(c->g, c->p, t, c->q[0], c->b, sig, scratch, c->st); }, &ms);
+        s = time_launches(c, reps, [&] {
+            // red-black: a half-sweep in place on a copy of Sigma in the stage-1 output buffer
+            return c->cfg.sigma_solver == SOLVER_RBGS
+                       ? c->ops->jacobi(c->g, c->p, t, c->q[0], c->b, c->q[1], c->q[1], 0, c->st)
+                       : c->ops->jacobi(c->g, c->p, t, c->q[0], c->b, sig, scratch, -1, c->st);
+        }, &ms);
         if (s != IGR_OK) return s;
         if (ms < tbest[1]) { tbest[1] = ms; best.zc_jacobi = t.zc_jacobi; }
         s = time_launches(c, reps, [&] {
@@ -1051,6 +1083,8 @@ igr_status igr_adjoint_step(igr_ctx *c, const void *q_n, const void *sigma_n, co
     if (!(dt > 0.0)) return fail(c, IGR_ERR_INVALID_ARG, "the adjoint needs a fixed dt > 0");
     if ((int)dtype != storage_dtype(c->cfg.prec))
         return fail(c, IGR_ERR_UNSUPPORTED, "q_n and sigma_n must use the storage dtype");
+    if (c->p.order != 5 || c->cfg.sigma_solver != SOLVER_JACOBI)
+        return fail(c, IGR_ERR_UNSUPPORTED, "the adjoint covers 5th-order faces with Jacobi sweeps");
     if (c->profiling) return fail(c, IGR_ERR_INVALID_ARG, "disable profiling before the adjoint");
     igr_status s = ensure_adjoint(c);
     if (s != IGR_OK) return s;
@@ -1070,7 +1104,7 @@ igr_status igr_adjoint_step(igr_ctx *c, const void *q_n, const void *sigma_n, co
     for (int st = 0; st < 3; st++) {
         CU(c, o->source(c->g, c->p, c->tiles, inflow_of(c), qs[st], A.b, c->st));
         for (int k = 0; k < S; k++)
-            CU(c, o->jacobi(c->g, c->p, c->tiles, qs[st], A.b, it(st, k), it(st, k + 1), c->st));
+            CU(c, o->jacobi(c->g, c->p, c->tiles, qs[st], A.b, it(st, k), it(st, k + 1), -1, c->st));
         if (st < 2) {
             CU(c, o->flux(c->g, c->p, c->tiles, inflow_of(c), st == 0 ? FLUX_STAGE1 : FLUX_STAGE2, qs[st],
                           it(st, S), q_n, (void *)qs[st + 1], nullptr, nullptr, A.sc, c->blockmax, &A.sc->err,

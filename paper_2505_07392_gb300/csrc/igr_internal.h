@@ -22,7 +22,11 @@ struct Geom {
 
 struct Phys {
     double dx, gamma, alpha, cfl;
+    int order;   // face reconstruction: 5 or 3
 };
+
+// Sigma sweep kinds (igr_config.sigma_solver)
+enum { SOLVER_JACOBI = 0, SOLVER_RBGS = 1 };
 
 // bits of Scalars::err
 enum { ERRF_NONFINITE = 1, ERRF_FACE = 2 };
@@ -61,9 +65,11 @@ struct Ops {
     // b = alpha [tr(G^2) + tr(G)^2] from q
     cudaError_t (*source)(const Geom &, const Phys &, const Tiles &, const Inflow &,
                           const void *q, void *b, cudaStream_t st);
-    // one Jacobi sweep s_out <- (b + beta sum c s_in) / (1/rho + beta sum c)
+    // one Jacobi sweep s_out <- (b + beta sum c s_in) / (1/rho + beta sum c) with
+    // colour < 0; with colour 0 or 1 one red-black Gauss-Seidel half-sweep in
+    // place (s_in == s_out), updating the cells with (i + j + k) % 2 == colour
     cudaError_t (*jacobi)(const Geom &, const Phys &, const Tiles &, const void *q,
-                          const void *b, const void *s_in, void *s_out, cudaStream_t st);
+                          const void *b, const void *s_in, void *s_out, int colour, cudaStream_t st);
     // flux divergence and RK stage (mode FLUX_STAGE*), or L(q; Sigma) into rhs (FLUX_RHS).
     // Stage 3 also writes the per-block maximum wave speed of its output to blockmax.
     // Stage 1 with base_out != NULL also copies its input qs there (the RK base of

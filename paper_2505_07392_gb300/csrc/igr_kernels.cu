@@ -444,10 +444,17 @@ __global__ void __launch_bounds__(BT) k_source(Fin<4> q, S *__restrict__ b, Geom
 // c_f = (1/rho_i + 1/rho_nb)/2; a face on a non-periodic boundary carries no
 // term. 1/rho and sigma of plane k sit in a shared tile with a halo of 1;
 // the z-neighbours stay in registers.
+//
+// colour >= 0 makes it one half of a red-black Gauss-Seidel sweep, in place
+// (s_in == s_out): only the cells with (i + j + k) % 2 == colour change.
+// Their neighbours all have the other colour (periodic axes have even
+// length), which no thread writes during the launch, so every updated value
+// is the same whatever the order of execution; values read from cells of
+// the updated colour feed only results that are discarded.
 
 __global__ void __launch_bounds__(BT) k_jacobi(const S *__restrict__ q, const S *__restrict__ b,
-                                                const S *__restrict__ sin, S *__restrict__ sout,
-                                                Geom g, C beta, int zc)
+                                                const S *sin, S *sout, Geom g, C beta, int zc,
+                                                int colour)
 {
     __shared__ C R[HY][HX], SG[HY][HX];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
@@ -522,7 +529,8 @@ __global__ void __launch_bounds__(BT) k_jacobi(const S *__restrict__ q, const S 
             C diag = r0 + c0 + c1 + c2 + c3 + c4 + c5;
             C off = c0 * SG[ty + 1][tx] + c1 * SG[ty + 1][tx + 2] + c2 * SG[ty][tx + 1] +
                     c3 * SG[ty + 2][tx + 1] + c4 * sm + c5 * sp;
-            stc(sout + (idx)k * pl + (idx)(j * g.nx + i), div_c(bv + off, diag));
+            if (colour < 0 || ((i + j + k) & 1) == colour)
+                stc(sout + (idx)k * pl + (idx)(j * g.nx + i), div_c(bv + off, diag));
         }
         rm = r0; sm = s0;
         r0 = rp; s0 = sp;
@@ -682,8 +690,8 @@ __device__ __forceinline__ V4 ld4_mapped(const S *__restrict__ a, const Geom &g,
 }
 
 __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : 2) k_jacobi_v4(const S *__restrict__ q, const S *__restrict__ b,
-                                                   const S *__restrict__ sin, S *__restrict__ sout,
-                                                   Geom g, C beta, int zc)
+                                                   const S *sin, S *sout, Geom g, C beta, int zc,
+                                                   int colour)
 {
     __shared__ __align__(16) C R[HY][HXV];
     __shared__ __align__(16) C SG[HY][HXV];
@@ -800,6 +808,9 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : 2) k_jacobi_v4(const 
                 C diag = r0[c] + c0 + c1 + c2 + c3 + c4 + c5;
                 C off = c0 * sxm + c1 * sxp + c2 * sy0[c] + c3 * sy1[c] + c4 * sm[c] + c5 * sp[c];
                 o[c] = div_c(bv[c] + off, diag);
+                // red-black half-sweep: cells of the other colour keep (and
+                // write back) the value read at the start of the launch
+                if (colour >= 0 && ((i0 + c + j + k) & 1) != colour) o[c] = s0[c];
             }
             st4(sout + (idx)k * pl + (idx)(j * g.nx + i0), o);
         }
@@ -873,6 +884,21 @@ __device__ __forceinline__ C2 rec_right2(C2 b, C2 c, C2 d, C2 e, C2 f)
     return pfma(bcast(C(2.0 / 60.0)), f, t);
 }
 
+// 3rd-order face values of a pair: the quadratic through the three cell
+// averages of the biased stencil (i-1..i+1 left, i..i+2 right) at the face
+__device__ __forceinline__ C2 rec3_left2(C2 b, C2 c, C2 d)
+{
+    C2 t = pmul(bcast(C(-1.0 / 6.0)), b);
+    t = pfma(bcast(C(5.0 / 6.0)), c, t);
+    return pfma(bcast(C(2.0 / 6.0)), d, t);
+}
+__device__ __forceinline__ C2 rec3_right2(C2 c, C2 d, C2 e)
+{
+    C2 t = pmul(bcast(C(2.0 / 6.0)), c);
+    t = pfma(bcast(C(5.0 / 6.0)), d, t);
+    return pfma(bcast(C(-1.0 / 6.0)), e, t);
+}
+
 constexpr int TILE2 = 3 * PH * PW;  // pairs in one plane tile
 constexpr int RING = 7;             // plane tiles resident: k-2..k+3 and k+4 in flight
 
@@ -904,15 +930,17 @@ __device__ __forceinline__ void plane_cell(int e, int &lx, int &ly)
     else { e -= 3 * TX + TY * PW; ly = TY + 3 + e / TX; lx = 3 + e % TX; }
 }
 
-template <int D>
+template <int D, int ORD>
 __device__ __forceinline__ void face_from_stencil(const C2 (&s)[6][3], C gamma, C gm1, C *F,
                                                   bool &bad)
 {
     C L[6], R[6];
 #pragma unroll
     for (int p = 0; p < 3; p++) {
-        C2 l = rec_left2(s[0][p], s[1][p], s[2][p], s[3][p], s[4][p]);
-        C2 r = rec_right2(s[1][p], s[2][p], s[3][p], s[4][p], s[5][p]);
+        C2 l = ORD == 3 ? rec3_left2(s[1][p], s[2][p], s[3][p])
+                        : rec_left2(s[0][p], s[1][p], s[2][p], s[3][p], s[4][p]);
+        C2 r = ORD == 3 ? rec3_right2(s[2][p], s[3][p], s[4][p])
+                        : rec_right2(s[1][p], s[2][p], s[3][p], s[4][p], s[5][p]);
         L[2 * p] = l.x;
         L[2 * p + 1] = l.y;
         R[2 * p] = r.x;
@@ -923,7 +951,7 @@ __device__ __forceinline__ void face_from_stencil(const C2 (&s)[6][3], C gamma, 
 
 // face along D (0, 1) from six consecutive cells of one plane tile starting
 // at element `at`, `step` elements apart
-template <int D>
+template <int D, int ORD>
 __device__ __forceinline__ void tile_face(const C2 *T, int at, int step, C gamma, C gm1, C *F,
                                           bool &bad)
 {
@@ -931,8 +959,9 @@ __device__ __forceinline__ void tile_face(const C2 *T, int at, int step, C gamma
 #pragma unroll
     for (int m = 0; m < 6; m++)
 #pragma unroll
-        for (int p = 0; p < 3; p++) s[m][p] = T[p * PH * PW + at + m * step];
-    face_from_stencil<D>(s, gamma, gm1, F, bad);
+        for (int p = 0; p < 3; p++)
+            s[m][p] = (ORD == 3 && (m == 0 || m == 5)) ? bcast(C(0)) : T[p * PH * PW + at + m * step];
+    face_from_stencil<D, ORD>(s, gamma, gm1, F, bad);
 }
 
 // registers per thread such that NWARP / 4 warps fit one sub-partition's 16K
@@ -952,7 +981,7 @@ constexpr int FLUX_MAXREG = sizeof(C) == 8 ? 224 : 128;
 // Planes k0 - 3..k0 + 2 are filled before the loop (with the boundary index
 // mapping and, below an inflow face, the jet blend). Every plane is read from
 // global memory once per block; nothing relies on the L1 cache.
-template <int mode>
+template <int mode, int ORD>
 __global__ void __maxnreg__(FLUX_MAXREG)
     k_flux(Fin<6> in, Fin<5> qn, Fout<5> out, Frhs rhs, Fout<5> base_out, Geom g, C gamma,
            C half_inv_dx, const Scalars *sc, double *blockmax, int *err, const C *W, const C *J,
@@ -1121,7 +1150,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
 #pragma unroll
                 for (int p = 0; p < 3; p++) sz[m][p] = T[p * PH * PW + tcell];
             }
-            face_from_stencil<2>(sz, gamma, gm1, Fzp, bad);  // z-face k + 1/2
+            face_from_stencil<2, ORD>(sz, gamma, gm1, Fzp, bad);  // z-face k + 1/2
         }
         if (k >= k0) {
             const C2 *T = tile(k);
@@ -1130,21 +1159,21 @@ __global__ void __maxnreg__(FLUX_MAXREG)
             C F[5];
             if (rowwarp) {
                 // x-face at the low side of cell `lane` of row w (tile cells lane-3..lane+2)
-                tile_face<0>(T, (w + 3) * PW + lane, 1, gamma, gm1, F, bad);
+                tile_face<0, ORD>(T, (w + 3) * PW + lane, 1, gamma, gm1, F, bad);
 #pragma unroll
                 for (int u = 0; u < 5; u++) FX[(u * TY + w) * (TX + 1) + lane] = F[u];
                 // y-face below row w in column lane (tile rows w-3..w+2)
-                tile_face<1>(T, w * PW + lane + 3, PW, gamma, gm1, F, bad);
+                tile_face<1, ORD>(T, w * PW + lane + 3, PW, gamma, gm1, F, bad);
 #pragma unroll
                 for (int u = 0; u < 5; u++) FY[(u * (TY + 1) + w) * TX + lane] = F[u];
             } else {
                 // y-face above the last row, column lane
-                tile_face<1>(T, TY * PW + lane + 3, PW, gamma, gm1, F, bad);
+                tile_face<1, ORD>(T, TY * PW + lane + 3, PW, gamma, gm1, F, bad);
 #pragma unroll
                 for (int u = 0; u < 5; u++) FY[(u * (TY + 1) + TY) * TX + lane] = F[u];
                 if (lane < TY) {
                     // x-face at the high end of row `lane`
-                    tile_face<0>(T, (lane + 3) * PW + TX, 1, gamma, gm1, F, bad);
+                    tile_face<0, ORD>(T, (lane + 3) * PW + TX, 1, gamma, gm1, F, bad);
 #pragma unroll
                     for (int u = 0; u < 5; u++) FX[(u * TY + lane) * (TX + 1) + TX] = F[u];
                 }
@@ -1656,17 +1685,17 @@ cudaError_t launch_source(const Geom &g, const Phys &p, const Tiles &t, const In
 }
 
 cudaError_t launch_jacobi(const Geom &g, const Phys &p, const Tiles &t, const void *q,
-                          const void *b, const void *s_in, void *s_out, cudaStream_t st)
+                          const void *b, const void *s_in, void *s_out, int colour, cudaStream_t st)
 {
     if (g.nx % VX == 0) {
         k_jacobi_v4<<<grid_of(g, TXV, BY, t.zc_jacobi), dim3(BX, BY), 0, st>>>(
             (const S *)q, (const S *)b, (const S *)s_in, (S *)s_out, g, C(p.alpha / (p.dx * p.dx)),
-            t.zc_jacobi);
+            t.zc_jacobi, colour);
         return cudaGetLastError();
     }
     k_jacobi<<<grid_of(g, BX, BY, t.zc_jacobi), dim3(BX, BY), 0, st>>>(
         (const S *)q, (const S *)b, (const S *)s_in, (S *)s_out, g, C(p.alpha / (p.dx * p.dx)),
-        t.zc_jacobi);
+        t.zc_jacobi, colour);
     return cudaGetLastError();
 }
 
@@ -1707,11 +1736,19 @@ cudaError_t launch_flux(const Geom &g, const Phys &p, const Tiles &t, const Infl
         }
         return e;
     };
+    if (p.order == 3) {
+        switch (mode) {
+        case FLUX_RHS: return go(k_flux<FLUX_RHS, 3>);
+        case FLUX_STAGE1: return go(k_flux<FLUX_STAGE1, 3>);
+        case FLUX_STAGE2: return go(k_flux<FLUX_STAGE2, 3>);
+        default: return go(k_flux<FLUX_STAGE3, 3>);
+        }
+    }
     switch (mode) {
-    case FLUX_RHS: return go(k_flux<FLUX_RHS>);
-    case FLUX_STAGE1: return go(k_flux<FLUX_STAGE1>);
-    case FLUX_STAGE2: return go(k_flux<FLUX_STAGE2>);
-    default: return go(k_flux<FLUX_STAGE3>);
+    case FLUX_RHS: return go(k_flux<FLUX_RHS, 5>);
+    case FLUX_STAGE1: return go(k_flux<FLUX_STAGE1, 5>);
+    case FLUX_STAGE2: return go(k_flux<FLUX_STAGE2, 5>);
+    default: return go(k_flux<FLUX_STAGE3, 5>);
     }
 }
 

@@ -105,6 +105,7 @@ igr_status igr_solve_sigma_noalloc(const igr_config *cfg, const void *q, void *s
     p.gamma = cfg->gamma;
     p.alpha = cfg->alpha;
     p.cfl = cfg->cfl;
+    p.order = cfg->order == 3 ? 3 : 5;
     Tiles t = default_tiles(g);
     Inflow none;
     none.W = nullptr;
@@ -117,12 +118,20 @@ igr_status igr_solve_sigma_noalloc(const igr_config *cfg, const void *q, void *s
     cudaError_t e = o->source(g, p, t, none, q, b, st);
     if (e != cudaSuccess) return fail(IGR_ERR_CUDA, "source kernel launch", e);
     void *src = sigma_inout, *dst = other;
-    for (int it = 0; it < sweeps; it++) {
-        e = o->jacobi(g, p, t, q, b, src, dst, st);
-        if (e != cudaSuccess) return fail(IGR_ERR_CUDA, "Jacobi kernel launch", e);
-        void *tmp = src;
-        src = dst;
-        dst = tmp;
+    if (cfg->sigma_solver == SOLVER_RBGS) {  // in place: red then black cells
+        for (int it = 0; it < sweeps; it++)
+            for (int colour = 0; colour < 2; colour++) {
+                e = o->jacobi(g, p, t, q, b, sigma_inout, sigma_inout, colour, st);
+                if (e != cudaSuccess) return fail(IGR_ERR_CUDA, "Gauss-Seidel kernel launch", e);
+            }
+    } else {
+        for (int it = 0; it < sweeps; it++) {
+            e = o->jacobi(g, p, t, q, b, src, dst, -1, st);
+            if (e != cudaSuccess) return fail(IGR_ERR_CUDA, "Jacobi kernel launch", e);
+            void *tmp = src;
+            src = dst;
+            dst = tmp;
+        }
     }
     if (src != sigma_inout) {
         e = cudaMemcpyAsync(sigma_inout, src, (size_t)g.n * o->storage_bytes,

@@ -42,7 +42,8 @@ class Config(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double),
                 ("gamma", C.c_double), ("alpha", C.c_double), ("cfl", C.c_double),
                 ("sweeps", C.c_int), ("prec", C.c_int), ("bc", C.c_int * 6),
-                ("jets", C.POINTER(Jet)), ("njets", C.c_int), ("host_rk_base", C.c_int)]
+                ("jets", C.POINTER(Jet)), ("njets", C.c_int), ("host_rk_base", C.c_int),
+                ("order", C.c_int), ("sigma_solver", C.c_int)]
 
 
 class IGRError(RuntimeError):
@@ -114,7 +115,8 @@ def make_config(case, precision: str = "f32", host_rk_base: bool = False):
     jets = (Jet * max(1, len(case.jets)))(*[Jet(*j) for j in case.jets])
     cfg = Config(int(case.nx), int(case.ny), int(case.nz), float(case.dx), float(case.gamma),
                  float(case.alpha), float(case.cfl), int(case.sweeps), PRECISIONS[precision],
-                 (C.c_int * 6)(*[int(b) for b in case.bc]), jets, len(case.jets), int(host_rk_base))
+                 (C.c_int * 6)(*[int(b) for b in case.bc]), jets, len(case.jets), int(host_rk_base),
+                 int(getattr(case, "order", 5)), int(getattr(case, "sigma_solver", 0)))
     return cfg, jets
 
 

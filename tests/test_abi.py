@@ -68,3 +68,14 @@ def test_host_only_calls(libigr):
     cfgh.host_rk_base = 2
     assert L.igr_create(ctypes.byref(cfgh), None, None, ctypes.byref(h)) == igr.ERR_INVALID_ARG
     assert b"host_rk_base" in L.igr_last_error(None)
+    # red-black sweeps work in place: one Sigma buffer fewer
+    from dataclasses import replace
+    cfgr, _ = igr.make_config(replace(case, sigma_solver=1), "f16")
+    sig = -(-2 * n // 256) * 256
+    assert L.igr_memory_bytes(ctypes.byref(cfgd)) - L.igr_memory_bytes(ctypes.byref(cfgr)) == sig
+    # ... and need even periodic axes; only orders 3 and 5 exist
+    for bad_case, word in ((replace(inputs.density_wave(31), sigma_solver=1), b"even"),
+                           (replace(case, order=4), b"order")):
+        cb, _ = igr.make_config(bad_case, "f32")
+        assert L.igr_create(ctypes.byref(cb), None, None, ctypes.byref(h)) == igr.ERR_INVALID_ARG
+        assert word in L.igr_last_error(None)

@@ -79,6 +79,34 @@ def test_noalloc_solve_matches_context_solve_twice():
     assert not np.array_equal(results[0], results[1])
 
 
+def test_noalloc_red_black_sweeps():
+    """With red-black Gauss-Seidel sweeps (in place, no second Sigma buffer)
+    the allocation-free solve gives the context solve's bits."""
+    import torch
+    from dataclasses import replace
+    from paper_2505_07392_gb300 import igr
+    L = igr.lib()
+    case = Case("noalloc", 40, 36, 28, 1.0 / 40, alpha=1.0 / 40 ** 2, sweeps=3, sigma_solver=1,
+                bc=(OUTFLOW, OUTFLOW, PERIODIC, PERIODIC, OUTFLOW, OUTFLOW))
+    cfg, _jets = igr.make_config(case, "f32")
+    stream = torch.cuda.current_stream()
+    q = torch.from_numpy(_state(case, 3)).float().cuda()
+    s0 = (0.05 * torch.from_numpy(_state(case, 13)[0])).float().cuda()
+    with igr.Solver(case, "f32") as s:
+        ref = s.solve_sigma(q, s0.clone(), 3)
+        torch.cuda.synchronize()
+        ref = ref.cpu()
+    sig = s0.clone()
+    st = L.igr_solve_sigma_noalloc(C.byref(cfg), C.c_void_p(q.data_ptr()), C.c_void_p(sig.data_ptr()),
+                                   3, C.c_void_p(stream.cuda_stream))
+    assert st == igr.OK, L.igr_noalloc_last_error().decode()
+    torch.cuda.synchronize()
+    assert torch.equal(sig.cpu(), ref)
+    with igr.Solver(replace(case, sigma_solver=0), "f32") as s:
+        jac = s.solve_sigma(q, s0.clone(), 3).cpu()
+    assert not torch.equal(jac, ref)  # the red-black path really ran
+
+
 def test_noalloc_rejects_what_it_cannot_hold():
     from paper_2505_07392_gb300 import igr
     L = igr.lib()
