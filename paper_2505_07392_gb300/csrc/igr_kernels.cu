@@ -1003,7 +1003,12 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     const C gm1 = gamma - C(1);
     bool bad = false;       // a face state with rho <= 0 or p <= 0 (warning)
     bool nonfinite = false; // a non-finite output (error)
-    auto tile = [&](int kk) { return P + ((kk - k0 + 3) % RING) * TILE2; };
+    // ring slot offsets (in pairs) of planes k-2..k+4 in iteration k, rotated
+    // once per plane: plane kk sits in slot (kk - k0 + 3) mod RING
+    int ro[RING];
+#pragma unroll
+    for (int m = 0; m < RING; m++) ro[m] = m * TILE2;  // k = k0 - 1: planes k0-3.. in slots 0..
+
 
     // tile cells this thread loads each plane: shared and in-plane offsets
     int soff[LPT];
@@ -1026,7 +1031,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     // jet blend below an inflow face)
 #pragma unroll 1
     for (int kk = k0 - 3; kk < k0 + 3; kk++) {
-        C2 *T = tile(kk);
+        C2 *T = P + (kk - k0 + 3) * TILE2;
         const idx zb = (idx)zmap(kk, g) * pl;
         const bool blend = kk < 0 && g.bc[4] == BC_INFLOW;
 #pragma unroll
@@ -1049,8 +1054,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     // cp.async; 16-bit storage loads raw values into registers at `fetch`
     // and converts and stores them at `land`
     S Rg[LPT][6];  // (unused with cp.async)
-    auto fetch = [&](int kk) {
-        C2 *T = tile(kk);
+    auto fetch = [&](int kk, C2 *T) {
         const idx zb = (idx)zmap(kk, g) * pl;
 #pragma unroll
         for (int r = 0; r < LPT; r++)
@@ -1065,11 +1069,10 @@ __global__ void __maxnreg__(FLUX_MAXREG)
             }
         if constexpr (kAsyncTile) cp_async_commit();
     };
-    auto land = [&](int kk) {
+    auto land = [&](C2 *T) {
         if constexpr (kAsyncTile) {
             cp_async_wait_all();
         } else {
-            C2 *T = tile(kk);
 #pragma unroll
             for (int r = 0; r < LPT; r++)
                 if (soff[r] >= 0)
@@ -1094,7 +1097,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     S qnv[5];  // q^n of plane k - 1 (stages 2 and 3), loaded one iteration ahead
 
     // divergence and stage combination of plane kk (face buffers of parity kk)
-    auto finish = [&](int kk) {
+    auto finish = [&](int kk, const C2 *T) {
         const C *FX = FXb + (kk & 1) * 5 * TY * (TX + 1);
         const C *FY = FYb + (kk & 1) * 5 * (TY + 1) * TX;
         idx c = (idx)kk * pl + own;
@@ -1111,7 +1114,6 @@ __global__ void __maxnreg__(FLUX_MAXREG)
             for (int u = 0; u < 5; u++) rhs.p[u][c] = Lv[u];
             nonfinite |= !isfinite((Lv[0] + Lv[1]) + (Lv[2] + Lv[3]) + Lv[4]);
         } else {
-            const C2 *T = tile(kk);
             C2 a = T[tcell], b = T[PH * PW + tcell], e = T[2 * PH * PW + tcell];
             const C qsv[5] = {a.x, a.y, b.x, b.y, e.x};
             if (mode == FLUX_STAGE1 && base_out.p[0]) {
@@ -1133,9 +1135,9 @@ __global__ void __maxnreg__(FLUX_MAXREG)
 
     for (int k = k0 - 1; k < k1; k++) {
         const bool more = k + 4 <= k1 + 2;  // plane k + 4 feeds the z-faces
-        if (more) fetch(k + 4);
+        if (more) fetch(k + 4, P + ro[6]);
         if (rowwarp) {
-            if (k > k0 && active) finish(k - 1);
+            if (k > k0 && active) finish(k - 1, P + ro[1]);
 #pragma unroll
             for (int u = 0; u < 5; u++) Fzm[u] = Fzp[u];
             if (k >= k0 && active && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3)) {
@@ -1146,14 +1148,14 @@ __global__ void __maxnreg__(FLUX_MAXREG)
             C2 sz[6][3];  // z-stencil: planes k - 2..k + 3 at this cell
 #pragma unroll
             for (int m = 0; m < 6; m++) {
-                const C2 *T = tile(k - 2 + m);
+                const C2 *T = P + ro[m];
 #pragma unroll
                 for (int p = 0; p < 3; p++) sz[m][p] = T[p * PH * PW + tcell];
             }
             face_from_stencil<2, ORD>(sz, gamma, gm1, Fzp, bad);  // z-face k + 1/2
         }
         if (k >= k0) {
-            const C2 *T = tile(k);
+            const C2 *T = P + ro[2];
             C *FX = FXb + (k & 1) * 5 * TY * (TX + 1);
             C *FY = FYb + (k & 1) * 5 * (TY + 1) * TX;
             C F[5];
@@ -1179,10 +1181,16 @@ __global__ void __maxnreg__(FLUX_MAXREG)
                 }
             }
         }
-        if (more) land(k + 4);
+        if (more) land(P + ro[6]);
         __syncthreads();
+        const int r0 = ro[0];
+#pragma unroll
+        for (int m = 0; m + 1 < RING; m++) ro[m] = ro[m + 1];
+        ro[RING - 1] = r0;
     }
-    if (active) finish(k1 - 1);  // the last plane (its faces are behind the final barrier)
+    // the last plane (its faces are behind the final barrier; after the
+    // rotation plane k1 - 1 sits at ro[1])
+    if (active) finish(k1 - 1, P + ro[1]);
     if (nonfinite || bad) atomicOr(err, (nonfinite ? ERRF_NONFINITE : 0) | (bad ? ERRF_FACE : 0));
     if (mode == FLUX_STAGE3) {
         double m = block_max<NT>(double(smax));
