@@ -10,7 +10,8 @@ arrays through ctypes. A grid description is any object with the attributes
 ``nx, ny, nz, dx, gamma, alpha, cfl, sweeps, bc`` (6 ints: 0 periodic,
 1 outflow, 2 inflow, faces -x,+x,-y,+y,-z,+z) and ``jets`` (list of
 ``(cx, cy, radius, rho, w, p, edge_width)``), and optionally ``order`` (5 or 3)
-and ``sigma_solver`` (0 Jacobi, 1 red-black Gauss-Seidel).
+``sigma_solver`` (0 Jacobi, 1 red-black Gauss-Seidel) and the viscosities
+``mu``, ``zeta`` (0: Euler).
 """
 import ctypes as C
 
@@ -26,7 +27,8 @@ class _Grid(C.Structure):
                 ("dx", C.c_double), ("gamma", C.c_double), ("alpha", C.c_double),
                 ("cfl", C.c_double), ("sweeps", C.c_int), ("bc", C.c_int * 6),
                 ("njets", C.c_int), ("jets", C.POINTER(C.c_double)),
-                ("order", C.c_int), ("sigma_solver", C.c_int)]
+                ("order", C.c_int), ("sigma_solver", C.c_int),
+                ("mu", C.c_double), ("zeta", C.c_double)]
 
 
 def lib():
@@ -67,7 +69,8 @@ class Grid:
                        float(cfg.alpha), float(cfg.cfl), int(cfg.sweeps),
                        (C.c_int * 6)(*[int(b) for b in cfg.bc]), int(jets.shape[0]),
                        jets.ctypes.data_as(C.POINTER(C.c_double)),
-                       int(getattr(cfg, "order", 5)), int(getattr(cfg, "sigma_solver", 0)))
+                       int(getattr(cfg, "order", 5)), int(getattr(cfg, "sigma_solver", 0)),
+                       float(getattr(cfg, "mu", 0.0)), float(getattr(cfg, "zeta", 0.0)))
 
     @property
     def n(self):
@@ -169,8 +172,9 @@ def run(cfg, q, sigma=None, nsteps=1, fixed_dt=0.0):
 
 def _jacobi5(cfg):
     """The adjoint is written for the default scheme: 5th-order faces, Jacobi."""
-    if getattr(cfg, "order", 5) != 5 or getattr(cfg, "sigma_solver", 0) != 0:
-        raise ValueError("the adjoint covers 5th-order faces with Jacobi sweeps only")
+    if (getattr(cfg, "order", 5) != 5 or getattr(cfg, "sigma_solver", 0) != 0
+            or getattr(cfg, "mu", 0.0) != 0.0 or getattr(cfg, "zeta", 0.0) != 0.0):
+        raise ValueError("the adjoint covers the inviscid scheme with 5th-order faces and Jacobi sweeps only")
 
 
 def adjoint_step(cfg, q, sigma, dt, lq, ls):

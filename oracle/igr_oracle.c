@@ -20,7 +20,9 @@
  *     like the conserved variables);
  *   - the alternatives the same section names: 3rd-order face values and
  *     (red-black) Gauss-Seidel sweeps, selected by orc_grid.order and
- *     orc_grid.sigma_solver (the adjoint covers the default scheme only).
+ *     orc_grid.sigma_solver (the adjoint covers the default scheme only);
+ *   - viscous stresses, Eq. (constitutive_law), when orc_grid.mu or
+ *     orc_grid.zeta is nonzero (Navier-Stokes form of the same system).
  * Readings where the paper is silent (face coefficient of the elliptic
  * operator, local LF speed, boundary treatment of Sigma, dt rule, jet
  * inflow ghosts) are listed next to the code that takes them.
@@ -46,6 +48,7 @@ typedef struct {
     const double *jets; /* njets x 7: cx, cy, radius, rho, w, p, edge_width */
     int order;          /* face reconstruction: 5 or 3 (Sec. "Discretization") */
     int sigma_solver;   /* Sigma sweeps: 0 Jacobi, 1 red-black Gauss-Seidel */
+    double mu, zeta;    /* shear and bulk viscosity, Eq. (constitutive_law); 0 = Euler */
 } orc_grid;
 
 /* ---------------------------------------------------------------- indexing */
@@ -126,7 +129,15 @@ static void fill_axis_z(const orc_grid *g, double *f, int var)
                 int shi = g->bc[5] == BC_PERIODIC ? hi % nz : nz - 1;
                 double vlo = f[GI(g, i, j, slo)];
                 if (g->bc[4] == BC_INFLOW && var >= 0) {
-                    double x = (i + 0.5) * g->dx, y = (j + 0.5) * g->dx;
+                    /* the blend weight of a ghost column outside the face's
+                     * extent is that of the face cell it maps to (the x and
+                     * y ghosts of the source plane hold those cells' values) */
+                    int mi = i, mj = j;
+                    if (mi < 0) mi = g->bc[0] == BC_PERIODIC ? ((mi % g->nx) + g->nx) % g->nx : 0;
+                    if (mi >= g->nx) mi = g->bc[1] == BC_PERIODIC ? mi % g->nx : g->nx - 1;
+                    if (mj < 0) mj = g->bc[2] == BC_PERIODIC ? ((mj % g->ny) + g->ny) % g->ny : 0;
+                    if (mj >= g->ny) mj = g->bc[3] == BC_PERIODIC ? mj % g->ny : g->ny - 1;
+                    double x = (mi + 0.5) * g->dx, y = (mj + 0.5) * g->dx;
                     double wsum = 0.0, jsum = 0.0;
                     for (int n = 0; n < g->njets; n++) {
                         const double *J = g->jets + 7 * n;
@@ -376,6 +387,58 @@ static double phys_flux(const orc_grid *g, const double qv[NV], double sig, int 
     return fabs(u[d]) + sqrt(g->gamma * p / rho);
 }
 
+/* velocity u = m / rho of ghost-array cell gi */
+static void vel_at(const orc_grid *g, const double *qg, long gi, double u[3])
+{
+    long NG = nghost(g);
+    for (int a = 0; a < 3; a++) u[a] = qg[(1 + a) * NG + gi] / qg[gi];
+}
+
+/* Viscous part of the flux through the face between cells A = c - e_d and
+ * B = c along axis d (c = (i, j, k)), Eqs. (igrmobalance)-(igrenbalance)
+ * with the stress of Eq. (constitutive_law)
+ *   tau_ab = mu (du_a/dx_b + du_b/dx_a) + (zeta - 2 mu / 3) delta_ab div u
+ * (reading: the garbled delta_ij du_i/dx_j term is the divergence, Stokes'
+ * form). Velocity derivatives at the face, second order (Sec.
+ * "Discretization": second-order derivatives of u suffice; reading: on the
+ * compact face stencil rather than reconstructed cell-centre gradients):
+ *   normal      du_a/dx_d = (u_a(B) - u_a(A)) / dx,
+ *   tangential  du_a/dx_t = [(u_a(A+e_t) - u_a(A-e_t)) + (u_a(B+e_t) - u_a(B-e_t))] / (4 dx),
+ * face velocity (u(A) + u(B)) / 2. The flux adds -tau_{a d} to momentum
+ * component a and -sum_a u_a tau_{a d} to energy. */
+static void viscous_flux(const orc_grid *g, const double *qg, int i, int j, int k, int d,
+                         double Fv[NV])
+{
+    int c[3] = {i, j, k}, a0[3] = {i, j, k};
+    a0[d] -= 1;
+    double uA[3], uB[3], Gr[3][3];
+    vel_at(g, qg, GI(g, a0[0], a0[1], a0[2]), uA);
+    vel_at(g, qg, GI(g, c[0], c[1], c[2]), uB);
+    for (int a = 0; a < 3; a++) Gr[a][d] = (uB[a] - uA[a]) / g->dx;
+    for (int t = 0; t < 3; t++) {
+        if (t == d) continue;
+        int Ap[3] = {a0[0], a0[1], a0[2]}, Am[3] = {a0[0], a0[1], a0[2]};
+        int Bp[3] = {c[0], c[1], c[2]}, Bm[3] = {c[0], c[1], c[2]};
+        Ap[t] += 1; Am[t] -= 1; Bp[t] += 1; Bm[t] -= 1;
+        double uAp[3], uAm[3], uBp[3], uBm[3];
+        vel_at(g, qg, GI(g, Ap[0], Ap[1], Ap[2]), uAp);
+        vel_at(g, qg, GI(g, Am[0], Am[1], Am[2]), uAm);
+        vel_at(g, qg, GI(g, Bp[0], Bp[1], Bp[2]), uBp);
+        vel_at(g, qg, GI(g, Bm[0], Bm[1], Bm[2]), uBm);
+        for (int a = 0; a < 3; a++)
+            Gr[a][t] = ((uAp[a] - uAm[a]) + (uBp[a] - uBm[a])) / (4.0 * g->dx);
+    }
+    double div = Gr[0][0] + Gr[1][1] + Gr[2][2];
+    double work = 0.0;
+    Fv[0] = 0.0;
+    for (int a = 0; a < 3; a++) {
+        double tau = g->mu * (Gr[a][d] + Gr[d][a]) + (a == d ? (g->zeta - 2.0 * g->mu / 3.0) * div : 0.0);
+        Fv[1 + a] = -tau;
+        work += 0.5 * (uA[a] + uB[a]) * tau;
+    }
+    Fv[4] = -work;
+}
+
 /* Spatial operator L(q; Sigma) = -div F_hat at every interior cell, with the
  * local Lax-Friedrichs flux (reading: local speed)
  *   F_hat = (F(q_L) + F(q_R)) / 2 - lambda (q_R - q_L) / 2,
@@ -421,6 +484,11 @@ static void rhs_from_ghosts(const orc_grid *g, const double *qg, const double *s
                     long fi = ((long)k * fy + j) * fx + i;
                     for (int v = 0; v < NV; v++)
                         F[v * NF + fi] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (qR[v] - qL[v]);
+                    if (g->mu != 0.0 || g->zeta != 0.0) {
+                        double Fv[NV];
+                        viscous_flux(g, qg, i, j, k, d, Fv);
+                        for (int v = 0; v < NV; v++) F[v * NF + fi] += Fv[v];
+                    }
                 }
         /* accumulate the flux difference of this direction */
         for (int k = 0; k < nz; k++)

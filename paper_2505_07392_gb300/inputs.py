@@ -55,6 +55,8 @@ class Case:
     mach: float = 0.0           # Mach number of the Taylor-Green initial state
     order: int = 5              # face reconstruction: 5th (default) or 3rd order
     sigma_solver: int = 0       # Sigma sweeps: 0 Jacobi, 1 red-black Gauss-Seidel
+    mu: float = 0.0             # shear viscosity (0: Euler)
+    zeta: float = 0.0           # bulk viscosity
 
     @property
     def ncells(self) -> int:

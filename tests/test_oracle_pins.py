@@ -327,6 +327,97 @@ def test_red_black_gauss_seidel_converges_to_direct_solve(bc):
         assert e_gs < e_j, (sweeps, e_gs, e_j)
 
 
+def _visc_rhs(c, q):
+    """Viscous part of L: L(mu, zeta) - L(0, 0) on the same state, Sigma = 0."""
+    z = np.zeros((c.nz, c.ny, c.nx))
+    return oracle.rhs(c, q, z) - oracle.rhs(replace(c, mu=0.0, zeta=0.0), q, z)
+
+
+def test_viscous_shear_wave_closed_form():
+    """u = (0, v(x), 0), rho = 1, p = 1 (Eq. constitutive_law, compact face
+    stencil): only tau_xy = mu dv/dx acts, so the viscous rates are exactly
+    m_y: mu (v[i+1] - 2 v[i] + v[i-1]) / dx^2 and
+    E:   mu (v[i+1]^2 - 2 v[i]^2 + v[i-1]^2) / (2 dx^2)
+    (the work term u . tau with the face velocity (v[i] + v[i+1]) / 2);
+    mass and the other momenta get nothing."""
+    n = 24
+    c = replace(box(n, (PERIODIC,) * 6, nx=n, ny=4, nz=3), mu=0.013)
+    x = (np.arange(n) + 0.5) / n
+    v1 = 0.3 * np.sin(2 * np.pi * x) + 0.1 * np.cos(6 * np.pi * x)
+    shape = (c.nz, c.ny, n)
+    v = np.broadcast_to(v1, shape)
+    q = cons(np.ones(shape), np.zeros(shape), v, np.zeros(shape), np.ones(shape))
+    L = _visc_rhs(c, q)
+    dx2 = c.dx ** 2
+    vp, vm = np.roll(v1, -1), np.roll(v1, 1)
+    assert np.allclose(L[2], c.mu * (vp - 2 * v1 + vm) / dx2, rtol=0, atol=1e-12)
+    assert np.allclose(L[4], c.mu * (vp ** 2 - 2 * v1 ** 2 + vm ** 2) / (2 * dx2), rtol=0, atol=1e-12)
+    for f in (0, 1, 3):
+        assert np.max(np.abs(L[f])) <= 1e-12
+
+
+def test_viscous_longitudinal_wave_closed_form():
+    """u = (u(x), 0, 0): tau_xx = (4 mu / 3 + zeta) du/dx (Stokes' form of the
+    normal stress), so m_x gains (4 mu/3 + zeta)(u[i+1] - 2u[i] + u[i-1]) / dx^2
+    and E the matching work term; separate mu and zeta pin both factors."""
+    n = 20
+    for mu, zeta in ((0.01, 0.0), (0.0, 0.02), (0.007, 0.015)):
+        c = replace(box(n, (PERIODIC,) * 6, nx=n, ny=3, nz=4), mu=mu, zeta=zeta)
+        x = (np.arange(n) + 0.5) / n
+        u1 = 0.2 * np.sin(2 * np.pi * x + 0.3)
+        shape = (c.nz, c.ny, n)
+        u = np.broadcast_to(u1, shape)
+        q = cons(np.ones(shape), u, np.zeros(shape), np.zeros(shape), np.ones(shape))
+        L = _visc_rhs(c, q)
+        k = 4 * mu / 3 + zeta
+        up, um = np.roll(u1, -1), np.roll(u1, 1)
+        dx2 = c.dx ** 2
+        assert np.allclose(L[1], k * (up - 2 * u1 + um) / dx2, rtol=0, atol=1e-12), (mu, zeta)
+        assert np.allclose(L[4], k * (up ** 2 - 2 * u1 ** 2 + um ** 2) / (2 * dx2), rtol=0, atol=1e-12)
+        for f in (0, 2, 3):
+            assert np.max(np.abs(L[f])) <= 1e-12
+
+
+def test_viscous_operator_second_order():
+    """A smooth periodic 3D flow with variable density: the viscous part of L
+    converges at second order to div tau and div (u . tau) of Eq.
+    (constitutive_law), differentiated symbolically (every tangential and
+    divergence term enters)."""
+    sp = pytest.importorskip("sympy")
+    X, Y, Z = sp.symbols("x y z")
+    tp = 2 * sp.pi
+    mu, zeta = 0.011, 0.023
+    rho = 1 + 0.2 * sp.sin(tp * (X + Y)) * sp.cos(tp * Z)
+    u = [0.3 * sp.sin(tp * Y) * sp.cos(tp * Z) + 0.1 * sp.cos(tp * X),
+         0.25 * sp.sin(tp * Z) * sp.cos(tp * X),
+         0.2 * sp.cos(tp * (X + Y)) + 0.1 * sp.sin(tp * Z)]
+    xs = (X, Y, Z)
+    Gr = [[sp.diff(u[a], xs[b]) for b in range(3)] for a in range(3)]
+    div = Gr[0][0] + Gr[1][1] + Gr[2][2]
+    tau = [[mu * (Gr[a][b] + Gr[b][a]) + (zeta - 2 * mu / 3) * div * (1 if a == b else 0)
+            for b in range(3)] for a in range(3)]
+    rhs_m = [sum(sp.diff(tau[a][b], xs[b]) for b in range(3)) for a in range(3)]
+    rhs_E = sum(sp.diff(sum(u[a] * tau[a][b] for a in range(3)), xs[b]) for b in range(3))
+    fr = sp.lambdify(xs, rho, "numpy")
+    fu = [sp.lambdify(xs, e, "numpy") for e in u]
+    fm = [sp.lambdify(xs, e, "numpy") for e in rhs_m]
+    fE = sp.lambdify(xs, rhs_E, "numpy")
+    errs = []
+    for n in (16, 32):
+        c = replace(box(n, (PERIODIC,) * 6, nx=n, ny=n, nz=n), mu=mu, zeta=zeta)
+        z, y, x = np.meshgrid(*[(np.arange(n) + 0.5) / n] * 3, indexing="ij")
+        r = fr(x, y, z)
+        uu = [fu[a](x, y, z) * np.ones_like(x) for a in range(3)]
+        q = cons(r, uu[0], uu[1], uu[2], np.ones_like(x))
+        L = _visc_rhs(c, q)
+        e = [np.max(np.abs(L[1 + a] - fm[a](x, y, z))) for a in range(3)]
+        e.append(np.max(np.abs(L[4] - fE(x, y, z))))
+        assert np.max(np.abs(L[0])) <= 1e-12
+        errs.append(np.array(e))
+    orders = np.log2(errs[0] / errs[1])
+    assert np.all(orders > 1.8) and np.all(orders < 2.4), (errs, orders)
+
+
 def test_time_step_rule():
     """dt = cfl dx / max_d(|u_d| + c): rho = 1.4, p = 1 gives c = 1; with
     u = (0.5, -2, 1) the maximum is 3."""
