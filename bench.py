@@ -132,6 +132,9 @@ def make_case(args):
     if args.sigma_solver == "rbgs":
         opts["sigma_solver"] = 1
         desc += ", red-black Gauss-Seidel sweeps"
+    if args.mu or args.zeta:
+        opts["mu"], opts["zeta"] = args.mu, args.zeta
+        desc += f", viscous (mu={args.mu:g}, zeta={args.zeta:g})"
     return (replace(c, **opts) if opts else c), desc
 
 
@@ -376,6 +379,8 @@ def main():
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--order", type=int, default=5, choices=[3, 5], help="face reconstruction order")
     ap.add_argument("--sigma-solver", default="jacobi", choices=["jacobi", "rbgs"])
+    ap.add_argument("--mu", type=float, default=0.0, help="shear viscosity (0: Euler)")
+    ap.add_argument("--zeta", type=float, default=0.0, help="bulk viscosity")
     ap.add_argument("--host-rk-base", action="store_true",
                     help="keep the RK base q^n in host memory (read over NVLink-C2C)")
     args = ap.parse_args()

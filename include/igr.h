@@ -113,6 +113,14 @@ typedef struct {
                            then black; one Sigma buffer; every periodic axis must
                            have even length). igr_adjoint_step covers order 5 with
                            Jacobi only. */
+    double mu, zeta;    /* shear and bulk viscosity, Eq. (constitutive_law); 0, 0 is the
+                           Euler system. Nonzero adds tau = mu (grad u + grad u^T)
+                           + (zeta - 2 mu/3)(div u) I to the momentum flux and u . tau
+                           to the energy flux, with second-order face derivatives (the
+                           two cells across the face; tangential derivatives averaged
+                           over both). dt keeps the convective CFL rule: the caller
+                           keeps dt within the viscous limit ~ rho dx^2 / mu. Not in
+                           igr_adjoint_step. */
 } igr_config;
 
 #define IGR_SOLVER_JACOBI 0

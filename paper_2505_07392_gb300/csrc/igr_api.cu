@@ -242,6 +242,8 @@ const char *igr::validate_config(const igr_config *c)
     if (c->host_rk_base != 0 && c->host_rk_base != 1) return "host_rk_base must be 0 or 1";
     if (c->order != 0 && c->order != 3 && c->order != 5) return "order must be 3 or 5 (0 means 5)";
     if (c->sigma_solver != SOLVER_JACOBI && c->sigma_solver != SOLVER_RBGS) return "unknown sigma_solver";
+    if (!(c->mu >= 0.0) || !(c->zeta >= 0.0) || isinf(c->mu) || isinf(c->zeta))
+        return "mu and zeta must be finite and >= 0";
     if (c->sigma_solver == SOLVER_RBGS) {
         const int len[3] = {c->nx, c->ny, c->nz};
         for (int a = 0; a < 3; a++)
@@ -455,6 +457,8 @@ igr_status igr_create(const igr_config *cfg, const igr_allocator *allocator, voi
     c->p.alpha = cfg->alpha;
     c->p.cfl = cfg->cfl;
     c->p.order = cfg->order == 3 ? 3 : 5;
+    c->p.mu = cfg->mu;
+    c->p.zeta = cfg->zeta;
     c->tiles = default_tiles(c->g);
     c->ops = ops_for(cfg->prec);
     if (allocator) {
@@ -1083,8 +1087,9 @@ igr_status igr_adjoint_step(igr_ctx *c, const void *q_n, const void *sigma_n, co
     if (!(dt > 0.0)) return fail(c, IGR_ERR_INVALID_ARG, "the adjoint needs a fixed dt > 0");
     if ((int)dtype != storage_dtype(c->cfg.prec))
         return fail(c, IGR_ERR_UNSUPPORTED, "q_n and sigma_n must use the storage dtype");
-    if (c->p.order != 5 || c->cfg.sigma_solver != SOLVER_JACOBI)
-        return fail(c, IGR_ERR_UNSUPPORTED, "the adjoint covers 5th-order faces with Jacobi sweeps");
+    if (c->p.order != 5 || c->cfg.sigma_solver != SOLVER_JACOBI || c->p.mu != 0.0 || c->p.zeta != 0.0)
+        return fail(c, IGR_ERR_UNSUPPORTED,
+                    "the adjoint covers the inviscid scheme with 5th-order faces and Jacobi sweeps");
     if (c->profiling) return fail(c, IGR_ERR_INVALID_ARG, "disable profiling before the adjoint");
     igr_status s = ensure_adjoint(c);
     if (s != IGR_OK) return s;

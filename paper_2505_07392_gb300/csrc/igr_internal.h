@@ -23,6 +23,7 @@ struct Geom {
 struct Phys {
     double dx, gamma, alpha, cfl;
     int order;   // face reconstruction: 5 or 3
+    double mu, zeta;  // shear and bulk viscosity (0: Euler)
 };
 
 // Sigma sweep kinds (igr_config.sigma_solver)

@@ -834,7 +834,10 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : 2) k_jacobi_v4(const 
 // block per SM, keep the stencil queue in registers.
 constexpr int TX = 32, TY = sizeof(C) == 8 ? 7 : 15, NWARP = TY + 1, NT = 32 * NWARP;
 constexpr int PW = TX + 6, PH = TY + 6;          // plane tile with a halo of 3
-constexpr int NPLANE = TY * PW + 6 * TX;         // tile cells that are read (no corners)
+// tile cells that are read: the rows of the tile with the x-halo, the three
+// rows above and below (no corner blocks), and the four cells diagonal to
+// the interior's corners (the viscous faces' tangential neighbours)
+constexpr int NPLANE = TY * PW + 6 * TX + 4;
 constexpr int LPT = (NPLANE + NT - 1) / NT;      // tile cells loaded per thread
 
 // The plane tile and the z-queue keep the six face variables as three pairs,
@@ -927,7 +930,8 @@ __device__ __forceinline__ void plane_cell(int e, int &lx, int &ly)
 {
     if (e < 3 * TX) { ly = e / TX; lx = 3 + e % TX; }
     else if (e < 3 * TX + TY * PW) { e -= 3 * TX; ly = 3 + e / PW; lx = e % PW; }
-    else { e -= 3 * TX + TY * PW; ly = TY + 3 + e / TX; lx = 3 + e % TX; }
+    else if (e < 6 * TX + TY * PW) { e -= 3 * TX + TY * PW; ly = TY + 3 + e / TX; lx = 3 + e % TX; }
+    else { e -= 6 * TX + TY * PW; ly = (e & 2) ? TY + 3 : 2; lx = (e & 1) ? TX + 3 : 2; }
 }
 
 template <int D, int ORD>
@@ -964,6 +968,58 @@ __device__ __forceinline__ void tile_face(const C2 *T, int at, int step, C gamma
     face_from_stencil<D, ORD>(s, gamma, gm1, F, bad);
 }
 
+// ------------------------------------------------------- viscous stresses
+// Velocity u = m / rho of the tile cell at pair offset `at`.
+__device__ __forceinline__ void tvel(const C2 *T, int at, C u[3])
+{
+    C2 a = T[at], b = T[PH * PW + at];
+    C r = rcp(a.x);
+    u[0] = a.y * r;
+    u[1] = b.x * r;
+    u[2] = b.y * r;
+}
+
+// Doubled viscous flux (like lf_flux2's 2 F_hat) through the face between
+// cells A and B along axis D, added to G (Eqs. igrmobalance-igrenbalance with
+// the stress of Eq. constitutive_law):
+//   tau_aD = mu (du_a/dx_D + du_D/dx_a) + lam delta_aD div u, lam = zeta - 2 mu / 3,
+//   G[1 + a] -= 2 tau_aD,  G[4] -= 2 sum_a ((u_a(A) + u_a(B)) / 2) tau_aD,
+// with second-order face derivatives: normal (u(B) - u(A)) / dx, tangential
+// along t the mean of the central differences at A and B. T1/T2 give the
+// tangential axes t1 < t2 (the two axes other than D) as the cells on each
+// side of A and B: a1m, a1p, b1m, b1p along t1 and a2m.. along t2.
+template <int D>
+__device__ __forceinline__ void visc_face(const C2 *TA, int a, const C2 *TB, int b, const C2 *T1Am,
+                                          int a1m, const C2 *T1Ap, int a1p, const C2 *T1Bm, int b1m,
+                                          const C2 *T1Bp, int b1p, const C2 *T2Am, int a2m,
+                                          const C2 *T2Ap, int a2p, const C2 *T2Bm, int b2m,
+                                          const C2 *T2Bp, int b2p, C mu, C lam, C inv_dx, C *G)
+{
+    constexpr int t1 = D == 0 ? 1 : 0, t2 = D == 2 ? 1 : 2;
+    C uA[3], uB[3], p[3], m[3], q[3], r[3], Gr[3][3];
+    tvel(TA, a, uA);
+    tvel(TB, b, uB);
+#pragma unroll
+    for (int c = 0; c < 3; c++) Gr[c][D] = (uB[c] - uA[c]) * inv_dx;
+    const C qd = C(0.25) * inv_dx;
+    tvel(T1Ap, a1p, p); tvel(T1Am, a1m, m); tvel(T1Bp, b1p, q); tvel(T1Bm, b1m, r);
+#pragma unroll
+    for (int c = 0; c < 3; c++) Gr[c][t1] = ((p[c] - m[c]) + (q[c] - r[c])) * qd;
+    tvel(T2Ap, a2p, p); tvel(T2Am, a2m, m); tvel(T2Bp, b2p, q); tvel(T2Bm, b2m, r);
+#pragma unroll
+    for (int c = 0; c < 3; c++) Gr[c][t2] = ((p[c] - m[c]) + (q[c] - r[c])) * qd;
+    const C div = (Gr[0][0] + Gr[1][1]) + Gr[2][2];
+    C work = C(0);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        C tau = mu * (Gr[c][D] + Gr[D][c]);
+        if (c == D) tau += lam * div;
+        G[1 + c] -= C(2) * tau;
+        work += C(0.5) * (uA[c] + uB[c]) * tau;
+    }
+    G[4] -= C(2) * work;
+}
+
 // registers per thread such that NWARP / 4 warps fit one sub-partition's 16K
 constexpr int FLUX_MAXREG = sizeof(C) == 8 ? 224 : 128;
 
@@ -981,11 +1037,11 @@ constexpr int FLUX_MAXREG = sizeof(C) == 8 ? 224 : 128;
 // Planes k0 - 3..k0 + 2 are filled before the loop (with the boundary index
 // mapping and, below an inflow face, the jet blend). Every plane is read from
 // global memory once per block; nothing relies on the L1 cache.
-template <int mode, int ORD>
+template <int mode, int ORD, bool VISC>
 __global__ void __maxnreg__(FLUX_MAXREG)
     k_flux(Fin<6> in, Fin<5> qn, Fout<5> out, Frhs rhs, Fout<5> base_out, Geom g, C gamma,
            C half_inv_dx, const Scalars *sc, double *blockmax, int *err, const C *W, const C *J,
-           int zc)
+           int zc, C mu, C lamv)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *P = reinterpret_cast<C2 *>(smem_raw);        // [RING][3][PH][PW]
@@ -1153,29 +1209,51 @@ __global__ void __maxnreg__(FLUX_MAXREG)
                 for (int p = 0; p < 3; p++) sz[m][p] = T[p * PH * PW + tcell];
             }
             face_from_stencil<2, ORD>(sz, gamma, gm1, Fzp, bad);  // z-face k + 1/2
+            if constexpr (VISC) {
+                const C2 *Ta = P + ro[2], *Tb = P + ro[3];  // planes k, k + 1
+                visc_face<2>(Ta, tcell, Tb, tcell, Ta, tcell - 1, Ta, tcell + 1, Tb, tcell - 1, Tb,
+                             tcell + 1, Ta, tcell - PW, Ta, tcell + PW, Tb, tcell - PW, Tb, tcell + PW,
+                             mu, lamv, C(2) * half_inv_dx, Fzp);
+            }
         }
         if (k >= k0) {
             const C2 *T = P + ro[2];
             C *FX = FXb + (k & 1) * 5 * TY * (TX + 1);
             C *FY = FYb + (k & 1) * 5 * (TY + 1) * TX;
             C F[5];
+            const C2 *Tm = P + ro[1], *Tp = P + ro[3];  // planes k - 1, k + 1 (viscous terms)
+            const C inv_dx = C(2) * half_inv_dx;
+            // viscous x-face between tile cells a and a + 1 (same row)
+            auto visc_x = [&](int a) {
+                visc_face<0>(T, a, T, a + 1, T, a - PW, T, a + PW, T, a + 1 - PW, T, a + 1 + PW, Tm, a, Tp,
+                             a, Tm, a + 1, Tp, a + 1, mu, lamv, inv_dx, F);
+            };
+            // viscous y-face between tile cells a and a + PW (same column)
+            auto visc_y = [&](int a) {
+                visc_face<1>(T, a, T, a + PW, T, a - 1, T, a + 1, T, a + PW - 1, T, a + PW + 1, Tm, a, Tp,
+                             a, Tm, a + PW, Tp, a + PW, mu, lamv, inv_dx, F);
+            };
             if (rowwarp) {
                 // x-face at the low side of cell `lane` of row w (tile cells lane-3..lane+2)
                 tile_face<0, ORD>(T, (w + 3) * PW + lane, 1, gamma, gm1, F, bad);
+                if constexpr (VISC) visc_x((w + 3) * PW + lane + 2);
 #pragma unroll
                 for (int u = 0; u < 5; u++) FX[(u * TY + w) * (TX + 1) + lane] = F[u];
                 // y-face below row w in column lane (tile rows w-3..w+2)
                 tile_face<1, ORD>(T, w * PW + lane + 3, PW, gamma, gm1, F, bad);
+                if constexpr (VISC) visc_y((w + 2) * PW + lane + 3);
 #pragma unroll
                 for (int u = 0; u < 5; u++) FY[(u * (TY + 1) + w) * TX + lane] = F[u];
             } else {
                 // y-face above the last row, column lane
                 tile_face<1, ORD>(T, TY * PW + lane + 3, PW, gamma, gm1, F, bad);
+                if constexpr (VISC) visc_y((TY + 2) * PW + lane + 3);
 #pragma unroll
                 for (int u = 0; u < 5; u++) FY[(u * (TY + 1) + TY) * TX + lane] = F[u];
                 if (lane < TY) {
                     // x-face at the high end of row `lane`
                     tile_face<0, ORD>(T, (lane + 3) * PW + TX, 1, gamma, gm1, F, bad);
+                    if constexpr (VISC) visc_x((lane + 3) * PW + TX + 2);
 #pragma unroll
                     for (int u = 0; u < 5; u++) FX[(u * TY + lane) * (TX + 1) + TX] = F[u];
                 }
@@ -1732,7 +1810,7 @@ cudaError_t launch_flux(const Geom &g, const Phys &p, const Tiles &t, const Infl
         }
         kern<<<grid_of(g, TX, TY, t.zc_flux), NT, smem, st>>>(
             fi, fields_in<5>(qn, g.n), fo, fr, fb, g, C(p.gamma), C(0.5 / p.dx), sc, blockmax, err,
-            (const C *)in.W, (const C *)in.J, t.zc_flux);
+            (const C *)in.W, (const C *)in.J, t.zc_flux, C(p.mu), C(p.zeta - 2.0 * p.mu / 3.0));
         e = cudaGetLastError();
         if (e != cudaSuccess) {
             cudaFuncAttributes fa;
@@ -1744,20 +1822,27 @@ cudaError_t launch_flux(const Geom &g, const Phys &p, const Tiles &t, const Infl
         }
         return e;
     };
-    if (p.order == 3) {
+    auto by_mode = [&](auto k0, auto k1, auto k2, auto k3) {
         switch (mode) {
-        case FLUX_RHS: return go(k_flux<FLUX_RHS, 3>);
-        case FLUX_STAGE1: return go(k_flux<FLUX_STAGE1, 3>);
-        case FLUX_STAGE2: return go(k_flux<FLUX_STAGE2, 3>);
-        default: return go(k_flux<FLUX_STAGE3, 3>);
+        case FLUX_RHS: return go(k0);
+        case FLUX_STAGE1: return go(k1);
+        case FLUX_STAGE2: return go(k2);
+        default: return go(k3);
         }
+    };
+    const bool visc = p.mu != 0.0 || p.zeta != 0.0;
+    if (p.order == 3) {
+        if (visc)
+            return by_mode(k_flux<FLUX_RHS, 3, true>, k_flux<FLUX_STAGE1, 3, true>,
+                           k_flux<FLUX_STAGE2, 3, true>, k_flux<FLUX_STAGE3, 3, true>);
+        return by_mode(k_flux<FLUX_RHS, 3, false>, k_flux<FLUX_STAGE1, 3, false>,
+                       k_flux<FLUX_STAGE2, 3, false>, k_flux<FLUX_STAGE3, 3, false>);
     }
-    switch (mode) {
-    case FLUX_RHS: return go(k_flux<FLUX_RHS, 5>);
-    case FLUX_STAGE1: return go(k_flux<FLUX_STAGE1, 5>);
-    case FLUX_STAGE2: return go(k_flux<FLUX_STAGE2, 5>);
-    default: return go(k_flux<FLUX_STAGE3, 5>);
-    }
+    if (visc)
+        return by_mode(k_flux<FLUX_RHS, 5, true>, k_flux<FLUX_STAGE1, 5, true>,
+                       k_flux<FLUX_STAGE2, 5, true>, k_flux<FLUX_STAGE3, 5, true>);
+    return by_mode(k_flux<FLUX_RHS, 5, false>, k_flux<FLUX_STAGE1, 5, false>,
+                   k_flux<FLUX_STAGE2, 5, false>, k_flux<FLUX_STAGE3, 5, false>);
 }
 
 cudaError_t launch_speed(const Geom &g, const Phys &p, const void *q, double *blockmax,

@@ -106,6 +106,8 @@ igr_status igr_solve_sigma_noalloc(const igr_config *cfg, const void *q, void *s
     p.alpha = cfg->alpha;
     p.cfl = cfg->cfl;
     p.order = cfg->order == 3 ? 3 : 5;
+    p.mu = cfg->mu;
+    p.zeta = cfg->zeta;
     Tiles t = default_tiles(g);
     Inflow none;
     none.W = nullptr;

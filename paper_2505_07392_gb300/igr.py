@@ -43,7 +43,7 @@ class Config(C.Structure):
                 ("gamma", C.c_double), ("alpha", C.c_double), ("cfl", C.c_double),
                 ("sweeps", C.c_int), ("prec", C.c_int), ("bc", C.c_int * 6),
                 ("jets", C.POINTER(Jet)), ("njets", C.c_int), ("host_rk_base", C.c_int),
-                ("order", C.c_int), ("sigma_solver", C.c_int)]
+                ("order", C.c_int), ("sigma_solver", C.c_int), ("mu", C.c_double), ("zeta", C.c_double)]
 
 
 class IGRError(RuntimeError):
@@ -116,7 +116,8 @@ def make_config(case, precision: str = "f32", host_rk_base: bool = False):
     cfg = Config(int(case.nx), int(case.ny), int(case.nz), float(case.dx), float(case.gamma),
                  float(case.alpha), float(case.cfl), int(case.sweeps), PRECISIONS[precision],
                  (C.c_int * 6)(*[int(b) for b in case.bc]), jets, len(case.jets), int(host_rk_base),
-                 int(getattr(case, "order", 5)), int(getattr(case, "sigma_solver", 0)))
+                 int(getattr(case, "order", 5)), int(getattr(case, "sigma_solver", 0)),
+                 float(getattr(case, "mu", 0.0)), float(getattr(case, "zeta", 0.0)))
     return cfg, jets
 
 
