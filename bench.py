@@ -41,7 +41,7 @@ FALLBACK_HBM_GBS = 6800.0
 # a changed source makes the figure stale (reported as null).
 NCU_TRAFFIC = {
     # profiles/flux_plume_f16.md: mean of the three stage launches, 512 x 512 x 128 plume
-    "flux_f16": {"bytes_per_cell": 29.005, "src": "29e9a0f8d22e5ea6"},
+    "flux_f16": {"bytes_per_cell": 29.114, "src": "1bbe02e68edeeca9"},
 }
 
 
