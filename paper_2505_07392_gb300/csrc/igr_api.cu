@@ -215,7 +215,7 @@ static int default_zc(const Geom &g, int tx, int ty, int resident)
 Tiles igr::default_tiles(const Geom &g)
 {
     Tiles t;
-    t.zc_source = default_zc(g, 32, 8, 5);
+    t.zc_source = default_zc(g, 128, 8, 3);
     t.zc_jacobi = default_zc(g, 128, 8, 3);
     t.zc_flux = default_zc(g, 32, 15, 1);
     return t;

@@ -822,6 +822,161 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : 2) k_jacobi_v4(const 
     }
 }
 
+// Vector form of the source for rows whose length is a multiple of 4, laid
+// out like k_jacobi_v4: each thread owns 4 consecutive cells of a row (one
+// 4-wide load per field), u of plane k sits in a shared tile with a halo of 1
+// (4-wide aligned rows), x-neighbours come from the thread's own registers
+// and z-neighbours from its register queue. The central differences are
+// taken undivided and 1/(2 dx)^2 is folded into alpha:
+//   b = (alpha / (4 dx^2)) [sum_ab D_ab D_ba + (sum_a D_aa)^2],
+//   D_ab = u_a(i + e_b) - u_a(i - e_b),
+// which is Eq. igrelliptic's left side with G = D / (2 dx).
+__global__ void __launch_bounds__(BT) k_source_v4(Fin<4> q, S *__restrict__ b, Geom g, C alpha_s,
+                                                   const C *W, const C *J, int zc)
+{
+    __shared__ __align__(16) C U[3][HY][HXV];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    const int x0 = blockIdx.x * TXV, y0 = blockIdx.y * BY;
+    const int i0 = x0 + VX * tx, j = y0 + ty;
+    const bool active = i0 < g.nx && j < g.ny;
+    const int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
+    const idx pl = (idx)g.plane;
+    const idx rowj = (idx)(map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx);
+    // halo tasks: 4-wide cells of the rows above/below the tile, then single
+    // cells left/right of each row
+    int htask = tid < NYH ? 0 : (tid < NYH + NXH ? 1 : 2);
+    int hsy = 0, hsx = 0, hx = 0;
+    idx hrow = 0;
+    if (htask == 0) {
+        int side = tid / BX, t = tid % BX;
+        hsy = side ? HY - 1 : 0;
+        hsx = VX + VX * t;
+        hx = x0 + VX * t;
+        hrow = (idx)(map_axis(y0 + (side ? BY : -1), g.ny, g.bc[2], g.bc[3]) * g.nx);
+    } else if (htask == 1) {
+        int e = tid - NYH, side = e / BY, r = e % BY;
+        hsy = 1 + r;
+        hsx = side ? VX + TXV : VX - 1;
+        hx = map_axis(side ? x0 + TXV : x0 - 1, g.nx, g.bc[0], g.bc[1]);
+        hrow = (idx)(map_axis(y0 + r, g.ny, g.bc[2], g.bc[3]) * g.nx);
+    }
+
+    // u = m / rho of 4 cells from raw values (products rounded before they
+    // are differenced: equal neighbours give an exact 0)
+    auto u4 = [&](const V4 (&r)[4], C u[3][VX]) {
+        C rho[VX], m[VX], rr[VX];
+        cv4(r[0], rho);
+#pragma unroll
+        for (int c = 0; c < VX; c++) rr[c] = rcp(rho[c]);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            cv4(r[1 + a], m);
+#pragma unroll
+            for (int c = 0; c < VX; c++) u[a][c] = mul_rn(m[c], rr[c]);
+        }
+    };
+    // u of the own 4 cells of plane kk (the jet blend below an inflow face)
+    auto own_u = [&](int kk, C u[3][VX]) {
+        idx zb = (idx)zmap(kk, g) * pl + rowj;
+        C v[4][VX];
+#pragma unroll
+        for (int f = 0; f < 4; f++) cv4(ld4_mapped(q.p[f], g, zb, i0), v[f]);
+        if (kk < 0 && g.bc[4] == BC_INFLOW) {
+#pragma unroll
+            for (int c = 0; c < VX; c++) {
+                idx fc = rowj + (idx)map_axis(i0 + c, g.nx, g.bc[0], g.bc[1]);
+                C w = C(1) - W[fc];
+#pragma unroll
+                for (int f = 0; f < 4; f++) v[f][c] = w * v[f][c] + J[(idx)f * pl + fc];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < VX; c++) {
+            C r = rcp(v[0][c]);
+#pragma unroll
+            for (int a = 0; a < 3; a++) u[a][c] = mul_rn(v[1 + a][c], r);
+        }
+    };
+    C um[3][VX], u0[3][VX], up[3][VX];
+    own_u(k0 - 1, um);
+    own_u(k0, u0);
+    // raw values one iteration ahead: own cells at k + 1, halo at k (planes >= 0)
+    V4 nc[4], nh[4];
+    S nxh[4];
+    auto pre = [&](int kk) {
+        idx pz = (idx)zmap(kk + 1, g) * pl + rowj;
+#pragma unroll
+        for (int f = 0; f < 4; f++) nc[f] = ld4_mapped(q.p[f], g, pz, i0);
+        if (htask == 0) {
+#pragma unroll
+            for (int f = 0; f < 4; f++) nh[f] = ld4_mapped(q.p[f], g, (idx)kk * pl + hrow, hx);
+        } else if (htask == 1) {
+#pragma unroll
+            for (int f = 0; f < 4; f++) nxh[f] = ldr(q.p[f] + (idx)kk * pl + hrow + hx);
+        }
+    };
+    pre(k0);
+    for (int k = k0; k < k1; k++) {
+        u4(nc, up);
+        C hu[3][VX];
+        if (htask == 0) {
+            u4(nh, hu);
+        } else if (htask == 1) {
+            C r = rcp(cv(nxh[0]));
+#pragma unroll
+            for (int a = 0; a < 3; a++) hu[a][0] = mul_rn(cv(nxh[1 + a]), r);
+        }
+        if (k + 1 < k1) pre(k + 1);
+        __syncthreads();  // readers of the previous plane are done
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            sh_st4(&U[a][ty + 1][VX + VX * tx], u0[a]);
+            if (htask == 0) sh_st4(&U[a][hsy][hsx], hu[a]);
+            else if (htask == 1) U[a][hsy][hsx] = hu[a][0];
+        }
+        __syncthreads();
+        if (active) {
+            const int col = VX + VX * tx;
+            C ym[3][VX], yp[3][VX], o[VX];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                sh_ld4(&U[a][ty][col], ym[a]);
+                sh_ld4(&U[a][ty + 2][col], yp[a]);
+            }
+            C xl[3], xr[3];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                xl[a] = U[a][ty + 1][col - 1];
+                xr[a] = U[a][ty + 1][col + VX];
+            }
+#pragma unroll
+            for (int c = 0; c < VX; c++) {
+                C D[3][3];  // D[a][d]: undivided central difference of u_a along d
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    C xm = c > 0 ? u0[a][c - 1] : xl[a];
+                    C xp = c < VX - 1 ? u0[a][c + 1] : xr[a];
+                    D[a][0] = xp - xm;
+                    D[a][1] = yp[a][c] - ym[a][c];
+                    D[a][2] = up[a][c] - um[a][c];
+                }
+                C tr = D[0][0] + D[1][1] + D[2][2];
+                C tr2 = D[0][0] * D[0][0] + D[1][1] * D[1][1] + D[2][2] * D[2][2] +
+                        C(2) * (D[0][1] * D[1][0] + D[0][2] * D[2][0] + D[1][2] * D[2][1]);
+                o[c] = alpha_s * (tr2 + tr * tr);
+            }
+            st4(b + (idx)k * pl + (idx)(j * g.nx + i0), o);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int c = 0; c < VX; c++) {
+                um[a][c] = u0[a][c];
+                u0[a][c] = up[a][c];
+            }
+    }
+}
+
 // ----------------------------------------------------------------- flux
 // Block of TY + 1 warps over a TX x TY tile of columns. Warps 0..TY-1 own a
 // row each: per plane a warp computes the x-face at the low side of each of
@@ -1764,6 +1919,12 @@ template <int N> Fin<N> fields_in(const void *base, long long n)
 cudaError_t launch_source(const Geom &g, const Phys &p, const Tiles &t, const Inflow &in,
                           const void *q, void *b, cudaStream_t st)
 {
+    if (g.nx % VX == 0) {
+        k_source_v4<<<grid_of(g, TXV, BY, t.zc_source), dim3(BX, BY), 0, st>>>(
+            fields_in<4>(q, g.n), (S *)b, g, C(p.alpha * 0.25 / (p.dx * p.dx)), (const C *)in.W,
+            (const C *)in.J, t.zc_source);
+        return cudaGetLastError();
+    }
     k_source<<<grid_of(g, BX, BY, t.zc_source), dim3(BX, BY), 0, st>>>(
         fields_in<4>(q, g.n), (S *)b, g, C(p.alpha), C(0.5 / p.dx), (const C *)in.W,
         (const C *)in.J, t.zc_source);
