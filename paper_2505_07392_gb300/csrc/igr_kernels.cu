@@ -124,6 +124,38 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 // NaN-propagating maximum (a NaN wave speed must reach dt)
 __device__ __forceinline__ double nanmax(double a, double b) { return (a > b || a != a) ? a : b; }
 
+// Pairs of arithmetic values for packed FP32x2 operations (add.rn.f32x2,
+// mul.rn.f32x2, fma.rn.f32x2 on sm_100 and later: each lane rounds exactly
+// like the scalar operation); FP64 pairs take two scalar operations.
+template <typename T> struct PairOf;
+template <> struct PairOf<float> { using T = float2; };
+template <> struct PairOf<double> { using T = double2; };
+using C2 = typename PairOf<C>::T;
+
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b)
+{
+    return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c)
+{
+    return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
+}
+__device__ __forceinline__ C2 pset(C x, C y)
+{
+    C2 r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+__device__ __forceinline__ C2 bcast(C v) { return pset(v, v); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 padd(double2 a, double2 b)
+{
+    return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
+}
+
 // ------------------------------------------------------------ indexing
 __device__ __forceinline__ int wrap(int c, int n)
 {
@@ -689,7 +721,7 @@ __device__ __forceinline__ V4 ld4_mapped(const S *__restrict__ a, const Geom &g,
     return pack4(v[0], v[1], v[2], v[3]);
 }
 
-__global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : 2) k_jacobi_v4(const S *__restrict__ q, const S *__restrict__ b,
+__global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : sizeof(S) == 4 ? 2 : 1) k_jacobi_v4(const S *__restrict__ q, const S *__restrict__ b,
                                                    const S *sin, S *sout, Geom g, C beta, int zc,
                                                    int colour)
 {
@@ -792,25 +824,62 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : 2) k_jacobi_v4(const 
             sh_ld4(&R[ty + 2][col], ry1);
             sh_ld4(&SG[ty][col], sy0);
             sh_ld4(&SG[ty + 2][col], sy1);
+            if constexpr (sizeof(C) == 4) {
+                // cells (0, 1) and (2, 3) as packed pairs; the faces in the
+                // order -x, +x, -y, +y, -z, +z as in the scalar form
+                const C rl = R[ty + 1][col - 1], sl = SG[ty + 1][col - 1];
+                const C rr = R[ty + 1][col + VX], sr = SG[ty + 1][col + VX];
+                const C2 r01 = pset(r0[0], r0[1]), r23 = pset(r0[2], r0[3]), r12 = pset(r0[1], r0[2]);
+                const C2 s01 = pset(s0[0], s0[1]), s23 = pset(s0[2], s0[3]), s12 = pset(s0[1], s0[2]);
+                const C2 rxm[2] = {pset(rl, r0[0]), r12}, rxp[2] = {r12, pset(r0[3], rr)};
+                const C2 sxm[2] = {pset(sl, s0[0]), s12}, sxp[2] = {s12, pset(s0[3], sr)};
+                const C2 exmp[2] = {pset(exm, hb), bcast(hb)}, expp[2] = {bcast(hb), pset(hb, exp_)};
+                const C2 rc[2] = {r01, r23};
 #pragma unroll
-            for (int c = 0; c < VX; c++) {
-                C rxm = c > 0 ? r0[c - 1] : R[ty + 1][col - 1];
-                C sxm = c > 0 ? s0[c - 1] : SG[ty + 1][col - 1];
-                C rxp = c < VX - 1 ? r0[c + 1] : R[ty + 1][col + VX];
-                C sxp = c < VX - 1 ? s0[c + 1] : SG[ty + 1][col + VX];
-                // faces in the order -x, +x, -y, +y, -z, +z
-                C c0 = (c > 0 ? hb : exm) * (r0[c] + rxm);
-                C c1 = (c < VX - 1 ? hb : exp_) * (r0[c] + rxp);
-                C c2 = eym * (r0[c] + ry0[c]);
-                C c3 = eyp * (r0[c] + ry1[c]);
-                C c4 = ezm * (r0[c] + rm[c]);
-                C c5 = ezp * (r0[c] + rp[c]);
-                C diag = r0[c] + c0 + c1 + c2 + c3 + c4 + c5;
-                C off = c0 * sxm + c1 * sxp + c2 * sy0[c] + c3 * sy1[c] + c4 * sm[c] + c5 * sp[c];
-                o[c] = div_c(bv[c] + off, diag);
-                // red-black half-sweep: cells of the other colour keep (and
-                // write back) the value read at the start of the launch
-                if (colour >= 0 && ((i0 + c + j + k) & 1) != colour) o[c] = s0[c];
+                for (int h = 0; h < 2; h++) {
+                    const int c = 2 * h;
+                    C2 c0 = pmul(exmp[h], padd(rc[h], rxm[h]));
+                    C2 c1 = pmul(expp[h], padd(rc[h], rxp[h]));
+                    C2 c2 = pmul(bcast(eym), padd(rc[h], pset(ry0[c], ry0[c + 1])));
+                    C2 c3 = pmul(bcast(eyp), padd(rc[h], pset(ry1[c], ry1[c + 1])));
+                    C2 c4 = pmul(bcast(ezm), padd(rc[h], pset(rm[c], rm[c + 1])));
+                    C2 c5 = pmul(bcast(ezp), padd(rc[h], pset(rp[c], rp[c + 1])));
+                    C2 diag = padd(padd(padd(padd(padd(padd(rc[h], c0), c1), c2), c3), c4), c5);
+                    C2 off = pmul(c0, sxm[h]);
+                    off = pfma(c1, sxp[h], off);
+                    off = pfma(c2, pset(sy0[c], sy0[c + 1]), off);
+                    off = pfma(c3, pset(sy1[c], sy1[c + 1]), off);
+                    off = pfma(c4, pset(sm[c], sm[c + 1]), off);
+                    off = pfma(c5, pset(sp[c], sp[c + 1]), off);
+                    C2 num = padd(pset(bv[c], bv[c + 1]), off);
+                    C2 res = pmul(num, pset(rcp(diag.x), rcp(diag.y)));
+                    o[c] = res.x;
+                    o[c + 1] = res.y;
+                }
+#pragma unroll
+                for (int c = 0; c < VX; c++)
+                    if (colour >= 0 && ((i0 + c + j + k) & 1) != colour) o[c] = s0[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < VX; c++) {
+                    C rxm = c > 0 ? r0[c - 1] : R[ty + 1][col - 1];
+                    C sxm = c > 0 ? s0[c - 1] : SG[ty + 1][col - 1];
+                    C rxp = c < VX - 1 ? r0[c + 1] : R[ty + 1][col + VX];
+                    C sxp = c < VX - 1 ? s0[c + 1] : SG[ty + 1][col + VX];
+                    // faces in the order -x, +x, -y, +y, -z, +z
+                    C c0 = (c > 0 ? hb : exm) * (r0[c] + rxm);
+                    C c1 = (c < VX - 1 ? hb : exp_) * (r0[c] + rxp);
+                    C c2 = eym * (r0[c] + ry0[c]);
+                    C c3 = eyp * (r0[c] + ry1[c]);
+                    C c4 = ezm * (r0[c] + rm[c]);
+                    C c5 = ezp * (r0[c] + rp[c]);
+                    C diag = r0[c] + c0 + c1 + c2 + c3 + c4 + c5;
+                    C off = c0 * sxm + c1 * sxp + c2 * sy0[c] + c3 * sy1[c] + c4 * sm[c] + c5 * sp[c];
+                    o[c] = div_c(bv[c] + off, diag);
+                    // red-black half-sweep: cells of the other colour keep (and
+                    // write back) the value read at the start of the launch
+                    if (colour >= 0 && ((i0 + c + j + k) & 1) != colour) o[c] = s0[c];
+                }
             }
             st4(sout + (idx)k * pl + (idx)(j * g.nx + i0), o);
         }
@@ -995,34 +1064,10 @@ constexpr int PW = TX + 6, PH = TY + 6;          // plane tile with a halo of 3
 constexpr int NPLANE = TY * PW + 6 * TX + 4;
 constexpr int LPT = (NPLANE + NT - 1) / NT;      // tile cells loaded per thread
 
-// The plane tile and the z-queue keep the six face variables as three pairs,
-// (rho, m_x), (m_y, m_z), (E, Sigma): a stencil point of a pair is one 8-byte
-// (16-byte in FP64) shared load, and the reconstruction of a pair is one
-// packed FP32x2 multiply-add per term (fma.rn.f32x2 on sm_100 and later;
-// each lane rounds exactly like the scalar fma.rn.f32).
-template <typename T> struct PairOf;
-template <> struct PairOf<float> { using T = float2; };
-template <> struct PairOf<double> { using T = double2; };
-using C2 = typename PairOf<C>::T;
-
-__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ double2 pmul(double2 a, double2 b)
-{
-    return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
-}
-__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c)
-{
-    return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
-}
-__device__ __forceinline__ C2 pset(C x, C y)
-{
-    C2 r;
-    r.x = x;
-    r.y = y;
-    return r;
-}
-__device__ __forceinline__ C2 bcast(C v) { return pset(v, v); }
+// The plane tiles keep the six face variables as three pairs, (rho, m_x),
+// (m_y, m_z), (E, Sigma): a stencil point of a pair is one 8-byte (16-byte in
+// FP64) shared load, and the reconstruction of a pair is one packed FP32x2
+// multiply-add per term.
 
 // 5th-order face values of a pair (weights as in rec_left / rec_right)
 __device__ __forceinline__ C2 rec_left2(C2 a, C2 b, C2 c, C2 d, C2 e)
