@@ -39,6 +39,14 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per cell of one launch from an ncu capture of each kernel on the
 # plume workload, keyed by a hash of the kernel source they were taken with;
 # a changed source makes the figure stale (reported as null).
+# Warp instructions per cell of the dominant kernel (ncu smsp__inst_executed.sum
+# over the cells of one launch, mean of the three stage launches), for the
+# issue roofline; tied to the kernel source like the traffic.
+NCU_INSTR = {
+    # profiles/flux_plume_f16.md
+    "flux_f16": {"warp_instr_per_cell": 24.15, "src": "1bbe02e68edeeca9"},
+}
+
 NCU_TRAFFIC = {
     # profiles/flux_plume_f16.md: mean of the three stage launches, 512 x 512 x 128 plume
     "flux_f16": {"bytes_per_cell": 29.114, "src": "1bbe02e68edeeca9"},
@@ -100,7 +108,7 @@ class ClockSampler:
             if len(parts) < 9:
                 continue
             try:
-                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9], _num(parts[3])))
             except ValueError:
                 continue
         os.unlink(self.path)
@@ -109,8 +117,17 @@ class ClockSampler:
         sm = sorted(r[0] for r in rows)
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        power = sorted(r[3] for r in rows if r[3] is not None)
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows),
+                "power_w": power[len(power) // 2] if power else None}
+
+
+def _num(x):
+    try:
+        return float(x)
+    except ValueError:
+        return None
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -272,6 +289,24 @@ def roofline_of(case, res, precision, peak, peak_kind):
     return {"bound": "hbm", "kernel": dom, "achieved": round(d["achieved_gbs"], 1), "peak": peak,
             "unit": "GB/s", "frac": round(d["achieved_gbs"] / peak, 4), "traffic": traffic,
             "peak_kind": f"of {peak_kind}"}, per
+
+
+def issue_roofline(case, res, precision, clocks):
+    """The flux kernel against its issue limit: ncu-counted warp instructions
+    per cell x cells per launch x launches / CUDA-event time, over the peak of
+    152 SMs x 4 schedulers x 1 warp instruction per clock at the sampled SM
+    clock. None when no count matches the current kernel source."""
+    t = NCU_INSTR.get(f"flux_{precision}")
+    if not t or t.get("src") != kernel_source_hash() or not clocks:
+        return None
+    n, ms = res["prof"]["flux"]
+    if n == 0 or ms <= 0:
+        return None
+    achieved = t["warp_instr_per_cell"] * case.ncells * n / (ms * 1e-3)
+    peak = 152 * 4 * clocks["sm_mhz"] * 1e6
+    return {"bound": "issue", "kernel": "flux", "achieved": achieved, "peak": peak,
+            "unit": "warp-instr/s", "frac": round(achieved / peak, 4),
+            "peak_kind": "152 SMs x 4 schedulers x 1 warp instr/clock at the sampled SM clock"}
 
 
 # ------------------------------------------------------------ batched arm
@@ -490,6 +525,12 @@ def main():
         "clocks": res["clocks"],
         "diagnostics_fp64": res["diag"],
     }
+    ri = issue_roofline(full, res, args.precision, res["clocks"])
+    if ri:
+        line["roofline_issue"] = ri
+    if res["clocks"] and res["clocks"].get("power_w"):
+        pw = res["clocks"]["power_w"]
+        line["energy"] = {"power_w": pw, "uJ_per_cell_update": pw * (ms / args.steps) * 1e-3 / full.ncells * 1e6}
     if plain:
         line["plain"] = plain
         line["speedup_vs_plain"] = value / plain["value"]
