@@ -311,7 +311,7 @@ def issue_roofline(case, res, precision, clocks):
 
 # ------------------------------------------------------------ batched arm
 
-def run_batch(args):
+def run_batch(args, sync_all=lambda: None):
     """64 periodic Taylor-Green instances of uneven size (edges drawn from
     {48,64,80,96,128}) advanced together: one CUDA graph per step with a
     branch per instance; z-chunks autotuned per distinct size."""
@@ -330,15 +330,18 @@ def run_batch(args):
             else:
                 inst.set_tiles(*tuned[key])
         b.step(args.warmup, sync=True)
+        sync_all()
+        torch.cuda.synchronize()
         stream = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         b.step(args.steps)
         e1.record(stream)
         b.sync()
+        sync_all()
         ms = e0.elapsed_time(e1)
     cells = sum(c.ncells for c in cases)
-    return {"metric": METRIC, "value": cells * args.steps / (ms * 1e-3), "unit": "cell-updates/s",
+    return {"metric": METRIC, "value": cells * args.steps / (ms * 1e-3), "_cells": cells, "unit": "cell-updates/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": f"f32 compute, {args.precision} storage", "data": "synthetic",
@@ -389,6 +392,24 @@ def cpu_baseline(full, steps=1, size=(256, 256, 64)):
 
 
 # -------------------------------------------------------------------- main
+
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time: every rank contributes its own and all get the
+    maximum (a no-op on one rank)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(cells_per_rank, steps, world, ms):
+    """Whole-job cell-updates/s: the cells all ranks advanced over the slowest
+    rank's time (replicas: every rank advances its own copy of the workload)."""
+    return cells_per_rank * steps * world / (ms * 1e-3)
+
 
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -476,7 +497,10 @@ def main():
     build.build()
 
     if args.workload == "tgv_batch":
-        line = run_batch(args)
+        line = run_batch(args, sync_all)
+        ms = max_over_ranks(line["ms_per_step"] * args.steps, world, "cuda")
+        line.update(value=job_rate(line.pop("_cells"), args.steps, world, ms), ms_per_step=ms / args.steps,
+                    n_gpus=world)
         if rank == 0:
             print(json.dumps(line))
         return
@@ -484,14 +508,8 @@ def main():
     res = run_form(full, args.precision, args.steps, args.warmup, sync_all,
                    e2e_steps=args.e2e_steps if rank == 0 else 0, host_rk_base=args.host_rk_base)
     res["prof_steps"] = args.steps
-    ms = res["ms"]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    cells = full.ncells * args.steps * world
-    value = cells / (ms * 1e-3)
+    ms = max_over_ranks(res["ms"], world, "cuda")
+    value = job_rate(full.ncells, args.steps, world, ms)
     peak, peak_kind = measured_peaks()
     roof, per_kernel = roofline_of(full, res, args.precision, peak, peak_kind)
 
@@ -500,8 +518,9 @@ def main():
         rp = run_form(full, args.plain, args.steps, args.warmup, sync_all, host_rk_base=args.host_rk_base)
         rp["prof_steps"] = args.steps
         roof_p, _ = roofline_of(full, rp, args.plain, peak, peak_kind)
-        plain = {"precision": args.plain, "value": full.ncells * args.steps * world / (rp["ms"] * 1e-3),
-                 "ms_per_step": rp["ms"] / args.steps, "roofline": roof_p, "clocks": rp["clocks"]}
+        ms_p = max_over_ranks(rp["ms"], world, "cuda")
+        plain = {"precision": args.plain, "value": job_rate(full.ncells, args.steps, world, ms_p),
+                 "ms_per_step": ms_p / args.steps, "roofline": roof_p, "clocks": rp["clocks"]}
 
     if rank != 0:
         return

@@ -1,0 +1,53 @@
+"""The N > 1 host path of bench.py without a GPU: replicas on two gloo ranks
+(127.0.0.1 rendezvous). Each rank times its own copy of the workload; the job
+takes the slowest rank's time and counts every rank's cells; rank 0 alone
+prints the reference arm's line."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = 10.0 * (rank + 1)                       # rank 1 is the slow one
+    got = bench.max_over_ranks(ms, world, "cpu")
+    dist.barrier()
+    dist.destroy_process_group()
+    with open(os.path.join(out, f"r{rank}.json"), "w") as f:
+        json.dump({"ms": got, "rate": bench.job_rate(1000, 5, world, got)}, f)
+
+
+def test_slowest_rank_and_all_cells(tmp_path):
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    world = 2
+    mp.start_processes(_rank, args=(world, _free_port(), str(tmp_path)), nprocs=world, start_method="spawn")
+    for r in range(world):
+        d = json.load(open(tmp_path / f"r{r}.json"))
+        assert d["ms"] == 20.0
+        assert d["rate"] == pytest.approx(1000 * 5 * world / 0.020)
+
+
+def test_reference_arm_prints_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", LOCAL_RANK="1", WORLD_SIZE="2", MASTER_ADDR="127.0.0.1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "3", "--workload", "density_wave"],
+                       capture_output=True, text=True, env=env, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
