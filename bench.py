@@ -547,8 +547,11 @@ def main():
     ri = issue_roofline(full, res, args.precision, res["clocks"])
     if ri:
         line["roofline_issue"] = ri
-    if res["clocks"] and res["clocks"].get("power_w"):
-        pw = res["clocks"]["power_w"]
+    # energy from the median sampled power, when the timed region is long
+    # enough (>= 1 s, >= 5 samples at 200 ms) for the samples to be under load
+    clk = res["clocks"]
+    if clk and clk.get("power_w") and clk.get("samples", 0) >= 5 and ms >= 1000.0:
+        pw = clk["power_w"]
         line["energy"] = {"power_w": pw, "uJ_per_cell_update": pw * (ms / args.steps) * 1e-3 / full.ncells * 1e6}
     if plain:
         line["plain"] = plain
