@@ -44,12 +44,12 @@ FALLBACK_HBM_GBS = 6800.0
 # issue roofline; tied to the kernel source like the traffic.
 NCU_INSTR = {
     # profiles/flux_plume_f16.md
-    "flux_f16": {"warp_instr_per_cell": 24.137, "src": "5a35899ab2498e9a"},
+    "flux_f16": {"warp_instr_per_cell": 24.137, "src": "0f939e942f38d191"},
 }
 
 NCU_TRAFFIC = {
     # profiles/flux_plume_f16.md: mean of the three stage launches, 512 x 512 x 128 plume
-    "flux_f16": {"bytes_per_cell": 29.109, "src": "5a35899ab2498e9a"},
+    "flux_f16": {"bytes_per_cell": 29.129, "src": "0f939e942f38d191"},
 }
 
 

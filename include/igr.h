@@ -283,6 +283,20 @@ typedef struct {
 } igr_diagnostics;
 igr_status igr_diagnose(igr_ctx *ctx, igr_diagnostics *out);
 
+/* ---- Bounds-checking debug build ------------------------------------
+ * A second library, libigr_debug.so, is compiled with IGR_DEBUG_BOUNDS: every
+ * global index the forward kernels (source, Jacobi, flux, stage epilogue)
+ * form is compared with its array's length, and an index out of range is
+ * counted and replaced by 0, so nothing is accessed out of bounds. This
+ * stands in for a memory checker (compute-sanitizer is not used).
+ * igr_debug_bounds_hits returns the count summed over all precisions since
+ * the last clear (clear != 0 resets it); igr_debug_bounds_selftest launches a
+ * kernel that forms one out-of-range index (checked, never dereferenced),
+ * which adds exactly 1. Both synchronise and return IGR_ERR_UNSUPPORTED in
+ * the normal library. */
+igr_status igr_debug_bounds_hits(unsigned long long *hits, int clear);
+igr_status igr_debug_bounds_selftest(void);
+
 /* Per-kernel timing with CUDA events on the context stream. While enabled,
  * every launch is bracketed by an event pair; igr_profile_read synchronises
  * and returns, for kernel class k (0 source, 1 jacobi, 2 flux, 3 other),

@@ -15,6 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libigr.so")
+# the bounds-checking debug build (IGR_DEBUG_BOUNDS; include/igr.h)
+OBJ_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libigr_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "-diag-suppress", "177"]
 
@@ -33,25 +36,28 @@ def _sources():
         [os.path.join(HERE, "..", "include", "igr.h")]
 
 
-def _jobs(extra):
+def _jobs(extra, obj):
     jobs = []
     for tag, ty in VARIANTS:
         jobs.append([nvcc(), *ARCH, *FLAGS, *extra, f"-DIGR_STORAGE={ty}", f"-DIGR_OPS=ops_{tag}",
-                     "-c", os.path.join(CSRC, "igr_kernels.cu"), "-o", os.path.join(OBJ, f"kern_{tag}.o")])
+                     "-c", os.path.join(CSRC, "igr_kernels.cu"), "-o", os.path.join(obj, f"kern_{tag}.o")])
     for name in ("igr_api", "igr_noalloc"):
         jobs.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, name + ".cu"),
-                     "-o", os.path.join(OBJ, name + ".o")])
+                     "-o", os.path.join(obj, name + ".o")])
     return jobs
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile and link libigr.so if it is missing or older than a source."""
-    if not force and os.path.exists(LIB):
+def build(force: bool = False, verbose: bool = False, extra=(), debug_bounds: bool = False) -> str:
+    """Compile and link libigr.so (libigr_debug.so with debug_bounds) if it is
+    missing or older than a source."""
+    lib, obj = (LIB_DEBUG, OBJ_DEBUG) if debug_bounds else (LIB, OBJ)
+    extra = list(extra) + (["-DIGR_DEBUG_BOUNDS"] if debug_bounds else [])
+    if not force and os.path.exists(lib):
         newest = max(os.path.getmtime(f) for f in _sources())
-        if os.path.getmtime(LIB) >= newest:
-            return LIB
-    os.makedirs(OBJ, exist_ok=True)
-    jobs = _jobs(list(extra))
+        if os.path.getmtime(lib) >= newest:
+            return lib
+    os.makedirs(obj, exist_ok=True)
+    jobs = _jobs(extra, obj)
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -64,10 +70,10 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if verbose:
         print("\n".join(logs))
     objs = [j[-1] for j in jobs]
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

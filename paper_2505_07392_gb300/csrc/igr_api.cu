@@ -1190,6 +1190,33 @@ igr_status igr_diagnose(igr_ctx *c, igr_diagnostics *out)
     return IGR_OK;
 }
 
+igr_status igr_debug_bounds_hits(unsigned long long *hits, int clear)
+{
+    if (!hits) return fail(nullptr, IGR_ERR_INVALID_ARG, "hits is NULL");
+    unsigned long long sum = 0;
+    for (const Ops *o : {&ops_f64, &ops_f32, &ops_f16, &ops_bf16}) {
+        unsigned long long h = o->bounds_hits(clear);
+        if (h == ~0ull) return fail(nullptr, IGR_ERR_UNSUPPORTED, "not a bounds-checking debug build");
+        sum += h;
+    }
+    *hits = sum;
+    return IGR_OK;
+}
+
+igr_status igr_debug_bounds_selftest(void)
+{
+    unsigned long long h;
+    igr_status s = igr_debug_bounds_hits(&h, 0);
+    if (s != IGR_OK) return s;
+    int *sink = nullptr;
+    if (cudaMalloc(&sink, sizeof(int)) != cudaSuccess) return fail(nullptr, IGR_ERR_OOM, "selftest buffer");
+    cudaError_t e = ops_f32.bounds_selftest(sink, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(sink);
+    if (e != cudaSuccess) return fail(nullptr, IGR_ERR_CUDA, "selftest: %s", cudaGetErrorString(e));
+    return IGR_OK;
+}
+
 igr_status igr_get_flags(igr_ctx *c, int *flags)
 {
     if (!c || !flags) return fail(c, IGR_ERR_INVALID_ARG, "ctx and flags are required");

@@ -116,6 +116,13 @@ struct Ops {
     // extrema and the elliptic residual; *nblocks <= DIAG_MAXBLOCKS blocks
     cudaError_t (*diag)(const Geom &, const Phys &, const Inflow &, const void *q, const void *sig,
                         double *part, int *nblocks, cudaStream_t st);
+
+    // ---- debug build (IGR_DEBUG_BOUNDS) ----
+    // out-of-range indices counted by the forward kernels since the last clear
+    // (~0 when the library is not a debug build); a self-test forming one
+    // out-of-range index (checked, never dereferenced; sink is never written)
+    unsigned long long (*bounds_hits)(int clear);
+    cudaError_t (*bounds_selftest)(int *sink, cudaStream_t st);
 };
 
 // layout of one block's diagnostics partials: sums of rho, mx, my, mz, E,

@@ -51,6 +51,65 @@ using A = Num<S>::A;
 // Offsets inside one field are 32-bit (grids hold fewer than 2^32 cells);
 // each field has its own base pointer, so an address is one 32x32->64 step.
 using idx = unsigned;
+// Index checks of the debug build (IGR_DEBUG_BOUNDS, a separate library):
+// every global index the forward kernels form, and every shared-memory index
+// that depends on more than the thread's position in its block (halo slots,
+// the flux kernel's tile and face-buffer offsets), is compared with its
+// array's length; an index out of range is counted and replaced by 0, so
+// nothing is accessed out of bounds and the count is read on the host. In
+// the normal build the checks compile to nothing.
+#ifdef IGR_DEBUG_BOUNDS
+static __device__ unsigned long long g_bounds_hits;
+// element offset c of an array of n values (offsets are unsigned: a
+// negative one wraps to a value >= n on the grids the checks run on)
+__device__ __forceinline__ idx ck(idx c, long long n)
+{
+    if ((long long)c >= n) {
+        atomicAdd(&g_bounds_hits, 1ull);
+        return 0;
+    }
+    return c;
+}
+// pointer p to w consecutive values of the array of n values at base
+template <class T>
+__device__ __forceinline__ T *ckp(T *p, T *base, long long n, int w)
+{
+    const long long d = p - base;
+    if (d < 0 || d + w > n) {
+        atomicAdd(&g_bounds_hits, 1ull);
+        return base;
+    }
+    return p;
+}
+#define CKP(p, base, n) ckp((p), (base), (long long)(n), 1)
+#define CKP4(p, base, n) ckp((p), (base), (long long)(n), 4)
+// shared-memory element index c of a tile of n elements
+__device__ __forceinline__ int cks(int c, int n)
+{
+    if (c < 0 || c >= n) {
+        atomicAdd(&g_bounds_hits, 1ull);
+        return 0;
+    }
+    return c;
+}
+// the first of 4 consecutive shared values of a vector access: in range and
+// a multiple of 4 (16-byte aligned for 4-byte values)
+__device__ __forceinline__ int cks4(int c, int n)
+{
+    if (c < 0 || c + 3 >= n || (c & 3)) {
+        atomicAdd(&g_bounds_hits, 1ull);
+        return 0;
+    }
+    return c;
+}
+#else
+__device__ __forceinline__ idx ck(idx c, long long) { return c; }
+#define CKP(p, base, n) (p)
+#define CKP4(p, base, n) (p)
+__device__ __forceinline__ int cks(int c, int) { return c; }
+__device__ __forceinline__ int cks4(int c, int) { return c; }
+#endif
+
 template <int N> struct Fin { const S *p[N]; };   // fields read
 template <int N> struct Fout { S *p[N]; };        // fields written
 struct Frhs { C *p[5]; };
@@ -374,10 +433,11 @@ __device__ __forceinline__ int zmap(int kk, const Geom &g)
 __device__ __forceinline__ void col_u(const Fin<4> &q, const Geom &g, const C *W, const C *J, idx f,
                                       int kk, C u[3])
 {
-    idx c = (idx)map_axis(kk, g.nz, g.bc[4], g.bc[5]) * (idx)g.plane + f;
+    idx c = ck((idx)map_axis(kk, g.nz, g.bc[4], g.bc[5]) * (idx)g.plane + f, g.n);
     C rho = ldc(q.p[0] + c), m0 = ldc(q.p[1] + c), m1 = ldc(q.p[2] + c), m2 = ldc(q.p[3] + c);
     if (kk < 0 && g.bc[4] == BC_INFLOW) {
         idx pl = (idx)g.plane;
+        f = ck(f, g.plane);
         C w = C(1) - W[f];
         rho = w * rho + J[f];
         m0 = w * m0 + J[pl + f];
@@ -423,7 +483,7 @@ __global__ void __launch_bounds__(BT) k_source(Fin<4> q, S *__restrict__ b, Geom
     // the column at k + 1 and the halo at k (planes >= 0 need no jet blend)
     S nc[4], nh[4];
     auto raw4 = [&](idx off, int kk, S v[4]) {
-        idx c = (idx)zmap(kk, g) * pl + off;
+        idx c = ck((idx)zmap(kk, g) * pl + off, g.n);
 #pragma unroll
         for (int a = 0; a < 4; a++) v[a] = ldr(q.p[a] + c);
     };
@@ -447,7 +507,7 @@ __global__ void __launch_bounds__(BT) k_source(Fin<4> q, S *__restrict__ b, Geom
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             U[a][ty + 1][tx + 1] = u0[a];
-            if (hv) (&U[a][0][0])[hs] = hu[a];
+            if (hv) (&U[a][0][0])[cks(hs, HY * HX)] = hu[a];
         }
         __syncthreads();
         if (active) {
@@ -461,7 +521,7 @@ __global__ void __launch_bounds__(BT) k_source(Fin<4> q, S *__restrict__ b, Geom
             C tr = G[0][0] + G[1][1] + G[2][2];
             C tr2 = G[0][0] * G[0][0] + G[1][1] * G[1][1] + G[2][2] * G[2][2] +
                     C(2) * (G[0][1] * G[1][0] + G[0][2] * G[2][0] + G[1][2] * G[2][1]);
-            stc(b + (idx)k * pl + (idx)(j * g.nx + i), alpha * (tr2 + tr * tr));
+            stc(CKP(b + (idx)k * pl + (idx)(j * g.nx + i), b, g.n), alpha * (tr2 + tr * tr));
         }
 #pragma unroll
         for (int a = 0; a < 3; a++) {
@@ -514,25 +574,25 @@ __global__ void __launch_bounds__(BT) k_jacobi(const S *__restrict__ q, const S 
     const C eyp = (j < g.ny - 1 || g.bc[3] == BC_PERIODIC) ? hb : C(0);
     C rm, sm, r0, s0, rp, sp;
     {
-        idx c = (idx)zmap(k0 - 1, g) * pl + f;
+        idx c = ck((idx)zmap(k0 - 1, g) * pl + f, g.n);
         rm = rcp(ldc(q + c));
         sm = ldc(sin + c);
-        c = (idx)k0 * pl + f;
+        c = ck((idx)k0 * pl + f, g.n);
         r0 = rcp(ldc(q + c));
         s0 = ldc(sin + c);
     }
     // raw values one iteration ahead: column at k + 1, halo and b at k
     S ncr, ncs, nhr = S(1.0f), nhs = S(0.0f), nb;
     auto pre = [&](int kk) {
-        idx c = (idx)zmap(kk + 1, g) * pl + f;
+        idx c = ck((idx)zmap(kk + 1, g) * pl + f, g.n);
         ncr = ldr(q + c);
         ncs = ldr(sin + c);
         if (hv) {
-            idx h = (idx)kk * pl + hf;
+            idx h = ck((idx)kk * pl + hf, g.n);
             nhr = ldr(q + h);
             nhs = ldr(sin + h);
         }
-        nb = ldr(b + (idx)kk * pl + f);
+        nb = ldr(CKP(b + (idx)kk * pl + f, b, g.n));
     };
     pre(k0);
     for (int k = k0; k < k1; k++) {
@@ -544,8 +604,8 @@ __global__ void __launch_bounds__(BT) k_jacobi(const S *__restrict__ q, const S 
         R[ty + 1][tx + 1] = r0;
         SG[ty + 1][tx + 1] = s0;
         if (hv) {
-            (&R[0][0])[hs] = hr;
-            (&SG[0][0])[hs] = hsg;
+            (&R[0][0])[cks(hs, HY * HX)] = hr;
+            (&SG[0][0])[cks(hs, HY * HX)] = hsg;
         }
         __syncthreads();
         if (active) {
@@ -562,7 +622,7 @@ __global__ void __launch_bounds__(BT) k_jacobi(const S *__restrict__ q, const S 
             C off = c0 * SG[ty + 1][tx] + c1 * SG[ty + 1][tx + 2] + c2 * SG[ty][tx + 1] +
                     c3 * SG[ty + 2][tx + 1] + c4 * sm + c5 * sp;
             if (colour < 0 || ((i + j + k) & 1) == colour)
-                stc(sout + (idx)k * pl + (idx)(j * g.nx + i), div_c(bv + off, diag));
+                stc(CKP(sout + (idx)k * pl + (idx)(j * g.nx + i), sout, g.n), div_c(bv + off, diag));
         }
         rm = r0; sm = s0;
         r0 = rp; s0 = sp;
@@ -714,10 +774,11 @@ constexpr int NYH = 2 * BX, NXH = 2 * BY;   // 4-wide y-halo tasks, scalar x-hal
 // one 4-wide load when the cells lie inside the row, mapped single loads otherwise
 __device__ __forceinline__ V4 ld4_mapped(const S *__restrict__ a, const Geom &g, idx rowoff, int x)
 {
-    if (x + VX <= g.nx) return ld4r(a + rowoff + x);
+    if (x + VX <= g.nx) return ld4r(CKP4(a + rowoff + x, a, g.n));
     S v[VX];
 #pragma unroll
-    for (int c = 0; c < VX; c++) v[c] = ldr(a + rowoff + (idx)map_axis(x + c, g.nx, g.bc[0], g.bc[1]));
+    for (int c = 0; c < VX; c++)
+        v[c] = ldr(CKP(a + rowoff + (idx)map_axis(x + c, g.nx, g.bc[0], g.bc[1]), a, g.n));
     return pack4(v[0], v[1], v[2], v[3]);
 }
 
@@ -777,13 +838,13 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : sizeof(S) == 4 ? 2 : 
         idx pz = (idx)zmap(kk + 1, g) * pl + rowj;
         ncr = ld4_mapped(q, g, pz, i0);
         ncs = ld4_mapped(sin, g, pz, i0);
-        if (active) nb = ld4r(b + (idx)kk * pl + rowj + (idx)i0);
+        if (active) nb = ld4r(CKP4(b + (idx)kk * pl + rowj + (idx)i0, b, g.n));
         if (htask == 0) {
             nhr = ld4_mapped(q, g, (idx)kk * pl + hrow, hx);
             nhs = ld4_mapped(sin, g, (idx)kk * pl + hrow, hx);
         } else if (htask == 1) {
-            nxr = ldr(q + (idx)kk * pl + hrow + hx);
-            nxs = ldr(sin + (idx)kk * pl + hrow + hx);
+            nxr = ldr(CKP(q + (idx)kk * pl + hrow + hx, q, g.n));
+            nxs = ldr(CKP(sin + (idx)kk * pl + hrow + hx, sin, g.n));
         }
     };
     pre(k0);
@@ -808,11 +869,11 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : sizeof(S) == 4 ? 2 : 
         sh_st4(&R[ty + 1][VX + VX * tx], r0);
         sh_st4(&SG[ty + 1][VX + VX * tx], s0);
         if (htask == 0) {
-            sh_st4(&R[hsy][hsx], hr);
-            sh_st4(&SG[hsy][hsx], hsg);
+            sh_st4(&R[cks(hsy, HY)][cks4(hsx, HXV)], hr);
+            sh_st4(&SG[cks(hsy, HY)][cks4(hsx, HXV)], hsg);
         } else if (htask == 1) {
-            R[hsy][hsx] = hr[0];
-            SG[hsy][hsx] = hsg[0];
+            R[cks(hsy, HY)][cks(hsx, HXV)] = hr[0];
+            SG[cks(hsy, HY)][cks(hsx, HXV)] = hsg[0];
         }
         __syncthreads();
         if (active) {
@@ -881,7 +942,7 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : sizeof(S) == 4 ? 2 : 
                     if (colour >= 0 && ((i0 + c + j + k) & 1) != colour) o[c] = s0[c];
                 }
             }
-            st4(sout + (idx)k * pl + (idx)(j * g.nx + i0), o);
+            st4(CKP4(sout + (idx)k * pl + (idx)(j * g.nx + i0), sout, g.n), o);
         }
 #pragma unroll
         for (int c = 0; c < VX; c++) {
@@ -953,7 +1014,7 @@ __global__ void __launch_bounds__(BT) k_source_v4(Fin<4> q, S *__restrict__ b, G
         if (kk < 0 && g.bc[4] == BC_INFLOW) {
 #pragma unroll
             for (int c = 0; c < VX; c++) {
-                idx fc = rowj + (idx)map_axis(i0 + c, g.nx, g.bc[0], g.bc[1]);
+                idx fc = ck(rowj + (idx)map_axis(i0 + c, g.nx, g.bc[0], g.bc[1]), g.plane);
                 C w = C(1) - W[fc];
 #pragma unroll
                 for (int f = 0; f < 4; f++) v[f][c] = w * v[f][c] + J[(idx)f * pl + fc];
@@ -981,7 +1042,7 @@ __global__ void __launch_bounds__(BT) k_source_v4(Fin<4> q, S *__restrict__ b, G
             for (int f = 0; f < 4; f++) nh[f] = ld4_mapped(q.p[f], g, (idx)kk * pl + hrow, hx);
         } else if (htask == 1) {
 #pragma unroll
-            for (int f = 0; f < 4; f++) nxh[f] = ldr(q.p[f] + (idx)kk * pl + hrow + hx);
+            for (int f = 0; f < 4; f++) nxh[f] = ldr(CKP(q.p[f] + (idx)kk * pl + hrow + hx, q.p[f], g.n));
         }
     };
     pre(k0);
@@ -1000,8 +1061,8 @@ __global__ void __launch_bounds__(BT) k_source_v4(Fin<4> q, S *__restrict__ b, G
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             sh_st4(&U[a][ty + 1][VX + VX * tx], u0[a]);
-            if (htask == 0) sh_st4(&U[a][hsy][hsx], hu[a]);
-            else if (htask == 1) U[a][hsy][hsx] = hu[a][0];
+            if (htask == 0) sh_st4(&U[a][cks(hsy, HY)][cks4(hsx, HXV)], hu[a]);
+            else if (htask == 1) U[a][cks(hsy, HY)][cks(hsx, HXV)] = hu[a][0];
         }
         __syncthreads();
         if (active) {
@@ -1034,7 +1095,7 @@ __global__ void __launch_bounds__(BT) k_source_v4(Fin<4> q, S *__restrict__ b, G
                         C(2) * (D[0][1] * D[1][0] + D[0][2] * D[2][0] + D[1][2] * D[2][1]);
                 o[c] = alpha_s * (tr2 + tr * tr);
             }
-            st4(b + (idx)k * pl + (idx)(j * g.nx + i0), o);
+            st4(CKP4(b + (idx)k * pl + (idx)(j * g.nx + i0), b, g.n), o);
         }
 #pragma unroll
         for (int a = 0; a < 3; a++)
@@ -1103,6 +1164,7 @@ __device__ __forceinline__ C2 rec3_right2(C2 c, C2 d, C2 e)
 }
 
 constexpr int TILE2 = 3 * PH * PW;  // pairs in one plane tile
+constexpr int NFX = 5 * TY * (TX + 1), NFY = 5 * (TY + 1) * TX;  // one parity of the face buffers
 constexpr int RING = 7;             // plane tiles resident: k-2..k+3 and k+4 in flight
 
 // Storage equal to the arithmetic type: plane tiles are copied global ->
@@ -1164,7 +1226,8 @@ __device__ __forceinline__ void tile_face(const C2 *T, int at, int step, C gamma
     for (int m = 0; m < 6; m++)
 #pragma unroll
         for (int p = 0; p < 3; p++)
-            s[m][p] = (ORD == 3 && (m == 0 || m == 5)) ? bcast(C(0)) : T[p * PH * PW + at + m * step];
+            s[m][p] = (ORD == 3 && (m == 0 || m == 5)) ? bcast(C(0))
+                                                       : T[p * PH * PW + cks(at + m * step, PH * PW)];
     face_from_stencil<D, ORD>(s, gamma, gm1, F, bad);
 }
 
@@ -1172,7 +1235,7 @@ __device__ __forceinline__ void tile_face(const C2 *T, int at, int step, C gamma
 // Velocity u = m / rho of the tile cell at pair offset `at`.
 __device__ __forceinline__ void tvel(const C2 *T, int at, C u[3])
 {
-    C2 a = T[at], b = T[PH * PW + at];
+    C2 a = T[cks(at, PH * PW)], b = T[PH * PW + cks(at, PH * PW)];
     C r = rcp(a.x);
     u[0] = a.y * r;
     u[1] = b.x * r;
@@ -1246,7 +1309,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *P = reinterpret_cast<C2 *>(smem_raw);        // [RING][3][PH][PW]
     C *FXb = reinterpret_cast<C *>(P + RING * TILE2); // [2][5][TY][TX+1]
-    C *FYb = FXb + 2 * 5 * TY * (TX + 1);            // [2][5][TY+1][TX]
+    C *FYb = FXb + 2 * NFX;                           // [2][5][TY+1][TX]
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
@@ -1295,14 +1358,14 @@ __global__ void __maxnreg__(FLUX_MAXREG)
             if (soff[r] >= 0) {
                 C v[6];
 #pragma unroll
-                for (int u = 0; u < 6; u++) v[u] = ldc(in.p[u] + zb + goff[r]);
+                for (int u = 0; u < 6; u++) v[u] = ldc(CKP(in.p[u] + zb + goff[r], in.p[u], g.n));
                 if (blend) {
-                    C wf = C(1) - W[goff[r]];
+                    C wf = C(1) - W[ck(goff[r], g.plane)];
 #pragma unroll
-                    for (int u = 0; u < 5; u++) v[u] = wf * v[u] + J[(idx)u * pl + goff[r]];
+                    for (int u = 0; u < 5; u++) v[u] = wf * v[u] + J[(idx)u * pl + ck(goff[r], g.plane)];
                 }
 #pragma unroll
-                for (int p = 0; p < 3; p++) T[p * PH * PW + soff[r]] = pset(v[2 * p], v[2 * p + 1]);
+                for (int p = 0; p < 3; p++) T[p * PH * PW + cks(soff[r], PH * PW)] = pset(v[2 * p], v[2 * p + 1]);
             }
     }
 
@@ -1318,9 +1381,10 @@ __global__ void __maxnreg__(FLUX_MAXREG)
 #pragma unroll
                 for (int u = 0; u < 6; u++) {
                     if constexpr (kAsyncTile)
-                        cp_async_elem(&T[(u >> 1) * PH * PW + soff[r]].x + (u & 1), in.p[u] + zb + goff[r]);
+                        cp_async_elem(&T[(u >> 1) * PH * PW + cks(soff[r], PH * PW)].x + (u & 1),
+                                      CKP(in.p[u] + zb + goff[r], in.p[u], g.n));
                     else
-                        Rg[r][u] = ldr(in.p[u] + zb + goff[r]);
+                        Rg[r][u] = ldr(CKP(in.p[u] + zb + goff[r], in.p[u], g.n));
                 }
             }
         if constexpr (kAsyncTile) cp_async_commit();
@@ -1334,7 +1398,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
                 if (soff[r] >= 0)
 #pragma unroll
                     for (int p = 0; p < 3; p++)
-                        T[p * PH * PW + soff[r]] = pset(cv(Rg[r][2 * p]), cv(Rg[r][2 * p + 1]));
+                        T[p * PH * PW + cks(soff[r], PH * PW)] = pset(cv(Rg[r][2 * p]), cv(Rg[r][2 * p + 1]));
         }
     };
     __syncthreads();
@@ -1354,14 +1418,16 @@ __global__ void __maxnreg__(FLUX_MAXREG)
 
     // divergence and stage combination of plane kk (face buffers of parity kk)
     auto finish = [&](int kk, const C2 *T) {
-        const C *FX = FXb + (kk & 1) * 5 * TY * (TX + 1);
-        const C *FY = FYb + (kk & 1) * 5 * (TY + 1) * TX;
-        idx c = (idx)kk * pl + own;
+        const C *FX = FXb + (kk & 1) * NFX;
+        const C *FY = FYb + (kk & 1) * NFY;
+        idx c = ck((idx)kk * pl + own, g.n);
         C Lv[5];
 #pragma unroll
         for (int u = 0; u < 5; u++) {
-            C dfx = FX[(u * TY + w) * (TX + 1) + lane + 1] - FX[(u * TY + w) * (TX + 1) + lane];
-            C dfy = FY[(u * (TY + 1) + w + 1) * TX + lane] - FY[(u * (TY + 1) + w) * TX + lane];
+            C dfx = FX[cks((u * TY + w) * (TX + 1) + lane + 1, NFX)] -
+                    FX[cks((u * TY + w) * (TX + 1) + lane, NFX)];
+            C dfy = FY[cks((u * (TY + 1) + w + 1) * TX + lane, NFY)] -
+                    FY[cks((u * (TY + 1) + w) * TX + lane, NFY)];
             C dfz = Fzp[u] - Fzm[u];
             Lv[u] = -((dfx + dfy) + dfz) * half_inv_dx;
         }
@@ -1370,7 +1436,8 @@ __global__ void __maxnreg__(FLUX_MAXREG)
             for (int u = 0; u < 5; u++) rhs.p[u][c] = Lv[u];
             nonfinite |= !isfinite((Lv[0] + Lv[1]) + (Lv[2] + Lv[3]) + Lv[4]);
         } else {
-            C2 a = T[tcell], b = T[PH * PW + tcell], e = T[2 * PH * PW + tcell];
+            const int tc = cks(tcell, PH * PW);
+            C2 a = T[tc], b = T[PH * PW + tc], e = T[2 * PH * PW + tc];
             const C qsv[5] = {a.x, a.y, b.x, b.y, e.x};
             if (mode == FLUX_STAGE1 && base_out.p[0]) {
                 // the RK base q^n for stages 2 and 3 (exact: qsv holds stored values)
@@ -1397,7 +1464,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
 #pragma unroll
             for (int u = 0; u < 5; u++) Fzm[u] = Fzp[u];
             if (k >= k0 && active && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3)) {
-                idx c = (idx)k * pl + own;
+                idx c = ck((idx)k * pl + own, g.n);
 #pragma unroll
                 for (int u = 0; u < 5; u++) qnv[u] = ldr(qn.p[u] + c);
             }
@@ -1406,7 +1473,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
             for (int m = 0; m < 6; m++) {
                 const C2 *T = P + ro[m];
 #pragma unroll
-                for (int p = 0; p < 3; p++) sz[m][p] = T[p * PH * PW + tcell];
+                for (int p = 0; p < 3; p++) sz[m][p] = T[p * PH * PW + cks(tcell, PH * PW)];
             }
             face_from_stencil<2, ORD>(sz, gamma, gm1, Fzp, bad);  // z-face k + 1/2
             if constexpr (VISC) {
@@ -1418,8 +1485,8 @@ __global__ void __maxnreg__(FLUX_MAXREG)
         }
         if (k >= k0) {
             const C2 *T = P + ro[2];
-            C *FX = FXb + (k & 1) * 5 * TY * (TX + 1);
-            C *FY = FYb + (k & 1) * 5 * (TY + 1) * TX;
+            C *FX = FXb + (k & 1) * NFX;
+            C *FY = FYb + (k & 1) * NFY;
             C F[5];
             const C2 *Tm = P + ro[1], *Tp = P + ro[3];  // planes k - 1, k + 1 (viscous terms)
             const C inv_dx = C(2) * half_inv_dx;
@@ -1438,24 +1505,24 @@ __global__ void __maxnreg__(FLUX_MAXREG)
                 tile_face<0, ORD>(T, (w + 3) * PW + lane, 1, gamma, gm1, F, bad);
                 if constexpr (VISC) visc_x((w + 3) * PW + lane + 2);
 #pragma unroll
-                for (int u = 0; u < 5; u++) FX[(u * TY + w) * (TX + 1) + lane] = F[u];
+                for (int u = 0; u < 5; u++) FX[cks((u * TY + w) * (TX + 1) + lane, NFX)] = F[u];
                 // y-face below row w in column lane (tile rows w-3..w+2)
                 tile_face<1, ORD>(T, w * PW + lane + 3, PW, gamma, gm1, F, bad);
                 if constexpr (VISC) visc_y((w + 2) * PW + lane + 3);
 #pragma unroll
-                for (int u = 0; u < 5; u++) FY[(u * (TY + 1) + w) * TX + lane] = F[u];
+                for (int u = 0; u < 5; u++) FY[cks((u * (TY + 1) + w) * TX + lane, NFY)] = F[u];
             } else {
                 // y-face above the last row, column lane
                 tile_face<1, ORD>(T, TY * PW + lane + 3, PW, gamma, gm1, F, bad);
                 if constexpr (VISC) visc_y((TY + 2) * PW + lane + 3);
 #pragma unroll
-                for (int u = 0; u < 5; u++) FY[(u * (TY + 1) + TY) * TX + lane] = F[u];
+                for (int u = 0; u < 5; u++) FY[cks((u * (TY + 1) + TY) * TX + lane, NFY)] = F[u];
                 if (lane < TY) {
                     // x-face at the high end of row `lane`
                     tile_face<0, ORD>(T, (lane + 3) * PW + TX, 1, gamma, gm1, F, bad);
                     if constexpr (VISC) visc_x((lane + 3) * PW + TX + 2);
 #pragma unroll
-                    for (int u = 0; u < 5; u++) FX[(u * TY + lane) * (TX + 1) + TX] = F[u];
+                    for (int u = 0; u < 5; u++) FX[cks((u * TY + lane) * (TX + 1) + TX, NFX)] = F[u];
                 }
             }
         }
@@ -2141,12 +2208,42 @@ cudaError_t launch_diag(const Geom &g, const Phys &p, const Inflow &in, const vo
     return cudaGetLastError();
 }
 
+// debug build: read (and clear) the bounds-check counter; the self-test
+// forms one index past the end of an array of n values (checked, not used)
+__global__ void k_bounds_selftest(long long n, int *sink)
+{
+    idx c = ck((idx)(n + 5), n);
+    if (c != 0) *sink = (int)c;  // never taken: the check returns 0
+}
+
+unsigned long long bounds_hits(int clear)
+{
+#ifdef IGR_DEBUG_BOUNDS
+    unsigned long long h = 0;
+    if (cudaMemcpyFromSymbol(&h, g_bounds_hits, sizeof h) != cudaSuccess) return ~0ull;
+    if (clear) {
+        unsigned long long z = 0;
+        if (cudaMemcpyToSymbol(g_bounds_hits, &z, sizeof z) != cudaSuccess) return ~0ull;
+    }
+    return h;
+#else
+    (void)clear;
+    return ~0ull;  // not a debug build
+#endif
+}
+
+cudaError_t bounds_selftest(int *sink, cudaStream_t st)
+{
+    k_bounds_selftest<<<1, 1, 0, st>>>(1000, sink);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 extern const Ops IGR_OPS = {
     (int)sizeof(S), (int)sizeof(C), launch_source, launch_jacobi, launch_flux, flux_blocks,
     launch_speed, launch_rk_combine, launch_adj_rk, launch_adj_rhs, launch_adj_jacobi, launch_adj_rho,
-    launch_adj_source, launch_adj_jets, launch_diag,
+    launch_adj_source, launch_adj_jets, launch_diag, bounds_hits, bounds_selftest,
 };
 
 }  // namespace igr

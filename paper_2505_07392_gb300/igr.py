@@ -15,7 +15,9 @@ from typing import Optional, Sequence
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libigr.so")
+# IGR_LIBRARY selects another build of the same library (the bounds-checking
+# libigr_debug.so); the default is the in-tree libigr.so
+LIB_PATH = os.environ.get("IGR_LIBRARY") or os.path.join(HERE, "libigr.so")
 
 # enums of igr.h
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
@@ -98,6 +100,8 @@ def lib():
             "igr_sync": (i, [p]),
             "igr_get_flags": (i, [p, C.POINTER(i)]),
             "igr_diagnose": (i, [p, C.POINTER(Diagnostics)]),
+            "igr_debug_bounds_hits": (i, [C.POINTER(C.c_ulonglong), i]),
+            "igr_debug_bounds_selftest": (i, []),
             "igr_profile_enable": (i, [p, i]),
             "igr_profile_read": (i, [p, i, C.POINTER(C.c_longlong), C.POINTER(d)]),
             "igr_last_error": (C.c_char_p, [p]),
