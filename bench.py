@@ -258,15 +258,28 @@ def run_e2e(s, case, precision, steps, sync_all):
         check(L.igr_step(s.h, 1, 0.0, None))
         check(L.igr_get_state(s.h, pq, ps, code, 0))
     sync_all()
+    # every call returns after its work is done (set_state and get_state
+    # synchronise the stream; igr_sync after the step), so the phases are
+    # timed on the host clock
+    phase = [0.0, 0.0, 0.0]
     t0 = time.perf_counter()
     for _ in range(steps):
+        ta = time.perf_counter()
         check(L.igr_set_state(s.h, pq, ps, code, 0))
+        tb = time.perf_counter()
         check(L.igr_step(s.h, 1, 0.0, None))
+        check(L.igr_sync(s.h))
+        tc = time.perf_counter()
         check(L.igr_get_state(s.h, pq, ps, code, 0))
+        td = time.perf_counter()
+        phase[0] += tb - ta
+        phase[1] += tc - tb
+        phase[2] += td - tc
     sync_all()
     sec = time.perf_counter() - t0
     nbytes = hq.numel() * hq.element_size() + hs.numel() * hs.element_size()
-    return {"sec": sec, "steps": steps, "bytes": nbytes}
+    return {"sec": sec, "steps": steps, "bytes": nbytes, "pinned": bool(hq.is_pinned() and hs.is_pinned()),
+            "phase_s": [x / steps for x in phase]}
 
 
 def roofline_of(case, res, precision, peak, peak_kind):
@@ -560,7 +573,9 @@ def main():
         e = res["e2e"]
         line["e2e"] = {"value": full.ncells * e["steps"] / e["sec"], "unit": "cell-updates/s",
                        "h2d_bytes_per_step": e["bytes"], "d2h_bytes_per_step": e["bytes"],
-                       "steps": e["steps"]}
+                       "steps": e["steps"], "pinned": e["pinned"],
+                       "s_per_step": {"set_state": round(e["phase_s"][0], 4), "step": round(e["phase_s"][1], 4),
+                                      "get_state": round(e["phase_s"][2], 4)}}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(full, args.cpu_steps, tuple(args.cpu_size))
     print(json.dumps(line))
