@@ -44,12 +44,12 @@ FALLBACK_HBM_GBS = 6800.0
 # issue roofline; tied to the kernel source like the traffic.
 NCU_INSTR = {
     # profiles/flux_plume_f16.md
-    "flux_f16": {"warp_instr_per_cell": 24.137, "src": "0f939e942f38d191"},
+    "flux_f16": {"warp_instr_per_cell": 22.944, "src": "5c560c20905903c7"},
 }
 
 NCU_TRAFFIC = {
     # profiles/flux_plume_f16.md: mean of the three stage launches, 512 x 512 x 128 plume
-    "flux_f16": {"bytes_per_cell": 29.129, "src": "0f939e942f38d191"},
+    "flux_f16": {"bytes_per_cell": 29.111, "src": "5c560c20905903c7"},
 }
 
 

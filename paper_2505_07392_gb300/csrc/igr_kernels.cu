@@ -309,30 +309,46 @@ __device__ __forceinline__ double block_max(double v)
 //   the slack covering the FP64 evaluation's own rounding and the FP32
 //   evaluation of e; where a rounding result is an FP32 subnormal its error
 //   is absolute (at most 2^-150), so e adds 2^-148 for the three roundings.
-// If v32 sits farther than e from every rounding boundary of the storage
-// format, RN16(v32) = RN16(v64); otherwise (for smooth data, about e / spacing
-// of the values, well under one in a thousand) the combination is redone in
-// FP64. The stored value therefore always equals the FP64 evaluation rounded
-// to nearest-even, with zeros stored as +0.
+// So v64 lies in [RD(v32 - e), RU(v32 + e)] (directed FP32 roundings).
+// Rounding to nearest-even is monotone: when both ends of that interval round
+// to the same storage value (with -0 equal to +0), so does v64. Both ends are
+// converted by one packed conversion and compared as a pair. Otherwise (for
+// smooth data, about e / spacing of the values, well under one in a
+// thousand) the combination is redone in FP64. The stored value therefore
+// always equals the FP64 evaluation rounded to nearest-even, with zeros
+// stored as +0.
 template <typename T> struct Narrow;
 template <> struct Narrow<__half> {
-    static constexpr int M = 10;                 // stored mantissa bits
-    static constexpr float tiny = 0x1p-25f;      // half-ulp of the subnormals
-    static __device__ __forceinline__ __half rn(float v) { return __float2half_rn(v); }
+    using T2 = __half2;
     static __device__ __forceinline__ __half rn(double v) { return __double2half(v); }
-    static __device__ __forceinline__ float f(__half h) { return __half2float(h); }
+    // (RN(a), RN(b)) in the low and high halves, one conversion
+    static __device__ __forceinline__ __half2 rn2(float a, float b) { return __floats2half2_rn(a, b); }
+    static __device__ __forceinline__ bool eq2(__half2 a, __half2 b) { return __hbeq2(a, b); }
+    static __device__ __forceinline__ __half2 swap(__half2 a) { return __lowhigh2highlow(a); }
+    static __device__ __forceinline__ __half lo(__half2 a) { return __low2half(a); }
+    static __device__ __forceinline__ __half hi(__half2 a) { return __high2half(a); }
     // zeros are stored as +0 (-0 + +0 = +0 under round-to-nearest)
     static __device__ __forceinline__ __half canon(__half h) { return __hadd(h, __ushort_as_half(0)); }
+    static __device__ __forceinline__ __half2 canon2(__half2 h)
+    {
+        return __hadd2(h, __halves2half2(__ushort_as_half(0), __ushort_as_half(0)));
+    }
 };
 template <> struct Narrow<__nv_bfloat16> {
-    static constexpr int M = 7;
-    static constexpr float tiny = 0x1p-134f;
-    static __device__ __forceinline__ __nv_bfloat16 rn(float v) { return __float2bfloat16_rn(v); }
+    using T2 = __nv_bfloat162;
     static __device__ __forceinline__ __nv_bfloat16 rn(double v) { return __double2bfloat16(v); }
-    static __device__ __forceinline__ float f(__nv_bfloat16 h) { return __bfloat162float(h); }
+    static __device__ __forceinline__ __nv_bfloat162 rn2(float a, float b) { return __floats2bfloat162_rn(a, b); }
+    static __device__ __forceinline__ bool eq2(__nv_bfloat162 a, __nv_bfloat162 b) { return __hbeq2(a, b); }
+    static __device__ __forceinline__ __nv_bfloat162 swap(__nv_bfloat162 a) { return __lowhigh2highlow(a); }
+    static __device__ __forceinline__ __nv_bfloat16 lo(__nv_bfloat162 a) { return __low2bfloat16(a); }
+    static __device__ __forceinline__ __nv_bfloat16 hi(__nv_bfloat162 a) { return __high2bfloat16(a); }
     static __device__ __forceinline__ __nv_bfloat16 canon(__nv_bfloat16 h)
     {
         return __hadd(h, __ushort_as_bfloat16(0));
+    }
+    static __device__ __forceinline__ __nv_bfloat162 canon2(__nv_bfloat162 h)
+    {
+        return __hadd2(h, __halves2bfloat162(__ushort_as_bfloat16(0), __ushort_as_bfloat16(0)));
     }
 };
 
@@ -347,54 +363,80 @@ __device__ __noinline__ T rk_fp64(float qn, float qs, float L, double dt, double
     return Narrow<T>::canon(Narrow<T>::rn(vd));
 }
 
-// FP32 evaluation and rounding; ok = false when the rounding could differ
-// from the FP64 evaluation's
-template <typename T>
-__device__ __forceinline__ T rk_narrow_fast(float qn, float qs, float L, float dt32, float w32, bool &ok)
+// FP32 evaluation v of one combination and the bound e on |v - v64|
+__device__ __forceinline__ float rk_eval32(float qn, float qs, float L, float dt32, float w32, float &e)
 {
-    using NR = Narrow<T>;
     float d = __fsub_rn(qs, qn);
     float pp = __fmaf_rn(dt32, L, d);
     float v = __fmaf_rn(w32, pp, qn);
     // relative rounding errors, plus 2^-148 for the three roundings whose
     // results may be FP32 subnormals (absolute error up to 2^-150 each)
-    float e = __fmaf_rn(fabsf(v) + fabsf(pp) + fabsf(d), 0x1p-22f, 0x1p-148f);
-    T h = NR::canon(NR::rn(v));
-    float hv = NR::f(h);
-    float r = v - hv;  // exact: v and hv are within a factor 2
-    // Distance from hv to the rounding boundaries of the storage format on
-    // either side: half the spacing of hv's binade (p2 2^-M with p2 the power
-    // of two at or below |hv|); a quarter of it when |hv| is itself a power of
-    // two (the spacing below is half as wide); half the subnormal spacing
-    // (tiny) at the bottom of the range and at zero.
-    float ah = fabsf(hv);
-    float p2 = __int_as_float(__float_as_int(ah) & 0x7f800000);
-    float hb = p2 * (ah == p2 ? 1.0f / float(1 << (NR::M + 2)) : 1.0f / float(1 << (NR::M + 1)));
-    hb = fmaxf(hb, NR::tiny);
-    // v64 lies within e of v, so it rounds to hv when |r| + e < hb (a zero
-    // result is stored as +0 on both paths, whatever the sign of v)
-    ok = fabsf(r) + e < hb;
-    return h;
+    e = __fmaf_rn(fabsf(v) + fabsf(pp) + fabsf(d), 0x1p-22f, 0x1p-148f);
+    return v;
+}
+
+// Two combinations rounded to the storage format (low, high); ok = false
+// when either rounding could differ from the FP64 evaluation's
+template <typename T>
+__device__ __forceinline__ typename Narrow<T>::T2 rk_narrow_pair(float qn0, float qs0, float L0, float qn1,
+                                                                 float qs1, float L1, float dt32, float w32,
+                                                                 bool &ok)
+{
+    using NR = Narrow<T>;
+    float e0, e1;
+    const float v0 = rk_eval32(qn0, qs0, L0, dt32, w32, e0);
+    const float v1 = rk_eval32(qn1, qs1, L1, dt32, w32, e1);
+    const typename NR::T2 a = NR::rn2(__fsub_rd(v0, e0), __fsub_rd(v1, e1));
+    const typename NR::T2 b = NR::rn2(__fadd_ru(v0, e0), __fadd_ru(v1, e1));
+    ok = NR::eq2(a, b);
+    return NR::canon2(b);
+}
+
+// One combination rounded to the storage format; ok as for the pair
+template <typename T>
+__device__ __forceinline__ T rk_narrow_one(float qn, float qs, float L, float dt32, float w32, bool &ok)
+{
+    using NR = Narrow<T>;
+    float e;
+    const float v = rk_eval32(qn, qs, L, dt32, w32, e);
+    const typename NR::T2 x = NR::rn2(__fsub_rd(v, e), __fadd_ru(v, e));
+    ok = NR::eq2(x, NR::swap(x));
+    return NR::canon(NR::hi(x));
 }
 
 constexpr bool kNarrow = sizeof(S) == 2;
 
+// The 16-bit stage combination of one cell's five values: two pairs and a
+// single value, one branch per cell for the rare FP64 re-evaluations (a pair
+// that failed is redone in FP64 for both of its values)
+template <typename T>
+__device__ __forceinline__ void rk_narrow5(const C qn[5], const C qs[5], const C L[5], C dt32, double dt,
+                                           C w32, double w, T h[5])
+{
+    using NR = Narrow<T>;
+    bool ok01, ok23, ok4;
+    const typename NR::T2 h01 = rk_narrow_pair<T>(qn[0], qs[0], L[0], qn[1], qs[1], L[1], dt32, w32, ok01);
+    const typename NR::T2 h23 = rk_narrow_pair<T>(qn[2], qs[2], L[2], qn[3], qs[3], L[3], dt32, w32, ok23);
+    h[0] = NR::lo(h01);
+    h[1] = NR::hi(h01);
+    h[2] = NR::lo(h23);
+    h[3] = NR::hi(h23);
+    h[4] = rk_narrow_one<T>(qn[4], qs[4], L[4], dt32, w32, ok4);
+    if (!(ok01 && ok23 && ok4)) {
+#pragma unroll
+        for (int u = 0; u < 5; u++)
+            if (!(u < 2 ? ok01 : u < 4 ? ok23 : ok4)) h[u] = rk_fp64<T>(qn[u], qs[u], L[u], dt, w);
+    }
+}
+
 // Stage combination of the five conserved values of one cell, stored at
-// offset c of each output field; returns the stored values in type C. In the
-// 16-bit modes one branch per cell covers the rare FP64 re-evaluations.
+// offset c of each output field; returns the stored values in type C.
 __device__ __forceinline__ void rk_store5(const Fout<5> &out, idx c, const C qn[5], const C qs[5],
                                           const C L[5], C dt32, double dt, C w32, double w, C o[5])
 {
     if constexpr (kNarrow) {
         S h[5];
-        bool ok[5];
-#pragma unroll
-        for (int u = 0; u < 5; u++) h[u] = rk_narrow_fast<S>(qn[u], qs[u], L[u], dt32, w32, ok[u]);
-        if (!(ok[0] && ok[1] && ok[2] && ok[3] && ok[4])) {
-#pragma unroll
-            for (int u = 0; u < 5; u++)
-                if (!ok[u]) h[u] = rk_fp64<S>(qn[u], qs[u], L[u], dt, w);
-        }
+        rk_narrow5<S>(qn, qs, L, dt32, dt, w32, w, h);
 #pragma unroll
         for (int u = 0; u < 5; u++) {
             out.p[u][c] = h[u];
@@ -1555,7 +1597,7 @@ __global__ void k_rk_combine(const S *__restrict__ qn, const S *__restrict__ qs,
         C a = ldc(qn + c), b = ldc(qs + c), l = L[c];
         if constexpr (kNarrow) {
             bool ok;
-            S h = rk_narrow_fast<S>(a, b, l, dt32, w32, ok);
+            S h = rk_narrow_one<S>(a, b, l, dt32, w32, ok);
             if (!ok) h = rk_fp64<S>(a, b, l, dt, wd);
             out[c] = h;
         } else {
