@@ -45,11 +45,15 @@ FALLBACK_HBM_GBS = 6800.0
 NCU_INSTR = {
     # profiles/flux_plume_f16.md
     "flux_f16": {"warp_instr_per_cell": 22.944, "src": "5c560c20905903c7"},
+    # profiles/flux_plume_f32.md
+    "flux_f32": {"warp_instr_per_cell": 20.478, "src": "5c560c20905903c7"},
 }
 
 NCU_TRAFFIC = {
     # profiles/flux_plume_f16.md: mean of the three stage launches, 512 x 512 x 128 plume
     "flux_f16": {"bytes_per_cell": 29.111, "src": "5c560c20905903c7"},
+    # profiles/flux_plume_f32.md: mean of the three stage launches, 512 x 512 x 128 plume
+    "flux_f32": {"bytes_per_cell": 58.891, "src": "5c560c20905903c7"},
 }
 
 
