@@ -331,7 +331,8 @@ def issue_roofline(case, res, precision, clocks):
 def run_batch(args, sync_all=lambda: None):
     """64 periodic Taylor-Green instances of uneven size (edges drawn from
     {48,64,80,96,128}) advanced together: one CUDA graph per step with a
-    branch per instance; z-chunks autotuned per distinct size."""
+    branch per instance; z-chunks and kernel forms autotuned per distinct
+    size."""
     import torch
     from paper_2505_07392_gb300 import igr
     cases = inputs.tgv_batch(count=args.batch_count)
@@ -343,9 +344,10 @@ def run_batch(args, sync_all=lambda: None):
             torch.cuda.synchronize()
             key = (c.nx, c.ny, c.nz)
             if key not in tuned:
-                tuned[key] = inst.autotune(reps=3)
+                tuned[key] = (inst.autotune(reps=3), inst.kernel_forms())
             else:
-                inst.set_tiles(*tuned[key])
+                inst.set_tiles(*tuned[key][0])
+                inst.set_kernel_forms(*tuned[key][1])
         b.step(args.warmup, sync=True)
         sync_all()
         torch.cuda.synchronize()
@@ -364,7 +366,8 @@ def run_batch(args, sync_all=lambda: None):
             "dtype": f"f32 compute, {args.precision} storage", "data": "synthetic",
             "config": {"workload": f"{len(cases)} periodic Taylor-Green instances, edges "
                                    f"{sorted(set(c.nx for c in cases))}, {cells} cells, S=5",
-                       "tiles": {f"{k[0]}^3": v for k, v in tuned.items()},
+                       "tiles": {f"{k[0]}^3": v[0] for k, v in tuned.items()},
+                       "vec4_forms": {f"{k[0]}^3": v[1] for k, v in tuned.items()},
                        "l2": "state %.2f GB" % (6 * cells * 2 / 1e9)}}
 
 

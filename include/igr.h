@@ -306,15 +306,28 @@ igr_status igr_profile_read(igr_ctx *ctx, int kernel_class, long long *launches,
 
 /* ---- Launch shapes and the autotuner ----------------------------------
  * Each kernel class marches blocks up chunks of z-planes; the chunk length
- * is the tunable launch shape (>= 4 planes, at most nz). Results do not
- * depend on it: every face flux comes out of the same instructions whatever
- * the chunking, and there are no atomics, so outputs are bitwise identical
- * for every choice. igr_autotune times each class on the current state for
- * the candidate lengths 4..128 (reps launches each, on the context stream;
- * only scratch buffers are written) and keeps the fastest; call it after
- * igr_set_state. It synchronises. */
+ * is the tunable launch shape (>= 4 planes, at most nz). The source and
+ * Jacobi kernels also come in two forms: one cell per thread (rows in
+ * blocks of 32 cells) and four cells per thread (rows in blocks of 128
+ * cells; only for nx % 4 == 0), which runs fewer instructions per cell but
+ * idles more lanes on short rows. By default the four-cell form is taken
+ * where its share of busy lanes is at least its instruction ratio (source
+ * 80/140, Jacobi 69/79) times the one-cell form's.
+ * Results do not depend on the launch shape: every face flux comes out of
+ * the same instructions whatever the chunking, both forms evaluate the same
+ * sequence of rounded operations, and there are no atomics, so outputs are
+ * bitwise identical for every choice.
+ * igr_set_kernel_forms: source_vec4 and jacobi_vec4 each -1 (the default
+ * rule), 0 (one cell per thread) or 1 (four cells; IGR_ERR_INVALID_ARG when
+ * nx % 4 != 0).
+ * igr_autotune times each class on the current state for the candidate
+ * lengths 4..128 and, where nx % 4 == 0, both forms (reps launches each, on
+ * the context stream; only scratch buffers are written) and keeps the
+ * fastest; call it after igr_set_state. It synchronises. */
 igr_status igr_set_tiles(igr_ctx *ctx, int zc_source, int zc_jacobi, int zc_flux);
 igr_status igr_get_tiles(igr_ctx *ctx, int *zc_source, int *zc_jacobi, int *zc_flux);
+igr_status igr_set_kernel_forms(igr_ctx *ctx, int source_vec4, int jacobi_vec4);
+igr_status igr_get_kernel_forms(igr_ctx *ctx, int *source_vec4, int *jacobi_vec4);
 igr_status igr_autotune(igr_ctx *ctx, int reps);
 
 /* ---- Batches of independent instances -----------------------------------

@@ -215,8 +215,10 @@ static int default_zc(const Geom &g, int tx, int ty, int resident)
 Tiles igr::default_tiles(const Geom &g)
 {
     Tiles t;
-    t.zc_source = default_zc(g, 128, 8, 3);
-    t.zc_jacobi = default_zc(g, 128, 8, 3);
+    t.vec_source = vec4_default_source(g.nx);
+    t.vec_jacobi = vec4_default_jacobi(g.nx);
+    t.zc_source = default_zc(g, t.vec_source ? 128 : 32, 8, 3);
+    t.zc_jacobi = default_zc(g, t.vec_jacobi ? 128 : 32, 8, 3);
     t.zc_flux = default_zc(g, 32, 15, 1);
     return t;
 }
@@ -791,6 +793,26 @@ igr_status igr_get_tiles(igr_ctx *c, int *zc_source, int *zc_jacobi, int *zc_flu
     return IGR_OK;
 }
 
+igr_status igr_set_kernel_forms(igr_ctx *c, int source_vec4, int jacobi_vec4)
+{
+    if (!c) return fail(c, IGR_ERR_INVALID_ARG, "ctx is NULL");
+    if (source_vec4 < -1 || source_vec4 > 1 || jacobi_vec4 < -1 || jacobi_vec4 > 1)
+        return fail(c, IGR_ERR_INVALID_ARG, "forms are -1 (default), 0 (1 cell) or 1 (4 cells)");
+    if ((source_vec4 == 1 || jacobi_vec4 == 1) && c->g.nx % 4)
+        return fail(c, IGR_ERR_INVALID_ARG, "the 4-cell form needs nx %% 4 == 0 (nx = %d)", c->g.nx);
+    c->tiles.vec_source = source_vec4 < 0 ? vec4_default_source(c->g.nx) : source_vec4;
+    c->tiles.vec_jacobi = jacobi_vec4 < 0 ? vec4_default_jacobi(c->g.nx) : jacobi_vec4;
+    return IGR_OK;
+}
+
+igr_status igr_get_kernel_forms(igr_ctx *c, int *source_vec4, int *jacobi_vec4)
+{
+    if (!c || !source_vec4 || !jacobi_vec4) return fail(c, IGR_ERR_INVALID_ARG, "null argument");
+    *source_vec4 = c->tiles.vec_source;
+    *jacobi_vec4 = c->tiles.vec_jacobi;
+    return IGR_OK;
+}
+
 }  // extern "C"
 
 // mean milliseconds of `reps` launches of fn() on the context stream
@@ -824,6 +846,7 @@ igr_status igr_autotune(igr_ctx *c, int reps)
     if (c->cfg.sigma_solver == SOLVER_RBGS)
         CU(c, cudaMemcpyAsync(c->q[1], sig, c->g.n * (size_t)c->ops->storage_bytes, cudaMemcpyDeviceToDevice,
                               c->st));
+    const int nforms = c->g.nx % 4 == 0 ? 2 : 1;  // the 4-cell forms need rows of a multiple of 4
     for (int zc : cand) {
         if (zc > c->g.nz && zc != cand[0]) continue;
         Tiles t = c->tiles;
@@ -831,17 +854,20 @@ igr_status igr_autotune(igr_ctx *c, int reps)
         float ms;
         igr_status s;
         // each kernel class writes only scratch: b, the other Sigma buffer, the stage-1 output
-        s = time_launches(c, reps, [&] { return c->ops->source(c->g, c->p, t, inflow_of(c), c->q[0], c->b, c->st); }, &ms);
-        if (s != IGR_OK) return s;
-        if (ms < tbest[0]) { tbest[0] = ms; best.zc_source = t.zc_source; }
-        s = time_launches(c, reps, [&] {
-            // red-black: a half-sweep in place on a copy of Sigma in the stage-1 output buffer
-            return c->cfg.sigma_solver == SOLVER_RBGS
-                       ? c->ops->jacobi(c->g, c->p, t, c->q[0], c->b, c->q[1], c->q[1], 0, c->st)
-                       : c->ops->jacobi(c->g, c->p, t, c->q[0], c->b, sig, scratch, -1, c->st);
-        }, &ms);
-        if (s != IGR_OK) return s;
-        if (ms < tbest[1]) { tbest[1] = ms; best.zc_jacobi = t.zc_jacobi; }
+        for (int v = 0; v < nforms; v++) {
+            t.vec_source = t.vec_jacobi = v;
+            s = time_launches(c, reps, [&] { return c->ops->source(c->g, c->p, t, inflow_of(c), c->q[0], c->b, c->st); }, &ms);
+            if (s != IGR_OK) return s;
+            if (ms < tbest[0]) { tbest[0] = ms; best.zc_source = t.zc_source; best.vec_source = v; }
+            s = time_launches(c, reps, [&] {
+                // red-black: a half-sweep in place on a copy of Sigma in the stage-1 output buffer
+                return c->cfg.sigma_solver == SOLVER_RBGS
+                           ? c->ops->jacobi(c->g, c->p, t, c->q[0], c->b, c->q[1], c->q[1], 0, c->st)
+                           : c->ops->jacobi(c->g, c->p, t, c->q[0], c->b, sig, scratch, -1, c->st);
+            }, &ms);
+            if (s != IGR_OK) return s;
+            if (ms < tbest[1]) { tbest[1] = ms; best.zc_jacobi = t.zc_jacobi; best.vec_jacobi = v; }
+        }
         s = time_launches(c, reps, [&] {
             return c->ops->flux(c->g, c->p, t, inflow_of(c), FLUX_STAGE1, c->q[0], sig, c->q[0], c->q[1],
                                 nullptr, nullptr, c->sc, c->blockmax, &c->sc->err, c->st);
@@ -868,7 +894,8 @@ struct igr_batch {
         bool operator==(const Host &o) const
         {
             return cur == o.cur && speed_nblocks == o.speed_nblocks && tiles.zc_source == o.tiles.zc_source &&
-                   tiles.zc_jacobi == o.tiles.zc_jacobi && tiles.zc_flux == o.tiles.zc_flux;
+                   tiles.zc_jacobi == o.tiles.zc_jacobi && tiles.zc_flux == o.tiles.zc_flux &&
+                   tiles.vec_source == o.tiles.vec_source && tiles.vec_jacobi == o.tiles.vec_jacobi;
         }
     };
     struct Graph {

@@ -172,13 +172,21 @@ __device__ __forceinline__ float sqrt_c(float x)
     asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
-__device__ __forceinline__ double div_c(double a, double b) { return a / b; }
-__device__ __forceinline__ float div_c(float a, float b) { return __fdividef(a, b); }
 
 // products that are never fused into a following add: velocities u = m/rho
 // must round before they are differenced, so equal neighbours give an exact 0
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+// rounded operations that the compiler neither fuses nor reorders, for
+// sequences that two kernel forms must evaluate identically
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+// a / b as the sweeps evaluate it: a times the approximate reciprocal in
+// FP32, the correctly rounded quotient in FP64
+__device__ __forceinline__ double quot(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float quot(float a, float b) { return __fmul_rn(a, rcp(b)); }
 
 // NaN-propagating maximum (a NaN wave speed must reach dt)
 __device__ __forceinline__ double nanmax(double a, double b) { return (a > b || a != a) ? a : b; }
@@ -481,10 +489,10 @@ __device__ __forceinline__ void col_u(const Fin<4> &q, const Geom &g, const C *W
         idx pl = (idx)g.plane;
         f = ck(f, g.plane);
         C w = C(1) - W[f];
-        rho = w * rho + J[f];
-        m0 = w * m0 + J[pl + f];
-        m1 = w * m1 + J[2 * pl + f];
-        m2 = w * m2 + J[3 * pl + f];
+        rho = fma_rn(w, rho, J[f]);
+        m0 = fma_rn(w, m0, J[pl + f]);
+        m1 = fma_rn(w, m1, J[2 * pl + f]);
+        m2 = fma_rn(w, m2, J[3 * pl + f]);
     }
     // products rounded before they are differenced: equal neighbours give an exact 0
     C r = rcp(rho);
@@ -493,10 +501,28 @@ __device__ __forceinline__ void col_u(const Fin<4> &q, const Geom &g, const C *W
     u[2] = mul_rn(m2, r);
 }
 
+// b = alpha [tr(G^2) + tr(G)^2] (Eq. igrelliptic) from the undivided central
+// differences D = 2 dx G of u, with alpha_s = alpha / (2 dx)^2:
+//   b = alpha_s [sum_ab D_ab D_ba + (sum_a D_aa)^2],
+// in one fixed order of rounded operations, so that the two forms of the
+// source kernel give the same bits
+__device__ __forceinline__ C source_b(const C (&D)[3][3], C alpha_s)
+{
+    const C tr = add_rn(add_rn(D[0][0], D[1][1]), D[2][2]);
+    C sq = mul_rn(D[0][0], D[0][0]);
+    sq = fma_rn(D[1][1], D[1][1], sq);
+    sq = fma_rn(D[2][2], D[2][2], sq);
+    C x = mul_rn(D[0][1], D[1][0]);
+    x = fma_rn(D[0][2], D[2][0], x);
+    x = fma_rn(D[1][2], D[2][1], x);
+    const C tr2 = fma_rn(C(2), x, sq);  // sum_ab D_ab D_ba
+    return mul_rn(alpha_s, fma_rn(tr, tr, tr2));
+}
+
 // grad u by central differences from a shared plane tile U (x, y) and the
-// column's registers (z); b = alpha [tr(G^2) + tr(G)^2]
-__global__ void __launch_bounds__(BT) k_source(Fin<4> q, S *__restrict__ b, Geom g, C alpha,
-                                                C inv2dx, const C *W, const C *J, int zc)
+// column's registers (z); b from source_b
+__global__ void __launch_bounds__(BT) k_source(Fin<4> q, S *__restrict__ b, Geom g, C alpha_s,
+                                                const C *W, const C *J, int zc)
 {
     __shared__ C U[3][HY][HX];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
@@ -553,17 +579,14 @@ __global__ void __launch_bounds__(BT) k_source(Fin<4> q, S *__restrict__ b, Geom
         }
         __syncthreads();
         if (active) {
-            C G[3][3];  // G[a][c] = d u_a / d x_c
+            C D[3][3];  // D[a][c]: undivided central difference of u_a along c
 #pragma unroll
             for (int a = 0; a < 3; a++) {
-                G[a][0] = (U[a][ty + 1][tx + 2] - U[a][ty + 1][tx]) * inv2dx;
-                G[a][1] = (U[a][ty + 2][tx + 1] - U[a][ty][tx + 1]) * inv2dx;
-                G[a][2] = (up[a] - um[a]) * inv2dx;
+                D[a][0] = U[a][ty + 1][tx + 2] - U[a][ty + 1][tx];
+                D[a][1] = U[a][ty + 2][tx + 1] - U[a][ty][tx + 1];
+                D[a][2] = up[a] - um[a];
             }
-            C tr = G[0][0] + G[1][1] + G[2][2];
-            C tr2 = G[0][0] * G[0][0] + G[1][1] * G[1][1] + G[2][2] * G[2][2] +
-                    C(2) * (G[0][1] * G[1][0] + G[0][2] * G[2][0] + G[1][2] * G[2][1]);
-            stc(CKP(b + (idx)k * pl + (idx)(j * g.nx + i), b, g.n), alpha * (tr2 + tr * tr));
+            stc(CKP(b + (idx)k * pl + (idx)(j * g.nx + i), b, g.n), source_b(D, alpha_s));
         }
 #pragma unroll
         for (int a = 0; a < 3; a++) {
@@ -585,6 +608,25 @@ __global__ void __launch_bounds__(BT) k_source(Fin<4> q, S *__restrict__ b, Geom
 // length), which no thread writes during the launch, so every updated value
 // is the same whatever the order of execution; values read from cells of
 // the updated colour feed only results that are discarded.
+
+// One update of one cell: e[f] the face factor (beta / 2, 0 for a face on a
+// non-periodic boundary), rn[f] the reciprocal density and sn[f] Sigma of
+// the neighbour across face f, faces in the order -x, +x, -y, +y, -z, +z. A
+// fixed order of rounded operations, lane for lane that of the packed form
+// of k_jacobi_v4, so that every form of the sweep gives the same bits.
+__device__ __forceinline__ C jacobi_cell(C r0, const C (&e)[6], const C (&rn)[6], const C (&sn)[6], C bv)
+{
+    C c[6];
+#pragma unroll
+    for (int f = 0; f < 6; f++) c[f] = mul_rn(e[f], add_rn(r0, rn[f]));
+    C diag = r0;
+#pragma unroll
+    for (int f = 0; f < 6; f++) diag = add_rn(diag, c[f]);
+    C off = mul_rn(c[0], sn[0]);
+#pragma unroll
+    for (int f = 1; f < 6; f++) off = fma_rn(c[f], sn[f], off);
+    return quot(add_rn(bv, off), diag);
+}
 
 __global__ void __launch_bounds__(BT) k_jacobi(const S *__restrict__ q, const S *__restrict__ b,
                                                 const S *sin, S *sout, Geom g, C beta, int zc,
@@ -654,17 +696,11 @@ __global__ void __launch_bounds__(BT) k_jacobi(const S *__restrict__ q, const S 
             const C ezm = (k > 0 || g.bc[4] == BC_PERIODIC) ? hb : C(0);
             const C ezp = (k < g.nz - 1 || g.bc[5] == BC_PERIODIC) ? hb : C(0);
             // faces in the order -x, +x, -y, +y, -z, +z
-            C c0 = exm * (r0 + R[ty + 1][tx]);
-            C c1 = exp_ * (r0 + R[ty + 1][tx + 2]);
-            C c2 = eym * (r0 + R[ty][tx + 1]);
-            C c3 = eyp * (r0 + R[ty + 2][tx + 1]);
-            C c4 = ezm * (r0 + rm);
-            C c5 = ezp * (r0 + rp);
-            C diag = r0 + c0 + c1 + c2 + c3 + c4 + c5;
-            C off = c0 * SG[ty + 1][tx] + c1 * SG[ty + 1][tx + 2] + c2 * SG[ty][tx + 1] +
-                    c3 * SG[ty + 2][tx + 1] + c4 * sm + c5 * sp;
+            const C e[6] = {exm, exp_, eym, eyp, ezm, ezp};
+            const C rn[6] = {R[ty + 1][tx], R[ty + 1][tx + 2], R[ty][tx + 1], R[ty + 2][tx + 1], rm, rp};
+            const C sn[6] = {SG[ty + 1][tx], SG[ty + 1][tx + 2], SG[ty][tx + 1], SG[ty + 2][tx + 1], sm, sp};
             if (colour < 0 || ((i + j + k) & 1) == colour)
-                stc(CKP(sout + (idx)k * pl + (idx)(j * g.nx + i), sout, g.n), div_c(bv + off, diag));
+                stc(CKP(sout + (idx)k * pl + (idx)(j * g.nx + i), sout, g.n), jacobi_cell(r0, e, rn, sn, bv));
         }
         rm = r0; sm = s0;
         r0 = rp; s0 = sp;
@@ -970,15 +1006,10 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : sizeof(S) == 4 ? 2 : 
                     C rxp = c < VX - 1 ? r0[c + 1] : R[ty + 1][col + VX];
                     C sxp = c < VX - 1 ? s0[c + 1] : SG[ty + 1][col + VX];
                     // faces in the order -x, +x, -y, +y, -z, +z
-                    C c0 = (c > 0 ? hb : exm) * (r0[c] + rxm);
-                    C c1 = (c < VX - 1 ? hb : exp_) * (r0[c] + rxp);
-                    C c2 = eym * (r0[c] + ry0[c]);
-                    C c3 = eyp * (r0[c] + ry1[c]);
-                    C c4 = ezm * (r0[c] + rm[c]);
-                    C c5 = ezp * (r0[c] + rp[c]);
-                    C diag = r0[c] + c0 + c1 + c2 + c3 + c4 + c5;
-                    C off = c0 * sxm + c1 * sxp + c2 * sy0[c] + c3 * sy1[c] + c4 * sm[c] + c5 * sp[c];
-                    o[c] = div_c(bv[c] + off, diag);
+                    const C e[6] = {c > 0 ? hb : exm, c < VX - 1 ? hb : exp_, eym, eyp, ezm, ezp};
+                    const C rn[6] = {rxm, rxp, ry0[c], ry1[c], rm[c], rp[c]};
+                    const C sn[6] = {sxm, sxp, sy0[c], sy1[c], sm[c], sp[c]};
+                    o[c] = jacobi_cell(r0[c], e, rn, sn, bv[c]);
                     // red-black half-sweep: cells of the other colour keep (and
                     // write back) the value read at the start of the launch
                     if (colour >= 0 && ((i0 + c + j + k) & 1) != colour) o[c] = s0[c];
@@ -1059,7 +1090,7 @@ __global__ void __launch_bounds__(BT) k_source_v4(Fin<4> q, S *__restrict__ b, G
                 idx fc = ck(rowj + (idx)map_axis(i0 + c, g.nx, g.bc[0], g.bc[1]), g.plane);
                 C w = C(1) - W[fc];
 #pragma unroll
-                for (int f = 0; f < 4; f++) v[f][c] = w * v[f][c] + J[(idx)f * pl + fc];
+                for (int f = 0; f < 4; f++) v[f][c] = fma_rn(w, v[f][c], J[(idx)f * pl + fc]);
             }
         }
 #pragma unroll
@@ -1132,10 +1163,7 @@ __global__ void __launch_bounds__(BT) k_source_v4(Fin<4> q, S *__restrict__ b, G
                     D[a][1] = yp[a][c] - ym[a][c];
                     D[a][2] = up[a][c] - um[a][c];
                 }
-                C tr = D[0][0] + D[1][1] + D[2][2];
-                C tr2 = D[0][0] * D[0][0] + D[1][1] * D[1][1] + D[2][2] * D[2][2] +
-                        C(2) * (D[0][1] * D[1][0] + D[0][2] * D[2][0] + D[1][2] * D[2][1]);
-                o[c] = alpha_s * (tr2 + tr * tr);
+                o[c] = source_b(D, alpha_s);
             }
             st4(CKP4(b + (idx)k * pl + (idx)(j * g.nx + i0), b, g.n), o);
         }
@@ -2073,14 +2101,14 @@ template <int N> Fin<N> fields_in(const void *base, long long n)
 cudaError_t launch_source(const Geom &g, const Phys &p, const Tiles &t, const Inflow &in,
                           const void *q, void *b, cudaStream_t st)
 {
-    if (g.nx % VX == 0) {
+    if (t.vec_source && g.nx % VX == 0) {
         k_source_v4<<<grid_of(g, TXV, BY, t.zc_source), dim3(BX, BY), 0, st>>>(
             fields_in<4>(q, g.n), (S *)b, g, C(p.alpha * 0.25 / (p.dx * p.dx)), (const C *)in.W,
             (const C *)in.J, t.zc_source);
         return cudaGetLastError();
     }
     k_source<<<grid_of(g, BX, BY, t.zc_source), dim3(BX, BY), 0, st>>>(
-        fields_in<4>(q, g.n), (S *)b, g, C(p.alpha), C(0.5 / p.dx), (const C *)in.W,
+        fields_in<4>(q, g.n), (S *)b, g, C(p.alpha * 0.25 / (p.dx * p.dx)), (const C *)in.W,
         (const C *)in.J, t.zc_source);
     return cudaGetLastError();
 }
@@ -2088,7 +2116,7 @@ cudaError_t launch_source(const Geom &g, const Phys &p, const Tiles &t, const In
 cudaError_t launch_jacobi(const Geom &g, const Phys &p, const Tiles &t, const void *q,
                           const void *b, const void *s_in, void *s_out, int colour, cudaStream_t st)
 {
-    if (g.nx % VX == 0) {
+    if (t.vec_jacobi && g.nx % VX == 0) {
         k_jacobi_v4<<<grid_of(g, TXV, BY, t.zc_jacobi), dim3(BX, BY), 0, st>>>(
             (const S *)q, (const S *)b, (const S *)s_in, (S *)s_out, g, C(p.alpha / (p.dx * p.dx)),
             t.zc_jacobi, colour);

@@ -90,6 +90,8 @@ def lib():
             "igr_adjoint_step": (i, [p, p, p, p, p, p, p, C.POINTER(d), d, i]),
             "igr_set_tiles": (i, [p, i, i, i]),
             "igr_get_tiles": (i, [p, C.POINTER(i), C.POINTER(i), C.POINTER(i)]),
+            "igr_set_kernel_forms": (i, [p, i, i]),
+            "igr_get_kernel_forms": (i, [p, C.POINTER(i), C.POINTER(i)]),
             "igr_autotune": (i, [p, i]),
             "igr_create_batch": (i, [C.POINTER(Config), i, C.POINTER(Allocator), p, C.POINTER(p)]),
             "igr_batch_instance": (p, [p, i]),
@@ -342,6 +344,16 @@ class Solver:
         a, b, c = C.c_int(), C.c_int(), C.c_int()
         self._check(lib().igr_get_tiles(self.h, C.byref(a), C.byref(b), C.byref(c)))
         return a.value, b.value, c.value
+
+    def set_kernel_forms(self, source_vec4: int = -1, jacobi_vec4: int = -1):
+        """Forms of the source and Jacobi kernels: -1 default rule, 0 one
+        cell per thread, 1 four cells per thread (nx % 4 == 0)."""
+        self._check(lib().igr_set_kernel_forms(self.h, int(source_vec4), int(jacobi_vec4)))
+
+    def kernel_forms(self):
+        a, b = C.c_int(), C.c_int()
+        self._check(lib().igr_get_kernel_forms(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def autotune(self, reps: int = 3):
         self._check(lib().igr_autotune(self.h, int(reps)))

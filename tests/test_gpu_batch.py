@@ -2,10 +2,12 @@
 
 A batch of independent instances (igr_create_batch / igr_step_batch) must
 give, instance by instance, the bits a lone context gives: the kernels are
-the same and nothing is shared between instances. The z-chunk length of
-every kernel class (igr_set_tiles / igr_autotune) must not change a bit
-either: no atomics, and every face flux comes out of the same instructions
-whatever the chunking.
+the same and nothing is shared between instances. The launch shape must not
+change a bit either: the z-chunk length of every kernel class
+(igr_set_tiles / igr_autotune; no atomics, and every face flux comes out of
+the same instructions whatever the chunking) and the one- or four-cell form
+of the source and Jacobi kernels (igr_set_kernel_forms; both evaluate the
+same sequence of rounded operations).
 """
 import numpy as np
 import pytest
@@ -26,13 +28,16 @@ def built():
     yield
 
 
-def _alone(case, q0, precision, steps, tiles=None):
+def _alone(case, q0, precision, steps, tiles=None, forms=None):
     import torch
     from paper_2505_07392_gb300 import igr
     with igr.Solver(case, precision) as s:
         s.set_state(q0)
         if tiles:
             s.set_tiles(*tiles)
+        if forms:
+            s.set_kernel_forms(*forms)
+            assert s.kernel_forms() == forms
         s.step(steps)
         q, sig = s.get_state()
     return q, sig
@@ -82,3 +87,66 @@ def test_results_do_not_depend_on_z_chunks():
         s.step(4)
         q, sig = s.get_state()
     assert torch.equal(q, ref[0])
+
+
+def _jets_case(n=40):
+    dx = 1.0 / n
+    w = 2.0 * np.sqrt(1.4 * 2.0)
+    return Case("jets", n, n - 4, n + 4, dx, alpha=dx * dx, sweeps=5,
+                bc=(OUTFLOW, OUTFLOW, OUTFLOW, OUTFLOW, INFLOW, OUTFLOW),
+                jets=[(0.3, 0.45, 4 * dx, 1.0, w, 2.0, 1.0), (0.7, 0.55, 3 * dx, 1.0, 0.9 * w, 2.0, 1.0)])
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("kind", ["jets", "tgv_rbgs"])
+def test_kernel_forms_give_the_same_bits(precision, kind):
+    """Every combination of the one- and four-cell forms of the source and
+    Jacobi kernels gives the same bits (rows of 40 and 24 cells: the default
+    rule picks the one-cell forms there, the four-cell forms are forced)."""
+    import torch
+    from dataclasses import replace
+    from paper_2505_07392_gb300 import igr
+    if kind == "jets":
+        case = _jets_case()
+        q0 = torch.from_numpy(inputs.jet_initial_state(case))
+    else:
+        case = replace(inputs.tgv(24, instance=3), sigma_solver=1)
+        q0 = torch.from_numpy(inputs.initial_state(case))
+    q0 = q0.to(igr.storage_torch_dtype(precision)).cuda()
+    with igr.Solver(case, precision) as s:
+        assert s.kernel_forms() == (0, 0)
+    ref = _alone(case, q0, precision, 3, forms=(0, 0))
+    for forms in ((1, 1), (1, 0), (0, 1)):
+        q, sig = _alone(case, q0, precision, 3, forms=forms)
+        assert torch.equal(q, ref[0]), forms
+        assert torch.equal(sig, ref[1]), forms
+    assert torch.isfinite(ref[0].double()).all()
+
+
+def test_kernel_form_rule_and_checks():
+    """The default rule (four cells where the busy-lane share is at least the
+    instruction ratio) and the argument checks of igr_set_kernel_forms."""
+    from paper_2505_07392_gb300 import igr
+    expect = {48: (0, 0), 64: (0, 0), 80: (1, 0), 96: (1, 0), 128: (1, 1), 130: (0, 0), 256: (1, 1),
+              1024: (1, 1)}
+    for nx, forms in expect.items():
+        c = Case("box", nx, 8, 8, 1.0 / nx, alpha=1.0 / nx ** 2, sweeps=1, bc=(OUTFLOW,) * 6)
+        with igr.Solver(c, "f32") as s:
+            assert s.kernel_forms() == forms, nx
+            if nx % 4 == 0:
+                s.set_kernel_forms(1, 1)
+                assert s.kernel_forms() == (1, 1)
+            else:
+                with pytest.raises(igr.IGRError):
+                    s.set_kernel_forms(1, 1)
+            s.set_kernel_forms(0, 0)
+            assert s.kernel_forms() == (0, 0)
+            s.set_kernel_forms(-1, -1)
+            assert s.kernel_forms() == forms
+    c = Case("odd", 30, 8, 8, 1.0 / 30, alpha=1.0 / 900, sweeps=1, bc=(OUTFLOW,) * 6)
+    with igr.Solver(c, "f32") as s:
+        with pytest.raises(igr.IGRError):
+            s.set_kernel_forms(1, 0)
+        with pytest.raises(igr.IGRError):
+            s.set_kernel_forms(0, 2)
+

@@ -1,6 +1,6 @@
 """The bounds-checking debug build (libigr_debug.so, IGR_DEBUG_BOUNDS): every
 global index the forward kernels form is checked against its array's length.
-Run over odd shapes (both the scalar and the 4-wide kernel forms), boundary
+Run over odd shapes (the one- and four-cell kernel forms), boundary
 kinds, inflow jets, the scheme alternatives, viscous terms, the host RK base,
 batches and the allocation-free solve, no index may fall outside its array;
 the self-test shows that a single out-of-range index is counted (and not
@@ -73,7 +73,8 @@ def test_no_index_out_of_bounds(debug_lib):
     shapes = [((7, 13, 33), (PERIODIC,) * 6), ((33, 7, 13), (OUTFLOW,) * 6),
               ((13, 33, 7), (OUTFLOW, OUTFLOW, PERIODIC, PERIODIC, OUTFLOW, OUTFLOW)),
               ((65, 9, 5), (PERIODIC, PERIODIC, OUTFLOW, OUTFLOW, PERIODIC, PERIODIC)),
-              ((4, 4, 4), (PERIODIC,) * 6), ((36, 12, 8), (OUTFLOW,) * 6)]
+              ((4, 4, 4), (PERIODIC,) * 6), ((36, 12, 8), (OUTFLOW,) * 6),
+              ((132, 5, 6), (PERIODIC, PERIODIC, OUTFLOW, OUTFLOW, OUTFLOW, OUTFLOW))]
     cases = []
     for (nx, ny, nz), bc in shapes:
         dx = 1.0 / max(nx, ny, nz)
@@ -85,15 +86,17 @@ def test_no_index_out_of_bounds(debug_lib):
     for c, prec in cases:
         q0 = inputs.jet_initial_state(c) if c.jets else _state(c, c.nx)
         dt = igr.storage_torch_dtype(prec)
-        with igr.Solver(c, prec) as s:
-            q = torch.from_numpy(q0).to(dt).cuda()
-            s.set_state(q)
-            s.step(2)
-            sig = torch.zeros(s.shape, dtype=dt, device="cuda")
-            s.solve_sigma(q, sig, 2)
-            s.rhs(q, sig)
-            s.diagnose()
-        assert _hits(L) == 0, (c.name, c.nx, c.ny, c.nz, prec)
+        for forms in ((0, 0), (1, 1)) if c.nx % 4 == 0 else ((0, 0),):
+            with igr.Solver(c, prec) as s:
+                s.set_kernel_forms(*forms)
+                q = torch.from_numpy(q0).to(dt).cuda()
+                s.set_state(q)
+                s.step(2)
+                sig = torch.zeros(s.shape, dtype=dt, device="cuda")
+                s.solve_sigma(q, sig, 2)
+                s.rhs(q, sig)
+                s.diagnose()
+            assert _hits(L) == 0, (c.name, c.nx, c.ny, c.nz, prec, forms)
     # RK base in host memory, batches, allocation-free solve
     c = inputs.blast(16, sweeps=2)
     with igr.Solver(c, "f16", host_rk_base=True) as s:
