@@ -152,6 +152,13 @@ igr_status igr_destroy(igr_ctx *ctx);
 igr_status igr_set_state(igr_ctx *ctx, const void *q, const void *sigma, igr_dtype dtype,
                          int on_device);
 
+/* Replace q alone (5 n values; dtype and on_device as for igr_set_state)
+ * and keep Sigma, the warm start of the next elliptic solve. This is the
+ * call for a host-driven loop that reads q out after each step
+ * (igr_get_state with sigma = NULL) and hands it back, possibly changed:
+ * Sigma never leaves the device. The next step recomputes dt from the new q. */
+igr_status igr_set_conserved(igr_ctx *ctx, const void *q, igr_dtype dtype, int on_device);
+
 /* Copy the state out (q: 5 n values, sigma: n values or NULL), same
  * dtype/on_device rules as igr_set_state. Synchronises the stream and
  * reports pending asynchronous errors. */

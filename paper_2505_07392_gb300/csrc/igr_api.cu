@@ -620,6 +620,19 @@ igr_status igr_set_state(igr_ctx *c, const void *q, const void *sigma, igr_dtype
     return IGR_OK;
 }
 
+igr_status igr_set_conserved(igr_ctx *c, const void *q, igr_dtype dtype, int on_device)
+{
+    if (!c || !q) return fail(c, IGR_ERR_INVALID_ARG, "ctx and q are required");
+    if (dtype < IGR_DT_F64 || dtype > IGR_DT_BF16) return fail(c, IGR_ERR_INVALID_ARG, "bad dtype");
+    igr_status s = copy_in(c, q, c->q[0], 5 * c->g.n, dtype, on_device);
+    if (s != IGR_OK) return s;
+    c->speed_nblocks = 0;  // dt from the new q
+    c->warn_flags = 0;
+    CU(c, cudaMemsetAsync(&c->sc->err, 0, sizeof(int), c->st));
+    if (!on_device) CU(c, cudaStreamSynchronize(c->st));
+    return IGR_OK;
+}
+
 igr_status igr_get_state(igr_ctx *c, void *q, void *sigma, igr_dtype dtype, int on_device)
 {
     if (!c || !q) return fail(c, IGR_ERR_INVALID_ARG, "ctx and q are required");

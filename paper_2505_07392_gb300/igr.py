@@ -79,6 +79,7 @@ def lib():
             "igr_destroy": (i, [p]),
             "igr_set_state": (i, [p, p, p, i, i]),
             "igr_get_state": (i, [p, p, p, i, i]),
+            "igr_set_conserved": (i, [p, p, i, i]),
             "igr_step": (i, [p, i, d, C.POINTER(d)]),
             "igr_solve_sigma": (i, [p, p, p, i, i]),
             "igr_rhs": (i, [p, p, p, p, i]),
@@ -243,6 +244,19 @@ class Solver:
                 sp = sigma.ctypes.data_as(C.c_void_p)
             self._check(lib().igr_set_state(self.h, q.ctypes.data_as(C.c_void_p), sp,
                                             _NP_DT[q.dtype], 0))
+
+    def set_conserved(self, q):
+        """Replace q alone and keep Sigma (igr_set_conserved); q as for
+        set_state."""
+        import torch
+        if isinstance(q, torch.Tensor):
+            q = q.contiguous()
+            self._check(lib().igr_set_conserved(self.h, C.c_void_p(q.data_ptr()), _dt_code(q.dtype), 1))
+            if self.stream != torch.cuda.current_stream(self.device):
+                q.record_stream(self.stream)
+        else:
+            q = np.ascontiguousarray(q)
+            self._check(lib().igr_set_conserved(self.h, q.ctypes.data_as(C.c_void_p), _NP_DT[q.dtype], 0))
 
     def get_state(self, dtype=None):
         """(q, sigma) as new CUDA tensors (default: the storage dtype)."""

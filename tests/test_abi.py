@@ -79,3 +79,8 @@ def test_host_only_calls(libigr):
         cb, _ = igr.make_config(bad_case, "f32")
         assert L.igr_create(ctypes.byref(cb), None, None, ctypes.byref(h)) == igr.ERR_INVALID_ARG
         assert word in L.igr_last_error(None)
+    # calls on a NULL context are rejected before any device work
+    i = ctypes.c_int()
+    assert L.igr_set_conserved(None, None, igr.DT_F32, 1) == igr.ERR_INVALID_ARG
+    assert L.igr_set_kernel_forms(None, 0, 0) == igr.ERR_INVALID_ARG
+    assert L.igr_get_kernel_forms(None, ctypes.byref(i), ctypes.byref(i)) == igr.ERR_INVALID_ARG
