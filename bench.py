@@ -44,16 +44,16 @@ FALLBACK_HBM_GBS = 6800.0
 # issue roofline; tied to the kernel source like the traffic.
 NCU_INSTR = {
     # profiles/flux_plume_f16.md
-    "flux_f16": {"warp_instr_per_cell": 22.944, "src": "5c560c20905903c7"},
+    "flux_f16": {"warp_instr_per_cell": 22.944, "src": "d3ef1c4c44b6fbff"},
     # profiles/flux_plume_f32.md
-    "flux_f32": {"warp_instr_per_cell": 20.478, "src": "5c560c20905903c7"},
+    "flux_f32": {"warp_instr_per_cell": 20.478, "src": "d3ef1c4c44b6fbff"},
 }
 
 NCU_TRAFFIC = {
     # profiles/flux_plume_f16.md: mean of the three stage launches, 512 x 512 x 128 plume
-    "flux_f16": {"bytes_per_cell": 29.111, "src": "5c560c20905903c7"},
+    "flux_f16": {"bytes_per_cell": 29.131, "src": "d3ef1c4c44b6fbff"},
     # profiles/flux_plume_f32.md: mean of the three stage launches, 512 x 512 x 128 plume
-    "flux_f32": {"bytes_per_cell": 58.891, "src": "5c560c20905903c7"},
+    "flux_f32": {"bytes_per_cell": 58.898, "src": "d3ef1c4c44b6fbff"},
 }
 
 
