@@ -46,7 +46,7 @@ typedef enum {
     IGR_ERR_CUDA = 3,        /* a CUDA call failed */
     IGR_ERR_NONFINITE = 4,   /* a stage produced a NaN/Inf value or time step */
     IGR_ERR_TIMEOUT = 5,     /* reserved for bounded device-side waits */
-    IGR_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+    IGR_ERR_UNSUPPORTED = 6  /* a valid request that the library does not implement */
 } igr_status;
 
 /* Arithmetic and storage of a context. */

@@ -1033,7 +1033,8 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : sizeof(S) == 4 ? 2 : 
 // taken undivided and 1/(2 dx)^2 is folded into alpha:
 //   b = (alpha / (4 dx^2)) [sum_ab D_ab D_ba + (sum_a D_aa)^2],
 //   D_ab = u_a(i + e_b) - u_a(i - e_b),
-// which is Eq. igrelliptic's left side with G = D / (2 dx).
+// which is Eq. igrelliptic's left side with G = D / (2 dx). k_source takes the
+// same differences and source_b, so both forms give the same bits.
 __global__ void __launch_bounds__(BT) k_source_v4(Fin<4> q, S *__restrict__ b, Geom g, C alpha_s,
                                                    const C *W, const C *J, int zc)
 {
