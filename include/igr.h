@@ -171,6 +171,15 @@ igr_status igr_get_state(igr_ctx *ctx, void *q, void *sigma, igr_dtype dtype, in
  * reports asynchronous errors; with NULL it only enqueues. */
 igr_status igr_step(igr_ctx *ctx, int nsteps, double fixed_dt, double *t_inout);
 
+/* nsteps SSP-RK3 steps from host memory to host memory: q_in (5 n values,
+ * the storage dtype, best pinned) is copied in, Sigma stays on the device
+ * (as with igr_set_conserved), the steps run, and the final q is written to
+ * q_out. The last stage's flux kernel runs in z-slabs and each slab is
+ * copied out while the next ones compute, so most of the read-back
+ * overlaps the last stage. q_in and q_out may be the same buffer. dt
+ * follows the CFL rule. Synchronises and reports asynchronous errors. */
+igr_status igr_step_host(igr_ctx *ctx, const void *q_in, void *q_out, int nsteps, igr_dtype dtype);
+
 /* Sigma solve alone, on caller buffers in the storage dtype (device
  * pointers): b from q, then `sweeps` Jacobi sweeps warm-started from
  * sigma_inout; the result overwrites sigma_inout. Uses the context's b and

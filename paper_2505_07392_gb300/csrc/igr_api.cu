@@ -28,6 +28,9 @@
 
 using namespace igr;
 
+// z-slabs of the last stage whose read-back overlaps the rest of the stage
+constexpr int kOutSlabs = 8;
+
 struct igr_ctx {
     igr_config cfg;
     std::vector<igr_jet> jets;
@@ -55,6 +58,10 @@ struct igr_ctx {
     int warn_flags;     // IGR_WARN_* seen at synchronising calls since the last igr_get_flags
     bool profiling;
     std::vector<cudaEvent_t> ev;  // start/stop pairs of the pending launches
+    // igr_step_host: a stream for the read-back and an event per z-slab of
+    // the last stage (created by its first call)
+    cudaStream_t copy_st;
+    cudaEvent_t slab_ev[kOutSlabs + 1];
     std::vector<int> ev_class;
     long long prof_launches[KC_COUNT];
     double prof_ms[KC_COUNT];
@@ -220,6 +227,7 @@ Tiles igr::default_tiles(const Geom &g)
     t.zc_source = default_zc(g, t.vec_source ? 128 : 32, 8, 3);
     t.zc_jacobi = default_zc(g, t.vec_jacobi ? 128 : 32, 8, 3);
     t.zc_flux = default_zc(g, 32, 15, 1);
+    t.z_begin = t.z_end = 0;
     return t;
 }
 
@@ -374,8 +382,12 @@ static igr_status launch_sweeps(igr_ctx *c, const void *q, const void *b, void *
     return IGR_OK;
 }
 
+// One stage: source, sweeps, flux. With host_out (the last stage of
+// igr_step_host) the flux runs in z-slabs of whole chunks, and each slab's
+// planes of `out` are copied to host_out on copy_st as soon as the slab is
+// done, while the next slabs compute; c->st then waits for the copies.
 static igr_status run_stage(igr_ctx *c, int mode, const void *qs, const void *qn, void *out,
-                            void *base_out = nullptr)
+                            void *base_out = nullptr, void *host_out = nullptr)
 {
     prof_begin(c, KC_SOURCE);
     CU(c, c->ops->source(c->g, c->p, c->tiles, inflow_of(c), qs, c->b, c->st));
@@ -384,10 +396,35 @@ static igr_status run_stage(igr_ctx *c, int mode, const void *qs, const void *qn
     igr_status s = launch_sweeps(c, qs, c->b, c->sig[c->cur], c->sig[1 - c->cur], c->cfg.sweeps, &res);
     if (s != IGR_OK) return s;
     c->cur = res == c->sig[0] ? 0 : 1;
-    prof_begin(c, KC_FLUX);
-    CU(c, c->ops->flux(c->g, c->p, c->tiles, inflow_of(c), mode, qs, c->sig[c->cur], qn, out,
-                       nullptr, base_out, c->sc, c->blockmax, &c->sc->err, c->st));
-    prof_end(c);
+    if (!host_out) {
+        prof_begin(c, KC_FLUX);
+        CU(c, c->ops->flux(c->g, c->p, c->tiles, inflow_of(c), mode, qs, c->sig[c->cur], qn, out,
+                           nullptr, base_out, c->sc, c->blockmax, &c->sc->err, c->st));
+        prof_end(c);
+        return IGR_OK;
+    }
+    const int zc = c->tiles.zc_flux, nchunk = (c->g.nz + zc - 1) / zc;
+    const int per = (nchunk + kOutSlabs - 1) / kOutSlabs;  // chunks per slab
+    const size_t sb = c->ops->storage_bytes, plane = (size_t)c->g.plane;
+    for (int c0 = 0, k = 0; c0 < nchunk; c0 += per, k++) {
+        Tiles t = c->tiles;
+        t.z_begin = c0 * zc;
+        t.z_end = std::min(c->g.nz, (c0 + per) * zc);
+        prof_begin(c, KC_FLUX);
+        CU(c, c->ops->flux(c->g, c->p, t, inflow_of(c), mode, qs, c->sig[c->cur], qn, out, nullptr,
+                           base_out, c->sc, c->blockmax, &c->sc->err, c->st));
+        prof_end(c);
+        CU(c, cudaEventRecord(c->slab_ev[k], c->st));
+        CU(c, cudaStreamWaitEvent(c->copy_st, c->slab_ev[k], 0));
+        const size_t off = (size_t)t.z_begin * plane, len = (size_t)(t.z_end - t.z_begin) * plane;
+        for (int u = 0; u < 5; u++) {
+            const size_t at = ((size_t)u * c->g.n + off) * sb;
+            CU(c, cudaMemcpyAsync((char *)host_out + at, (const char *)out + at, len * sb,
+                                  cudaMemcpyDeviceToHost, c->copy_st));
+        }
+    }
+    CU(c, cudaEventRecord(c->slab_ev[kOutSlabs], c->copy_st));
+    CU(c, cudaStreamWaitEvent(c->st, c->slab_ev[kOutSlabs], 0));
     return IGR_OK;
 }
 
@@ -555,6 +592,11 @@ igr_status igr_destroy(igr_ctx *c)
     for (void *p : c->adj.all)
         if (p) c->alloc.free(p, c->alloc.user);
     if (c->hbase) cudaFreeHost(c->hbase);
+    if (c->copy_st) {
+        cudaStreamSynchronize(c->copy_st);
+        for (cudaEvent_t e : c->slab_ev) cudaEventDestroy(e);
+        cudaStreamDestroy(c->copy_st);
+    }
     delete c;
     return IGR_OK;
 }
@@ -643,6 +685,41 @@ igr_status igr_get_state(igr_ctx *c, void *q, void *sigma, igr_dtype dtype, int 
     return read_flags(c);
 }
 
+}  // extern "C"
+
+// One SSP-RK3 step; with host_out the final state is also copied there,
+// overlapped with the last stage (see run_stage).
+static igr_status one_step(igr_ctx *c, double fixed_dt, void *host_out)
+{
+    if (fixed_dt <= 0.0) {
+        igr_status s = refresh_speed(c);
+        if (s != IGR_OK) return s;
+    }
+    prof_begin(c, KC_OTHER);
+    k_finalize_dt<<<1, 1024, 0, c->st>>>(c->blockmax, c->speed_nblocks, c->sc, c->cfg.cfl * c->cfg.dx,
+                                        fixed_dt);
+    CU(c, cudaGetLastError());
+    prof_end(c);
+    igr_status s;
+    if (c->hbase) {
+        // RK base in host memory: stage 1 copies q^n there while it reads it,
+        // stages 2 and 3 read it back; the two device buffers alternate
+        s = run_stage(c, FLUX_STAGE1, c->q[0], c->q[0], c->q[1], c->hbase_dev);
+        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE2, c->q[1], c->hbase_dev, c->q[0]);
+        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE3, c->q[0], c->hbase_dev, c->q[1], nullptr, host_out);
+        std::swap(c->q[0], c->q[1]);
+    } else {
+        s = run_stage(c, FLUX_STAGE1, c->q[0], c->q[0], c->q[1]);
+        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE2, c->q[1], c->q[0], c->q[2]);
+        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE3, c->q[2], c->q[0], c->q[0], nullptr, host_out);
+    }
+    if (s != IGR_OK) return s;
+    c->speed_nblocks = (int)c->ops->flux_blocks(c->g, c->tiles);
+    return IGR_OK;
+}
+
+extern "C" {
+
 igr_status igr_step(igr_ctx *c, int nsteps, double fixed_dt, double *t_inout)
 {
     if (!c) return fail(c, IGR_ERR_INVALID_ARG, "ctx is NULL");
@@ -654,30 +731,8 @@ igr_status igr_step(igr_ctx *c, int nsteps, double fixed_dt, double *t_inout)
         CU(c, cudaStreamSynchronize(c->st));
     }
     for (int n = 0; n < nsteps; n++) {
-        if (fixed_dt <= 0.0) {
-            igr_status s = refresh_speed(c);
-            if (s != IGR_OK) return s;
-        }
-        prof_begin(c, KC_OTHER);
-        k_finalize_dt<<<1, 1024, 0, c->st>>>(c->blockmax, c->speed_nblocks, c->sc,
-                                            c->cfg.cfl * c->cfg.dx, fixed_dt);
-        CU(c, cudaGetLastError());
-        prof_end(c);
-        igr_status s;
-        if (c->hbase) {
-            // RK base in host memory: stage 1 copies q^n there while it reads it,
-            // stages 2 and 3 read it back; the two device buffers alternate
-            s = run_stage(c, FLUX_STAGE1, c->q[0], c->q[0], c->q[1], c->hbase_dev);
-            if (s == IGR_OK) s = run_stage(c, FLUX_STAGE2, c->q[1], c->hbase_dev, c->q[0]);
-            if (s == IGR_OK) s = run_stage(c, FLUX_STAGE3, c->q[0], c->hbase_dev, c->q[1]);
-            std::swap(c->q[0], c->q[1]);
-        } else {
-            s = run_stage(c, FLUX_STAGE1, c->q[0], c->q[0], c->q[1]);
-            if (s == IGR_OK) s = run_stage(c, FLUX_STAGE2, c->q[1], c->q[0], c->q[2]);
-            if (s == IGR_OK) s = run_stage(c, FLUX_STAGE3, c->q[2], c->q[0], c->q[0]);
-        }
+        igr_status s = one_step(c, fixed_dt, nullptr);
         if (s != IGR_OK) return s;
-        c->speed_nblocks = (int)c->ops->flux_blocks(c->g, c->tiles);
     }
     if (t_inout) {
         double t1 = 0.0;
@@ -687,6 +742,30 @@ igr_status igr_step(igr_ctx *c, int nsteps, double fixed_dt, double *t_inout)
         if (s != IGR_OK) return s;
     }
     return IGR_OK;
+}
+
+igr_status igr_step_host(igr_ctx *c, const void *q_in, void *q_out, int nsteps, igr_dtype dtype)
+{
+    if (!c || !q_in || !q_out) return fail(c, IGR_ERR_INVALID_ARG, "ctx, q_in and q_out are required");
+    if (nsteps < 1) return fail(c, IGR_ERR_INVALID_ARG, "nsteps < 1");
+    if ((int)dtype != storage_dtype(c->cfg.prec))
+        return fail(c, IGR_ERR_UNSUPPORTED, "host buffers must use the storage dtype (%d)",
+                    storage_dtype(c->cfg.prec));
+    if (!c->copy_st) {
+        CU(c, cudaStreamCreateWithFlags(&c->copy_st, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : c->slab_ev) CU(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    // q in; Sigma stays on the device (as with igr_set_conserved)
+    igr_status s = copy_in(c, q_in, c->q[0], 5 * c->g.n, dtype, 0);
+    if (s != IGR_OK) return s;
+    c->speed_nblocks = 0;
+    c->warn_flags = 0;
+    CU(c, cudaMemsetAsync(&c->sc->err, 0, sizeof(int), c->st));
+    for (int n = 0; n < nsteps; n++) {
+        s = one_step(c, 0.0, n == nsteps - 1 ? q_out : nullptr);
+        if (s != IGR_OK) return s;
+    }
+    return read_flags(c);  // synchronises the stream, which waits for the copies
 }
 
 igr_status igr_solve_sigma(igr_ctx *c, const void *q, void *sigma_inout, int sweeps, igr_dtype dtype)

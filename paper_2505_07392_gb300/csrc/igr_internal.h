@@ -55,6 +55,8 @@ struct Tiles {
     int zc_flux;    // z-planes per block of the flux kernel
     int vec_source; // 1: 4 cells per thread (128-cell rows; nx % 4 == 0), 0: one cell per thread
     int vec_jacobi; // the same for the Jacobi kernel
+    int z_begin;    // a flux launch covers planes [z_begin, z_end) only (z_begin a multiple
+    int z_end;      // of zc_flux, z_end a multiple or nz); z_end = 0: all planes
 };
 
 // Default form of the source and Jacobi kernels for rows of nx cells. The

@@ -1375,7 +1375,7 @@ template <int mode, int ORD, bool VISC>
 __global__ void __maxnreg__(FLUX_MAXREG)
     k_flux(Fin<6> in, Fin<5> qn, Fout<5> out, Frhs rhs, Fout<5> base_out, Geom g, C gamma,
            C half_inv_dx, const Scalars *sc, double *blockmax, int *err, const C *W, const C *J,
-           int zc, C mu, C lamv)
+           int zc, int cz0, C mu, C lamv)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *P = reinterpret_cast<C2 *>(smem_raw);        // [RING][3][PH][PW]
@@ -1383,7 +1383,8 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     C *FYb = FXb + 2 * NFX;                           // [2][5][TY+1][TX]
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
+    const int cz = cz0 + blockIdx.z;  // z-chunk (a launch may cover chunks cz0.. only)
+    const int k0 = cz * zc, k1 = min(g.nz, k0 + zc);
     const bool rowwarp = w < TY;  // warp-uniform
     const int i = x0 + lane, j = y0 + (rowwarp ? w : 0);
     const bool active = rowwarp && i < g.nx && j < g.ny;
@@ -1611,7 +1612,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     if (mode == FLUX_STAGE3) {
         double m = block_max<NT>(double(smax));
         if (tid == 0)
-            blockmax[(blockIdx.z * (long long)gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = m;
+            blockmax[(cz * (long long)gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = m;
     }
 }
 
@@ -2152,9 +2153,13 @@ cudaError_t launch_flux(const Geom &g, const Phys &p, const Tiles &t, const Infl
             fb.p[u] = base_out ? (S *)base_out + u * g.n : nullptr;
             fr.p[u] = rhs ? (C *)rhs + u * g.n : nullptr;
         }
-        kern<<<grid_of(g, TX, TY, t.zc_flux), NT, smem, st>>>(
-            fi, fields_in<5>(qn, g.n), fo, fr, fb, g, C(p.gamma), C(0.5 / p.dx), sc, blockmax, err,
-            (const C *)in.W, (const C *)in.J, t.zc_flux, C(p.mu), C(p.zeta - 2.0 * p.mu / 3.0));
+        // the z-chunks of planes [z_begin, z_end) (all chunks when z_end = 0)
+        dim3 gr = grid_of(g, TX, TY, t.zc_flux);
+        const int cz0 = t.z_begin / t.zc_flux;
+        if (t.z_end > 0) gr.z = (t.z_end - t.z_begin + t.zc_flux - 1) / t.zc_flux;
+        kern<<<gr, NT, smem, st>>>(fi, fields_in<5>(qn, g.n), fo, fr, fb, g, C(p.gamma), C(0.5 / p.dx), sc,
+                                   blockmax, err, (const C *)in.W, (const C *)in.J, t.zc_flux, cz0, C(p.mu),
+                                   C(p.zeta - 2.0 * p.mu / 3.0));
         e = cudaGetLastError();
         if (e != cudaSuccess) {
             cudaFuncAttributes fa;

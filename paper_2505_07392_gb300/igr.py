@@ -80,6 +80,7 @@ def lib():
             "igr_set_state": (i, [p, p, p, i, i]),
             "igr_get_state": (i, [p, p, p, i, i]),
             "igr_set_conserved": (i, [p, p, i, i]),
+            "igr_step_host": (i, [p, p, p, i, i]),
             "igr_step": (i, [p, i, d, C.POINTER(d)]),
             "igr_solve_sigma": (i, [p, p, p, i, i]),
             "igr_rhs": (i, [p, p, p, p, i]),
@@ -257,6 +258,16 @@ class Solver:
         else:
             q = np.ascontiguousarray(q)
             self._check(lib().igr_set_conserved(self.h, q.ctypes.data_as(C.c_void_p), _NP_DT[q.dtype], 0))
+
+    def step_host(self, q_in: np.ndarray, q_out: Optional[np.ndarray] = None, nsteps: int = 1):
+        """igr_step_host: q_in (host, storage dtype) in, nsteps steps, the
+        final q into q_out (default: q_in, in place). Sigma stays on the device."""
+        q_in = np.ascontiguousarray(q_in)
+        q_out = q_in if q_out is None else q_out
+        assert q_out.flags.c_contiguous and q_out.dtype == q_in.dtype and q_out.shape == q_in.shape
+        self._check(lib().igr_step_host(self.h, q_in.ctypes.data_as(C.c_void_p), q_out.ctypes.data_as(C.c_void_p),
+                                        int(nsteps), _NP_DT[q_in.dtype]))
+        return q_out
 
     def get_state(self, dtype=None):
         """(q, sigma) as new CUDA tensors (default: the storage dtype)."""

@@ -82,5 +82,6 @@ def test_host_only_calls(libigr):
     # calls on a NULL context are rejected before any device work
     i = ctypes.c_int()
     assert L.igr_set_conserved(None, None, igr.DT_F32, 1) == igr.ERR_INVALID_ARG
+    assert L.igr_step_host(None, None, None, 1, igr.DT_F32) == igr.ERR_INVALID_ARG
     assert L.igr_set_kernel_forms(None, 0, 0) == igr.ERR_INVALID_ARG
     assert L.igr_get_kernel_forms(None, ctypes.byref(i), ctypes.byref(i)) == igr.ERR_INVALID_ARG

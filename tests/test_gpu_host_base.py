@@ -99,3 +99,41 @@ def test_set_conserved_round_trip_is_bitwise(precision, host_rk_base):
         qb, sb = s.get_state()
     assert torch.equal(qa, qb)
     assert torch.equal(sa, sb)
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+@pytest.mark.parametrize("host_rk_base", [False, True])
+def test_step_host_equals_separate_calls(precision, host_rk_base):
+    """igr_step_host (q in from host memory, steps, q out with the read-back
+    overlapped with the last stage's z-slabs) gives the bits of
+    igr_set_conserved + igr_step + igr_get_state, with several slabs (short
+    z-chunks), in place or into another buffer, for one or several steps."""
+    import torch
+    from paper_2505_07392_gb300 import igr
+    c = _jets()
+    npdt = {"f32": np.float32, "f16": np.float16}[precision]
+    q0 = inputs.jet_initial_state(c).astype(npdt)
+    with igr.Solver(c, precision, host_rk_base=host_rk_base) as s:
+        s.set_tiles(4, 4, 4)  # nz = 32: eight flux chunks, so several slabs
+        s.set_state(torch.from_numpy(q0).cuda())
+        s.step(1)
+        ref = []
+        for n in (1, 3):
+            s.step(n)
+            qh = np.empty((5,) + s.shape, dtype=npdt)
+            s.get_state_host(qh)
+            ref.append(qh)
+        _, sig_ref = s.get_state()
+    with igr.Solver(c, precision, host_rk_base=host_rk_base) as s:
+        s.set_tiles(4, 4, 4)
+        s.set_state(torch.from_numpy(q0).cuda())
+        s.step(1)
+        qh = np.empty((5,) + s.shape, dtype=npdt)
+        s.get_state_host(qh)
+        s.step_host(qh)  # in place
+        assert np.array_equal(qh.view(np.uint8), ref[0].view(np.uint8))
+        out = np.empty_like(qh)
+        s.step_host(qh, out, nsteps=3)
+        assert np.array_equal(out.view(np.uint8), ref[1].view(np.uint8))
+        _, sig = s.get_state()
+    assert torch.equal(sig, sig_ref)
