@@ -226,6 +226,36 @@ def test_nonfinite_flag():
         assert s.flags() == 0
 
 
+@pytest.mark.parametrize("precision", ["f64", "f16"])
+def test_checkpoint_resume_bitwise(precision):
+    """Checkpoint/resume: the state (q and Sigma, the warm start) read out
+    after 3 steps, through host memory, into a new context, which steps 3
+    more, gives the bits of 6 uninterrupted steps, and the same time."""
+    import torch
+    from paper_2505_07392_gb300 import igr
+    c = small_jet_case()
+    dt = igr.storage_torch_dtype(precision)
+    npdt = {"f64": np.float64, "f16": np.float16}[precision]
+    q0 = torch.from_numpy(inputs.jet_initial_state(c)).to(dt).cuda()
+    with igr.Solver(c, precision) as s:
+        s.set_state(q0)
+        t_ref = s.step(6)
+        q_ref, sig_ref = s.get_state()
+    with igr.Solver(c, precision) as s:
+        s.set_state(q0)
+        t_a = s.step(3)
+        qh = np.empty((5,) + s.shape, dtype=npdt)
+        sh = np.empty(s.shape, dtype=npdt)
+        s.get_state_host(qh, sh)
+    with igr.Solver(c, precision) as s:
+        s.set_state(qh, sh)
+        t_b = s.step(3)
+        q, sig = s.get_state()
+    assert torch.equal(q, q_ref)
+    assert torch.equal(sig, sig_ref)
+    assert t_a + t_b == pytest.approx(t_ref, rel=1e-12)
+
+
 # ------------------------------------------------- full-size sampled parity
 
 def _patch_case(full, i0, i1, j0, j1, k0, k1):
