@@ -351,7 +351,7 @@ igr_status igr_autotune(igr_ctx *ctx, int reps);
  * igr_create_batch creates one context per config, each on its own stream
  * forked from and joined into cuda_stream. igr_batch_instance(b, i) gives
  * instance i's context for igr_set_state / igr_get_state / igr_autotune /
- * igr_get_dt (not for igr_step: step the batch). igr_step_batch advances
+ * igr_get_dt (not for igr_step or igr_step_host: step the batch). igr_step_batch advances
  * every instance by nsteps SSP-RK3 steps, each with its own CFL dt; a step
  * is captured once as a CUDA graph (one branch per instance, so instances
  * progress independently) and replayed, except the first step after a
