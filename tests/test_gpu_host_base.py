@@ -137,3 +137,33 @@ def test_step_host_equals_separate_calls(precision, host_rk_base):
         assert np.array_equal(out.view(np.uint8), ref[1].view(np.uint8))
         _, sig = s.get_state()
     assert torch.equal(sig, sig_ref)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "f16"])
+def test_step_host_ragged_slabs(precision):
+    """igr_step_host with nz not a multiple of the chunk (29 planes in chunks
+    of 4: eight chunks, the last one short, in eight slabs), through raw
+    pinned host tensors (BF16 has no numpy type), against separate calls."""
+    import ctypes
+    import torch
+    from dataclasses import replace
+    from paper_2505_07392_gb300 import igr
+    c = replace(_jets(), nz=29)
+    dt = igr.storage_torch_dtype(precision)
+    code = {"bf16": igr.DT_BF16, "f16": igr.DT_F16}[precision]
+    q0 = torch.from_numpy(inputs.jet_initial_state(c)).to(dt)
+    L = igr.lib()
+    with igr.Solver(c, precision) as s:
+        s.set_tiles(4, 4, 4)
+        s.set_state(q0.cuda())
+        s.step(2)
+        ref, _ = s.get_state()
+    with igr.Solver(c, precision) as s:
+        s.set_tiles(4, 4, 4)
+        s.set_state(q0.cuda())
+        s.step(1)
+        h = torch.empty((5,) + s.shape, dtype=dt, pin_memory=True)
+        assert L.igr_get_state(s.h, ctypes.c_void_p(h.data_ptr()), None, code, 0) == igr.OK
+        assert L.igr_step_host(s.h, ctypes.c_void_p(h.data_ptr()), ctypes.c_void_p(h.data_ptr()), 1,
+                               code) == igr.OK
+    assert torch.equal(h.cuda(), ref)
