@@ -85,3 +85,23 @@ def test_host_only_calls(libigr):
     assert L.igr_step_host(None, None, None, 1, igr.DT_F32) == igr.ERR_INVALID_ARG
     assert L.igr_set_kernel_forms(None, 0, 0) == igr.ERR_INVALID_ARG
     assert L.igr_get_kernel_forms(None, ctypes.byref(i), ctypes.byref(i)) == igr.ERR_INVALID_ARG
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """With no CUDA library at the configured path the binding raises at its
+    first call: there is no CPU fallback."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2505_07392_gb300 import igr, inputs\n"
+            "try:\n"
+            "    igr.memory_bytes(inputs.density_wave(8))\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n"
+            "    sys.exit(0)\n"
+            "sys.exit(1)\n") % root
+    env = dict(os.environ, IGR_LIBRARY=str(tmp_path / "absent" / "libigr.so"))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "is missing" in r.stdout
