@@ -160,6 +160,37 @@ def _dt_code(t):
 _NP_DT = {np.dtype(np.float64): DT_F64, np.dtype(np.float32): DT_F32, np.dtype(np.float16): DT_F16}
 
 
+def autotune_key(case, precision: str, host_rk_base: bool, device_name: str) -> str:
+    """What a tuned launch shape depends on: grid shape, storage precision,
+    scheme variant, RK base placement and GPU model."""
+    visc = float(getattr(case, "mu", 0.0)) > 0 or float(getattr(case, "zeta", 0.0)) > 0
+    return "%dx%dx%d:%s:order%d:solver%d:visc%d:hostbase%d:%s" % (
+        case.nx, case.ny, case.nz, precision, int(getattr(case, "order", 5)),
+        int(getattr(case, "sigma_solver", 0)), int(visc), int(bool(host_rk_base)), device_name)
+
+
+def autotune_cache_load(path: str) -> dict:
+    """The stored launch shapes ({} when the file is missing or unreadable)."""
+    import json
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def autotune_cache_store(path: str, key: str, value: dict) -> None:
+    """Add one entry, written to a temporary file and renamed into place."""
+    import json
+    d = autotune_cache_load(path)
+    d[key] = value
+    tmp = "%s.tmp%d" % (path, os.getpid())
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 class Solver:
     """One IGR context on the current CUDA device and PyTorch's current stream."""
 
@@ -380,8 +411,24 @@ class Solver:
         self._check(lib().igr_get_kernel_forms(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
 
-    def autotune(self, reps: int = 3):
+    def autotune(self, reps: int = 3, cache: Optional[str] = None):
+        """igr_autotune, or the launch shape stored for the same problem and
+        GPU in the JSON file `cache` (default: $IGR_AUTOTUNE_CACHE; none when
+        unset). A tuned shape is stored there for the next context."""
+        path = cache if cache is not None else os.environ.get("IGR_AUTOTUNE_CACHE")
+        key = None
+        if path:
+            import torch
+            key = autotune_key(self.case, self.precision, getattr(self, "host_rk_base", False),
+                               torch.cuda.get_device_name(self.device))
+            hit = autotune_cache_load(path).get(key)
+            if hit:
+                self.set_tiles(*hit["tiles"])
+                self.set_kernel_forms(*hit["forms"])
+                return self.tiles()
         self._check(lib().igr_autotune(self.h, int(reps)))
+        if key:
+            autotune_cache_store(path, key, {"tiles": list(self.tiles()), "forms": list(self.kernel_forms())})
         return self.tiles()
 
     # -- per-kernel timing

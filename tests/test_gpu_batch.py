@@ -150,3 +150,31 @@ def test_kernel_form_rule_and_checks():
         with pytest.raises(igr.IGRError):
             s.set_kernel_forms(0, 2)
 
+
+
+def test_autotune_cache(tmp_path, monkeypatch):
+    """A tuned launch shape is stored under its problem and GPU; a second
+    context for the same problem takes it from the file; another precision
+    is tuned and stored apart."""
+    import torch
+    from paper_2505_07392_gb300 import igr
+    path = str(tmp_path / "tiles.json")
+    monkeypatch.setenv("IGR_AUTOTUNE_CACHE", path)
+    c = inputs.tgv(32)
+    q0 = torch.from_numpy(inputs.initial_state(c))
+    with igr.Solver(c, "f16") as s:
+        s.set_state(q0.half().cuda())
+        tiles = s.autotune(reps=2)
+        forms = s.kernel_forms()
+    stored = igr.autotune_cache_load(path)
+    assert len(stored) == 1
+    (entry,) = stored.values()
+    assert entry == {"tiles": list(tiles), "forms": list(forms)}
+    with igr.Solver(c, "f16") as s:
+        s.set_state(q0.half().cuda())
+        s.set_tiles(5, 5, 5)
+        assert s.autotune(reps=2) == tiles and s.kernel_forms() == forms
+    with igr.Solver(c, "f32") as s:
+        s.set_state(q0.float().cuda())
+        s.autotune(reps=2)
+    assert len(igr.autotune_cache_load(path)) == 2
