@@ -27,8 +27,8 @@
  *    the call returns.
  *  - A context is not thread-safe; distinct contexts are independent.
  *  - Asynchronous faults (CUDA errors, non-finite results) surface at the
- *    next call that synchronises: igr_get_state, igr_sync, or igr_step with
- *    a non-NULL t_inout.
+ *    next call that synchronises: igr_get_state, igr_sync, igr_step_host,
+ *    or igr_step with a non-NULL t_inout.
  */
 #ifndef IGR_H
 #define IGR_H
