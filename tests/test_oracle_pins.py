@@ -107,6 +107,21 @@ def test_source_for_linear_velocity():
     assert not np.isclose(expect, c.alpha * (np.sum(Gm * Gm) + np.trace(Gm) ** 2))
 
 
+def test_source_for_quadratic_velocity():
+    """Quadratic u: the central difference (u(x+h) - u(x-h)) / (2h) is still
+    exact at the cell centre, while a one-sided difference would be off by
+    O(h), which the linear field above cannot reveal. With
+    u = (x^2, x y, z^2 / 2) (rho = 1) the gradient at a centre is
+    G = [[2x, 0, 0], [y, x, 0], [0, 0, z]], so
+    b = alpha [4x^2 + x^2 + z^2 + (3x + z)^2]."""
+    c = box(9, (OUTFLOW,) * 6, alpha_scale=0.4)
+    z, y, x = centres(c)
+    q = cons(1 + 0 * x, x * x, x * y, 0.5 * z * z, 5 + 0 * x)
+    b = oracle.source(c, q)
+    expect = c.alpha * (4 * x * x + x * x + z * z + (3 * x + z) ** 2)
+    assert np.allclose(b[1:-1, 1:-1, 1:-1], expect[1:-1, 1:-1, 1:-1], rtol=1e-11, atol=1e-14)
+
+
 # ------------------------------------------------------- elliptic solve
 
 @pytest.mark.parametrize("alpha_scale", [1.0, 0.3])
