@@ -298,13 +298,16 @@ def test_third_order_faces_exact_for_quadratic_only(axis):
     assert out[1] > 1e-6, out
 
 
-def test_red_black_gauss_seidel_closed_form():
+@pytest.mark.parametrize("alpha_scale", [1.0, 0.3])
+def test_red_black_gauss_seidel_closed_form(alpha_scale):
     """Red-black Gauss-Seidel (Sec. "Discretization": Jacobi or Gauss-Seidel)
     on a periodic box of even size with rho = 1, b = 0, Sigma = 1: every red
     update multiplies the (uniform) black values by l = 6 beta / (1 + 6 beta)
     and every black update the red ones, so after n sweeps red cells hold
-    l^(2n-1) and black cells l^(2n) (Jacobi gives l^n everywhere)."""
-    c = box(8, (PERIODIC,) * 6, nx=8, ny=6, nz=4)
+    l^(2n-1) and black cells l^(2n) (Jacobi gives l^n everywhere). beta =
+    alpha / dx^2 other than 1 as well, where a beta dropped from the
+    diagonal would show."""
+    c = box(8, (PERIODIC,) * 6, nx=8, ny=6, nz=4, alpha_scale=alpha_scale)
     c = replace(c, sigma_solver=1)
     beta = c.alpha / c.dx ** 2
     lam = 6 * beta / (1 + 6 * beta)
@@ -320,11 +323,12 @@ def test_red_black_gauss_seidel_closed_form():
     assert np.allclose(sj, lam ** 3, rtol=1e-14, atol=0)
 
 
+@pytest.mark.parametrize("alpha_scale", [1.0, 0.3])
 @pytest.mark.parametrize("bc", [(OUTFLOW,) * 6, (PERIODIC,) * 4 + (OUTFLOW,) * 2])
-def test_red_black_gauss_seidel_converges_to_direct_solve(bc):
+def test_red_black_gauss_seidel_converges_to_direct_solve(bc, alpha_scale):
     """Red-black sweeps reach the dense direct solve of A Sigma = b (A
     assembled from the oracle's operator), and faster than Jacobi."""
-    c = box(6, bc, nx=6, ny=4, nz=6)
+    c = box(6, bc, nx=6, ny=4, nz=6, alpha_scale=alpha_scale)
     rng = np.random.Generator(np.random.Philox(5))
     shape = (c.nz, c.ny, c.nx)
     rho = 1 + 0.3 * rng.uniform(-1, 1, shape)
