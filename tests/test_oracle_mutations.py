@@ -87,6 +87,14 @@ MUTATIONS = {
         "static const double cl[6] = {2.0 / 60, -13.0 / 60, 46.0 / 60,", 1),
     "adjoint: stage-2 weight": (
         "const double wst[3] = {1.0, 0.25, 2.0 / 3.0};", "const double wst[3] = {1.0, 0.3, 2.0 / 3.0};", 1),
+    "adjoint: Jacobi mu without the diagonal": (
+        "mu[c] = sb[c] / diag;", "mu[c] = sb[c];", 1),
+    "adjoint: Jacobi density term sign": (
+        "rhob[c] -= rb[c] / (rho[c] * rho[c]);", "rhob[c] += rb[c] / (rho[c] * rho[c]);", 1),
+    "adjoint: pressure work into the energy": (
+        "    Eb += Fb[4] * u[d];\n    Pb += Fb[4] * u[d];", "    Eb += Fb[4] * u[d];\n    Pb += 0.0 * Fb[4] * u[d];", 1),
+    "adjoint: sound-speed derivative in p": (
+        "pb += ab * gm / (2.0 * c * rho);", "pb += ab * gm / (c * rho);", 1),
 }
 
 RUNNER = r'''
