@@ -73,6 +73,9 @@ MUTATIONS = {
         "return (-v[1] + 5.0 * v[2] + 2.0 * v[3]) / 6.0;", "return (-v[1] + 4.0 * v[2] + 3.0 * v[3]) / 6.0;", 1),
     "jet energy without the kinetic term": (
         "qj[4] = p / (g->gamma - 1.0) + 0.5 * rho * w * w;", "qj[4] = p / (g->gamma - 1.0);", 1),
+    "inflow corner ghost blended at its own (unmapped) column": (
+        "double x = (mi + 0.5) * g->dx, y = (mj + 0.5) * g->dx;",
+        "double x = (i + 0.5) * g->dx, y = (j + 0.5) * g->dx;", 1),
     "Sigma ghosts blended with the jet state": (
         "    fill_axis_z(g, sg, -1);\n}", "    fill_axis_z(g, sg, 0);\n}", 1),
     "periodic z-ghost wrapped one cell too far": (

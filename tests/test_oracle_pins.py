@@ -480,6 +480,49 @@ def test_inflow_ghost_blend():
     assert np.array_equal(qg[:, G:-G, G:-G, 0], q[:, :, :, 0])
 
 
+@pytest.mark.parametrize("xbc", ["outflow", "periodic"])
+def test_inflow_corner_ghost_blend(xbc):
+    """Inflow ghosts below the -z face whose column lies outside the face's
+    x/y extent (the corner blocks the viscous tangential stencils read). The
+    reading: such a ghost is the blend of the face cell its column maps to
+    (clamp on an outflow axis, wrap on a periodic one), taken with that face
+    cell's own weight s, i.e. ghost(i, j) = ghost(map(i), map(j)).
+    Jet centred on cell (1, 5) with R = 2 dx and one-cell edges, so the
+    weights are hand-computable: the clamped column i = -1..-3 maps to cell 0,
+    at r = dx, r - R = -dx, s = (1 - tanh(-1))/2; the wrapped column i = -2
+    of a 12-cell periodic axis maps to cell 10, at r = 9 dx, s = (1 - tanh(7))/2.
+    Blending with the unmapped ghost coordinate (x = -1.5 dx: r = 3 dx,
+    s = (1 - tanh(1))/2) fails both."""
+    n = 12
+    dx = 1.0 / n
+    jet = (1.5 * dx, 5.5 * dx, 2.0 * dx, 0.8, 3.0, 2.0, 1.0)
+    xb = OUTFLOW if xbc == "outflow" else PERIODIC
+    c = Case("pin", n, n, 6, dx, alpha=dx * dx, bc=(xb, xb, OUTFLOW, OUTFLOW, INFLOW, OUTFLOW), jets=[jet])
+    shape = (c.nz, c.ny, c.nx)
+    rng = np.random.Generator(np.random.Philox(6))
+    rho = rng.uniform(0.9, 1.1, size=shape)
+    q = cons(rho, 0.1 + 0 * rho, -0.05 + 0 * rho, 0.2 + 0 * rho, rng.uniform(0.9, 1.1, size=shape))
+    qg = oracle.fill_ghosts(c, q)
+    qj = np.array([0.8, 0.0, 0.0, 0.8 * 3.0, 2.0 / 0.4 + 0.5 * 0.8 * 9.0])
+    G = 3
+    at = lambda layer, i, j: qg[:, layer, j + G, i + G]
+    blend = lambda s, face: (1 - s) * face + s * qj
+    for layer in (0, 1, 2):
+        if xbc == "outflow":
+            s = 0.5 * (1 - math.tanh(-1.0))  # face cell (0, 5): r - R = -dx
+            for i in (-1, -2, -3):
+                assert np.allclose(at(layer, i, 5), blend(s, q[:, 0, 5, 0]), rtol=1e-14, atol=0)
+            # corner column (-1, -1) -> face cell (0, 0): r = sqrt(26) dx
+            s00 = 0.5 * (1 - math.tanh(math.sqrt(26.0) - 2.0))
+            assert np.allclose(at(layer, -1, -1), blend(s00, q[:, 0, 0, 0]), rtol=1e-14, atol=0)
+        else:
+            s = 0.5 * (1 - math.tanh(7.0))  # face cell (10, 5): r = 9 dx
+            assert np.allclose(at(layer, -2, 5), blend(s, q[:, 0, 5, 10]), rtol=1e-14, atol=0)
+            # the +x ghost column 12 wraps to cell 0: r - R = -dx
+            s0 = 0.5 * (1 - math.tanh(-1.0))
+            assert np.allclose(at(layer, 12, 5), blend(s0, q[:, 0, 5, 0]), rtol=1e-14, atol=0)
+
+
 # ---------------------------------------------------- convergence and symmetry
 
 @pytest.mark.slow
