@@ -43,17 +43,15 @@ FALLBACK_HBM_GBS = 6800.0
 # Warp instructions per cell of the dominant kernel (ncu smsp__inst_executed.sum
 # over the cells of one launch, mean of the three stage launches), for the
 # issue roofline; tied to the kernel source like the traffic.
+# Both from ncu captures of the flux kernel on the 512 x 512 x 128 plume,
+# mean of the three stage launches of one step.
 NCU_INSTR = {
-    # profiles/flux_plume_f16.md
     "flux_f16": {"warp_instr_per_cell": 22.945, "src": "8eb9327fb53b00ea"},
-    # profiles/flux_plume_f32.md
     "flux_f32": {"warp_instr_per_cell": 20.479, "src": "8eb9327fb53b00ea"},
 }
 
 NCU_TRAFFIC = {
-    # profiles/flux_plume_f16.md: mean of the three stage launches, 512 x 512 x 128 plume
     "flux_f16": {"bytes_per_cell": 29.105, "src": "8eb9327fb53b00ea"},
-    # profiles/flux_plume_f32.md: mean of the three stage launches, 512 x 512 x 128 plume
     "flux_f32": {"bytes_per_cell": 58.879, "src": "8eb9327fb53b00ea"},
 }
 
@@ -318,11 +316,12 @@ def roofline_of(case, res, precision, peak, peak_kind):
             "peak_kind": f"of {peak_kind}"}, per
 
 
-def issue_roofline(case, res, precision, clocks):
+def issue_roofline(case, res, precision, clocks, sms):
     """The flux kernel against its issue limit: ncu-counted warp instructions
     per cell x cells per launch x launches / CUDA-event time, over the peak of
-    152 SMs x 4 schedulers x 1 warp instruction per clock at the sampled SM
-    clock. None when no count matches the current kernel source."""
+    `sms` SMs (the device's count) x 4 schedulers x 1 warp instruction per
+    clock at the sampled SM clock. None when no count matches the current
+    kernel source."""
     t = NCU_INSTR.get(f"flux_{precision}")
     if not t or t.get("src") != kernel_source_hash() or not clocks:
         return None
@@ -330,10 +329,10 @@ def issue_roofline(case, res, precision, clocks):
     if n == 0 or ms <= 0:
         return None
     achieved = t["warp_instr_per_cell"] * case.ncells * n / (ms * 1e-3)
-    peak = 152 * 4 * clocks["sm_mhz"] * 1e6
+    peak = sms * 4 * clocks["sm_mhz"] * 1e6
     return {"bound": "issue", "kernel": "flux", "achieved": achieved, "peak": peak,
             "unit": "warp-instr/s", "frac": round(achieved / peak, 4),
-            "peak_kind": "152 SMs x 4 schedulers x 1 warp instr/clock at the sampled SM clock"}
+            "peak_kind": f"{sms} SMs x 4 schedulers x 1 warp instr/clock at the sampled SM clock"}
 
 
 # ------------------------------------------------------------ batched arm
@@ -577,7 +576,8 @@ def main():
         "clocks": res["clocks"],
         "diagnostics_fp64": res["diag"],
     }
-    ri = issue_roofline(full, res, args.precision, res["clocks"])
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    ri = issue_roofline(full, res, args.precision, res["clocks"], sms)
     if ri:
         line["roofline_issue"] = ri
     # energy from the median sampled power, when the timed region is long

@@ -25,6 +25,14 @@
  *    the context's stream; the caller keeps the memory alive until that
  *    stream has passed the call. Host pointers are read or written before
  *    the call returns.
+ *  - Alignment: a device pointer must be aligned to its element size (2, 4
+ *    or 8 bytes), else the call returns IGR_ERR_INVALID_ARG before any
+ *    launch. Where a call could take the 4-cell kernel forms (igr_solve_sigma,
+ *    igr_solve_sigma_noalloc), pointers that are element-aligned but not
+ *    aligned to 4 elements (8 bytes at 16-bit storage, 16 bytes for FP32 and
+ *    FP64; a sliced tensor can start anywhere) make that call take the
+ *    1-cell forms, which give the same bits. Buffers from cudaMalloc or a
+ *    caching allocator are 256-byte aligned.
  *  - A context is not thread-safe; distinct contexts are independent.
  *  - Asynchronous faults (CUDA errors, non-finite results) surface at the
  *    next call that synchronises: igr_get_state, igr_sync, igr_step_host,
@@ -246,7 +254,8 @@ igr_status igr_rk_combine(igr_ctx *ctx, const void *qn, const void *qs, const vo
  *    allocating library routine.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture. The address is kept for later calls, so a
+ *    cudaDeviceReset between calls is not supported.
  *  - All calls on a device share the one array, which keeps the last call's
  *    contents (every value is written before it is read, so nothing needs
  *    clearing). Calls whose work overlaps on the GPU (concurrent streams or
@@ -257,7 +266,8 @@ igr_status igr_solve_sigma_noalloc(const igr_config *cfg, const void *q, void *s
                                    int sweeps, void *cuda_stream);
 /* Largest grid (cells) igr_solve_sigma_noalloc takes in precision prec. */
 size_t igr_noalloc_max_cells(igr_precision prec);
-/* Message of the last failed igr_solve_sigma_noalloc call. Never NULL. */
+/* Message of the calling thread's last failed igr_solve_sigma_noalloc call
+ * (one buffer per thread). Never NULL. */
 const char *igr_noalloc_last_error(void);
 
 /* Time step dt = cfl dx / max_d(|u_d| + c) of the current state.

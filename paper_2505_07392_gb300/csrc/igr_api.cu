@@ -364,14 +364,14 @@ static Inflow inflow_of(igr_ctx *c)
 // `sweeps` sweeps warm-started from s_first: Jacobi ping-pongs between
 // s_first and s_other; red-black Gauss-Seidel updates s_first in place (two
 // half-sweeps each). *result is the buffer holding the solution.
-static igr_status launch_sweeps(igr_ctx *c, const void *q, const void *b, void *s_first,
-                                void *s_other, int sweeps, void **result)
+static igr_status launch_sweeps(igr_ctx *c, const Tiles &t, const void *q, const void *b,
+                                void *s_first, void *s_other, int sweeps, void **result)
 {
     if (c->cfg.sigma_solver == SOLVER_RBGS) {
         for (int it = 0; it < sweeps; it++)
             for (int colour = 0; colour < 2; colour++) {
                 prof_begin(c, KC_JACOBI);
-                CU(c, c->ops->jacobi(c->g, c->p, c->tiles, q, b, s_first, s_first, colour, c->st));
+                CU(c, c->ops->jacobi(c->g, c->p, t, q, b, s_first, s_first, colour, c->st));
                 prof_end(c);
             }
         *result = s_first;
@@ -380,7 +380,7 @@ static igr_status launch_sweeps(igr_ctx *c, const void *q, const void *b, void *
     void *src = s_first, *dst = s_other;
     for (int it = 0; it < sweeps; it++) {
         prof_begin(c, KC_JACOBI);
-        CU(c, c->ops->jacobi(c->g, c->p, c->tiles, q, b, src, dst, -1, c->st));
+        CU(c, c->ops->jacobi(c->g, c->p, t, q, b, src, dst, -1, c->st));
         prof_end(c);
         void *t = src;
         src = dst;
@@ -401,7 +401,7 @@ static igr_status run_stage(igr_ctx *c, int mode, const void *qs, const void *qn
     CU(c, c->ops->source(c->g, c->p, c->tiles, inflow_of(c), qs, c->b, c->st));
     prof_end(c);
     void *res;
-    igr_status s = launch_sweeps(c, qs, c->b, c->sig[c->cur], c->sig[1 - c->cur], c->cfg.sweeps, &res);
+    igr_status s = launch_sweeps(c, c->tiles, qs, c->b, c->sig[c->cur], c->sig[1 - c->cur], c->cfg.sweeps, &res);
     if (s != IGR_OK) return s;
     c->cur = res == c->sig[0] ? 0 : 1;
     if (!host_out) {
@@ -614,6 +614,8 @@ static igr_status copy_in(igr_ctx *c, const void *src, void *dst, long long coun
 {
     int sdt = storage_dtype(c->cfg.prec);
     size_t sb = dtype_bytes(sdt);
+    if (on_device && !is_aligned(src, dtype_bytes(dt)))
+        return fail(c, IGR_ERR_INVALID_ARG, "device buffer not aligned to its element size");
     if (!on_device) {
         if ((int)dt != sdt)
             return fail(c, IGR_ERR_UNSUPPORTED, "host buffers must use the storage dtype (%d)", sdt);
@@ -634,6 +636,8 @@ static igr_status copy_out(igr_ctx *c, const void *src, void *dst, long long cou
 {
     int sdt = storage_dtype(c->cfg.prec);
     size_t sb = dtype_bytes(sdt);
+    if (on_device && !is_aligned(dst, dtype_bytes(dt)))
+        return fail(c, IGR_ERR_INVALID_ARG, "device buffer not aligned to its element size");
     if (!on_device) {
         if ((int)dt != sdt)
             return fail(c, IGR_ERR_UNSUPPORTED, "host buffers must use the storage dtype (%d)", sdt);
@@ -784,14 +788,20 @@ igr_status igr_solve_sigma(igr_ctx *c, const void *q, void *sigma_inout, int swe
     if (sweeps < 0) return fail(c, IGR_ERR_INVALID_ARG, "sweeps < 0");
     if ((int)dtype != storage_dtype(c->cfg.prec))
         return fail(c, IGR_ERR_UNSUPPORTED, "dtype must be the storage dtype");
+    const size_t sb = c->ops->storage_bytes;
+    if (!is_aligned(q, sb) || !is_aligned(sigma_inout, sb))
+        return fail(c, IGR_ERR_INVALID_ARG, "q and sigma_inout must be aligned to %zu bytes", sb);
+    Tiles t = c->tiles;
+    if (!is_aligned(q, vec4_align((int)sb)) || !is_aligned(sigma_inout, vec4_align((int)sb)))
+        t.vec_source = t.vec_jacobi = 0;  // the 1-cell forms: same bits, element alignment only
     prof_begin(c, KC_SOURCE);
-    CU(c, c->ops->source(c->g, c->p, c->tiles, inflow_of(c), q, c->b, c->st));
+    CU(c, c->ops->source(c->g, c->p, t, inflow_of(c), q, c->b, c->st));
     prof_end(c);
     // the context's second Sigma buffer is scratch: sweeps alternate between
     // the caller's buffer and it, and an odd count copies the result back
     void *scratch = c->sig[1 - c->cur];
     void *res;
-    igr_status s = launch_sweeps(c, q, c->b, sigma_inout, scratch, sweeps, &res);
+    igr_status s = launch_sweeps(c, t, q, c->b, sigma_inout, scratch, sweeps, &res);
     if (s != IGR_OK) return s;
     if (res != sigma_inout)
         CU(c, cudaMemcpyAsync(sigma_inout, res, c->g.n * (size_t)c->ops->storage_bytes,
@@ -804,6 +814,9 @@ igr_status igr_rhs(igr_ctx *c, const void *q, const void *sigma, void *rhs, igr_
     if (!c || !q || !sigma || !rhs) return fail(c, IGR_ERR_INVALID_ARG, "ctx, q, sigma, rhs are required");
     if ((int)dtype != storage_dtype(c->cfg.prec))
         return fail(c, IGR_ERR_UNSUPPORTED, "dtype must be the storage dtype");
+    if (!is_aligned(q, c->ops->storage_bytes) || !is_aligned(sigma, c->ops->storage_bytes) ||
+        !is_aligned(rhs, c->ops->compute_bytes))
+        return fail(c, IGR_ERR_INVALID_ARG, "q, sigma and rhs must be aligned to their element size");
     prof_begin(c, KC_FLUX);
     CU(c, c->ops->flux(c->g, c->p, c->tiles, inflow_of(c), FLUX_RHS, q, sigma, nullptr, nullptr,
                        rhs, nullptr, c->sc, c->blockmax, &c->sc->err, c->st));
@@ -816,6 +829,9 @@ igr_status igr_rk_combine(igr_ctx *c, const void *qn, const void *qs, const void
 {
     if (!c || !qn || !qs || !L || !out) return fail(c, IGR_ERR_INVALID_ARG, "null buffer");
     if (count < 0 || stage < 1 || stage > 3) return fail(c, IGR_ERR_INVALID_ARG, "bad count or stage");
+    if (!is_aligned(qn, c->ops->storage_bytes) || !is_aligned(qs, c->ops->storage_bytes) ||
+        !is_aligned(out, c->ops->storage_bytes) || !is_aligned(L, c->ops->compute_bytes))
+        return fail(c, IGR_ERR_INVALID_ARG, "buffers must be aligned to their element size");
     double w = stage == 1 ? 1.0 : stage == 2 ? 0.25 : 2.0 / 3.0;
     if (count == 0) return IGR_OK;
     prof_begin(c, KC_OTHER);
@@ -1216,6 +1232,12 @@ igr_status igr_adjoint_step(igr_ctx *c, const void *q_n, const void *sigma_n, co
     if (!(dt > 0.0)) return fail(c, IGR_ERR_INVALID_ARG, "the adjoint needs a fixed dt > 0");
     if ((int)dtype != storage_dtype(c->cfg.prec))
         return fail(c, IGR_ERR_UNSUPPORTED, "q_n and sigma_n must use the storage dtype");
+    {
+        const size_t sb = c->ops->storage_bytes, cb = c->ops->compute_bytes;
+        if (!is_aligned(q_n, sb) || !is_aligned(sigma_n, sb) || !is_aligned(lam_q_np1, cb) ||
+            !is_aligned(lam_sigma_np1, cb) || !is_aligned(lam_q_n, cb) || !is_aligned(lam_sigma_n, cb))
+            return fail(c, IGR_ERR_INVALID_ARG, "buffers must be aligned to their element size");
+    }
     if (c->p.order != 5 || c->cfg.sigma_solver != SOLVER_JACOBI || c->p.mu != 0.0 || c->p.zeta != 0.0)
         return fail(c, IGR_ERR_UNSUPPORTED,
                     "the adjoint covers the inviscid scheme with 5th-order faces and Jacobi sweeps");

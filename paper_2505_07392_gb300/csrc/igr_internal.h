@@ -74,6 +74,16 @@ inline int vec4_default(int nx, int num, int den)
 inline int vec4_default_source(int nx) { return vec4_default(nx, 80, 140); }
 inline int vec4_default_jacobi(int nx) { return vec4_default(nx, 69, 79); }
 
+// Alignment of caller device pointers. Every kernel reads and writes whole
+// elements, so a pointer must be aligned to its element size. The 4-cell
+// forms of the source and Jacobi kernels also load and store 4 consecutive
+// values at once (8 bytes at 16-bit storage, 16 bytes for FP32 and, as two
+// 16-byte accesses, for FP64), so they need the field bases aligned to that;
+// a call whose pointers are not takes the 1-cell forms, which give the same
+// bits.
+inline bool is_aligned(const void *p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+inline size_t vec4_align(int storage_bytes) { return storage_bytes * 4 > 16 ? 16 : (size_t)storage_bytes * 4; }
+
 // Stage modes of the flux kernel.
 enum { FLUX_RHS = 0, FLUX_STAGE1 = 1, FLUX_STAGE2 = 2, FLUX_STAGE3 = 3 };
 

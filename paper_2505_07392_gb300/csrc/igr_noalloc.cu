@@ -11,7 +11,9 @@
 // The array is a file-scope __device__ object. Host code cannot use its name
 // as a device address (in host code the symbol is only a host-side stand-in),
 // so the first call on each device looks the address up with
-// cudaGetSymbolAddress while that device is current and caches it.
+// cudaGetSymbolAddress while that device is current and caches it. The
+// cached address belongs to the device's primary context: a cudaDeviceReset
+// between calls (which tears that context down) is not supported.
 #include <stdio.h>
 
 #include <mutex>
@@ -29,7 +31,8 @@ namespace {
 constexpr int kMaxDevices = 256;
 std::mutex g_lock;
 void *g_scratch_addr[kMaxDevices];  // device address of g_noalloc_scratch per device
-char g_noalloc_err[512] = "";
+// message of the calling thread's last failed call
+thread_local char g_noalloc_err[512] = "";
 
 igr_status fail(igr_status s, const char *msg, cudaError_t e = cudaSuccess)
 {
@@ -77,6 +80,9 @@ igr_status igr_solve_sigma_noalloc(const igr_config *cfg, const void *q, void *s
     if (const char *why = validate_config(cfg)) return fail(IGR_ERR_INVALID_ARG, why);
     if (!q || !sigma_inout) return fail(IGR_ERR_INVALID_ARG, "q and sigma_inout are required");
     if (sweeps < 0) return fail(IGR_ERR_INVALID_ARG, "sweeps < 0");
+    const int sb = ops_for(cfg->prec)->storage_bytes;
+    if (!is_aligned(q, sb) || !is_aligned(sigma_inout, sb))
+        return fail(IGR_ERR_INVALID_ARG, "q and sigma_inout must be aligned to their element size");
     for (int f = 0; f < 6; f++)
         if (cfg->bc[f] == IGR_BC_INFLOW)
             return fail(IGR_ERR_UNSUPPORTED, "the allocation-free solve takes periodic and outflow faces only");
@@ -109,6 +115,8 @@ igr_status igr_solve_sigma_noalloc(const igr_config *cfg, const void *q, void *s
     p.mu = cfg->mu;
     p.zeta = cfg->zeta;
     Tiles t = default_tiles(g);
+    if (!is_aligned(q, vec4_align(sb)) || !is_aligned(sigma_inout, vec4_align(sb)))
+        t.vec_source = t.vec_jacobi = 0;  // the 1-cell forms: same bits, element alignment only
     Inflow none;
     none.W = nullptr;
     none.J = nullptr;
