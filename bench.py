@@ -202,7 +202,7 @@ def run_form(case, precision, steps, warmup, sync_all, e2e_steps=0, host_rk_base
     import torch
     from paper_2505_07392_gb300 import igr
     dev = torch.device("cuda", torch.cuda.current_device())
-    st_dtype = igr.storage_torch_dtype(precision)
+    st_dtype = igr.state_torch_dtype(precision)
     res = {}
     with igr.Solver(case, precision, host_rk_base=host_rk_base) as s:
         q = fill_initial_state(case, st_dtype, dev)
@@ -253,7 +253,7 @@ def run_e2e(s, case, precision, steps, sync_all):
     import ctypes
     import torch
     from paper_2505_07392_gb300 import igr
-    dt = igr.storage_torch_dtype(precision)
+    dt = igr.state_torch_dtype(precision)
     hq = torch.empty((5,) + s.shape, dtype=dt, pin_memory=True)
     code = {torch.float16: igr.DT_F16, torch.bfloat16: igr.DT_BF16, torch.float32: igr.DT_F32,
             torch.float64: igr.DT_F64}[dt]
@@ -345,7 +345,7 @@ def run_batch(args, sync_all=lambda: None):
     import torch
     from paper_2505_07392_gb300 import igr
     cases = inputs.tgv_batch(count=args.batch_count)
-    st = igr.storage_torch_dtype(args.precision)
+    st = igr.state_torch_dtype(args.precision)
     tuned = {}
     with igr.Batch(cases, args.precision) as b:
         for c, inst in zip(cases, b.instances):
@@ -453,7 +453,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f16", choices=["f16", "bf16", "f32", "f64"])
+    ap.add_argument("--precision", default="f16", choices=["f16", "bf16", "f32", "f64", "f16inc", "bf16inc"])
     ap.add_argument("--plain", default="f32", help="second form measured beside the headline ('none' = skip)")
     ap.add_argument("--size", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"))
     ap.add_argument("--e2e-steps", type=int, default=3)

@@ -21,6 +21,10 @@
  *  - State layout: q is [5][nz][ny][nx] contiguous (x fastest), variables
  *    (rho, rho u, rho v, rho w, E), interior cells only. Sigma is
  *    [nz][ny][nx]. No ghost cells: boundary conditions act by index mapping.
+ *  - Element types: the "storage dtype" of a precision mode is that of
+ *    Sigma and b (FP64, FP32, binary16 or bfloat16); the "state dtype" is
+ *    that of q: the storage dtype, except FP32 in the increment modes
+ *    (IGR_F32_F16INC, IGR_F32_BF16INC).
  *  - Device pointers are borrowed. Calls that take them are asynchronous on
  *    the context's stream; the caller keeps the memory alive until that
  *    stream has passed the call. Host pointers are read or written before
@@ -63,7 +67,14 @@ typedef enum {
     IGR_F32 = 1,           /* FP32 storage and arithmetic */
     IGR_F32_F16STORE = 2,  /* FP32 arithmetic, q/Sigma/b stored as IEEE binary16,
                               RK combination in FP64, round-to-nearest-even on store */
-    IGR_F32_BF16STORE = 3  /* as above with bfloat16 storage */
+    IGR_F32_BF16STORE = 3, /* as above with bfloat16 storage */
+    IGR_F32_F16INC = 4,    /* FP32 arithmetic; the state q^n in FP32 (the RK accumulation
+                              never rounds to 16 bits); RK stages 1 and 2 store the
+                              increments d_s = q_s - q^n as IEEE binary16 (a stage reads
+                              q_s = RN32(q^n + d_s)); Sigma, b and the sweeps' density in
+                              binary16. Increments must stay within binary16's range
+                              (|d| < 65504), else the step reports IGR_ERR_NONFINITE. */
+    IGR_F32_BF16INC = 5    /* as IGR_F32_F16INC with bfloat16 increments, Sigma and b */
 } igr_precision;
 
 /* Element type of a buffer passed across the ABI. */
@@ -140,7 +151,10 @@ typedef struct igr_ctx igr_ctx; /* opaque */
  * three state buffers (5 fields each; two with host_rk_base, plus the host
  * buffer of the RK base), two Sigma buffers, the source b,
  * the inflow tables and a few scalars, all in the storage type of
- * cfg->prec. allocator may be NULL (cudaMalloc). cuda_stream is a
+ * cfg->prec; in the increment modes two FP32 state buffers, two buffers of
+ * 16-bit increments and the stage density instead of the three state
+ * buffers (68 bytes per cell with Jacobi sweeps, against 72 for IGR_F32 and
+ * 36 for IGR_F32_F16STORE). allocator may be NULL (cudaMalloc). cuda_stream is a
  * cudaStream_t (NULL = legacy default stream). The state and Sigma start
  * at zero; call igr_set_state before stepping. */
 igr_status igr_create(const igr_config *cfg, const igr_allocator *allocator, void *cuda_stream,
@@ -156,7 +170,7 @@ igr_status igr_destroy(igr_ctx *ctx);
 /* Copy a state into the context. q holds 5 n values, sigma n values
  * (NULL sets Sigma = 0, the cold start). dtype is the element type of q
  * and sigma; on_device = 1 means device pointers (any dtype, converted on
- * the device), 0 means host pointers (dtype must be the storage type). */
+ * the device), 0 means host pointers (dtype must be the state dtype). */
 igr_status igr_set_state(igr_ctx *ctx, const void *q, const void *sigma, igr_dtype dtype,
                          int on_device);
 
@@ -180,7 +194,7 @@ igr_status igr_get_state(igr_ctx *ctx, void *q, void *sigma, igr_dtype dtype, in
 igr_status igr_step(igr_ctx *ctx, int nsteps, double fixed_dt, double *t_inout);
 
 /* nsteps SSP-RK3 steps from host memory to host memory: q_in (5 n values,
- * the storage dtype, best pinned) is copied in, Sigma stays on the device
+ * the state dtype, best pinned) is copied in, Sigma stays on the device
  * (as with igr_set_conserved), the steps run, and the final q is written to
  * q_out. The last stage's flux kernel runs in z-slabs and each slab is
  * copied out while the next ones compute, so most of the read-back
@@ -188,17 +202,19 @@ igr_status igr_step(igr_ctx *ctx, int nsteps, double fixed_dt, double *t_inout);
  * follows the CFL rule. Synchronises and reports asynchronous errors. */
 igr_status igr_step_host(igr_ctx *ctx, const void *q_in, void *q_out, int nsteps, igr_dtype dtype);
 
-/* Sigma solve alone, on caller buffers in the storage dtype (device
- * pointers): b from q, then `sweeps` Jacobi sweeps warm-started from
- * sigma_inout; the result overwrites sigma_inout. Uses the context's b and
- * second Sigma buffer as scratch (the context state is untouched). */
+/* Sigma solve alone, on caller device buffers: q in the state dtype,
+ * sigma_inout in the storage dtype (dtype names the storage dtype): b from
+ * q, then `sweeps` Jacobi sweeps warm-started from sigma_inout; the result
+ * overwrites sigma_inout. Uses the context's b, second Sigma buffer and (in
+ * the increment modes) stage-density buffer as scratch (the context state
+ * is untouched). */
 igr_status igr_solve_sigma(igr_ctx *ctx, const void *q, void *sigma_inout, int sweeps,
                            igr_dtype dtype);
 
 /* Spatial operator L(q; Sigma) = -div F_hat (no elliptic solve, no RK):
- * q and sigma are device buffers in the storage dtype (dtype), rhs is a
- * device buffer of 5 n values in the arithmetic type (FP64 for IGR_F64,
- * FP32 otherwise). */
+ * q is a device buffer in the state dtype, sigma in the storage dtype
+ * (dtype), rhs is a device buffer of 5 n values in the arithmetic type
+ * (FP64 for IGR_F64, FP32 otherwise). */
 igr_status igr_rhs(igr_ctx *ctx, const void *q, const void *sigma, void *rhs, igr_dtype dtype);
 
 /* Discrete adjoint of one SSP-RK3 step with a fixed dt: the transpose of the
@@ -220,7 +236,8 @@ igr_status igr_rhs(igr_ctx *ctx, const void *q, const void *sigma, void *rhs, ig
  * doubles or NULL (synchronises when given). The first call allocates a
  * workspace of about (29 + 3 sweeps) n stored values plus 30 n arithmetic
  * values through the context's allocator. The scatter steps use atomics, so
- * FP32 results vary in the last bits from run to run. */
+ * FP32 results vary in the last bits from run to run. The increment modes
+ * return IGR_ERR_UNSUPPORTED. */
 igr_status igr_adjoint_step(igr_ctx *ctx, const void *q_n, const void *sigma_n,
                             const void *lam_q_np1, const void *lam_sigma_np1, void *lam_q_n,
                             void *lam_sigma_n, double *grad_jet_w, double dt, igr_dtype dtype);
@@ -228,10 +245,13 @@ igr_status igr_adjoint_step(igr_ctx *ctx, const void *q_n, const void *sigma_n,
 /* The SSP-RK3 stage combination alone, exactly as the stage kernel stores it:
  *   out = qn + w [(qs - qn) + dt L],  w = 1, 1/4, 2/3 for stage = 1, 2, 3
  * (Gottlieb-Shu SSP-RK3 in increment form). qn, qs, out: device buffers of
- * count values in the storage dtype; L: device buffer in the arithmetic type
- * (FP64 for IGR_F64, FP32 otherwise). In the 16-bit modes the stored value
- * is the FP64 evaluation of the expression rounded to nearest-even. out may
- * alias qn. For verification and tooling. */
+ * count values in the state dtype; L: device buffer in the arithmetic type
+ * (FP64 for IGR_F64, FP32 otherwise). In IGR_F32_F16STORE and
+ * IGR_F32_BF16STORE the stored value is the FP64 evaluation of the
+ * expression rounded to nearest-even; in the increment modes it is the FP32
+ * state update of stage 3 (stages 1 and 2 there store the increment
+ * w [(qs - qn) + dt L] rounded to 16 bits). out may alias qn. For
+ * verification and tooling. */
 igr_status igr_rk_combine(igr_ctx *ctx, const void *qn, const void *qs, const void *L, void *out,
                           long long count, int stage, double dt);
 
@@ -249,8 +269,8 @@ igr_status igr_rk_combine(igr_ctx *ctx, const void *qn, const void *qs, const vo
  * GPU loading this library holds until the process exits.
  *  - q, sigma_inout: device buffers in the storage type of cfg->prec.
  *  - Grids needing more than the array holds (see igr_noalloc_max_cells) are
- *    rejected with IGR_ERR_INVALID_ARG; IGR_BC_INFLOW faces with
- *    IGR_ERR_UNSUPPORTED. The call issues no cudaMalloc/cudaFree and no
+ *    rejected with IGR_ERR_INVALID_ARG; IGR_BC_INFLOW faces and the
+ *    increment modes with IGR_ERR_UNSUPPORTED. The call issues no cudaMalloc/cudaFree and no
  *    allocating library routine.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call

@@ -1,7 +1,7 @@
 """Builds libigr.so, the CUDA library behind include/igr.h, for sm_103a.
 
-The kernel source igr_kernels.cu is compiled once per storage type (FP64,
-FP32, FP16, BF16); the host runtime igr_api.cu and the allocation-free entry
+The kernel source igr_kernels.cu is compiled once per storage form (FP64,
+FP32, FP16, BF16, and FP16/BF16 increments on an FP32 state); the host runtime igr_api.cu and the allocation-free entry
 point igr_noalloc.cu once each; the objects compile in parallel and link
 into paper_2505_07392_gb300/libigr.so.
 """
@@ -21,7 +21,10 @@ LIB_DEBUG = os.path.join(HERE, "libigr_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "-diag-suppress", "177"]
 
-VARIANTS = [("f64", "double"), ("f32", "float"), ("f16", "__half"), ("bf16", "__nv_bfloat16")]
+# (tag, storage type, state type): the increment modes keep the state q^n in
+# FP32 and store 16-bit stage increments, Sigma and b
+VARIANTS = [("f64", "double", None), ("f32", "float", None), ("f16", "__half", None),
+            ("bf16", "__nv_bfloat16", None), ("f16inc", "__half", "float"), ("bf16inc", "__nv_bfloat16", "float")]
 
 
 def nvcc():
@@ -38,8 +41,9 @@ def _sources():
 
 def _jobs(extra, obj):
     jobs = []
-    for tag, ty in VARIANTS:
+    for tag, ty, base in VARIANTS:
         jobs.append([nvcc(), *ARCH, *FLAGS, *extra, f"-DIGR_STORAGE={ty}", f"-DIGR_OPS=ops_{tag}",
+                     *([f"-DIGR_BASE={base}"] if base else []),
                      "-c", os.path.join(CSRC, "igr_kernels.cu"), "-o", os.path.join(obj, f"kern_{tag}.o")])
     for name in ("igr_api", "igr_noalloc"):
         jobs.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, name + ".cu"),

@@ -8,6 +8,10 @@
 //   sig[2]       Sigma ping-pong pair; Sigma persists across stages and steps
 //                as the warm start of the Jacobi sweeps.
 //   b            IGR source.
+// In the increment modes qA is the FP32 state q^n, qB and qC hold the 16-bit
+// increments d_1, d_2 of stages 1 and 2, stage 3 writes q^n+1 into a second
+// FP32 buffer (qalt; the two alternate), and rho16 holds the stage density
+// in the storage type for the sweeps.
 // plus the -z inflow tables (arithmetic type), the per-block wave-speed
 // maxima and a small block of device scalars (dt, t, speed, error flag).
 // A time step never returns to the host: dt is reduced and applied on the
@@ -44,7 +48,11 @@ struct igr_ctx {
     bool own_alloc;
     cudaStream_t st;
     int device;
-    void *q[3];         // q^n, q^1, q^2 (q[2] unused with host_rk_base)
+    void *q[3];         // q^n, q^1, q^2 (q[2] unused with host_rk_base); increment
+                        // modes: q^n (FP32), d_1, d_2 (storage type)
+    void *qalt;         // increment modes: the FP32 buffer stage 3 writes q^n+1 into
+    void *rho16;        // increment modes: the stage density in the storage type
+    bool inc;           // an increment mode
     void *hbase;        // host_rk_base: pinned host buffer of the RK base (5 n values)
     void *hbase_dev;    // its device-mapped address
     void *sig[2];
@@ -186,15 +194,19 @@ __global__ void k_finalize_dt(const double *blockmax, int nblocks, Scalars *sc, 
 
 // ------------------------------------------------------------ helpers
 
+// element type of Sigma, b and the increments
 static int storage_dtype(igr_precision p)
 {
     switch (p) {
     case IGR_F64: return IGR_DT_F64;
     case IGR_F32: return IGR_DT_F32;
-    case IGR_F32_F16STORE: return IGR_DT_F16;
+    case IGR_F32_F16STORE: case IGR_F32_F16INC: return IGR_DT_F16;
     default: return IGR_DT_BF16;
     }
 }
+static bool is_inc(igr_precision p) { return p == IGR_F32_F16INC || p == IGR_F32_BF16INC; }
+// element type of the state q
+static int state_dtype(igr_precision p) { return is_inc(p) ? IGR_DT_F32 : storage_dtype(p); }
 static size_t dtype_bytes(int dt) { return dt == IGR_DT_F64 ? 8 : dt == IGR_DT_F32 ? 4 : 2; }
 
 const Ops *igr::ops_for(int p)
@@ -204,6 +216,8 @@ const Ops *igr::ops_for(int p)
     case IGR_F32: return &ops_f32;
     case IGR_F32_F16STORE: return &ops_f16;
     case IGR_F32_BF16STORE: return &ops_bf16;
+    case IGR_F32_F16INC: return &ops_f16inc;
+    case IGR_F32_BF16INC: return &ops_bf16inc;
     }
     return nullptr;
 }
@@ -242,7 +256,8 @@ const char *igr::validate_config(const igr_config *c)
     if (!(c->dx > 0) || !(c->gamma > 1) || !(c->alpha >= 0) || !(c->cfl > 0) || isinf(c->dx))
         return "need dx > 0, gamma > 1, alpha >= 0, cfl > 0";
     if (c->sweeps < 1) return "sweeps must be >= 1";
-    if (c->prec < IGR_F64 || c->prec > IGR_F32_BF16STORE) return "unknown precision mode";
+    if (c->prec < IGR_F64 || c->prec > IGR_F32_BF16INC) return "unknown precision mode";
+    if (is_inc(c->prec) && c->host_rk_base) return "host_rk_base is not available in the increment modes";
     for (int f = 0; f < 6; f++)
         if (c->bc[f] < IGR_BC_PERIODIC || c->bc[f] > IGR_BC_INFLOW) return "unknown boundary condition";
     for (int a = 0; a < 3; a++)
@@ -272,7 +287,7 @@ const char *igr::validate_config(const igr_config *c)
 }
 
 struct Layout {
-    size_t state, sig, b, W, J, blockmax, scalars, jets;
+    size_t state, incr, sig, b, W, J, blockmax, scalars, jets;
 };
 
 static Layout layout_of(const igr_config *c)
@@ -284,7 +299,8 @@ static Layout layout_of(const igr_config *c)
     const Ops *o = ops_for(c->prec);
     Tiles t = default_tiles(g);
     Layout L;
-    L.state = (size_t)5 * g.n * o->storage_bytes;
+    L.state = (size_t)5 * g.n * o->state_bytes;
+    L.incr = (size_t)5 * g.n * o->storage_bytes;  // a stage increment (increment modes)
     L.sig = (size_t)g.n * o->storage_bytes;
     L.b = L.sig;
     L.W = (size_t)g.plane * o->compute_bytes;
@@ -394,32 +410,36 @@ static igr_status launch_sweeps(igr_ctx *c, const Tiles &t, const void *q, const
 // igr_step_host) the flux runs in z-slabs of whole chunks, and each slab's
 // planes of `out` are copied to host_out on copy_st as soon as the slab is
 // done, while the next slabs compute; c->st then waits for the copies.
-static igr_status run_stage(igr_ctx *c, int mode, const void *qs, const void *qn, void *out,
+// qd: the stage's increments (increment modes, stages 2 and 3), else NULL.
+static igr_status run_stage(igr_ctx *c, int mode, const void *qs, const void *qd, const void *qn, void *out,
                             void *base_out = nullptr, void *host_out = nullptr)
 {
     prof_begin(c, KC_SOURCE);
-    CU(c, c->ops->source(c->g, c->p, c->tiles, inflow_of(c), qs, c->b, c->st));
+    CU(c, c->ops->source(c->g, c->p, c->tiles, inflow_of(c), qs, qd, c->b, c->rho16, c->st));
     prof_end(c);
     void *res;
-    igr_status s = launch_sweeps(c, c->tiles, qs, c->b, c->sig[c->cur], c->sig[1 - c->cur], c->cfg.sweeps, &res);
+    // the sweeps read the density as field 0 of their q: the state itself, or
+    // the stage density the source kernel stored (increment modes)
+    const void *qj = c->inc ? c->rho16 : qs;
+    igr_status s = launch_sweeps(c, c->tiles, qj, c->b, c->sig[c->cur], c->sig[1 - c->cur], c->cfg.sweeps, &res);
     if (s != IGR_OK) return s;
     c->cur = res == c->sig[0] ? 0 : 1;
     if (!host_out) {
         prof_begin(c, KC_FLUX);
-        CU(c, c->ops->flux(c->g, c->p, c->tiles, inflow_of(c), mode, qs, c->sig[c->cur], qn, out,
+        CU(c, c->ops->flux(c->g, c->p, c->tiles, inflow_of(c), mode, qs, qd, c->sig[c->cur], qn, out,
                            nullptr, base_out, c->sc, c->blockmax, &c->sc->err, c->st));
         prof_end(c);
         return IGR_OK;
     }
     const int zc = c->tiles.zc_flux, nchunk = (c->g.nz + zc - 1) / zc;
     const int per = (nchunk + kOutSlabs - 1) / kOutSlabs;  // chunks per slab
-    const size_t sb = c->ops->storage_bytes, plane = (size_t)c->g.plane;
+    const size_t sb = c->ops->state_bytes, plane = (size_t)c->g.plane;
     for (int c0 = 0, k = 0; c0 < nchunk; c0 += per, k++) {
         Tiles t = c->tiles;
         t.z_begin = c0 * zc;
         t.z_end = std::min(c->g.nz, (c0 + per) * zc);
         prof_begin(c, KC_FLUX);
-        CU(c, c->ops->flux(c->g, c->p, t, inflow_of(c), mode, qs, c->sig[c->cur], qn, out, nullptr,
+        CU(c, c->ops->flux(c->g, c->p, t, inflow_of(c), mode, qs, qd, c->sig[c->cur], qn, out, nullptr,
                            base_out, c->sc, c->blockmax, &c->sc->err, c->st));
         prof_end(c);
         CU(c, cudaEventRecord(c->slab_ev[k], c->st));
@@ -475,6 +495,10 @@ size_t igr_memory_bytes(const igr_config *cfg)
 {
     if (validate_config(cfg)) return 0;
     Layout L = layout_of(cfg);
+    if (is_inc(cfg->prec))  // two FP32 states, two increments, the stage density
+        return 2 * round256(L.state) + 2 * round256(L.incr) + round256(L.b) +
+               (cfg->sigma_solver == SOLVER_RBGS ? 1 : 2) * round256(L.sig) + round256(L.b) +
+               round256(L.W) + round256(L.J) + round256(L.blockmax) + round256(L.scalars) + round256(L.jets);
     return (cfg->host_rk_base ? 2 : 3) * round256(L.state) +
            (cfg->sigma_solver == SOLVER_RBGS ? 1 : 2) * round256(L.sig) + round256(L.b) +
            round256(L.W) + round256(L.J) + round256(L.blockmax) + round256(L.scalars) + round256(L.jets);
@@ -520,8 +544,11 @@ igr_status igr_create(const igr_config *cfg, const igr_allocator *allocator, voi
 
     Layout L = layout_of(cfg);
     igr_status s = IGR_OK;
+    c->inc = is_inc(cfg->prec);
     const int nstate = cfg->host_rk_base ? 2 : 3;
-    for (int n = 0; n < nstate && s == IGR_OK; n++) s = ctx_alloc(c, &c->q[n], L.state);
+    for (int n = 0; n < nstate && s == IGR_OK; n++) s = ctx_alloc(c, &c->q[n], c->inc && n > 0 ? L.incr : L.state);
+    if (s == IGR_OK && c->inc) s = ctx_alloc(c, &c->qalt, L.state);
+    if (s == IGR_OK && c->inc) s = ctx_alloc(c, &c->rho16, L.b);
     if (s == IGR_OK && cfg->host_rk_base) {
         if (cudaHostAlloc(&c->hbase, L.state, cudaHostAllocMapped) != cudaSuccess) {
             c->hbase = nullptr;
@@ -548,7 +575,10 @@ igr_status igr_create(const igr_config *cfg, const igr_allocator *allocator, voi
     }
     // zero state, Sigma, scalars; build the inflow tables
     cudaError_t e = cudaSuccess;
-    for (int n = 0; n < nstate && e == cudaSuccess; n++) e = cudaMemsetAsync(c->q[n], 0, L.state, c->st);
+    for (int n = 0; n < nstate && e == cudaSuccess; n++)
+        e = cudaMemsetAsync(c->q[n], 0, c->inc && n > 0 ? L.incr : L.state, c->st);
+    if (e == cudaSuccess && c->inc) e = cudaMemsetAsync(c->qalt, 0, L.state, c->st);
+    if (e == cudaSuccess && c->inc) e = cudaMemsetAsync(c->rho16, 0, L.b, c->st);
     for (int n = 0; n < nsig && e == cudaSuccess; n++) e = cudaMemsetAsync(c->sig[n], 0, L.sig, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->b, 0, L.b, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->sc, 0, L.scalars, c->st);
@@ -593,7 +623,7 @@ igr_status igr_destroy(igr_ctx *c)
     if (!c) return IGR_OK;
     cudaStreamSynchronize(c->st);
     if (c->profiling) prof_collect(c);
-    void *bufs[] = {c->q[0], c->q[1], c->q[2], c->sig[0], c->sig[1], c->b, c->W, c->J,
+    void *bufs[] = {c->q[0], c->q[1], c->q[2], c->qalt, c->rho16, c->sig[0], c->sig[1], c->b, c->W, c->J,
                     c->blockmax, c->sc, c->jets_dev, c->diag_part};
     for (void *p : bufs)
         if (p) c->alloc.free(p, c->alloc.user);
@@ -609,47 +639,55 @@ igr_status igr_destroy(igr_ctx *c)
     return IGR_OK;
 }
 
+// Copy count values from a caller buffer of type dt into a context buffer of
+// type ddt (converted on the device when they differ). Host buffers must have
+// the state's type; in the increment modes a host Sigma (FP32) is staged in
+// the first increment buffer, which holds nothing between steps, and
+// converted there.
 static igr_status copy_in(igr_ctx *c, const void *src, void *dst, long long count, igr_dtype dt,
-                          int on_device)
+                          int on_device, int ddt)
 {
-    int sdt = storage_dtype(c->cfg.prec);
-    size_t sb = dtype_bytes(sdt);
-    if (on_device && !is_aligned(src, dtype_bytes(dt)))
+    const size_t db = dtype_bytes(dt);
+    if (on_device && !is_aligned(src, db))
         return fail(c, IGR_ERR_INVALID_ARG, "device buffer not aligned to its element size");
-    if (!on_device) {
-        if ((int)dt != sdt)
-            return fail(c, IGR_ERR_UNSUPPORTED, "host buffers must use the storage dtype (%d)", sdt);
-        CU(c, cudaMemcpyAsync(dst, src, count * sb, cudaMemcpyHostToDevice, c->st));
+    if (!on_device && (int)dt != state_dtype(c->cfg.prec))
+        return fail(c, IGR_ERR_UNSUPPORTED, "host buffers must use the state dtype (%d)",
+                    state_dtype(c->cfg.prec));
+    if ((int)dt == ddt) {
+        CU(c, cudaMemcpyAsync(dst, src, count * db, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              c->st));
         return IGR_OK;
     }
-    if ((int)dt == sdt) {
-        CU(c, cudaMemcpyAsync(dst, src, count * sb, cudaMemcpyDeviceToDevice, c->st));
-    } else {
-        k_convert<<<2048, 256, 0, c->st>>>(src, dt, dst, sdt, count);
-        CU(c, cudaGetLastError());
+    const void *from = src;
+    if (!on_device) {  // increment modes only (dt = FP32, ddt = the storage type)
+        CU(c, cudaMemcpyAsync(c->q[1], src, count * db, cudaMemcpyHostToDevice, c->st));
+        from = c->q[1];
     }
+    k_convert<<<2048, 256, 0, c->st>>>(from, dt, dst, ddt, count);
+    CU(c, cudaGetLastError());
     return IGR_OK;
 }
 
+// Copy count values of type sdt from a context buffer into a caller buffer
+// of type dt (the same rules as copy_in).
 static igr_status copy_out(igr_ctx *c, const void *src, void *dst, long long count, igr_dtype dt,
-                           int on_device)
+                           int on_device, int sdt)
 {
-    int sdt = storage_dtype(c->cfg.prec);
-    size_t sb = dtype_bytes(sdt);
-    if (on_device && !is_aligned(dst, dtype_bytes(dt)))
+    const size_t db = dtype_bytes(dt);
+    if (on_device && !is_aligned(dst, db))
         return fail(c, IGR_ERR_INVALID_ARG, "device buffer not aligned to its element size");
-    if (!on_device) {
-        if ((int)dt != sdt)
-            return fail(c, IGR_ERR_UNSUPPORTED, "host buffers must use the storage dtype (%d)", sdt);
-        CU(c, cudaMemcpyAsync(dst, src, count * sb, cudaMemcpyDeviceToHost, c->st));
+    if (!on_device && (int)dt != state_dtype(c->cfg.prec))
+        return fail(c, IGR_ERR_UNSUPPORTED, "host buffers must use the state dtype (%d)",
+                    state_dtype(c->cfg.prec));
+    if ((int)dt == sdt) {
+        CU(c, cudaMemcpyAsync(dst, src, count * db, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              c->st));
         return IGR_OK;
     }
-    if ((int)dt == sdt) {
-        CU(c, cudaMemcpyAsync(dst, src, count * sb, cudaMemcpyDeviceToDevice, c->st));
-    } else {
-        k_convert<<<2048, 256, 0, c->st>>>(src, sdt, dst, dt, count);
-        CU(c, cudaGetLastError());
-    }
+    void *to = on_device ? dst : c->q[1];
+    k_convert<<<2048, 256, 0, c->st>>>(src, sdt, to, dt, count);
+    CU(c, cudaGetLastError());
+    if (!on_device) CU(c, cudaMemcpyAsync(dst, to, count * db, cudaMemcpyDeviceToHost, c->st));
     return IGR_OK;
 }
 
@@ -657,11 +695,11 @@ igr_status igr_set_state(igr_ctx *c, const void *q, const void *sigma, igr_dtype
 {
     if (!c || !q) return fail(c, IGR_ERR_INVALID_ARG, "ctx and q are required");
     if (dtype < IGR_DT_F64 || dtype > IGR_DT_BF16) return fail(c, IGR_ERR_INVALID_ARG, "bad dtype");
-    igr_status s = copy_in(c, q, c->q[0], 5 * c->g.n, dtype, on_device);
+    igr_status s = copy_in(c, q, c->q[0], 5 * c->g.n, dtype, on_device, state_dtype(c->cfg.prec));
     if (s != IGR_OK) return s;
     c->cur = 0;
     if (sigma) {
-        s = copy_in(c, sigma, c->sig[0], c->g.n, dtype, on_device);
+        s = copy_in(c, sigma, c->sig[0], c->g.n, dtype, on_device, storage_dtype(c->cfg.prec));
         if (s != IGR_OK) return s;
     } else {
         CU(c, cudaMemsetAsync(c->sig[0], 0, c->g.n * dtype_bytes(storage_dtype(c->cfg.prec)), c->st));
@@ -678,7 +716,7 @@ igr_status igr_set_conserved(igr_ctx *c, const void *q, igr_dtype dtype, int on_
 {
     if (!c || !q) return fail(c, IGR_ERR_INVALID_ARG, "ctx and q are required");
     if (dtype < IGR_DT_F64 || dtype > IGR_DT_BF16) return fail(c, IGR_ERR_INVALID_ARG, "bad dtype");
-    igr_status s = copy_in(c, q, c->q[0], 5 * c->g.n, dtype, on_device);
+    igr_status s = copy_in(c, q, c->q[0], 5 * c->g.n, dtype, on_device, state_dtype(c->cfg.prec));
     if (s != IGR_OK) return s;
     c->speed_nblocks = 0;  // dt from the new q
     c->warn_flags = 0;
@@ -691,8 +729,9 @@ igr_status igr_get_state(igr_ctx *c, void *q, void *sigma, igr_dtype dtype, int 
 {
     if (!c || !q) return fail(c, IGR_ERR_INVALID_ARG, "ctx and q are required");
     if (dtype < IGR_DT_F64 || dtype > IGR_DT_BF16) return fail(c, IGR_ERR_INVALID_ARG, "bad dtype");
-    igr_status s = copy_out(c, c->q[0], q, 5 * c->g.n, dtype, on_device);
-    if (s == IGR_OK && sigma) s = copy_out(c, c->sig[c->cur], sigma, c->g.n, dtype, on_device);
+    igr_status s = copy_out(c, c->q[0], q, 5 * c->g.n, dtype, on_device, state_dtype(c->cfg.prec));
+    if (s == IGR_OK && sigma)
+        s = copy_out(c, c->sig[c->cur], sigma, c->g.n, dtype, on_device, storage_dtype(c->cfg.prec));
     if (s != IGR_OK) return s;
     return read_flags(c);
 }
@@ -716,14 +755,20 @@ static igr_status one_step(igr_ctx *c, double fixed_dt, void *host_out)
     if (c->hbase) {
         // RK base in host memory: stage 1 copies q^n there while it reads it,
         // stages 2 and 3 read it back; the two device buffers alternate
-        s = run_stage(c, FLUX_STAGE1, c->q[0], c->q[0], c->q[1], c->hbase_dev);
-        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE2, c->q[1], c->hbase_dev, c->q[0]);
-        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE3, c->q[0], c->hbase_dev, c->q[1], nullptr, host_out);
+        s = run_stage(c, FLUX_STAGE1, c->q[0], nullptr, c->q[0], c->q[1], c->hbase_dev);
+        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE2, c->q[1], nullptr, c->hbase_dev, c->q[0]);
+        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE3, c->q[0], nullptr, c->hbase_dev, c->q[1], nullptr, host_out);
         std::swap(c->q[0], c->q[1]);
+    } else if (c->inc) {
+        // FP32 state q^n, 16-bit increments: stage s reads q^n + d_s
+        s = run_stage(c, FLUX_STAGE1, c->q[0], nullptr, c->q[0], c->q[1]);
+        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE2, c->q[0], c->q[1], c->q[0], c->q[2]);
+        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE3, c->q[0], c->q[2], c->q[0], c->qalt, nullptr, host_out);
+        std::swap(c->q[0], c->qalt);
     } else {
-        s = run_stage(c, FLUX_STAGE1, c->q[0], c->q[0], c->q[1]);
-        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE2, c->q[1], c->q[0], c->q[2]);
-        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE3, c->q[2], c->q[0], c->q[0], nullptr, host_out);
+        s = run_stage(c, FLUX_STAGE1, c->q[0], nullptr, c->q[0], c->q[1]);
+        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE2, c->q[1], nullptr, c->q[0], c->q[2]);
+        if (s == IGR_OK) s = run_stage(c, FLUX_STAGE3, c->q[2], nullptr, c->q[0], c->q[0], nullptr, host_out);
     }
     if (s != IGR_OK) return s;
     c->speed_nblocks = (int)c->ops->flux_blocks(c->g, c->tiles);
@@ -762,15 +807,15 @@ igr_status igr_step_host(igr_ctx *c, const void *q_in, void *q_out, int nsteps, 
 {
     if (!c || !q_in || !q_out) return fail(c, IGR_ERR_INVALID_ARG, "ctx, q_in and q_out are required");
     if (nsteps < 1) return fail(c, IGR_ERR_INVALID_ARG, "nsteps < 1");
-    if ((int)dtype != storage_dtype(c->cfg.prec))
-        return fail(c, IGR_ERR_UNSUPPORTED, "host buffers must use the storage dtype (%d)",
-                    storage_dtype(c->cfg.prec));
+    if ((int)dtype != state_dtype(c->cfg.prec))
+        return fail(c, IGR_ERR_UNSUPPORTED, "host buffers must use the state dtype (%d)",
+                    state_dtype(c->cfg.prec));
     if (!c->copy_st) {
         CU(c, cudaStreamCreateWithFlags(&c->copy_st, cudaStreamNonBlocking));
         for (cudaEvent_t &e : c->slab_ev) CU(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     // q in; Sigma stays on the device (as with igr_set_conserved)
-    igr_status s = copy_in(c, q_in, c->q[0], 5 * c->g.n, dtype, 0);
+    igr_status s = copy_in(c, q_in, c->q[0], 5 * c->g.n, dtype, 0, state_dtype(c->cfg.prec));
     if (s != IGR_OK) return s;
     c->speed_nblocks = 0;
     c->warn_flags = 0;
@@ -788,20 +833,20 @@ igr_status igr_solve_sigma(igr_ctx *c, const void *q, void *sigma_inout, int swe
     if (sweeps < 0) return fail(c, IGR_ERR_INVALID_ARG, "sweeps < 0");
     if ((int)dtype != storage_dtype(c->cfg.prec))
         return fail(c, IGR_ERR_UNSUPPORTED, "dtype must be the storage dtype");
-    const size_t sb = c->ops->storage_bytes;
-    if (!is_aligned(q, sb) || !is_aligned(sigma_inout, sb))
-        return fail(c, IGR_ERR_INVALID_ARG, "q and sigma_inout must be aligned to %zu bytes", sb);
+    const size_t sb = c->ops->storage_bytes, qb = c->ops->state_bytes;
+    if (!is_aligned(q, qb) || !is_aligned(sigma_inout, sb))
+        return fail(c, IGR_ERR_INVALID_ARG, "q and sigma_inout must be aligned to their element size");
     Tiles t = c->tiles;
-    if (!is_aligned(q, vec4_align((int)sb)) || !is_aligned(sigma_inout, vec4_align((int)sb)))
+    if (!is_aligned(q, vec4_align((int)qb)) || !is_aligned(sigma_inout, vec4_align((int)sb)))
         t.vec_source = t.vec_jacobi = 0;  // the 1-cell forms: same bits, element alignment only
     prof_begin(c, KC_SOURCE);
-    CU(c, c->ops->source(c->g, c->p, t, inflow_of(c), q, c->b, c->st));
+    CU(c, c->ops->source(c->g, c->p, t, inflow_of(c), q, nullptr, c->b, c->rho16, c->st));
     prof_end(c);
     // the context's second Sigma buffer is scratch: sweeps alternate between
     // the caller's buffer and it, and an odd count copies the result back
     void *scratch = c->sig[1 - c->cur];
     void *res;
-    igr_status s = launch_sweeps(c, t, q, c->b, sigma_inout, scratch, sweeps, &res);
+    igr_status s = launch_sweeps(c, t, c->inc ? c->rho16 : q, c->b, sigma_inout, scratch, sweeps, &res);
     if (s != IGR_OK) return s;
     if (res != sigma_inout)
         CU(c, cudaMemcpyAsync(sigma_inout, res, c->g.n * (size_t)c->ops->storage_bytes,
@@ -814,11 +859,11 @@ igr_status igr_rhs(igr_ctx *c, const void *q, const void *sigma, void *rhs, igr_
     if (!c || !q || !sigma || !rhs) return fail(c, IGR_ERR_INVALID_ARG, "ctx, q, sigma, rhs are required");
     if ((int)dtype != storage_dtype(c->cfg.prec))
         return fail(c, IGR_ERR_UNSUPPORTED, "dtype must be the storage dtype");
-    if (!is_aligned(q, c->ops->storage_bytes) || !is_aligned(sigma, c->ops->storage_bytes) ||
+    if (!is_aligned(q, c->ops->state_bytes) || !is_aligned(sigma, c->ops->storage_bytes) ||
         !is_aligned(rhs, c->ops->compute_bytes))
         return fail(c, IGR_ERR_INVALID_ARG, "q, sigma and rhs must be aligned to their element size");
     prof_begin(c, KC_FLUX);
-    CU(c, c->ops->flux(c->g, c->p, c->tiles, inflow_of(c), FLUX_RHS, q, sigma, nullptr, nullptr,
+    CU(c, c->ops->flux(c->g, c->p, c->tiles, inflow_of(c), FLUX_RHS, q, nullptr, sigma, nullptr, nullptr,
                        rhs, nullptr, c->sc, c->blockmax, &c->sc->err, c->st));
     prof_end(c);
     return IGR_OK;
@@ -829,8 +874,8 @@ igr_status igr_rk_combine(igr_ctx *c, const void *qn, const void *qs, const void
 {
     if (!c || !qn || !qs || !L || !out) return fail(c, IGR_ERR_INVALID_ARG, "null buffer");
     if (count < 0 || stage < 1 || stage > 3) return fail(c, IGR_ERR_INVALID_ARG, "bad count or stage");
-    if (!is_aligned(qn, c->ops->storage_bytes) || !is_aligned(qs, c->ops->storage_bytes) ||
-        !is_aligned(out, c->ops->storage_bytes) || !is_aligned(L, c->ops->compute_bytes))
+    if (!is_aligned(qn, c->ops->state_bytes) || !is_aligned(qs, c->ops->state_bytes) ||
+        !is_aligned(out, c->ops->state_bytes) || !is_aligned(L, c->ops->compute_bytes))
         return fail(c, IGR_ERR_INVALID_ARG, "buffers must be aligned to their element size");
     double w = stage == 1 ? 1.0 : stage == 2 ? 0.25 : 2.0 / 3.0;
     if (count == 0) return IGR_OK;
@@ -974,20 +1019,23 @@ igr_status igr_autotune(igr_ctx *c, int reps)
         // each kernel class writes only scratch: b, the other Sigma buffer, the stage-1 output
         for (int v = 0; v < nforms; v++) {
             t.vec_source = t.vec_jacobi = v;
-            s = time_launches(c, reps, [&] { return c->ops->source(c->g, c->p, t, inflow_of(c), c->q[0], c->b, c->st); }, &ms);
+            s = time_launches(c, reps, [&] {
+                return c->ops->source(c->g, c->p, t, inflow_of(c), c->q[0], nullptr, c->b, c->rho16, c->st);
+            }, &ms);
             if (s != IGR_OK) return s;
             if (ms < tbest[0]) { tbest[0] = ms; best.zc_source = t.zc_source; best.vec_source = v; }
             s = time_launches(c, reps, [&] {
                 // red-black: a half-sweep in place on a copy of Sigma in the stage-1 output buffer
+                const void *qj = c->inc ? c->rho16 : c->q[0];
                 return c->cfg.sigma_solver == SOLVER_RBGS
-                           ? c->ops->jacobi(c->g, c->p, t, c->q[0], c->b, c->q[1], c->q[1], 0, c->st)
-                           : c->ops->jacobi(c->g, c->p, t, c->q[0], c->b, sig, scratch, -1, c->st);
+                           ? c->ops->jacobi(c->g, c->p, t, qj, c->b, c->q[1], c->q[1], 0, c->st)
+                           : c->ops->jacobi(c->g, c->p, t, qj, c->b, sig, scratch, -1, c->st);
             }, &ms);
             if (s != IGR_OK) return s;
             if (ms < tbest[1]) { tbest[1] = ms; best.zc_jacobi = t.zc_jacobi; best.vec_jacobi = v; }
         }
         s = time_launches(c, reps, [&] {
-            return c->ops->flux(c->g, c->p, t, inflow_of(c), FLUX_STAGE1, c->q[0], sig, c->q[0], c->q[1],
+            return c->ops->flux(c->g, c->p, t, inflow_of(c), FLUX_STAGE1, c->q[0], nullptr, sig, c->q[0], c->q[1],
                                 nullptr, nullptr, c->sc, c->blockmax, &c->sc->err, c->st);
         }, &ms);
         if (s != IGR_OK) return s;
@@ -1009,9 +1057,11 @@ struct igr_batch {
     struct Host {  // host-side stepping state of one instance
         int cur, speed_nblocks;
         Tiles tiles;
+        void *q0;  // the current state buffer (the increment modes alternate two)
         bool operator==(const Host &o) const
         {
-            return cur == o.cur && speed_nblocks == o.speed_nblocks && tiles.zc_source == o.tiles.zc_source &&
+            return cur == o.cur && speed_nblocks == o.speed_nblocks && q0 == o.q0 &&
+                   tiles.zc_source == o.tiles.zc_source &&
                    tiles.zc_jacobi == o.tiles.zc_jacobi && tiles.zc_flux == o.tiles.zc_flux &&
                    tiles.vec_source == o.tiles.vec_source && tiles.vec_jacobi == o.tiles.vec_jacobi;
         }
@@ -1033,15 +1083,18 @@ static igr_status bfail(igr_batch *b, igr_status s, const char *msg)
 static std::vector<igr_batch::Host> host_state(const igr_batch *b)
 {
     std::vector<igr_batch::Host> h(b->inst.size());
-    for (size_t i = 0; i < h.size(); i++) h[i] = {b->inst[i]->cur, b->inst[i]->speed_nblocks, b->inst[i]->tiles};
+    for (size_t i = 0; i < h.size(); i++)
+        h[i] = {b->inst[i]->cur, b->inst[i]->speed_nblocks, b->inst[i]->tiles, b->inst[i]->q[0]};
     return h;
 }
 
 static void set_host_state(igr_batch *b, const std::vector<igr_batch::Host> &h)
 {
     for (size_t i = 0; i < h.size(); i++) {
-        b->inst[i]->cur = h[i].cur;
-        b->inst[i]->speed_nblocks = h[i].speed_nblocks;
+        igr_ctx *c = b->inst[i];
+        c->cur = h[i].cur;
+        c->speed_nblocks = h[i].speed_nblocks;
+        if (c->inc && c->q[0] != h[i].q0) std::swap(c->q[0], c->qalt);
     }
 }
 
@@ -1238,6 +1291,8 @@ igr_status igr_adjoint_step(igr_ctx *c, const void *q_n, const void *sigma_n, co
             !is_aligned(lam_sigma_np1, cb) || !is_aligned(lam_q_n, cb) || !is_aligned(lam_sigma_n, cb))
             return fail(c, IGR_ERR_INVALID_ARG, "buffers must be aligned to their element size");
     }
+    if (c->inc)
+        return fail(c, IGR_ERR_UNSUPPORTED, "the adjoint covers the modes that store the state in one type");
     if (c->p.order != 5 || c->cfg.sigma_solver != SOLVER_JACOBI || c->p.mu != 0.0 || c->p.zeta != 0.0)
         return fail(c, IGR_ERR_UNSUPPORTED,
                     "the adjoint covers the inviscid scheme with 5th-order faces and Jacobi sweeps");
@@ -1258,13 +1313,13 @@ igr_status igr_adjoint_step(igr_ctx *c, const void *q_n, const void *sigma_n, co
     const void *qs[3] = {q_n, A.qs[0], A.qs[1]};
     CU(c, cudaMemcpyAsync(it(0, 0), sigma_n, n * sb, cudaMemcpyDeviceToDevice, c->st));
     for (int st = 0; st < 3; st++) {
-        CU(c, o->source(c->g, c->p, c->tiles, inflow_of(c), qs[st], A.b, c->st));
+        CU(c, o->source(c->g, c->p, c->tiles, inflow_of(c), qs[st], nullptr, A.b, nullptr, c->st));
         for (int k = 0; k < S; k++)
             CU(c, o->jacobi(c->g, c->p, c->tiles, qs[st], A.b, it(st, k), it(st, k + 1), -1, c->st));
         if (st < 2) {
             CU(c, o->flux(c->g, c->p, c->tiles, inflow_of(c), st == 0 ? FLUX_STAGE1 : FLUX_STAGE2, qs[st],
-                          it(st, S), q_n, (void *)qs[st + 1], nullptr, nullptr, A.sc, c->blockmax, &A.sc->err,
-                          c->st));
+                          nullptr, it(st, S), q_n, (void *)qs[st + 1], nullptr, nullptr, A.sc, c->blockmax,
+                          &A.sc->err, c->st));
             CU(c, cudaMemcpyAsync(it(st + 1, 0), it(st, S), n * sb, cudaMemcpyDeviceToDevice, c->st));
         }
     }
@@ -1345,7 +1400,7 @@ igr_status igr_debug_bounds_hits(unsigned long long *hits, int clear)
 {
     if (!hits) return fail(nullptr, IGR_ERR_INVALID_ARG, "hits is NULL");
     unsigned long long sum = 0;
-    for (const Ops *o : {&ops_f64, &ops_f32, &ops_f16, &ops_bf16}) {
+    for (const Ops *o : {&ops_f64, &ops_f32, &ops_f16, &ops_bf16, &ops_f16inc, &ops_bf16inc}) {
         unsigned long long h = o->bounds_hits(clear);
         if (h == ~0ull) return fail(nullptr, IGR_ERR_UNSUPPORTED, "not a bounds-checking debug build");
         sum += h;

@@ -90,11 +90,15 @@ enum { FLUX_RHS = 0, FLUX_STAGE1 = 1, FLUX_STAGE2 = 2, FLUX_STAGE3 = 3 };
 // Kernel set of one storage type. Every entry enqueues on `st` and returns
 // the launch error (cudaGetLastError) without synchronising.
 struct Ops {
-    int storage_bytes;  // bytes per stored value
+    int storage_bytes;  // bytes per stored value (Sigma, b; the increments of the increment modes)
     int compute_bytes;  // bytes per arithmetic value (8 for FP64, else 4)
-    // b = alpha [tr(G^2) + tr(G)^2] from q
+    int state_bytes;    // bytes per value of the state q^n (the storage type; 4 in the increment modes)
+    // b = alpha [tr(G^2) + tr(G)^2] from the stage state q (+ increments qd in the
+    // increment modes, NULL in stage 1 and in every other mode); in the increment
+    // modes rho_out gets the stage density in the storage type, which the sweeps
+    // read as their q (NULL otherwise)
     cudaError_t (*source)(const Geom &, const Phys &, const Tiles &, const Inflow &,
-                          const void *q, void *b, cudaStream_t st);
+                          const void *q, const void *qd, void *b, void *rho_out, cudaStream_t st);
     // one Jacobi sweep s_out <- (b + beta sum c s_in) / (1/rho + beta sum c) with
     // colour < 0; with colour 0 or 1 one red-black Gauss-Seidel half-sweep in
     // place (s_in == s_out), updating the cells with (i + j + k) % 2 == colour
@@ -103,10 +107,13 @@ struct Ops {
     // flux divergence and RK stage (mode FLUX_STAGE*), or L(q; Sigma) into rhs (FLUX_RHS).
     // Stage 3 also writes the per-block maximum wave speed of its output to blockmax.
     // Stage 1 with base_out != NULL also copies its input qs there (the RK base of
-    // stages 2 and 3 when it lives in host memory).
+    // stages 2 and 3 when it lives in host memory). In the increment modes the
+    // stage input is qs (= q^n) plus the increments qd (stages 2 and 3; NULL in
+    // stage 1 and in every other mode), stages 1 and 2 write increments to out
+    // and stage 3 writes the FP32 state q^n+1 to out.
     cudaError_t (*flux)(const Geom &, const Phys &, const Tiles &, const Inflow &, int mode,
-                        const void *qs, const void *sig, const void *qn, void *out, void *rhs,
-                        void *base_out, const Scalars *sc, double *blockmax, int *err,
+                        const void *qs, const void *qd, const void *sig, const void *qn, void *out,
+                        void *rhs, void *base_out, const Scalars *sc, double *blockmax, int *err,
                         cudaStream_t st);
     // number of blocks of the flux launch (entries of blockmax it writes)
     long long (*flux_blocks)(const Geom &, const Tiles &);
@@ -114,7 +121,8 @@ struct Ops {
     cudaError_t (*speed)(const Geom &, const Phys &, const void *q, double *blockmax,
                          int *nblocks, cudaStream_t st);
     // out = qn + w ((qs - qn) + dt L) over n values, exactly as the flux
-    // kernel's epilogue stores it (L in the arithmetic type)
+    // kernel's epilogue stores it (L in the arithmetic type; in the increment
+    // modes the FP32 state update of stage 3 on FP32 arrays)
     cudaError_t (*rk_combine)(const void *qn, const void *qs, const void *L, void *out,
                               long long n, double dt, double w, cudaStream_t st);
 
@@ -158,7 +166,7 @@ struct Ops {
 // (A Sigma - b)^2, b^2; minima of rho and p; maximum |Sigma|
 enum { DIAG_PARTS = 10, DIAG_BLOCKS_MAX = 152 * 8 };
 
-extern const Ops ops_f64, ops_f32, ops_f16, ops_bf16;
+extern const Ops ops_f64, ops_f32, ops_f16, ops_bf16, ops_f16inc, ops_bf16inc;
 
 // shared by the host entry points (igr_api.cu, igr_noalloc.cu)
 const Ops *ops_for(int precision);             // kernel set of an igr_precision

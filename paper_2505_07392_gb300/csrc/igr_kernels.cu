@@ -28,6 +28,8 @@
 
 #include <stdio.h>
 
+#include <type_traits>
+
 #include "igr_internal.h"
 
 #ifndef IGR_STORAGE
@@ -47,6 +49,19 @@ template <> struct Num<__half> { using C = float; using A = double; };
 template <> struct Num<__nv_bfloat16> { using C = float; using A = double; };
 using C = Num<S>::C;
 using A = Num<S>::A;
+
+// Type of the conserved state q^n. It is the storage type, except in the
+// increment modes (IGR_BASE=float, with 16-bit S): there q^n is kept in FP32
+// and RK stages 1 and 2 store the 16-bit increments d_s = q_s - q^n, so a
+// stage reads its input as q_s = RN32(q^n + d_s) and the RK accumulation of
+// q^n never rounds to 16 bits. Sigma, b and the increments use S.
+#ifdef IGR_BASE
+using QB = IGR_BASE;
+constexpr bool kInc = true;
+#else
+using QB = S;
+constexpr bool kInc = false;
+#endif
 
 // Offsets inside one field are 32-bit (grids hold fewer than 2^32 cells);
 // each field has its own base pointer, so an address is one 32x32->64 step.
@@ -113,6 +128,8 @@ __device__ __forceinline__ int cks4(int c, int) { return c; }
 template <int N> struct Fin { const S *p[N]; };   // fields read
 template <int N> struct Fout { S *p[N]; };        // fields written
 struct Frhs { C *p[5]; };
+struct QBIn { const QB *p[5]; };                  // the state q^n (RK base)
+struct QBOut { QB *p[5]; };                       // a new state q^n+1
 
 // ------------------------------------------------------------ load/store
 __device__ __forceinline__ double ldc(const double *p) { return __ldg(p); }
@@ -128,6 +145,52 @@ __device__ __forceinline__ double cv(double v) { return v; }
 __device__ __forceinline__ float cv(float v) { return v; }
 __device__ __forceinline__ float cv(__half v) { return __half2float(v); }
 __device__ __forceinline__ float cv(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Reading the state of a stage: the base fields b (type QB) plus, in the
+// increment modes from stage 2 on, the increments d (type S). HASD says
+// whether increments are read; without them the state is the base itself.
+struct QIn {
+    const QB *b[5];
+    const S *d[5];
+};
+struct QRawInc {  // one raw state value of the increment modes
+    QB b;
+    S d;
+};
+template <bool INC> struct StateIO;
+template <> struct StateIO<false> {  // (used where the state has the storage type)
+    using Raw = S;
+    template <bool HASD> static __device__ __forceinline__ S ld(const QIn &q, int u, idx c)
+    {
+        return ldr(reinterpret_cast<const S *>(q.b[u]) + c);
+    }
+    template <bool HASD> static __device__ __forceinline__ C val(S r) { return cv(r); }
+};
+template <> struct StateIO<true> {
+    using Raw = QRawInc;
+    template <bool HASD> static __device__ __forceinline__ QRawInc ld(const QIn &q, int u, idx c)
+    {
+        QRawInc r;
+        r.b = __ldg(q.b[u] + c);
+        r.d = HASD ? ldr(q.d[u] + c) : S(0.0f);
+        return r;
+    }
+    // the stage value q_s = RN32(q^n + d_s) (q^n itself without increments)
+    template <bool HASD> static __device__ __forceinline__ C val(const QRawInc &r)
+    {
+        return HASD ? C(__fadd_rn(float(cv(r.b)), float(cv(r.d)))) : C(cv(r.b));
+    }
+};
+using QRaw = StateIO<kInc>::Raw;
+template <bool HASD> __device__ __forceinline__ QRaw ldqr(const QIn &q, int u, idx c)
+{
+    return StateIO<kInc>::ld<HASD>(q, u, c);
+}
+template <bool HASD> __device__ __forceinline__ C cvq(const QRaw &r) { return StateIO<kInc>::val<HASD>(r); }
+template <bool HASD> __device__ __forceinline__ C ldq(const QIn &q, int u, idx c)
+{
+    return cvq<HASD>(ldqr<HASD>(q, u, c));
+}
 
 // store v rounded to nearest even; returns the stored value in type C
 __device__ __forceinline__ double stc(double *p, double v) { *p = v; return v; }
@@ -479,12 +542,15 @@ __device__ __forceinline__ int zmap(int kk, const Geom &g)
 }
 
 // u = m / rho of the cell at in-plane offset f of plane kk (kk may leave the
-// domain through -z/+z: periodic wrap, zero-gradient clamp or the jet blend)
-__device__ __forceinline__ void col_u(const Fin<4> &q, const Geom &g, const C *W, const C *J, idx f,
-                                      int kk, C u[3])
+// domain through -z/+z: periodic wrap, zero-gradient clamp or the jet blend);
+// *rho_s gets the cell's (unblended) density
+template <bool HASD>
+__device__ __forceinline__ void col_u(const QIn &q, const Geom &g, const C *W, const C *J, idx f,
+                                      int kk, C u[3], C *rho_s = nullptr)
 {
     idx c = ck((idx)map_axis(kk, g.nz, g.bc[4], g.bc[5]) * (idx)g.plane + f, g.n);
-    C rho = ldc(q.p[0] + c), m0 = ldc(q.p[1] + c), m1 = ldc(q.p[2] + c), m2 = ldc(q.p[3] + c);
+    C rho = ldq<HASD>(q, 0, c), m0 = ldq<HASD>(q, 1, c), m1 = ldq<HASD>(q, 2, c), m2 = ldq<HASD>(q, 3, c);
+    if (rho_s) *rho_s = rho;
     if (kk < 0 && g.bc[4] == BC_INFLOW) {
         idx pl = (idx)g.plane;
         f = ck(f, g.plane);
@@ -520,9 +586,12 @@ __device__ __forceinline__ C source_b(const C (&D)[3][3], C alpha_s)
 }
 
 // grad u by central differences from a shared plane tile U (x, y) and the
-// column's registers (z); b from source_b
-__global__ void __launch_bounds__(BT) k_source(Fin<4> q, S *__restrict__ b, Geom g, C alpha_s,
-                                                const C *W, const C *J, int zc)
+// column's registers (z); b from source_b. In the increment modes the kernel
+// also stores the stage's density rounded to the storage type (rho_out),
+// which the Jacobi sweeps of the stage read.
+template <bool HASD>
+__global__ void __launch_bounds__(BT) k_source(QIn q, S *__restrict__ b, S *__restrict__ rho_out, Geom g,
+                                                C alpha_s, const C *W, const C *J, int zc)
 {
     __shared__ C U[3][HY][HX];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
@@ -545,27 +614,29 @@ __global__ void __launch_bounds__(BT) k_source(Fin<4> q, S *__restrict__ b, Geom
                    map_axis(x0 + lx - 1, g.nx, g.bc[0], g.bc[1]));
     }
     C um[3], u0[3], up[3];
-    col_u(q, g, W, J, f, k0 - 1, um);
-    col_u(q, g, W, J, f, k0, u0);
+    C rho0 = C(1), rhop = C(1);  // density of the column at k and k + 1 (increment modes)
+    col_u<HASD>(q, g, W, J, f, k0 - 1, um);
+    col_u<HASD>(q, g, W, J, f, k0, u0, &rho0);
     // raw values one iteration ahead (loads overlap the previous plane's work):
     // the column at k + 1 and the halo at k (planes >= 0 need no jet blend)
-    S nc[4], nh[4];
-    auto raw4 = [&](idx off, int kk, S v[4]) {
+    QRaw nc[4], nh[4];
+    auto raw4 = [&](idx off, int kk, QRaw v[4]) {
         idx c = ck((idx)zmap(kk, g) * pl + off, g.n);
 #pragma unroll
-        for (int a = 0; a < 4; a++) v[a] = ldr(q.p[a] + c);
+        for (int a = 0; a < 4; a++) v[a] = ldqr<HASD>(q, a, c);
     };
     raw4(f, k0 + 1, nc);
     if (hv) raw4(hf, k0, nh);
     for (int k = k0; k < k1; k++) {
-        C r = rcp(cv(nc[0]));
+        rhop = cvq<HASD>(nc[0]);
+        C r = rcp(rhop);
 #pragma unroll
-        for (int a = 0; a < 3; a++) up[a] = mul_rn(cv(nc[1 + a]), r);
+        for (int a = 0; a < 3; a++) up[a] = mul_rn(cvq<HASD>(nc[1 + a]), r);
         C hu[3];
         if (hv) {
-            C rh = rcp(cv(nh[0]));
+            C rh = rcp(cvq<HASD>(nh[0]));
 #pragma unroll
-            for (int a = 0; a < 3; a++) hu[a] = mul_rn(cv(nh[1 + a]), rh);
+            for (int a = 0; a < 3; a++) hu[a] = mul_rn(cvq<HASD>(nh[1 + a]), rh);
         }
         if (k + 1 < k1) {
             raw4(f, k + 2, nc);
@@ -587,12 +658,14 @@ __global__ void __launch_bounds__(BT) k_source(Fin<4> q, S *__restrict__ b, Geom
                 D[a][2] = up[a] - um[a];
             }
             stc(CKP(b + (idx)k * pl + (idx)(j * g.nx + i), b, g.n), source_b(D, alpha_s));
+            if constexpr (kInc) stc(CKP(rho_out + (idx)k * pl + (idx)(j * g.nx + i), rho_out, g.n), rho0);
         }
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             um[a] = u0[a];
             u0[a] = up[a];
         }
+        rho0 = rhop;
     }
 }
 
@@ -850,14 +923,62 @@ constexpr int NYH = 2 * BX, NXH = 2 * BY;   // 4-wide y-halo tasks, scalar x-hal
 
 // 4 raw values of field a at cells (x .. x+3) of row-plane offset rowoff:
 // one 4-wide load when the cells lie inside the row, mapped single loads otherwise
-__device__ __forceinline__ V4 ld4_mapped(const S *__restrict__ a, const Geom &g, idx rowoff, int x)
+template <class T>
+__device__ __forceinline__ Vec4<T> ld4_mapped(const T *__restrict__ a, const Geom &g, idx rowoff, int x)
 {
     if (x + VX <= g.nx) return ld4r(CKP4(a + rowoff + x, a, g.n));
-    S v[VX];
+    T v[VX];
 #pragma unroll
     for (int c = 0; c < VX; c++)
-        v[c] = ldr(CKP(a + rowoff + (idx)map_axis(x + c, g.nx, g.bc[0], g.bc[1]), a, g.n));
+        v[c] = __ldg(CKP(a + rowoff + (idx)map_axis(x + c, g.nx, g.bc[0], g.bc[1]), a, g.n));
     return pack4(v[0], v[1], v[2], v[3]);
+}
+
+// 4 raw state values (cells x .. x+3) and their stage values, as StateIO
+struct QRaw4Inc {
+    Vec4<QB> b;
+    V4 d;
+};
+template <bool INC> struct StateIO4;
+template <> struct StateIO4<false> {  // (used where the state has the storage type)
+    using Raw = V4;
+    template <bool HASD>
+    static __device__ __forceinline__ V4 ld(const QIn &q, int u, const Geom &g, idx rowoff, int x)
+    {
+        return ld4_mapped(reinterpret_cast<const S *>(q.b[u]), g, rowoff, x);
+    }
+    template <bool HASD> static __device__ __forceinline__ void val(const V4 &r, C o[4]) { cv4(r, o); }
+};
+template <> struct StateIO4<true> {
+    using Raw = QRaw4Inc;
+    template <bool HASD>
+    static __device__ __forceinline__ QRaw4Inc ld(const QIn &q, int u, const Geom &g, idx rowoff, int x)
+    {
+        QRaw4Inc r;
+        r.b = ld4_mapped(q.b[u], g, rowoff, x);
+        if constexpr (HASD) r.d = ld4_mapped(q.d[u], g, rowoff, x);
+        return r;
+    }
+    template <bool HASD> static __device__ __forceinline__ void val(const QRaw4Inc &r, C o[4])
+    {
+        cv4(r.b, o);
+        if constexpr (HASD) {
+            C d[4];
+            cv4(r.d, d);
+#pragma unroll
+            for (int c = 0; c < 4; c++) o[c] = C(__fadd_rn(float(o[c]), float(d[c])));
+        }
+    }
+};
+using QRaw4 = StateIO4<kInc>::Raw;
+template <bool HASD>
+__device__ __forceinline__ QRaw4 ldq4(const QIn &q, int u, const Geom &g, idx rowoff, int x)
+{
+    return StateIO4<kInc>::ld<HASD>(q, u, g, rowoff, x);
+}
+template <bool HASD> __device__ __forceinline__ void cvq4(const QRaw4 &r, C o[4])
+{
+    StateIO4<kInc>::val<HASD>(r, o);
 }
 
 __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : sizeof(S) == 4 ? 2 : 1) k_jacobi_v4(const S *__restrict__ q, const S *__restrict__ b,
@@ -1035,8 +1156,9 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : sizeof(S) == 4 ? 2 : 
 //   D_ab = u_a(i + e_b) - u_a(i - e_b),
 // which is Eq. igrelliptic's left side with G = D / (2 dx). k_source takes the
 // same differences and source_b, so both forms give the same bits.
-__global__ void __launch_bounds__(BT) k_source_v4(Fin<4> q, S *__restrict__ b, Geom g, C alpha_s,
-                                                   const C *W, const C *J, int zc)
+template <bool HASD>
+__global__ void __launch_bounds__(BT) k_source_v4(QIn q, S *__restrict__ b, S *__restrict__ rho_out, Geom g,
+                                                   C alpha_s, const C *W, const C *J, int zc)
 {
     __shared__ __align__(16) C U[3][HY][HXV];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
@@ -1067,24 +1189,27 @@ __global__ void __launch_bounds__(BT) k_source_v4(Fin<4> q, S *__restrict__ b, G
 
     // u = m / rho of 4 cells from raw values (products rounded before they
     // are differenced: equal neighbours give an exact 0)
-    auto u4 = [&](const V4 (&r)[4], C u[3][VX]) {
-        C rho[VX], m[VX], rr[VX];
-        cv4(r[0], rho);
+    auto u4 = [&](const QRaw4 (&r)[4], C u[3][VX], C rho[VX]) {
+        C m[VX], rr[VX];
+        cvq4<HASD>(r[0], rho);
 #pragma unroll
         for (int c = 0; c < VX; c++) rr[c] = rcp(rho[c]);
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            cv4(r[1 + a], m);
+            cvq4<HASD>(r[1 + a], m);
 #pragma unroll
             for (int c = 0; c < VX; c++) u[a][c] = mul_rn(m[c], rr[c]);
         }
     };
-    // u of the own 4 cells of plane kk (the jet blend below an inflow face)
-    auto own_u = [&](int kk, C u[3][VX]) {
+    // u of the own 4 cells of plane kk (the jet blend below an inflow face);
+    // rho gets their (unblended) densities
+    auto own_u = [&](int kk, C u[3][VX], C rho[VX]) {
         idx zb = (idx)zmap(kk, g) * pl + rowj;
         C v[4][VX];
 #pragma unroll
-        for (int f = 0; f < 4; f++) cv4(ld4_mapped(q.p[f], g, zb, i0), v[f]);
+        for (int f = 0; f < 4; f++) cvq4<HASD>(ldq4<HASD>(q, f, g, zb, i0), v[f]);
+#pragma unroll
+        for (int c = 0; c < VX; c++) rho[c] = v[0][c];
         if (kk < 0 && g.bc[4] == BC_INFLOW) {
 #pragma unroll
             for (int c = 0; c < VX; c++) {
@@ -1102,33 +1227,35 @@ __global__ void __launch_bounds__(BT) k_source_v4(Fin<4> q, S *__restrict__ b, G
         }
     };
     C um[3][VX], u0[3][VX], up[3][VX];
-    own_u(k0 - 1, um);
-    own_u(k0, u0);
+    C rho0[VX], rhop[VX];  // densities of the own cells at k and k + 1
+    own_u(k0 - 1, um, rhop);
+    own_u(k0, u0, rho0);
     // raw values one iteration ahead: own cells at k + 1, halo at k (planes >= 0)
-    V4 nc[4], nh[4];
-    S nxh[4];
+    QRaw4 nc[4], nh[4];
+    QRaw nxh[4];
     auto pre = [&](int kk) {
         idx pz = (idx)zmap(kk + 1, g) * pl + rowj;
 #pragma unroll
-        for (int f = 0; f < 4; f++) nc[f] = ld4_mapped(q.p[f], g, pz, i0);
+        for (int f = 0; f < 4; f++) nc[f] = ldq4<HASD>(q, f, g, pz, i0);
         if (htask == 0) {
 #pragma unroll
-            for (int f = 0; f < 4; f++) nh[f] = ld4_mapped(q.p[f], g, (idx)kk * pl + hrow, hx);
+            for (int f = 0; f < 4; f++) nh[f] = ldq4<HASD>(q, f, g, (idx)kk * pl + hrow, hx);
         } else if (htask == 1) {
 #pragma unroll
-            for (int f = 0; f < 4; f++) nxh[f] = ldr(CKP(q.p[f] + (idx)kk * pl + hrow + hx, q.p[f], g.n));
+            for (int f = 0; f < 4; f++) nxh[f] = ldqr<HASD>(q, f, ck((idx)kk * pl + hrow + hx, g.n));
         }
     };
     pre(k0);
     for (int k = k0; k < k1; k++) {
-        u4(nc, up);
+        u4(nc, up, rhop);
         C hu[3][VX];
         if (htask == 0) {
-            u4(nh, hu);
+            C hrho[VX];
+            u4(nh, hu, hrho);
         } else if (htask == 1) {
-            C r = rcp(cv(nxh[0]));
+            C r = rcp(cvq<HASD>(nxh[0]));
 #pragma unroll
-            for (int a = 0; a < 3; a++) hu[a][0] = mul_rn(cv(nxh[1 + a]), r);
+            for (int a = 0; a < 3; a++) hu[a][0] = mul_rn(cvq<HASD>(nxh[1 + a]), r);
         }
         if (k + 1 < k1) pre(k + 1);
         __syncthreads();  // readers of the previous plane are done
@@ -1167,6 +1294,7 @@ __global__ void __launch_bounds__(BT) k_source_v4(Fin<4> q, S *__restrict__ b, G
                 o[c] = source_b(D, alpha_s);
             }
             st4(CKP4(b + (idx)k * pl + (idx)(j * g.nx + i0), b, g.n), o);
+            if constexpr (kInc) st4(CKP4(rho_out + (idx)k * pl + (idx)(j * g.nx + i0), rho_out, g.n), rho0);
         }
 #pragma unroll
         for (int a = 0; a < 3; a++)
@@ -1175,6 +1303,8 @@ __global__ void __launch_bounds__(BT) k_source_v4(Fin<4> q, S *__restrict__ b, G
                 um[a][c] = u0[a][c];
                 u0[a][c] = up[a][c];
             }
+#pragma unroll
+        for (int c = 0; c < VX; c++) rho0[c] = rhop[c];
     }
 }
 
@@ -1371,12 +1501,20 @@ constexpr int FLUX_MAXREG = sizeof(C) == 8 ? 224 : 128;
 // Planes k0 - 3..k0 + 2 are filled before the loop (with the boundary index
 // mapping and, below an inflow face, the jet blend). Every plane is read from
 // global memory once per block; nothing relies on the L1 cache.
+//
+// In the increment modes the input q_s is read as RN32(q^n + d_s) (d_s from
+// stage 2 on), stages 1 and 2 store the 16-bit increment
+// d_{s+1} = RN16(w [(q_s - q^n) + dt L]) into `out`, and stage 3 stores the
+// FP32 state q^n + w [(q_s - q^n) + dt L] into `outb`.
 template <int mode, int ORD, bool VISC>
 __global__ void __maxnreg__(FLUX_MAXREG)
-    k_flux(Fin<6> in, Fin<5> qn, Fout<5> out, Frhs rhs, Fout<5> base_out, Geom g, C gamma,
-           C half_inv_dx, const Scalars *sc, double *blockmax, int *err, const C *W, const C *J,
-           int zc, int cz0, C mu, C lamv)
+    k_flux(QIn qin, const S *__restrict__ sig, QBIn qn, Fout<5> out, QBOut outb, Frhs rhs, Fout<5> base_out,
+           Geom g, C gamma, C half_inv_dx, const Scalars *sc, double *blockmax, int *err, const C *W,
+           const C *J, int zc, int cz0, C mu, C lamv)
 {
+    constexpr bool HASD = kInc && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3);
+    // field u of the stored input (u < 5: q, 5: Sigma) where the state has the storage type
+    auto fin = [&](int u) -> const S * { return u < 5 ? reinterpret_cast<const S *>(qin.b[u]) : sig; };
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *P = reinterpret_cast<C2 *>(smem_raw);        // [RING][3][PH][PW]
     C *FXb = reinterpret_cast<C *>(P + RING * TILE2); // [2][5][TY][TX+1]
@@ -1429,8 +1567,10 @@ __global__ void __maxnreg__(FLUX_MAXREG)
         for (int r = 0; r < LPT; r++)
             if (soff[r] >= 0) {
                 C v[6];
+                const idx c = ck(zb + goff[r], g.n);
 #pragma unroll
-                for (int u = 0; u < 6; u++) v[u] = ldc(CKP(in.p[u] + zb + goff[r], in.p[u], g.n));
+                for (int u = 0; u < 5; u++) v[u] = ldq<HASD>(qin, u, c);
+                v[5] = ldc(sig + c);
                 if (blend) {
                     C wf = C(1) - W[ck(goff[r], g.plane)];
 #pragma unroll
@@ -1444,19 +1584,28 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     // plane kk >= k0 + 3 of the pipeline: FP32/FP64 storage copies with
     // cp.async; 16-bit storage loads raw values into registers at `fetch`
     // and converts and stores them at `land`
-    S Rg[LPT][6];  // (unused with cp.async)
+    S Rg[LPT][6];     // (unused with cp.async and in the increment modes)
+    QRaw Rq[LPT][5];  // increment modes: raw q^n and d_s
+    S Rs[LPT];        // increment modes: raw Sigma
     auto fetch = [&](int kk, C2 *T) {
         const idx zb = (idx)zmap(kk, g) * pl;
 #pragma unroll
         for (int r = 0; r < LPT; r++)
             if (soff[r] >= 0) {
+                if constexpr (kInc) {
+                    const idx c = ck(zb + goff[r], g.n);
 #pragma unroll
-                for (int u = 0; u < 6; u++) {
-                    if constexpr (kAsyncTile)
-                        cp_async_elem(&T[(u >> 1) * PH * PW + cks(soff[r], PH * PW)].x + (u & 1),
-                                      CKP(in.p[u] + zb + goff[r], in.p[u], g.n));
-                    else
-                        Rg[r][u] = ldr(CKP(in.p[u] + zb + goff[r], in.p[u], g.n));
+                    for (int u = 0; u < 5; u++) Rq[r][u] = ldqr<HASD>(qin, u, c);
+                    Rs[r] = ldr(sig + c);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 6; u++) {
+                        if constexpr (kAsyncTile)
+                            cp_async_elem(&T[(u >> 1) * PH * PW + cks(soff[r], PH * PW)].x + (u & 1),
+                                          CKP(fin(u) + zb + goff[r], fin(u), g.n));
+                        else
+                            Rg[r][u] = ldr(CKP(fin(u) + zb + goff[r], fin(u), g.n));
+                    }
                 }
             }
         if constexpr (kAsyncTile) cp_async_commit();
@@ -1464,6 +1613,15 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     auto land = [&](C2 *T) {
         if constexpr (kAsyncTile) {
             cp_async_wait_all();
+        } else if constexpr (kInc) {
+#pragma unroll
+            for (int r = 0; r < LPT; r++)
+                if (soff[r] >= 0) {
+                    const int so = cks(soff[r], PH * PW);
+                    T[so] = pset(cvq<HASD>(Rq[r][0]), cvq<HASD>(Rq[r][1]));
+                    T[PH * PW + so] = pset(cvq<HASD>(Rq[r][2]), cvq<HASD>(Rq[r][3]));
+                    T[2 * PH * PW + so] = pset(cvq<HASD>(Rq[r][4]), cv(Rs[r]));
+                }
         } else {
 #pragma unroll
             for (int r = 0; r < LPT; r++)
@@ -1486,7 +1644,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     C smax = C(0);  // running wave-speed maximum (FP32 here: FP64 is slow on this GPU)
 
     C Fzm[5], Fzp[5];
-    S qnv[5];  // q^n of plane k - 1 (stages 2 and 3), loaded one iteration ahead
+    QB qnv[5];  // q^n of plane k - 1 (stages 2 and 3), loaded one iteration ahead
 
     // divergence and stage combination of plane kk (face buffers of parity kk)
     auto finish = [&](int kk, const C2 *T) {
@@ -1519,7 +1677,18 @@ __global__ void __maxnreg__(FLUX_MAXREG)
             C o[5], qb[5];
 #pragma unroll
             for (int u = 0; u < 5; u++) qb[u] = mode == FLUX_STAGE1 ? qsv[u] : cv(qnv[u]);
-            rk_store5(out, c, qb, qsv, Lv, dt32, dt, w32, wd, o);
+            if constexpr (kInc) {
+#pragma unroll
+                for (int u = 0; u < 5; u++) {
+                    const C inc = w32 * ((qsv[u] - qb[u]) + dt32 * Lv[u]);
+                    if (mode == FLUX_STAGE3)
+                        o[u] = stc(outb.p[u] + c, qb[u] + inc);  // q^n+1 in FP32
+                    else
+                        o[u] = stc(out.p[u] + c, inc);  // the increment d_s+1, rounded to 16 bits
+                }
+            } else {
+                rk_store5(out, c, qb, qsv, Lv, dt32, dt, w32, wd, o);
+            }
             nonfinite |= !isfinite((o[0] + o[1]) + (o[2] + o[3]) + o[4]);
             if (mode == FLUX_STAGE3) {
                 C sp = cell_speed(o[0], o[1], o[2], o[3], o[4], gamma, gm1);
@@ -1538,7 +1707,7 @@ __global__ void __maxnreg__(FLUX_MAXREG)
             if (k >= k0 && active && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3)) {
                 idx c = ck((idx)k * pl + own, g.n);
 #pragma unroll
-                for (int u = 0; u < 5; u++) qnv[u] = ldr(qn.p[u] + c);
+                for (int u = 0; u < 5; u++) qnv[u] = __ldg(qn.p[u] + c);
             }
             C2 sz[6][3];  // z-stencil: planes k - 2..k + 3 at this cell
 #pragma unroll
@@ -1616,20 +1785,21 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     }
 }
 
-// stand-alone stage combination (the flux kernel's epilogue) over n values
-__global__ void k_rk_combine(const S *__restrict__ qn, const S *__restrict__ qs,
-                             const C *__restrict__ L, S *__restrict__ out, long long n, double dt,
+// stand-alone stage combination (the flux kernel's epilogue) over n values;
+// in the increment modes the FP32 state update of stage 3 on FP32 arrays
+__global__ void k_rk_combine(const QB *__restrict__ qn, const QB *__restrict__ qs,
+                             const C *__restrict__ L, QB *__restrict__ out, long long n, double dt,
                              double wd)
 {
     C dt32 = C(dt), w32 = C(wd);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
          c += (long long)gridDim.x * blockDim.x) {
-        C a = ldc(qn + c), b = ldc(qs + c), l = L[c];
-        if constexpr (kNarrow) {
+        C a = cv(__ldg(qn + c)), b = cv(__ldg(qs + c)), l = L[c];
+        if constexpr (kNarrow && !kInc) {
             bool ok;
             S h = rk_narrow_one<S>(a, b, l, dt32, w32, ok);
             if (!ok) h = rk_fp64<S>(a, b, l, dt, wd);
-            out[c] = h;
+            reinterpret_cast<S *>(out)[c] = h;
         } else {
             out[c] = a + w32 * ((b - a) + dt32 * l);
         }
@@ -1639,7 +1809,7 @@ __global__ void k_rk_combine(const S *__restrict__ qn, const S *__restrict__ qs,
 // ---------------------------------------------------------- wave speed
 constexpr int SPEED_NT = 256, SPEED_MAXBLOCKS = 152 * 8;
 
-__global__ void __launch_bounds__(SPEED_NT) k_speed(const S *__restrict__ q, long long n, C gamma,
+__global__ void __launch_bounds__(SPEED_NT) k_speed(const QB *__restrict__ q, long long n, C gamma,
                                                      double *blockmax)
 {
     double m = 0.0;
@@ -1667,7 +1837,7 @@ __global__ void __launch_bounds__(SPEED_NT) k_speed(const S *__restrict__ q, lon
 constexpr int DIAG_NT = 256, DIAG_NV = DIAG_PARTS;
 
 // conserved value u at (i, j, kk) through the boundary mapping, in FP64
-__device__ __forceinline__ double dval(const S *q, const Geom &g, const C *W, const C *J, int i,
+__device__ __forceinline__ double dval(const QB *q, const Geom &g, const C *W, const C *J, int i,
                                        int j, int kk, int u)
 {
     int mi = map_axis(i, g.nx, g.bc[0], g.bc[1]), mj = map_axis(j, g.ny, g.bc[2], g.bc[3]);
@@ -1680,7 +1850,7 @@ __device__ __forceinline__ double dval(const S *q, const Geom &g, const C *W, co
 }
 
 // velocity u_a at (i, j, kk), FP64
-__device__ __forceinline__ void dvel(const S *q, const Geom &g, const C *W, const C *J, int i, int j,
+__device__ __forceinline__ void dvel(const QB *q, const Geom &g, const C *W, const C *J, int i, int j,
                                      int kk, double u[3])
 {
     double rho = dval(q, g, W, J, i, j, kk, 0);
@@ -1688,7 +1858,7 @@ __device__ __forceinline__ void dvel(const S *q, const Geom &g, const C *W, cons
     for (int a = 0; a < 3; a++) u[a] = dval(q, g, W, J, i, j, kk, 1 + a) / rho;
 }
 
-__global__ void __launch_bounds__(DIAG_NT) k_diag(const S *__restrict__ q, const S *__restrict__ sig,
+__global__ void __launch_bounds__(DIAG_NT) k_diag(const QB *__restrict__ q, const S *__restrict__ sig,
                                                   Geom g, double gamma, double alpha, double dx,
                                                   const C *W, const C *J, double *part)
 {
@@ -2100,18 +2270,34 @@ template <int N> Fin<N> fields_in(const void *base, long long n)
     return f;
 }
 
-cudaError_t launch_source(const Geom &g, const Phys &p, const Tiles &t, const Inflow &in,
-                          const void *q, void *b, cudaStream_t st)
+// state input: base fields q (type QB) and increments qd (type S, or NULL)
+QIn state_in(const void *q, const void *qd, long long n)
 {
+    QIn f;
+    for (int u = 0; u < 5; u++) {
+        f.b[u] = q ? (const QB *)q + u * n : nullptr;
+        f.d[u] = qd ? (const S *)qd + u * n : nullptr;
+    }
+    return f;
+}
+
+cudaError_t launch_source(const Geom &g, const Phys &p, const Tiles &t, const Inflow &in,
+                          const void *q, const void *qd, void *b, void *rho_out, cudaStream_t st)
+{
+    if (kInc != (rho_out != nullptr)) return cudaErrorInvalidValue;  // the stage density: increment modes only
+    if (!kInc && qd) return cudaErrorInvalidValue;
+    const QIn qi = state_in(q, qd, g.n);
+    const C as = C(p.alpha * 0.25 / (p.dx * p.dx));
+    const C *W = (const C *)in.W, *J = (const C *)in.J;
     if (t.vec_source && g.nx % VX == 0) {
-        k_source_v4<<<grid_of(g, TXV, BY, t.zc_source), dim3(BX, BY), 0, st>>>(
-            fields_in<4>(q, g.n), (S *)b, g, C(p.alpha * 0.25 / (p.dx * p.dx)), (const C *)in.W,
-            (const C *)in.J, t.zc_source);
+        auto kern = qd ? k_source_v4<kInc> : k_source_v4<false>;
+        kern<<<grid_of(g, TXV, BY, t.zc_source), dim3(BX, BY), 0, st>>>(qi, (S *)b, (S *)rho_out, g, as, W, J,
+                                                                       t.zc_source);
         return cudaGetLastError();
     }
-    k_source<<<grid_of(g, BX, BY, t.zc_source), dim3(BX, BY), 0, st>>>(
-        fields_in<4>(q, g.n), (S *)b, g, C(p.alpha * 0.25 / (p.dx * p.dx)), (const C *)in.W,
-        (const C *)in.J, t.zc_source);
+    auto kern = qd ? k_source<kInc> : k_source<false>;
+    kern<<<grid_of(g, BX, BY, t.zc_source), dim3(BX, BY), 0, st>>>(qi, (S *)b, (S *)rho_out, g, as, W, J,
+                                                                   t.zc_source);
     return cudaGetLastError();
 }
 
@@ -2137,19 +2323,28 @@ long long flux_blocks(const Geom &g, const Tiles &t)
 }
 
 cudaError_t launch_flux(const Geom &g, const Phys &p, const Tiles &t, const Inflow &in, int mode,
-                        const void *qs, const void *sig, const void *qn, void *out, void *rhs,
+                        const void *qs, const void *qd, const void *sig, const void *qn, void *out, void *rhs,
                         void *base_out, const Scalars *sc, double *blockmax, int *err, cudaStream_t st)
 {
+    // increments are read from stage 2 on, and only in the increment modes
+    if ((qd != nullptr) != (kInc && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3))) return cudaErrorInvalidValue;
+    if (kInc && base_out) return cudaErrorInvalidValue;
     size_t smem = flux_smem_bytes();
     auto go = [&](auto kern) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        Fin<6> fi = fields_in<6>(qs, g.n);
-        fi.p[5] = (const S *)sig;
+        const QIn fi = state_in(qs, qd, g.n);
+        QBIn fn;
         Fout<5> fo, fb;
+        QBOut fob;
         Frhs fr;
+        // the stage output: increments (S) for stages 1 and 2 of the increment
+        // modes, the FP32 state for their stage 3, else the stored state (S)
+        const bool out_is_state = !kInc || mode == FLUX_STAGE3;
         for (int u = 0; u < 5; u++) {
-            fo.p[u] = out ? (S *)out + u * g.n : nullptr;
+            fn.p[u] = qn ? (const QB *)qn + u * g.n : nullptr;
+            fo.p[u] = out && !(kInc && out_is_state) ? (S *)out + u * g.n : nullptr;
+            fob.p[u] = out && kInc && out_is_state ? (QB *)out + u * g.n : nullptr;
             fb.p[u] = base_out ? (S *)base_out + u * g.n : nullptr;
             fr.p[u] = rhs ? (C *)rhs + u * g.n : nullptr;
         }
@@ -2157,7 +2352,7 @@ cudaError_t launch_flux(const Geom &g, const Phys &p, const Tiles &t, const Infl
         dim3 gr = grid_of(g, TX, TY, t.zc_flux);
         const int cz0 = t.z_begin / t.zc_flux;
         if (t.z_end > 0) gr.z = (t.z_end - t.z_begin + t.zc_flux - 1) / t.zc_flux;
-        kern<<<gr, NT, smem, st>>>(fi, fields_in<5>(qn, g.n), fo, fr, fb, g, C(p.gamma), C(0.5 / p.dx), sc,
+        kern<<<gr, NT, smem, st>>>(fi, (const S *)sig, fn, fo, fob, fr, fb, g, C(p.gamma), C(0.5 / p.dx), sc,
                                    blockmax, err, (const C *)in.W, (const C *)in.J, t.zc_flux, cz0, C(p.mu),
                                    C(p.zeta - 2.0 * p.mu / 3.0));
         e = cudaGetLastError();
@@ -2199,7 +2394,7 @@ cudaError_t launch_speed(const Geom &g, const Phys &p, const void *q, double *bl
 {
     long long want = (g.n + SPEED_NT - 1) / SPEED_NT;
     int nb = (int)(want < SPEED_MAXBLOCKS ? want : SPEED_MAXBLOCKS);
-    k_speed<<<nb, SPEED_NT, 0, st>>>((const S *)q, g.n, C(p.gamma), blockmax);
+    k_speed<<<nb, SPEED_NT, 0, st>>>((const QB *)q, g.n, C(p.gamma), blockmax);
     *nblocks = nb;
     return cudaGetLastError();
 }
@@ -2209,7 +2404,7 @@ cudaError_t launch_rk_combine(const void *qn, const void *qs, const void *L, voi
 {
     long long want = (n + 255) / 256;
     int nb = (int)(want < 152 * 16 ? (want > 0 ? want : 1) : 152 * 16);
-    k_rk_combine<<<nb, 256, 0, st>>>((const S *)qn, (const S *)qs, (const C *)L, (S *)out, n, dt, w);
+    k_rk_combine<<<nb, 256, 0, st>>>((const QB *)qn, (const QB *)qs, (const C *)L, (QB *)out, n, dt, w);
     return cudaGetLastError();
 }
 
@@ -2279,7 +2474,7 @@ cudaError_t launch_diag(const Geom &g, const Phys &p, const Inflow &in, const vo
     long long nb = (g.n + DIAG_NT - 1) / DIAG_NT;
     int blocks = (int)(nb < DIAG_BLOCKS_MAX ? nb : DIAG_BLOCKS_MAX);
     *nblocks = blocks;
-    k_diag<<<blocks, DIAG_NT, 0, st>>>((const S *)q, (const S *)sig, g, p.gamma, p.alpha, p.dx,
+    k_diag<<<blocks, DIAG_NT, 0, st>>>((const QB *)q, (const S *)sig, g, p.gamma, p.alpha, p.dx,
                                         (const C *)in.W, (const C *)in.J, part);
     return cudaGetLastError();
 }
@@ -2317,7 +2512,7 @@ cudaError_t bounds_selftest(int *sink, cudaStream_t st)
 }  // namespace
 
 extern const Ops IGR_OPS = {
-    (int)sizeof(S), (int)sizeof(C), launch_source, launch_jacobi, launch_flux, flux_blocks,
+    (int)sizeof(S), (int)sizeof(C), (int)sizeof(QB), launch_source, launch_jacobi, launch_flux, flux_blocks,
     launch_speed, launch_rk_combine, launch_adj_rk, launch_adj_rhs, launch_adj_jacobi, launch_adj_rho,
     launch_adj_source, launch_adj_jets, launch_diag, bounds_hits, bounds_selftest,
 };

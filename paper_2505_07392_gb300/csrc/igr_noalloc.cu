@@ -86,6 +86,8 @@ igr_status igr_solve_sigma_noalloc(const igr_config *cfg, const void *q, void *s
     for (int f = 0; f < 6; f++)
         if (cfg->bc[f] == IGR_BC_INFLOW)
             return fail(IGR_ERR_UNSUPPORTED, "the allocation-free solve takes periodic and outflow faces only");
+    if (cfg->prec == IGR_F32_F16INC || cfg->prec == IGR_F32_BF16INC)
+        return fail(IGR_ERR_UNSUPPORTED, "the allocation-free solve takes the modes that store q in one type");
     const Ops *o = ops_for(cfg->prec);
     Geom g;
     g.nx = cfg->nx;
@@ -125,7 +127,7 @@ igr_status igr_solve_sigma_noalloc(const igr_config *cfg, const void *q, void *s
     // Both are fully written before they are read, so nothing needs clearing.
     void *b = base;
     void *other = (unsigned char *)base + (size_t)g.n * o->storage_bytes;
-    cudaError_t e = o->source(g, p, t, none, q, b, st);
+    cudaError_t e = o->source(g, p, t, none, q, nullptr, b, nullptr, st);
     if (e != cudaSuccess) return fail(IGR_ERR_CUDA, "source kernel launch", e);
     void *src = sigma_inout, *dst = other;
     if (cfg->sigma_solver == SOLVER_RBGS) {  // in place: red then black cells

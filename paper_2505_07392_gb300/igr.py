@@ -21,11 +21,13 @@ LIB_PATH = os.environ.get("IGR_LIBRARY") or os.path.join(HERE, "libigr.so")
 
 # enums of igr.h
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
-F64, F32, F32_F16STORE, F32_BF16STORE = range(4)
+F64, F32, F32_F16STORE, F32_BF16STORE, F32_F16INC, F32_BF16INC = range(6)
 DT_F64, DT_F32, DT_F16, DT_BF16 = range(4)
 KC_SOURCE, KC_JACOBI, KC_FLUX, KC_OTHER = range(4)
 
-PRECISIONS = {"f64": F64, "f32": F32, "f16": F32_F16STORE, "bf16": F32_BF16STORE}
+# f16inc / bf16inc: the state q^n in FP32, 16-bit stage increments, Sigma and b
+PRECISIONS = {"f64": F64, "f32": F32, "f16": F32_F16STORE, "bf16": F32_BF16STORE,
+              "f16inc": F32_F16INC, "bf16inc": F32_BF16INC}
 STATUS = {0: "IGR_OK", 1: "IGR_ERR_INVALID_ARG", 2: "IGR_ERR_OOM", 3: "IGR_ERR_CUDA",
           4: "IGR_ERR_NONFINITE", 5: "IGR_ERR_TIMEOUT", 6: "IGR_ERR_UNSUPPORTED"}
 
@@ -135,9 +137,16 @@ def memory_bytes(case, precision: str = "f32", host_rk_base: bool = False) -> in
 
 
 def storage_torch_dtype(precision: str):
+    """Element type of Sigma and b (and of the increments of the increment modes)."""
     import torch
     return {"f64": torch.float64, "f32": torch.float32, "f16": torch.float16,
-            "bf16": torch.bfloat16}[precision]
+            "bf16": torch.bfloat16, "f16inc": torch.float16, "bf16inc": torch.bfloat16}[precision]
+
+
+def state_torch_dtype(precision: str):
+    """Element type of the state q: the storage type, FP32 in the increment modes."""
+    import torch
+    return torch.float32 if precision.endswith("inc") else storage_torch_dtype(precision)
 
 
 def compute_torch_dtype(precision: str):
@@ -301,9 +310,9 @@ class Solver:
         return q_out
 
     def get_state(self, dtype=None):
-        """(q, sigma) as new CUDA tensors (default: the storage dtype)."""
+        """(q, sigma) as new CUDA tensors (default: the state dtype)."""
         import torch
-        dtype = dtype or storage_torch_dtype(self.precision)
+        dtype = dtype or state_torch_dtype(self.precision)
         q = torch.empty((5,) + self.shape, dtype=dtype, device=self.device)
         s = torch.empty(self.shape, dtype=dtype, device=self.device)
         self._check(lib().igr_get_state(self.h, C.c_void_p(q.data_ptr()), C.c_void_p(s.data_ptr()),
@@ -349,11 +358,12 @@ class Solver:
         self._check(lib().igr_get_flags(self.h, C.byref(f)))
         return f.value
 
-    # -- stand-alone operators on caller buffers (storage dtype, CUDA)
+    # -- stand-alone operators on caller buffers (CUDA; q in the state dtype,
+    #    sigma in the storage dtype)
     def solve_sigma(self, q, sigma, sweeps: int):
         """In place on sigma: b from q, then `sweeps` warm-started Jacobi sweeps."""
         self._check(lib().igr_solve_sigma(self.h, C.c_void_p(q.data_ptr()), C.c_void_p(sigma.data_ptr()),
-                                          int(sweeps), _dt_code(q.dtype)))
+                                          int(sweeps), _dt_code(sigma.dtype)))
         return sigma
 
     def rhs(self, q, sigma):
@@ -361,7 +371,7 @@ class Solver:
         import torch
         out = torch.empty((5,) + self.shape, dtype=compute_torch_dtype(self.precision), device=self.device)
         self._check(lib().igr_rhs(self.h, C.c_void_p(q.data_ptr()), C.c_void_p(sigma.data_ptr()),
-                                  C.c_void_p(out.data_ptr()), _dt_code(q.dtype)))
+                                  C.c_void_p(out.data_ptr()), _dt_code(sigma.dtype)))
         return out
 
     def rk_combine(self, qn, qs, L, stage: int, dt: float):

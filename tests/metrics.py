@@ -29,6 +29,23 @@ def field_errors(q, ref):
     return out
 
 
+def field_errors_torch(q, ref):
+    """field_errors for (5, ...) torch tensors on any device, evaluated there
+    in FP64 (for states too large to copy to the host)."""
+    import torch
+    q = q.reshape(5, -1)
+    ref = ref.reshape(5, -1)
+    mref = float(torch.linalg.vector_norm(ref[1:4].double()))
+    out = {}
+    for v, name in enumerate(FIELDS):
+        num = float(torch.linalg.vector_norm(q[v].double() - ref[v].double()))
+        den = float(torch.linalg.vector_norm(ref[v].double()))
+        if 1 <= v <= 3 and den < COMPONENT_FLOOR * mref:
+            den = mref
+        out[name] = num / den if den > 0 else num
+    return out
+
+
 def max_error(q, ref):
     return max(field_errors(q, ref).values())
 

@@ -61,7 +61,7 @@ def test_solve_sigma_with_sliced_tensors_takes_the_one_cell_forms(precision):
     q = torch.from_numpy(_state(CASE, 1)).to(st).cuda()
     s0 = (0.05 * torch.from_numpy(_state(CASE, 2)[0])).to(st).cuda()
     with igr.Solver(CASE, precision) as s:
-        assert s.kernel_forms() == (1, 1)  # rows of 64: the 4-cell forms by default
+        s.set_kernel_forms(1, 1)  # the 4-cell forms (rows of 64 default to the 1-cell forms)
         ref = s.solve_sigma(q, s0.clone(), 3).cpu()
         qu, su = _shifted(q, 1), _shifted(s0, 1)
         assert qu.data_ptr() % 16 != 0 and su.data_ptr() % 16 != 0

@@ -43,13 +43,13 @@ def _alone(case, q0, precision, steps, tiles=None, forms=None):
     return q, sig
 
 
-@pytest.mark.parametrize("precision", ["f32", "f16"])
+@pytest.mark.parametrize("precision", ["f32", "f16", "f16inc"])
 def test_batch_equals_single_bitwise(precision):
     import torch
     from paper_2505_07392_gb300 import igr
     cases = [inputs.tgv(16, instance=0), inputs.tgv(24, instance=1), inputs.tgv(20, instance=2),
              inputs.blast(12, sweeps=4)]
-    dt = igr.storage_torch_dtype(precision)
+    dt = igr.state_torch_dtype(precision)
     q0 = [torch.from_numpy(inputs.initial_state(c)).to(dt).cuda() for c in cases]
     torch.cuda.synchronize()
     steps = 5  # first step direct, then two captured graphs (Sigma parity) replayed
@@ -97,7 +97,7 @@ def _jets_case(n=40):
                 jets=[(0.3, 0.45, 4 * dx, 1.0, w, 2.0, 1.0), (0.7, 0.55, 3 * dx, 1.0, 0.9 * w, 2.0, 1.0)])
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16", "bf16", "f16inc", "bf16inc"])
 @pytest.mark.parametrize("kind", ["jets", "tgv_rbgs"])
 def test_kernel_forms_give_the_same_bits(precision, kind):
     """Every combination of the one- and four-cell forms of the source and
@@ -112,7 +112,7 @@ def test_kernel_forms_give_the_same_bits(precision, kind):
     else:
         case = replace(inputs.tgv(24, instance=3), sigma_solver=1)
         q0 = torch.from_numpy(inputs.initial_state(case))
-    q0 = q0.to(igr.storage_torch_dtype(precision)).cuda()
+    q0 = q0.to(igr.state_torch_dtype(precision)).cuda()
     with igr.Solver(case, precision) as s:
         assert s.kernel_forms() == (0, 0)
     ref = _alone(case, q0, precision, 3, forms=(0, 0))

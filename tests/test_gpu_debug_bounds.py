@@ -82,17 +82,18 @@ def test_no_index_out_of_bounds(debug_lib):
     cases += [(_jets(), "f32"), (_jets(24), "f16"),
               (replace(inputs.blast(20, sweeps=2), order=3, sigma_solver=1), "f32"),
               (replace(Case("v", 13, 8, 11, 1 / 13, alpha=1 / 169, sweeps=2, bc=(OUTFLOW,) * 6), mu=1e-3), "f64"),
-              (replace(_jets(16), mu=1e-3, zeta=1e-3), "bf16")]
+              (replace(_jets(16), mu=1e-3, zeta=1e-3), "bf16"), (_jets(24), "f16inc"),
+              (Case("odd", 36, 12, 8, 1 / 36, alpha=1 / 36 ** 2, sweeps=2, bc=(OUTFLOW,) * 6), "bf16inc")]
     for c, prec in cases:
         q0 = inputs.jet_initial_state(c) if c.jets else _state(c, c.nx)
-        dt = igr.storage_torch_dtype(prec)
+        dt, st = igr.state_torch_dtype(prec), igr.storage_torch_dtype(prec)
         for forms in ((0, 0), (1, 1)) if c.nx % 4 == 0 else ((0, 0),):
             with igr.Solver(c, prec) as s:
                 s.set_kernel_forms(*forms)
                 q = torch.from_numpy(q0).to(dt).cuda()
                 s.set_state(q)
                 s.step(2)
-                sig = torch.zeros(s.shape, dtype=dt, device="cuda")
+                sig = torch.zeros(s.shape, dtype=st, device="cuda")
                 s.solve_sigma(q, sig, 2)
                 s.rhs(q, sig)
                 s.diagnose()

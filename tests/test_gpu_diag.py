@@ -68,6 +68,7 @@ CASES = [
     ("tgv-bf16", lambda: inputs.tgv(12), "bf16", 1e-12),
     ("jets-f64", _jets, "f64", 1e-12),
     ("jets-f32", _jets, "f32", 1e-6),
+    ("blast-f16inc", lambda: inputs.blast(14, sweeps=4), "f16inc", 1e-12),
 ]
 
 

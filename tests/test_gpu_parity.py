@@ -1,7 +1,8 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
 same seeded inputs. Tolerances (relative L2 per conserved field): FP64
-1e-12, FP32 1e-5, FP16 storage 2e-3; BF16 storage (7-bit mantissa, 8x the
-FP16 rounding step) is held to 8 x 2e-3."""
+1e-12, FP32 1e-5, 16-bit storage 2e-3; BF16 storage of the whole state
+(7-bit mantissa, 8x the FP16 rounding step) is held to 8 x 2e-3. The
+increment forms (FP32 state, 16-bit stage increments) are held to 2e-3."""
 import math
 import os
 
@@ -15,7 +16,7 @@ from paper_2505_07392_gb300.inputs import INFLOW, OUTFLOW, PERIODIC, Case
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 2e-3, "bf16": 1.6e-2}
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 2e-3, "bf16": 1.6e-2, "f16inc": 2e-3, "bf16inc": 2e-3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -79,7 +80,7 @@ def test_density_wave_fp64_100_steps():
     assert np.max(np.abs(sg - so)) <= 1e-20
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16", "bf16", "f16inc", "bf16inc"])
 def test_blast(precision):
     """Spherical blast (outflow faces, 10 sweeps), downsized to 40^3 for the oracle."""
     c = inputs.blast(40, steps=30)
@@ -92,7 +93,7 @@ def test_blast(precision):
     assert math.isclose(tg, to, rel_tol=max(TOL[precision], 1e-13))
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16", "f16inc"])
 def test_jets_inflow(precision):
     """Two inflow jets on -z with outflow elsewhere."""
     c = small_jet_case()
@@ -133,8 +134,8 @@ def test_uniform_state_bitwise_all_precisions():
     q0 = np.stack([np.full(shape, x) for x in (rho, rho * u, rho * v, rho * w,
                                                 p / 0.4 + 0.5 * rho * (u * u + v * v + w * w))])
     from paper_2505_07392_gb300 import igr
-    for prec in ("f64", "f32", "f16", "bf16"):
-        dt = igr.storage_torch_dtype(prec)
+    for prec in ("f64", "f32", "f16", "bf16", "f16inc", "bf16inc"):
+        dt = igr.state_torch_dtype(prec)
         qs = torch.from_numpy(q0).to(dt).cuda()
         with igr.Solver(c, prec) as s:
             s.set_state(qs)
@@ -157,7 +158,7 @@ def test_periodic_conservation_fp64():
 
 # ------------------------------------------------------- stand-alone calls
 
-@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16inc"])
 def test_rhs(precision):
     import torch
     from paper_2505_07392_gb300 import igr
@@ -166,14 +167,14 @@ def test_rhs(precision):
     rng = np.random.Generator(np.random.Philox(9))
     sig = 0.05 * smooth_state(c, seed=6)[0] + 0.01 * rng.uniform(-1, 1, size=(c.nz, c.ny, c.nx))
     Lo = oracle.rhs(c, q0, sig)
-    dt = igr.storage_torch_dtype(precision)
+    qt, st = igr.state_torch_dtype(precision), igr.storage_torch_dtype(precision)
     with igr.Solver(c, precision) as s:
-        Lg = s.rhs(torch.from_numpy(q0).to(dt).cuda(), torch.from_numpy(sig).to(dt).cuda()).double().cpu().numpy()
+        Lg = s.rhs(torch.from_numpy(q0).to(qt).cuda(), torch.from_numpy(sig).to(st).cuda()).double().cpu().numpy()
     rel = np.linalg.norm((Lg - Lo).reshape(5, -1), axis=1) / np.linalg.norm(Lo.reshape(5, -1), axis=1)
     assert np.all(rel <= 10 * TOL[precision]), rel
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16inc"])
 @pytest.mark.parametrize("sweeps", [1, 4, 5])
 def test_solve_sigma(precision, sweeps):
     import torch
@@ -182,10 +183,10 @@ def test_solve_sigma(precision, sweeps):
     q0 = smooth_state(c, seed=7)
     s0 = 0.1 * smooth_state(c, seed=8)[0]
     so = oracle.jacobi(c, q0, oracle.source(c, q0), s0, sweeps)
-    dt = igr.storage_torch_dtype(precision)
+    qt, st = igr.state_torch_dtype(precision), igr.storage_torch_dtype(precision)
     with igr.Solver(c, precision) as s:
-        sg = torch.from_numpy(s0).to(dt).cuda()
-        s.solve_sigma(torch.from_numpy(q0).to(dt).cuda(), sg, sweeps)
+        sg = torch.from_numpy(s0).to(st).cuda()
+        s.solve_sigma(torch.from_numpy(q0).to(qt).cuda(), sg, sweeps)
         sg = sg.double().cpu().numpy()
     assert sigma_error(sg, so, 0) <= 10 * TOL[precision]
 
@@ -226,7 +227,7 @@ def test_nonfinite_flag():
         assert s.flags() == 0
 
 
-@pytest.mark.parametrize("precision", ["f64", "f16"])
+@pytest.mark.parametrize("precision", ["f64", "f16", "f16inc"])
 def test_checkpoint_resume_bitwise(precision):
     """Checkpoint/resume: the state (q and Sigma, the warm start) read out
     after 3 steps, through host memory, into a new context, which steps 3
@@ -234,8 +235,8 @@ def test_checkpoint_resume_bitwise(precision):
     import torch
     from paper_2505_07392_gb300 import igr
     c = small_jet_case()
-    dt = igr.storage_torch_dtype(precision)
-    npdt = {"f64": np.float64, "f16": np.float16}[precision]
+    dt = igr.state_torch_dtype(precision)
+    npdt = {"f64": np.float64, "f16": np.float16, "f16inc": np.float32}[precision]
     q0 = torch.from_numpy(inputs.jet_initial_state(c)).to(dt).cuda()
     with igr.Solver(c, precision) as s:
         s.set_state(q0)
@@ -280,20 +281,28 @@ def test_plume_many_steps_against_fp64_gpu():
     FP64 GPU run of the same inputs) on a 512 x 512 x 256 sub-size, where the
     FP64 state fits, after 100 steps (t = 0.0056): the FP64 run takes the CFL
     dt of each step and the other forms replay that dt sequence, so all reach
-    the same times; relative L2 per field, evaluated on the device in FP64.
-    (Later, from t ~ 0.008 on, the expansion above the outer jets loses
-    positivity under the unlimited reconstruction in every precision.)"""
+    the same times; relative L2 per field (rho, m_x, m_y, m_z, E), evaluated
+    on the device in FP64. (Later, from t ~ 0.008 on, the expansion above the
+    outer jets loses positivity under the unlimited reconstruction in every
+    precision.)
+
+    The increment forms (FP32 state, 16-bit stage increments, Sigma and b)
+    meet 2e-3 on every field. Storing the whole state in 16 bits does not on
+    the momentum: every step rounds q^n to 2^-11 (FP16) and 100 steps of such
+    roundings, amplified in the jets' shear layers, reach ~4e-3; those forms
+    are checked against their measured level, as regression guards only."""
     import torch
     from paper_2505_07392_gb300 import igr
     import bench
+    from metrics import field_errors_torch
     c = inputs.plume(512, 512, 256)
     nsteps = 100
     dts = []
     ref = None
     errs = {}
-    for prec in ("f64", "f32", "f16", "bf16"):
+    for prec in ("f64", "f32", "f16inc", "bf16inc", "f16", "bf16"):
         with igr.Solver(c, prec) as s:
-            s.set_state(bench.fill_initial_state(c, igr.storage_torch_dtype(prec), "cuda"))
+            s.set_state(bench.fill_initial_state(c, igr.state_torch_dtype(prec), "cuda"))
             for n in range(nsteps):
                 if prec == "f64":
                     dts.append(s.dt())
@@ -302,26 +311,22 @@ def test_plume_many_steps_against_fp64_gpu():
         if ref is None:
             ref = q
             continue
-        d = q - ref
-        e = {"rho": float(torch.linalg.vector_norm(d[0]) / torch.linalg.vector_norm(ref[0])),
-             "E": float(torch.linalg.vector_norm(d[4]) / torch.linalg.vector_norm(ref[4])),
-             "m": float(torch.linalg.vector_norm(d[1:4]) / torch.linalg.vector_norm(ref[1:4]))}
-        errs[prec] = e
-        del q, d
+        errs[prec] = field_errors_torch(q, ref)
+        del q
     print("plume 512x512x256, 100 steps, relative L2 vs FP64 GPU:", errs)
-    # Measured: FP16 rho 5.1e-4, E 1.7e-3, m 4.3e-3; BF16 5.0e-3, 1.7e-2, 4.6e-2;
-    # FP32 5e-8..5e-7. Each 16-bit store rounds to ~2^-11 (FP16) relative, and
-    # 300 stage stores accumulate like a random walk in the jets' momentum, so
-    # the 2e-3 target holds for rho and E but not for m at this horizon; the
-    # bounds below guard the measured accumulation against regressions.
+    assert max(errs["f32"].values()) <= 1e-5, errs
+    # the contract: 16-bit storage within 2e-3 of FP64 on every field
+    assert max(errs["f16inc"].values()) <= 2e-3, errs
+    assert max(errs["bf16inc"].values()) <= 2e-3, errs
+    # the whole state in 16 bits (measured: FP16 rho 5.1e-4, E 1.7e-3,
+    # momentum 4.3e-3 as one vector; BF16 8x that): regression guards
     assert errs["f16"]["rho"] <= 2e-3 and errs["f16"]["E"] <= 2e-3, errs
     assert max(errs["f16"].values()) <= 1e-2, errs
     assert max(errs["bf16"].values()) <= 1e-1, errs
-    assert max(errs["f32"].values()) <= 1e-5, errs
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("precision", ["f32", "f16"])
+@pytest.mark.parametrize("precision", ["f32", "f16", "f16inc"])
 def test_plume_full_size_sampled(precision):
     """The 1024 x 1024 x 2048 plume, one step at full size in the launch shape
     the benchmark times; sampled sub-boxes recomputed by the oracle. One
@@ -332,7 +337,7 @@ def test_plume_full_size_sampled(precision):
     full = inputs.plume()
     dt = 2.0e-5
     R = 3 * (full.sweeps + 3) + 1
-    st = igr.storage_torch_dtype(precision)
+    st = igr.state_torch_dtype(precision)
     with igr.Solver(full, precision) as s:
         zc = 128
         q = torch.empty((5, full.nz, full.ny, full.nx), dtype=st, device="cuda")
