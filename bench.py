@@ -189,12 +189,39 @@ def fill_initial_state(case, dtype, device):
     return q
 
 
-def words_per_cell(sweeps):
-    """Algorithmic words moved per cell by each kernel class over one step:
-    source 4 read + 1 write per stage; a Jacobi sweep reads Sigma, rho, b and
-    writes Sigma; the flux kernel reads q and Sigma, writes q, and reads the
-    RK base in stages 2 and 3."""
-    return {"source": 3 * 5, "jacobi": 3 * sweeps * 4, "flux": 11 + 16 + 16}
+DTYPE_LABEL = {"f16": "f32 compute, f16 storage", "bf16": "f32 compute, bf16 storage",
+               "f16inc": "f32 compute, f32 state, f16 stage increments/Sigma/b",
+               "bf16inc": "f32 compute, f32 state, bf16 stage increments/Sigma/b",
+               "f32": "f32", "f64": "f64"}
+
+
+def bytes_per_cell(sweeps, precision):
+    """Algorithmic bytes moved per cell by each kernel class over one step.
+
+    One storage type of w bytes: the source reads rho, m (4 words) and writes
+    b per stage; a Jacobi sweep reads Sigma, rho, b and writes Sigma; the
+    flux kernel reads q and Sigma and writes q (11 words in stage 1), and
+    also reads the RK base in stages 2 and 3 (16 words each).
+
+    The increment forms (FP32 state, 16-bit increments, Sigma, b and stage
+    density): the source reads rho, m of the state (16 B) and, in stages 2
+    and 3, their increments (8 B), and writes b and the stage density (4 B);
+    a sweep reads Sigma, the stage density and b and writes Sigma (8 B); the
+    flux kernel reads the state (20 B) and Sigma (2 B) in every stage, the
+    increments (10 B) in stages 2 and 3, and writes increments (10 B) in
+    stages 1 and 2 and the FP32 state (20 B) in stage 3; the RK base of its
+    own cell is the state already read for the stencil."""
+    if precision.endswith("inc"):
+        return {"source": 20 + 28 + 28, "jacobi": 3 * sweeps * 8, "flux": 32 + 42 + 52}
+    w = 8 if precision == "f64" else 4 if precision == "f32" else 2
+    return {"source": 3 * 5 * w, "jacobi": 3 * sweeps * 4 * w, "flux": (11 + 16 + 16) * w}
+
+
+def igr_state_bytes(case, precision):
+    """Bytes of the state q and Sigma of one case."""
+    qb = 8 if precision == "f64" else 4 if precision in ("f32", "f16inc", "bf16inc") else 2
+    sb = 8 if precision == "f64" else 4 if precision == "f32" else 2
+    return case.ncells * (5 * qb + sb)
 
 
 def run_form(case, precision, steps, warmup, sync_all, e2e_steps=0, host_rk_base=False):
@@ -295,14 +322,13 @@ def run_e2e(s, case, precision, steps, sync_all):
 
 
 def roofline_of(case, res, precision, peak, peak_kind):
-    wb = 8 if precision == "f64" else 4 if precision == "f32" else 2
-    wpc = words_per_cell(case.sweeps)
+    bpc = bytes_per_cell(case.sweeps, precision)
     per = {}
     for name in ("flux", "jacobi", "source"):
         n, ms = res["prof"][name]
         if n == 0 or ms <= 0:
             continue
-        algo_bytes = wpc[name] * wb * case.ncells * (res["prof_steps"])  # over the timed region
+        algo_bytes = bpc[name] * case.ncells * (res["prof_steps"])  # over the timed region
         gbs = algo_bytes / (ms * 1e-3) / 1e9
         per[name] = {"launches": n, "total_ms": ms, "avg_ms": ms / n,
                      "bytes_per_launch": algo_bytes / n, "achieved_gbs": gbs}
@@ -372,12 +398,13 @@ def run_batch(args, sync_all=lambda: None):
     return {"metric": METRIC, "value": cells * args.steps / (ms * 1e-3), "_cells": cells, "unit": "cell-updates/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": f"f32 compute, {args.precision} storage", "data": "synthetic",
+            "dtype": DTYPE_LABEL[args.precision], "data": "synthetic",
             "config": {"workload": f"{len(cases)} periodic Taylor-Green instances, edges "
                                    f"{sorted(set(c.nx for c in cases))}, {cells} cells, S=5",
                        "tiles": {f"{k[0]}^3": v[0] for k, v in tuned.items()},
                        "vec4_forms": {f"{k[0]}^3": v[1] for k, v in tuned.items()},
-                       "l2": "state %.2f GB" % (6 * cells * 2 / 1e9)}}
+                       "l2": "state q and Sigma %.2f GB" % (sum(igr_state_bytes(c, args.precision)
+                                                                 for c in cases) / 1e9)}}
 
 
 # ------------------------------------------------------------ CPU baseline
@@ -557,18 +584,17 @@ def main():
     if rank != 0:
         return
     launches = sum(v[0] for v in res["prof"].values())
-    wb = 2 if args.precision in ("f16", "bf16") else 4 if args.precision == "f32" else 8
+    state_gb = igr_state_bytes(full, args.precision) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"f16": "f32 compute, f16 storage", "bf16": "f32 compute, bf16 storage",
-                  "f32": "f32", "f64": "f64"}[args.precision],
+        "dtype": DTYPE_LABEL[args.precision],
         "data": "synthetic",
         "config": {"workload": workload, "cells": full.ncells, "precision": args.precision,
                    "sweeps": full.sweeps, "parallelism": f"replicas x{world}",
                    "rk_base": "host memory (NVLink-C2C)" if args.host_rk_base else "device",
-                   "l2": "inputs larger than L2 (state %.1f GB)" % (6 * full.ncells * wb / 1e9)},
+                   "l2": "inputs larger than L2 (state q and Sigma %.1f GB)" % state_gb},
         "gpu_launches": launches,
         "roofline": roof,
         "kernels": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in v.items()}

@@ -127,31 +127,52 @@ def _rollout_oracle(c, q0, nsteps, dt, k):
 
 
 def _four_jets(n):
+    """The 4-jet workload's geometry with its mirror symmetry broken (the
+    jets' radii and velocities differ by a few percent). With four identical
+    jets the x = 1/2 and y = 1/2 planes are faces where |u_L| + c_L and
+    |u_R| + c_R tie exactly in exact arithmetic while m_R - m_L does not
+    vanish: the LF speed's max is not differentiable there, and which side a
+    rounded evaluation favours differs between an FMA and a non-FMA build, so
+    the two adjoints differ by O(1) at those faces (a gradient ill-posed at
+    the 1e-5 level, not rounding)."""
+    from dataclasses import replace
     c = inputs.jets4(n)
-    return c
+    jets = [(j[0], j[1], j[2] * f, j[3], j[4] * g) + tuple(j[5:])
+            for j, f, g in zip(c.jets, (1.0, 0.9, 1.1, 0.95), (1.0, 1.04, 0.97, 1.02))]
+    return replace(c, jets=jets)
+
+
+def _with_background(c, q, U=(0.11, -0.07, 0.05)):
+    """q plus a uniform velocity U (pressure and density kept), so that no
+    velocity component is exactly 0 where |u| enters the LF speed."""
+    g = c.gamma
+    rho = q[0]
+    u = q[1:4] / rho + np.asarray(U)[:, None, None, None]
+    p = (g - 1) * (q[4] - 0.5 * (q[1] ** 2 + q[2] ** 2 + q[3] ** 2) / rho)
+    return np.stack([rho, rho * u[0], rho * u[1], rho * u[2], p / (g - 1) + 0.5 * rho * (u ** 2).sum(axis=0)])
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_jet_gradient_small(precision):
-    """Reduced jet workload (32^3, 4 Mach-2 jets, 12 steps, checkpoints every
-    5, pressure on the plane between layers 4 and 5, which the jets reach in
+    """Reduced jet workload (32^3, 4 Mach-2 jets of slightly different radii
+    and speeds in a uniform background flow, 12 steps, checkpoints every 5,
+    pressure on the plane between layers 4 and 5, which the jets reach in
     that time): dJ/dw by the GPU adjoint rollout against the oracle's FP64
-    adjoint and against central differences of the FP64 GPU forward."""
+    adjoint (FP64 1e-9, FP32 1e-4) and against central differences of the
+    FP64 GPU forward (1e-4)."""
     import torch
     from paper_2505_07392_gb300 import adjoint
     n, nsteps, dt = 32, 12, 2e-3
     c = _four_jets(n)
     k = 4
-    q0 = inputs.jet_initial_state(c)
+    q0 = _with_background(c, inputs.jet_initial_state(c))
     w0 = [j[4] for j in c.jets]
     J, gw = adjoint.rollout_jet_gradient(c, precision, torch.from_numpy(q0).cuda(), nsteps, dt, k,
                                          checkpoint_every=5)
     Jo, gwo = _rollout_oracle(c, q0, nsteps, dt, k)
     assert abs(J - Jo) <= (1e-10 if precision == "f64" else 1e-5) * abs(Jo)
-    assert max(abs(x) for x in gwo) > 1e-8  # the jets reach the plane (leakage alone is ~1e-15)
-    # the gradient is a small difference of larger terms (the four symmetric
-    # jets' oracle values already differ at the 5th digit), so 1e-4 for both
-    assert _rel(gw, gwo) <= 1e-4, (gw, gwo)
+    assert max(abs(x) for x in gwo) > 1e-6  # the jets reach the plane
+    assert _rel(gw, gwo) <= (1e-9 if precision == "f64" else 1e-4), (_rel(gw, gwo), gw, gwo)
     h = 1e-4
     for jn in range(len(w0)):
         vals = []
@@ -199,16 +220,16 @@ def test_igr_step_autograd_function():
 
 
 def test_jet_rollout_autograd_function():
-    """torch.autograd through JetRollout (16^3, 4 jets, 6 steps, checkpoints
-    every 4): the chain rule gives 3 dJ/dw of the direct checkpointed rollout
-    (its atomics reorder FP64 sums, hence 1e-9), and J, dJ/dw agree with the
-    oracle (the gradient, ~4e-6 against J ~ 1.4, is a small difference of
-    larger terms: 1e-5)."""
+    """torch.autograd through JetRollout (16^3, 4 jets of slightly different
+    radii and speeds in a background flow, 6 steps, checkpoints every 4): the
+    chain rule gives 3 dJ/dw of the direct checkpointed rollout (its atomics
+    reorder FP64 sums, hence 1e-9), and J, dJ/dw agree with the oracle's FP64
+    adjoint (1e-10, 1e-8)."""
     import torch
     from paper_2505_07392_gb300 import adjoint
     c = _four_jets(16)
     nsteps, dt, k = 6, 4e-3, 2
-    q0 = inputs.jet_initial_state(c)
+    q0 = _with_background(c, inputs.jet_initial_state(c))
     q0d = torch.from_numpy(q0).cuda()
     w = torch.tensor([j[4] for j in c.jets], dtype=torch.float64, requires_grad=True)
     J = adjoint.JetRollout.apply(w, c, "f64", q0d, nsteps, dt, k, 4)
@@ -220,7 +241,7 @@ def test_jet_rollout_autograd_function():
     Jo, gwo = _rollout_oracle(c, q0, nsteps, dt, k)
     assert abs(float(J) - Jo) <= 1e-10 * abs(Jo)
     assert max(abs(x) for x in gwo) > 1e-8
-    assert _rel(gwd, gwo) <= 1e-5
+    assert _rel(gwd, gwo) <= 1e-8, (_rel(gwd, gwo), gwd, gwo)
 
 
 @pytest.mark.slow
