@@ -224,7 +224,8 @@ def igr_state_bytes(case, precision):
     return case.ncells * (5 * qb + sb)
 
 
-def run_form(case, precision, steps, warmup, sync_all, e2e_steps=0, host_rk_base=False):
+def run_form(case, precision, steps, warmup, sync_all, e2e_steps=0, host_rk_base=False, forms=None,
+             autotune=False):
     """Time `steps` steps of one precision form; returns a result dict."""
     import torch
     from paper_2505_07392_gb300 import igr
@@ -236,6 +237,11 @@ def run_form(case, precision, steps, warmup, sync_all, e2e_steps=0, host_rk_base
         s.set_state(q)
         del q
         torch.cuda.synchronize()
+        if forms:
+            s.set_kernel_forms(*forms)
+        if autotune:
+            s.autotune(reps=2)
+        res["tiles"], res["forms"] = s.tiles(), s.kernel_forms()
         s.step(warmup)
         stream = s.stream
         sync_all()
@@ -493,6 +499,9 @@ def main():
     ap.add_argument("--sigma-solver", default="jacobi", choices=["jacobi", "rbgs"])
     ap.add_argument("--mu", type=float, default=0.0, help="shear viscosity (0: Euler)")
     ap.add_argument("--zeta", type=float, default=0.0, help="bulk viscosity")
+    ap.add_argument("--forms", type=int, nargs=2, default=None, metavar=("SOURCE", "JACOBI"),
+                    help="kernel forms of the source and Jacobi kernels (1: four cells per thread, 0: one)")
+    ap.add_argument("--autotune", action="store_true", help="autotune the launch shape before timing")
     ap.add_argument("--host-rk-base", action="store_true",
                     help="keep the RK base q^n in host memory (read over NVLink-C2C)")
     args = ap.parse_args()
@@ -562,7 +571,8 @@ def main():
         return
 
     res = run_form(full, args.precision, args.steps, args.warmup, sync_all,
-                   e2e_steps=args.e2e_steps, host_rk_base=args.host_rk_base)
+                   e2e_steps=args.e2e_steps, host_rk_base=args.host_rk_base, forms=args.forms,
+                   autotune=args.autotune)
     res["prof_steps"] = args.steps
     ms = max_over_ranks(res["ms"], world, "cuda")
     value = job_rate(full.ncells, args.steps, world, ms)
@@ -574,7 +584,8 @@ def main():
 
     plain = None
     if args.plain not in ("", "none") and args.plain != args.precision:
-        rp = run_form(full, args.plain, args.steps, args.warmup, sync_all, host_rk_base=args.host_rk_base)
+        rp = run_form(full, args.plain, args.steps, args.warmup, sync_all, host_rk_base=args.host_rk_base,
+                      forms=args.forms, autotune=args.autotune)
         rp["prof_steps"] = args.steps
         roof_p, _ = roofline_of(full, rp, args.plain, peak, peak_kind)
         ms_p = max_over_ranks(rp["ms"], world, "cuda")
@@ -594,6 +605,7 @@ def main():
         "config": {"workload": workload, "cells": full.ncells, "precision": args.precision,
                    "sweeps": full.sweeps, "parallelism": f"replicas x{world}",
                    "rk_base": "host memory (NVLink-C2C)" if args.host_rk_base else "device",
+                   "z_chunks": list(res["tiles"]), "kernel_forms": list(res["forms"]),
                    "l2": "inputs larger than L2 (state q and Sigma %.1f GB)" % state_gb},
         "gpu_launches": launches,
         "roofline": roof,

@@ -382,11 +382,15 @@ igr_status igr_autotune(igr_ctx *ctx, int reps);
  * forked from and joined into cuda_stream. igr_batch_instance(b, i) gives
  * instance i's context for igr_set_state / igr_get_state / igr_autotune /
  * igr_get_dt (not for igr_step or igr_step_host: step the batch). igr_step_batch advances
- * every instance by nsteps SSP-RK3 steps, each with its own CFL dt; a step
- * is captured once as a CUDA graph (one branch per instance, so instances
- * progress independently) and replayed, except the first step after a
- * set_state, which launches directly. Asynchronous on cuda_stream;
- * igr_sync_batch synchronises and reports any instance's error. */
+ * every instance by nsteps SSP-RK3 steps, each with its own CFL dt. A step
+ * runs each kernel class as one grouped launch over all instances' blocks
+ * (one launch per precision, kernel form and scheme among the instances, at
+ * most 64 instances each), so the GPU fills even when every instance is
+ * small; every instance keeps its own buffers, launch shape and dt, and its
+ * results are bitwise those of a context stepping alone. The step is
+ * captured once as a CUDA graph and replayed, except the first step after a
+ * set_state, which launches per instance directly. Asynchronous on
+ * cuda_stream; igr_sync_batch synchronises and reports any instance's error. */
 typedef struct igr_batch igr_batch;
 igr_status igr_create_batch(const igr_config *cfgs, int n, const igr_allocator *allocator,
                             void *cuda_stream, igr_batch **out);

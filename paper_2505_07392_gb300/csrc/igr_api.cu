@@ -23,6 +23,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <utility>
 #include <vector>
@@ -172,8 +173,33 @@ __global__ void k_convert(const void *src, int sdt, void *dst, int ddt, long lon
 __device__ __forceinline__ double nanmax_d(double a, double b) { return (a > b || a != a) ? a : b; }
 
 // dt from the per-block wave-speed maxima (or the fixed dt), t += dt
+__device__ __forceinline__ void finalize_dt_body(const double *blockmax, int nblocks, Scalars *sc, double cfl_dx,
+                                                 double fixed_dt);
 __global__ void k_finalize_dt(const double *blockmax, int nblocks, Scalars *sc, double cfl_dx,
                               double fixed_dt)
+{
+    finalize_dt_body(blockmax, nblocks, sc, cfl_dx, fixed_dt);
+}
+
+// the same for several instances at once, one block each
+struct DtInst {
+    const double *blockmax;
+    int nblocks;
+    Scalars *sc;
+    double cfl_dx;
+};
+struct DtGroup {
+    int count;
+    DtInst d[kGroupMax];
+};
+__global__ void k_finalize_dt_group(const __grid_constant__ DtGroup a)
+{
+    const DtInst &d = a.d[blockIdx.x];
+    finalize_dt_body(d.blockmax, d.nblocks, d.sc, d.cfl_dx, 0.0);
+}
+
+__device__ __forceinline__ void finalize_dt_body(const double *blockmax, int nblocks, Scalars *sc, double cfl_dx,
+                                                 double fixed_dt)
 {
     __shared__ double red[32];
     double m = 0.0;
@@ -1113,6 +1139,100 @@ static igr_status step_forkjoin(igr_batch *b)
     return IGR_OK;
 }
 
+// Inputs and output of stage `stage` of a context's step (see one_step).
+struct StageIO {
+    const void *qs, *qd, *qn;
+    void *out;
+};
+static StageIO stage_io(const igr_ctx *c, int stage)
+{
+    if (c->inc) {
+        if (stage == 1) return {c->q[0], nullptr, c->q[0], c->q[1]};
+        if (stage == 2) return {c->q[0], c->q[1], c->q[0], c->q[2]};
+        return {c->q[0], c->q[2], c->q[0], c->qalt};
+    }
+    if (stage == 1) return {c->q[0], nullptr, c->q[0], c->q[1]};
+    if (stage == 2) return {c->q[1], nullptr, c->q[0], c->q[2]};
+    return {c->q[2], nullptr, c->q[0], c->q[0]};
+}
+
+// One step of every instance with grouped launches: each kernel class runs
+// as one launch over all instances' blocks (per precision and kernel form),
+// instead of one launch per instance. Every instance keeps its own buffers,
+// launch shape and CFL dt, and runs the same kernel bodies on the same data
+// as a step of its own context, so the results are bitwise the same. Needs a
+// valid wave-speed reduction in every instance (not the first step after a
+// set_state).
+static igr_status step_grouped(igr_batch *b)
+{
+    cudaStream_t st = b->main;
+    const int n = (int)b->inst.size();
+    // instances of one precision run together; batches are usually uniform
+    std::vector<const Ops *> kinds;
+    for (igr_ctx *c : b->inst)
+        if (std::find(kinds.begin(), kinds.end(), c->ops) == kinds.end()) kinds.push_back(c->ops);
+    // dt of every instance from the wave-speed maxima of its last stage
+    for (int i0 = 0; i0 < n; i0 += kGroupMax) {
+        DtGroup a;
+        a.count = std::min(n - i0, (int)kGroupMax);
+        for (int i = 0; i < a.count; i++) {
+            igr_ctx *c = b->inst[i0 + i];
+            a.d[i] = {c->blockmax, c->speed_nblocks, c->sc, c->cfg.cfl * c->cfg.dx};
+        }
+        k_finalize_dt_group<<<a.count, 1024, 0, st>>>(a);
+        if (cudaGetLastError() != cudaSuccess) return bfail(b, IGR_ERR_CUDA, "grouped dt launch");
+    }
+    int maxs = 0;
+    for (igr_ctx *c : b->inst) maxs = std::max(maxs, c->cfg.sweeps);
+    std::vector<SourceCall> sc;
+    std::vector<JacobiCall> jc;
+    std::vector<FluxCall> fc;
+    for (int stage = 1; stage <= 3; stage++) {
+        for (const Ops *o : kinds) {
+            sc.clear();
+            for (igr_ctx *c : b->inst)
+                if (c->ops == o) {
+                    const StageIO io = stage_io(c, stage);
+                    sc.push_back({c->g, c->p, c->tiles, inflow_of(c), io.qs, io.qd, c->b, c->rho16});
+                }
+            if (o->source_group(sc.data(), (int)sc.size(), st) != cudaSuccess)
+                return bfail(b, IGR_ERR_CUDA, "grouped source launch");
+            // sweep k of every instance that makes at least k + 1 sweeps
+            for (int k = 0; k < maxs; k++)
+                for (int colour = -1; colour < 2; colour++) {
+                    jc.clear();
+                    for (igr_ctx *c : b->inst) {
+                        const bool rb = c->cfg.sigma_solver == SOLVER_RBGS;
+                        if (c->ops != o || k >= c->cfg.sweeps || (rb ? colour < 0 : colour >= 0)) continue;
+                        const void *qj = c->inc ? c->rho16 : stage_io(c, stage).qs;
+                        void *src = c->sig[c->cur], *dst = rb ? src : c->sig[1 - c->cur];
+                        jc.push_back({c->g, c->p, c->tiles, qj, c->b, src, dst});
+                    }
+                    if (jc.empty()) continue;
+                    if (o->jacobi_group(jc.data(), (int)jc.size(), colour, st) != cudaSuccess)
+                        return bfail(b, IGR_ERR_CUDA, "grouped sweep launch");
+                    for (igr_ctx *c : b->inst)  // Jacobi sweeps alternate the two Sigma buffers
+                        if (c->ops == o && k < c->cfg.sweeps && c->cfg.sigma_solver != SOLVER_RBGS && colour < 0)
+                            c->cur = 1 - c->cur;
+                }
+            fc.clear();
+            for (igr_ctx *c : b->inst)
+                if (c->ops == o) {
+                    const StageIO io = stage_io(c, stage);
+                    fc.push_back({c->g, c->p, c->tiles, inflow_of(c), io.qs, io.qd, c->sig[c->cur], io.qn, io.out,
+                                  c->sc, c->blockmax, &c->sc->err});
+                }
+            if (o->flux_group(fc.data(), (int)fc.size(), stage, st) != cudaSuccess)
+                return bfail(b, IGR_ERR_CUDA, "grouped flux launch");
+        }
+    }
+    for (igr_ctx *c : b->inst) {
+        if (c->inc) std::swap(c->q[0], c->qalt);
+        c->speed_nblocks = (int)c->ops->flux_blocks(c->g, c->tiles);
+    }
+    return IGR_OK;
+}
+
 static igr_status step_batch_steps(igr_batch *b, int nsteps);
 
 igr_status igr_create_batch(const igr_config *cfgs, int n, const igr_allocator *allocator,
@@ -1194,7 +1314,7 @@ static igr_status step_batch_steps(igr_batch *b, int nsteps)
             cudaGraph_t graph;
             if (cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
                 return bfail(b, IGR_ERR_CUDA, "begin capture");
-            igr_status s = step_forkjoin(b);
+            igr_status s = step_grouped(b);
             cudaError_t e = cudaStreamEndCapture(b->main, &graph);
             if (s != IGR_OK) return s;
             if (e != cudaSuccess) return bfail(b, IGR_ERR_CUDA, cudaGetErrorString(e));

@@ -160,7 +160,50 @@ struct Ops {
     // out-of-range index (checked, never dereferenced; sink is never written)
     unsigned long long (*bounds_hits)(int clear);
     cudaError_t (*bounds_selftest)(int *sink, cudaStream_t st);
+
+    // ---- grouped launches over independent instances (batches) ----
+    // One launch per kernel class covers every instance's blocks; each
+    // instance keeps its own grid, launch shape and buffers, so its results
+    // are bitwise those of its own launches. The launchers split the calls
+    // into groups a single launch can take (the same kernel form, at most
+    // kGroupMax instances).
+    cudaError_t (*source_group)(const struct SourceCall *calls, int n, cudaStream_t st);
+    cudaError_t (*jacobi_group)(const struct JacobiCall *calls, int n, int colour, cudaStream_t st);
+    cudaError_t (*flux_group)(const struct FluxCall *calls, int n, int mode, cudaStream_t st);
 };
+
+// One instance's arguments of a grouped launch (the same as the single
+// launch's, see Ops::source, Ops::jacobi, Ops::flux).
+struct SourceCall {
+    Geom g;
+    Phys p;
+    Tiles t;
+    Inflow in;
+    const void *q, *qd;
+    void *b, *rho_out;
+};
+struct JacobiCall {
+    Geom g;
+    Phys p;
+    Tiles t;
+    const void *q, *b, *s_in;
+    void *s_out;
+};
+struct FluxCall {
+    Geom g;
+    Phys p;
+    Tiles t;
+    Inflow in;
+    const void *qs, *qd, *sig, *qn;
+    void *out;
+    const Scalars *sc;
+    double *blockmax;
+    int *err;
+};
+
+// instances per grouped launch: their descriptors travel as one kernel
+// parameter (at most 32 KB)
+enum { kGroupMax = 64 };
 
 // layout of one block's diagnostics partials: sums of rho, mx, my, mz, E,
 // (A Sigma - b)^2, b^2; minima of rho and p; maximum |Sigma|

@@ -519,6 +519,22 @@ __device__ __forceinline__ void rk_store5(const Fout<5> &out, idx c, const C qn[
     }
 }
 
+// Block coordinates of a stage kernel's body: those of the launch itself, or,
+// in a grouped launch over several instances, the block's place in its own
+// instance's grid.
+struct BlockPos {
+    int x, y, z, gx, gy;
+    static __device__ __forceinline__ BlockPos of_launch()
+    {
+        return {(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x, (int)gridDim.y};
+    }
+    // the l-th block of a grid of gx x gy x * blocks
+    static __device__ __forceinline__ BlockPos of_index(int l, int gx, int gy)
+    {
+        return {l % gx, (l / gx) % gy, l / (gx * gy), gx, gy};
+    }
+};
+
 // --------------------------------------------- tiles of the 7-point kernels
 constexpr int BX = 32, BY = 8, BT = BX * BY;
 constexpr int HX = BX + 2, HY = BY + 2;   // plane tile with a halo of 1
@@ -590,15 +606,16 @@ __device__ __forceinline__ C source_b(const C (&D)[3][3], C alpha_s)
 // also stores the stage's density rounded to the storage type (rho_out),
 // which the Jacobi sweeps of the stage read.
 template <bool HASD>
-__global__ void __launch_bounds__(BT) k_source(QIn q, S *__restrict__ b, S *__restrict__ rho_out, Geom g,
-                                                C alpha_s, const C *W, const C *J, int zc)
+__device__ __forceinline__ void source_body(const QIn &q, S *__restrict__ b, S *__restrict__ rho_out,
+                                            const Geom &g, C alpha_s, const C *W, const C *J, int zc,
+                                            const BlockPos &bp)
 {
     __shared__ C U[3][HY][HX];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
-    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const int x0 = bp.x * BX, y0 = bp.y * BY;
     const int i = x0 + tx, j = y0 + ty;
     const bool active = i < g.nx && j < g.ny;
-    const int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
+    const int k0 = bp.z * zc, k1 = min(g.nz, k0 + zc);
     const idx pl = (idx)g.plane;
     // the own slot of the tile holds the mapped cell (it is a neighbour of
     // active cells even when this thread is outside the domain)
@@ -668,6 +685,13 @@ __global__ void __launch_bounds__(BT) k_source(QIn q, S *__restrict__ b, S *__re
         rho0 = rhop;
     }
 }
+template <bool HASD>
+__global__ void __launch_bounds__(BT) k_source(QIn q, S *__restrict__ b, S *__restrict__ rho_out, Geom g,
+                                                C alpha_s, const C *W, const C *J, int zc)
+{
+    source_body<HASD>(q, b, rho_out, g, alpha_s, W, J, zc, BlockPos::of_launch());
+}
+
 
 // --------------------------------------------------------------- Jacobi
 // One sweep s_out = (b + beta sum_f c_f s_nb) / (1/rho + beta sum_f c_f),
@@ -701,16 +725,16 @@ __device__ __forceinline__ C jacobi_cell(C r0, const C (&e)[6], const C (&rn)[6]
     return quot(add_rn(bv, off), diag);
 }
 
-__global__ void __launch_bounds__(BT) k_jacobi(const S *__restrict__ q, const S *__restrict__ b,
-                                                const S *sin, S *sout, Geom g, C beta, int zc,
-                                                int colour)
+__device__ __forceinline__ void jacobi_body(const S *__restrict__ q, const S *__restrict__ b, const S *sin,
+                                            S *sout, const Geom &g, C beta, int zc, int colour,
+                                            const BlockPos &bp)
 {
     __shared__ C R[HY][HX], SG[HY][HX];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
-    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const int x0 = bp.x * BX, y0 = bp.y * BY;
     const int i = x0 + tx, j = y0 + ty;
     const bool active = i < g.nx && j < g.ny;
-    const int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
+    const int k0 = bp.z * zc, k1 = min(g.nz, k0 + zc);
     const idx pl = (idx)g.plane;
     const idx f = (idx)(map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx + map_axis(i, g.nx, g.bc[0], g.bc[1]));
     const bool hv = tid < NHALO1;
@@ -779,6 +803,13 @@ __global__ void __launch_bounds__(BT) k_jacobi(const S *__restrict__ q, const S 
         r0 = rp; s0 = sp;
     }
 }
+__global__ void __launch_bounds__(BT) k_jacobi(const S *__restrict__ q, const S *__restrict__ b,
+                                                const S *sin, S *sout, Geom g, C beta, int zc,
+                                                int colour)
+{
+    jacobi_body(q, b, sin, sout, g, beta, zc, colour, BlockPos::of_launch());
+}
+
 
 // Vector form of the sweep for rows whose length is a multiple of 4: each
 // thread owns 4 consecutive cells of a row (one 4-wide load/store per field),
@@ -981,17 +1012,17 @@ template <bool HASD> __device__ __forceinline__ void cvq4(const QRaw4 &r, C o[4]
     StateIO4<kInc>::val<HASD>(r, o);
 }
 
-__global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : sizeof(S) == 4 ? 2 : 1) k_jacobi_v4(const S *__restrict__ q, const S *__restrict__ b,
-                                                   const S *sin, S *sout, Geom g, C beta, int zc,
-                                                   int colour)
+__device__ __forceinline__ void jacobi_v4_body(const S *__restrict__ q, const S *__restrict__ b, const S *sin,
+                                               S *sout, const Geom &g, C beta, int zc, int colour,
+                                               const BlockPos &bp)
 {
     __shared__ __align__(16) C R[HY][HXV];
     __shared__ __align__(16) C SG[HY][HXV];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
-    const int x0 = blockIdx.x * TXV, y0 = blockIdx.y * BY;
+    const int x0 = bp.x * TXV, y0 = bp.y * BY;
     const int i0 = x0 + VX * tx, j = y0 + ty;
     const bool active = i0 < g.nx && j < g.ny;
-    const int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
+    const int k0 = bp.z * zc, k1 = min(g.nz, k0 + zc);
     const idx pl = (idx)g.plane;
     const idx rowj = (idx)(map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx);
     // halo tasks: 4-wide cells of the rows above/below the tile, then single
@@ -1145,6 +1176,14 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : sizeof(S) == 4 ? 2 : 
         }
     }
 }
+constexpr int JACOBI_V4_BLOCKS = sizeof(S) == 2 ? 3 : sizeof(S) == 4 ? 2 : 1;  // resident per SM
+__global__ void __launch_bounds__(BT, JACOBI_V4_BLOCKS) k_jacobi_v4(const S *__restrict__ q, const S *__restrict__ b,
+                                                                  const S *sin, S *sout, Geom g, C beta, int zc,
+                                                                  int colour)
+{
+    jacobi_v4_body(q, b, sin, sout, g, beta, zc, colour, BlockPos::of_launch());
+}
+
 
 // Vector form of the source for rows whose length is a multiple of 4, laid
 // out like k_jacobi_v4: each thread owns 4 consecutive cells of a row (one
@@ -1157,15 +1196,16 @@ __global__ void __launch_bounds__(BT, sizeof(S) == 2 ? 3 : sizeof(S) == 4 ? 2 : 
 // which is Eq. igrelliptic's left side with G = D / (2 dx). k_source takes the
 // same differences and source_b, so both forms give the same bits.
 template <bool HASD>
-__global__ void __launch_bounds__(BT) k_source_v4(QIn q, S *__restrict__ b, S *__restrict__ rho_out, Geom g,
-                                                   C alpha_s, const C *W, const C *J, int zc)
+__device__ __forceinline__ void source_v4_body(const QIn &q, S *__restrict__ b, S *__restrict__ rho_out,
+                                               const Geom &g, C alpha_s, const C *W, const C *J, int zc,
+                                               const BlockPos &bp)
 {
     __shared__ __align__(16) C U[3][HY][HXV];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
-    const int x0 = blockIdx.x * TXV, y0 = blockIdx.y * BY;
+    const int x0 = bp.x * TXV, y0 = bp.y * BY;
     const int i0 = x0 + VX * tx, j = y0 + ty;
     const bool active = i0 < g.nx && j < g.ny;
-    const int k0 = blockIdx.z * zc, k1 = min(g.nz, k0 + zc);
+    const int k0 = bp.z * zc, k1 = min(g.nz, k0 + zc);
     const idx pl = (idx)g.plane;
     const idx rowj = (idx)(map_axis(j, g.ny, g.bc[2], g.bc[3]) * g.nx);
     // halo tasks: 4-wide cells of the rows above/below the tile, then single
@@ -1307,6 +1347,17 @@ __global__ void __launch_bounds__(BT) k_source_v4(QIn q, S *__restrict__ b, S *_
         for (int c = 0; c < VX; c++) rho0[c] = rhop[c];
     }
 }
+// the increment modes' 4-cell source holds raw FP32 values and 16-bit
+// increments one plane ahead: two blocks per SM (a few spilled registers)
+// against one without the bound
+constexpr int SOURCE_V4_BLOCKS = kInc ? 2 : 1;
+template <bool HASD>
+__global__ void __launch_bounds__(BT, SOURCE_V4_BLOCKS) k_source_v4(QIn q, S *__restrict__ b, S *__restrict__ rho_out, Geom g,
+                                                   C alpha_s, const C *W, const C *J, int zc)
+{
+    source_v4_body<HASD>(q, b, rho_out, g, alpha_s, W, J, zc, BlockPos::of_launch());
+}
+
 
 // ----------------------------------------------------------------- flux
 // Block of TY + 1 warps over a TX x TY tile of columns. Warps 0..TY-1 own a
@@ -1507,10 +1558,11 @@ constexpr int FLUX_MAXREG = sizeof(C) == 8 ? 224 : 128;
 // d_{s+1} = RN16(w [(q_s - q^n) + dt L]) into `out`, and stage 3 stores the
 // FP32 state q^n + w [(q_s - q^n) + dt L] into `outb`.
 template <int mode, int ORD, bool VISC>
-__global__ void __maxnreg__(FLUX_MAXREG)
-    k_flux(QIn qin, const S *__restrict__ sig, QBIn qn, Fout<5> out, QBOut outb, Frhs rhs, Fout<5> base_out,
-           Geom g, C gamma, C half_inv_dx, const Scalars *sc, double *blockmax, int *err, const C *W,
-           const C *J, int zc, int cz0, C mu, C lamv)
+__device__ __forceinline__ void flux_body(const QIn &qin, const S *__restrict__ sig, const QBIn &qn,
+                                          const Fout<5> &out, const QBOut &outb, const Frhs &rhs,
+                                          const Fout<5> &base_out, const Geom &g, C gamma, C half_inv_dx,
+                                          const Scalars *sc, double *blockmax, int *err, const C *W,
+                                          const C *J, int zc, int cz0, C mu, C lamv, const BlockPos &bp)
 {
     constexpr bool HASD = kInc && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3);
     // field u of the stored input (u < 5: q, 5: Sigma) where the state has the storage type
@@ -1520,8 +1572,8 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     C *FXb = reinterpret_cast<C *>(P + RING * TILE2); // [2][5][TY][TX+1]
     C *FYb = FXb + 2 * NFX;                           // [2][5][TY+1][TX]
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int cz = cz0 + blockIdx.z;  // z-chunk (a launch may cover chunks cz0.. only)
+    const int x0 = bp.x * TX, y0 = bp.y * TY;
+    const int cz = cz0 + bp.z;  // z-chunk (a launch may cover chunks cz0.. only)
     const int k0 = cz * zc, k1 = min(g.nz, k0 + zc);
     const bool rowwarp = w < TY;  // warp-uniform
     const int i = x0 + lane, j = y0 + (rowwarp ? w : 0);
@@ -1781,9 +1833,19 @@ __global__ void __maxnreg__(FLUX_MAXREG)
     if (mode == FLUX_STAGE3) {
         double m = block_max<NT>(double(smax));
         if (tid == 0)
-            blockmax[(cz * (long long)gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = m;
+            blockmax[(cz * (long long)bp.gy + bp.y) * bp.gx + bp.x] = m;
     }
 }
+template <int mode, int ORD, bool VISC>
+__global__ void __maxnreg__(FLUX_MAXREG)
+    k_flux(QIn qin, const S *__restrict__ sig, QBIn qn, Fout<5> out, QBOut outb, Frhs rhs, Fout<5> base_out,
+           Geom g, C gamma, C half_inv_dx, const Scalars *sc, double *blockmax, int *err, const C *W,
+           const C *J, int zc, int cz0, C mu, C lamv)
+{
+    flux_body<mode, ORD, VISC>(qin, sig, qn, out, outb, rhs, base_out, g, gamma, half_inv_dx, sc, blockmax, err,
+                               W, J, zc, cz0, mu, lamv, BlockPos::of_launch());
+}
+
 
 // stand-alone stage combination (the flux kernel's epilogue) over n values;
 // in the increment modes the FP32 state update of stage 3 on FP32 arrays
@@ -2257,6 +2319,95 @@ __global__ void k_adj_jets(const double *jets, const C *lamJ, double *gw, int nx
     if (threadIdx.x == 0) gw[blockIdx.x] += red[0];
 }
 
+// ------------------------------------------------- grouped launches
+// One launch covers the blocks of several independent instances: block b
+// belongs to the instance whose first block blk0 is the largest <= b, and
+// runs the instance's own body at its place in the instance's own grid.
+struct SourceInst {
+    QIn q;
+    S *b, *rho_out;
+    Geom g;
+    C alpha_s;
+    const C *W, *J;
+    int zc, gx, gy, blk0;
+};
+struct JacobiInst {
+    const S *q, *b, *sin;
+    S *sout;
+    Geom g;
+    C beta;
+    int zc, gx, gy, blk0;
+};
+struct FluxInst {
+    QIn qin;
+    const S *sig;
+    QBIn qn;
+    Fout<5> out;
+    QBOut outb;
+    Geom g;
+    C gamma, half_inv_dx, mu, lamv;
+    const Scalars *sc;
+    double *blockmax;
+    int *err;
+    const C *W, *J;
+    int zc, gx, gy, blk0;
+};
+template <class I> struct Group {
+    int count;
+    I d[kGroupMax];
+};
+static_assert(sizeof(Group<FluxInst>) <= 32000, "grouped launch descriptors exceed the kernel parameter space");
+
+// index of the instance that owns block b (blk0 ascending, d[0].blk0 = 0)
+template <class I> __device__ __forceinline__ int group_find(const Group<I> &a, int b)
+{
+    int lo = 0, hi = a.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.d[mid].blk0 <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <bool HASD>
+__global__ void __launch_bounds__(BT) k_source_group(const __grid_constant__ Group<SourceInst> a)
+{
+    const SourceInst &d = a.d[group_find(a, blockIdx.x)];
+    source_body<HASD>(d.q, d.b, d.rho_out, d.g, d.alpha_s, d.W, d.J, d.zc,
+                      BlockPos::of_index(blockIdx.x - d.blk0, d.gx, d.gy));
+}
+template <bool HASD>
+__global__ void __launch_bounds__(BT, SOURCE_V4_BLOCKS) k_source_v4_group(const __grid_constant__ Group<SourceInst> a)
+{
+    const SourceInst &d = a.d[group_find(a, blockIdx.x)];
+    source_v4_body<HASD>(d.q, d.b, d.rho_out, d.g, d.alpha_s, d.W, d.J, d.zc,
+                         BlockPos::of_index(blockIdx.x - d.blk0, d.gx, d.gy));
+}
+__global__ void __launch_bounds__(BT) k_jacobi_group(const __grid_constant__ Group<JacobiInst> a, int colour)
+{
+    const JacobiInst &d = a.d[group_find(a, blockIdx.x)];
+    jacobi_body(d.q, d.b, d.sin, d.sout, d.g, d.beta, d.zc, colour,
+                BlockPos::of_index(blockIdx.x - d.blk0, d.gx, d.gy));
+}
+__global__ void __launch_bounds__(BT, JACOBI_V4_BLOCKS) k_jacobi_v4_group(const __grid_constant__ Group<JacobiInst> a,
+                                                                         int colour)
+{
+    const JacobiInst &d = a.d[group_find(a, blockIdx.x)];
+    jacobi_v4_body(d.q, d.b, d.sin, d.sout, d.g, d.beta, d.zc, colour,
+                   BlockPos::of_index(blockIdx.x - d.blk0, d.gx, d.gy));
+}
+template <int mode, int ORD, bool VISC>
+__global__ void __maxnreg__(FLUX_MAXREG) k_flux_group(const __grid_constant__ Group<FluxInst> a)
+{
+    const FluxInst &d = a.d[group_find(a, blockIdx.x)];
+    const Frhs none_rhs = {};
+    const Fout<5> none_base = {};
+    flux_body<mode, ORD, VISC>(d.qin, d.sig, d.qn, d.out, d.outb, none_rhs, none_base, d.g, d.gamma,
+                               d.half_inv_dx, d.sc, d.blockmax, d.err, d.W, d.J, d.zc, 0, d.mu, d.lamv,
+                               BlockPos::of_index(blockIdx.x - d.blk0, d.gx, d.gy));
+}
+
 // ------------------------------------------------------------ launchers
 dim3 grid_of(const Geom &g, int bx, int by, int zc)
 {
@@ -2389,6 +2540,157 @@ cudaError_t launch_flux(const Geom &g, const Phys &p, const Tiles &t, const Infl
                    k_flux<FLUX_STAGE2, 5, false>, k_flux<FLUX_STAGE3, 5, false>);
 }
 
+// ---- grouped launches: calls are split by kernel form and in chunks of
+// kGroupMax; each chunk is one launch over all its instances' blocks
+
+// run fn(first, count) over the runs of consecutive calls with equal key(call)
+template <class T, class K, class F>
+cudaError_t by_runs(const T *calls, int n, K key, F fn)
+{
+    for (int i = 0; i < n;) {
+        int j = i + 1;
+        while (j < n && j - i < kGroupMax && key(calls[j]) == key(calls[i])) j++;
+        cudaError_t e = fn(calls + i, j - i);
+        if (e != cudaSuccess) return e;
+        i = j;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_source_group(const SourceCall *calls, int n, cudaStream_t st)
+{
+    for (int i = 0; i < n; i++)
+        if ((kInc != (calls[i].rho_out != nullptr)) || (!kInc && calls[i].qd)) return cudaErrorInvalidValue;
+    auto vec = [](const SourceCall &c) { return c.t.vec_source && c.g.nx % VX == 0 ? 1 : 0; };
+    auto key = [&](const SourceCall &c) { return 2 * vec(c) + (c.qd ? 1 : 0); };
+    return by_runs(calls, n, key, [&](const SourceCall *cs, int m) {
+        Group<SourceInst> a;
+        a.count = m;
+        int blk = 0;
+        const int v = vec(cs[0]);
+        for (int i = 0; i < m; i++) {
+            const SourceCall &c = cs[i];
+            SourceInst &d = a.d[i];
+            d.q = state_in(c.q, c.qd, c.g.n);
+            d.b = (S *)c.b;
+            d.rho_out = (S *)c.rho_out;
+            d.g = c.g;
+            d.alpha_s = C(c.p.alpha * 0.25 / (c.p.dx * c.p.dx));
+            d.W = (const C *)c.in.W;
+            d.J = (const C *)c.in.J;
+            d.zc = c.t.zc_source;
+            const dim3 gr = grid_of(c.g, v ? TXV : BX, BY, d.zc);
+            d.gx = (int)gr.x;
+            d.gy = (int)gr.y;
+            d.blk0 = blk;
+            blk += (int)(gr.x * gr.y * gr.z);
+        }
+        auto kern = v ? (cs[0].qd ? k_source_v4_group<kInc> : k_source_v4_group<false>)
+                      : (cs[0].qd ? k_source_group<kInc> : k_source_group<false>);
+        kern<<<blk, dim3(BX, BY), 0, st>>>(a);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_jacobi_group(const JacobiCall *calls, int n, int colour, cudaStream_t st)
+{
+    auto vec = [](const JacobiCall &c) { return c.t.vec_jacobi && c.g.nx % VX == 0 ? 1 : 0; };
+    return by_runs(calls, n, vec, [&](const JacobiCall *cs, int m) {
+        Group<JacobiInst> a;
+        a.count = m;
+        int blk = 0;
+        const int v = vec(cs[0]);
+        for (int i = 0; i < m; i++) {
+            const JacobiCall &c = cs[i];
+            JacobiInst &d = a.d[i];
+            d.q = (const S *)c.q;
+            d.b = (const S *)c.b;
+            d.sin = (const S *)c.s_in;
+            d.sout = (S *)c.s_out;
+            d.g = c.g;
+            d.beta = C(c.p.alpha / (c.p.dx * c.p.dx));
+            d.zc = c.t.zc_jacobi;
+            const dim3 gr = grid_of(c.g, v ? TXV : BX, BY, d.zc);
+            d.gx = (int)gr.x;
+            d.gy = (int)gr.y;
+            d.blk0 = blk;
+            blk += (int)(gr.x * gr.y * gr.z);
+        }
+        if (v) k_jacobi_v4_group<<<blk, dim3(BX, BY), 0, st>>>(a, colour);
+        else k_jacobi_group<<<blk, dim3(BX, BY), 0, st>>>(a, colour);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_flux_group(const FluxCall *calls, int n, int mode, cudaStream_t st)
+{
+    if (mode == FLUX_RHS) return cudaErrorInvalidValue;
+    for (int i = 0; i < n; i++)
+        if ((calls[i].qd != nullptr) != (kInc && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3)) ||
+            calls[i].t.z_end != 0)
+            return cudaErrorInvalidValue;
+    auto kind = [](const FluxCall &c) {
+        return 2 * (c.p.order == 3 ? 1 : 0) + (c.p.mu != 0.0 || c.p.zeta != 0.0 ? 1 : 0);
+    };
+    const size_t smem = flux_smem_bytes();
+    return by_runs(calls, n, kind, [&](const FluxCall *cs, int m) {
+        Group<FluxInst> a;
+        a.count = m;
+        int blk = 0;
+        const bool out_is_state = !kInc || mode == FLUX_STAGE3;
+        for (int i = 0; i < m; i++) {
+            const FluxCall &c = cs[i];
+            FluxInst &d = a.d[i];
+            d.qin = state_in(c.qs, c.qd, c.g.n);
+            d.sig = (const S *)c.sig;
+            for (int u = 0; u < 5; u++) {
+                d.qn.p[u] = c.qn ? (const QB *)c.qn + u * c.g.n : nullptr;
+                d.out.p[u] = c.out && !(kInc && out_is_state) ? (S *)c.out + u * c.g.n : nullptr;
+                d.outb.p[u] = c.out && kInc && out_is_state ? (QB *)c.out + u * c.g.n : nullptr;
+            }
+            d.g = c.g;
+            d.gamma = C(c.p.gamma);
+            d.half_inv_dx = C(0.5 / c.p.dx);
+            d.mu = C(c.p.mu);
+            d.lamv = C(c.p.zeta - 2.0 * c.p.mu / 3.0);
+            d.sc = c.sc;
+            d.blockmax = c.blockmax;
+            d.err = c.err;
+            d.W = (const C *)c.in.W;
+            d.J = (const C *)c.in.J;
+            d.zc = c.t.zc_flux;
+            const dim3 gr = grid_of(c.g, TX, TY, d.zc);
+            d.gx = (int)gr.x;
+            d.gy = (int)gr.y;
+            d.blk0 = blk;
+            blk += (int)(gr.x * gr.y * gr.z);
+        }
+        auto go = [&](auto kern) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            kern<<<blk, NT, smem, st>>>(a);
+            return cudaGetLastError();
+        };
+        auto by_mode = [&](auto k1, auto k2, auto k3) {
+            return mode == FLUX_STAGE1 ? go(k1) : mode == FLUX_STAGE2 ? go(k2) : go(k3);
+        };
+        switch (kind(cs[0])) {
+        case 0:
+            return by_mode(k_flux_group<FLUX_STAGE1, 5, false>, k_flux_group<FLUX_STAGE2, 5, false>,
+                           k_flux_group<FLUX_STAGE3, 5, false>);
+        case 1:
+            return by_mode(k_flux_group<FLUX_STAGE1, 5, true>, k_flux_group<FLUX_STAGE2, 5, true>,
+                           k_flux_group<FLUX_STAGE3, 5, true>);
+        case 2:
+            return by_mode(k_flux_group<FLUX_STAGE1, 3, false>, k_flux_group<FLUX_STAGE2, 3, false>,
+                           k_flux_group<FLUX_STAGE3, 3, false>);
+        default:
+            return by_mode(k_flux_group<FLUX_STAGE1, 3, true>, k_flux_group<FLUX_STAGE2, 3, true>,
+                           k_flux_group<FLUX_STAGE3, 3, true>);
+        }
+    });
+}
+
 cudaError_t launch_speed(const Geom &g, const Phys &p, const void *q, double *blockmax,
                          int *nblocks, cudaStream_t st)
 {
@@ -2515,6 +2817,7 @@ extern const Ops IGR_OPS = {
     (int)sizeof(S), (int)sizeof(C), (int)sizeof(QB), launch_source, launch_jacobi, launch_flux, flux_blocks,
     launch_speed, launch_rk_combine, launch_adj_rk, launch_adj_rhs, launch_adj_jacobi, launch_adj_rho,
     launch_adj_source, launch_adj_jets, launch_diag, bounds_hits, bounds_selftest,
+    launch_source_group, launch_jacobi_group, launch_flux_group,
 };
 
 }  // namespace igr

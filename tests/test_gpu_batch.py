@@ -47,12 +47,18 @@ def _alone(case, q0, precision, steps, tiles=None, forms=None):
 def test_batch_equals_single_bitwise(precision):
     import torch
     from paper_2505_07392_gb300 import igr
+    from dataclasses import replace
+    # uneven sizes, different sweep counts, red-black sweeps, 3rd-order
+    # faces and an inflow face in one batch: the grouped launches split by
+    # kernel form and scheme, every instance keeps its own buffers
     cases = [inputs.tgv(16, instance=0), inputs.tgv(24, instance=1), inputs.tgv(20, instance=2),
-             inputs.blast(12, sweeps=4)]
+             inputs.blast(12, sweeps=4), replace(inputs.tgv(16, instance=3), sigma_solver=1),
+             replace(inputs.blast(12, sweeps=3), order=3), _jets_case(20)]
     dt = igr.state_torch_dtype(precision)
-    q0 = [torch.from_numpy(inputs.initial_state(c)).to(dt).cuda() for c in cases]
+    q0 = [torch.from_numpy(inputs.jet_initial_state(c) if c.jets else inputs.initial_state(c)).to(dt).cuda()
+          for c in cases]
     torch.cuda.synchronize()
-    steps = 5  # first step direct, then two captured graphs (Sigma parity) replayed
+    steps = 6  # first step direct, then captured graphs of grouped launches replayed
     with igr.Batch(cases, precision) as b:
         for inst, q in zip(b.instances, q0):
             inst.set_state(q)
