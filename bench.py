@@ -372,9 +372,8 @@ def issue_roofline(case, res, precision, clocks, sms):
 def run_batch(args, sync_all=lambda: None):
     """64 periodic Taylor-Green instances of uneven size (edges drawn from
     {48,64,80,96,128}) advanced together: each kernel class one grouped
-    launch over all instances, one CUDA graph per step; the batch's launch
-    shapes, or (--autotune) z-chunks and kernel forms tuned per distinct size
-    on a lone instance."""
+    launch over all instances, one CUDA graph per step; z-chunks and kernel
+    forms autotuned per distinct size."""
     import torch
     from paper_2505_07392_gb300 import igr
     cases = inputs.tgv_batch(count=args.batch_count)
@@ -385,9 +384,7 @@ def run_batch(args, sync_all=lambda: None):
             inst.set_state(torch.from_numpy(inputs.initial_state(c)).to(st).cuda())
             torch.cuda.synchronize()
             key = (c.nx, c.ny, c.nz)
-            if not args.autotune:  # the batch's own launch shapes (grouped launches)
-                tuned.setdefault(key, (inst.tiles(), inst.kernel_forms()))
-            elif key not in tuned:
+            if key not in tuned:
                 tuned[key] = (inst.autotune(reps=3), inst.kernel_forms())
             else:
                 inst.set_tiles(*tuned[key][0])

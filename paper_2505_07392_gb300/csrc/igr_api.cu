@@ -1235,40 +1235,6 @@ static igr_status step_grouped(igr_batch *b)
 
 static igr_status step_batch_steps(igr_batch *b, int nsteps);
 
-// Launch shapes of a batch: a grouped launch fills the GPU with all
-// instances' blocks together, so each kernel class takes the longest z-chunk
-// (at most 128 planes, at least 16, at most each instance's nz) that still
-// gives the whole batch six waves of blocks (a lone instance's default
-// shortens its chunks to fill the GPU by itself). The kernel forms keep the
-// single-instance rule.
-static void batch_default_tiles(igr_batch *b)
-{
-    auto blocks = [&](int cls, int zc) {
-        long long total = 0;
-        for (igr_ctx *c : b->inst) {
-            const Geom &g = c->g;
-            const int z = std::min(zc, g.nz);
-            int tx = 32, ty = 8;
-            if (cls == 0) tx = c->tiles.vec_source ? 128 : 32;
-            if (cls == 1) tx = c->tiles.vec_jacobi ? 128 : 32;
-            if (cls == 2) ty = 15;  // the flux kernel's tile (FP32 arithmetic; 7 rows in FP64)
-            total += (long long)((g.nx + tx - 1) / tx) * ((g.ny + ty - 1) / ty) * ((g.nz + z - 1) / z);
-        }
-        return total;
-    };
-    const int resident[3] = {3, 3, 1};
-    int zc[3];
-    for (int cls = 0; cls < 3; cls++) {
-        zc[cls] = 128;
-        while (zc[cls] > 16 && blocks(cls, zc[cls]) < 6LL * 152 * resident[cls]) zc[cls] /= 2;
-    }
-    for (igr_ctx *c : b->inst) {
-        c->tiles.zc_source = std::min(zc[0], c->g.nz);
-        c->tiles.zc_jacobi = std::min(zc[1], c->g.nz);
-        c->tiles.zc_flux = std::min(zc[2], c->g.nz);
-    }
-}
-
 igr_status igr_create_batch(const igr_config *cfgs, int n, const igr_allocator *allocator,
                             void *cuda_stream, igr_batch **out)
 {
@@ -1307,7 +1273,6 @@ igr_status igr_create_batch(const igr_config *cfgs, int n, const igr_allocator *
         snprintf(g_create_err, sizeof g_create_err, "%s", msg);
         return s;
     }
-    batch_default_tiles(b);
     *out = b;
     return IGR_OK;
 }

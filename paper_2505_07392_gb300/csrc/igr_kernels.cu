@@ -96,6 +96,15 @@ __device__ __forceinline__ T *ckp(T *p, T *base, long long n, int w)
     }
     return p;
 }
+// 64-bit element offset c of an array of n values
+__device__ __forceinline__ size_t ckl(size_t c, long long n)
+{
+    if ((long long)c >= n) {
+        atomicAdd(&g_bounds_hits, 1ull);
+        return 0;
+    }
+    return c;
+}
 #define CKP(p, base, n) ckp((p), (base), (long long)(n), 1)
 #define CKP4(p, base, n) ckp((p), (base), (long long)(n), 4)
 // shared-memory element index c of a tile of n elements
@@ -119,6 +128,7 @@ __device__ __forceinline__ int cks4(int c, int n)
 }
 #else
 __device__ __forceinline__ idx ck(idx c, long long) { return c; }
+__device__ __forceinline__ size_t ckl(size_t c, long long) { return c; }
 #define CKP(p, base, n) (p)
 #define CKP4(p, base, n) (p)
 __device__ __forceinline__ int cks(int c, int) { return c; }
@@ -2018,11 +2028,12 @@ __device__ __forceinline__ C val_at(const S *q, const S *sig, const Geom &g, con
 {
     int mi = map_axis(i, g.nx, g.bc[0], g.bc[1]), mj = map_axis(j, g.ny, g.bc[2], g.bc[3]);
     int mk = map_axis(kk, g.nz, g.bc[4], g.bc[5]);
-    idx f = (idx)(mj * g.nx + mi);
-    idx c = (idx)mk * (idx)g.plane + f;
+    idx f = ck((idx)(mj * g.nx + mi), g.plane);
+    idx c = ck((idx)mk * (idx)g.plane + f, g.n);
     if (u == 5) return ldc(sig + c);
-    C v = ldc(q + (size_t)u * (size_t)g.n + c);
-    if (kk < 0 && g.bc[4] == BC_INFLOW) v = (C(1) - W[f]) * v + J[(idx)u * (idx)g.plane + f];
+    C v = ldc(q + ckl((size_t)u * (size_t)g.n + c, 5 * g.n));
+    if (kk < 0 && g.bc[4] == BC_INFLOW)
+        v = (C(1) - W[f]) * v + J[ckl((size_t)u * (size_t)g.plane + f, 5 * g.plane)];
     return v;
 }
 
@@ -2032,18 +2043,19 @@ __device__ __forceinline__ void scatter_at(C *lq, C *lsig, C *lamJ, const Geom &
 {
     int mi = map_axis(i, g.nx, g.bc[0], g.bc[1]), mj = map_axis(j, g.ny, g.bc[2], g.bc[3]);
     int mk = map_axis(kk, g.nz, g.bc[4], g.bc[5]);
-    idx f = (idx)(mj * g.nx + mi);
-    idx c = (idx)mk * (idx)g.plane + f;
+    idx f = ck((idx)(mj * g.nx + mi), g.plane);
+    idx c = ck((idx)mk * (idx)g.plane + f, g.n);
     if (u == 5) {
         aadd(lsig + c, a);
         return;
     }
+    const size_t qc = ckl((size_t)u * (size_t)g.n + c, 5 * g.n);
     if (kk < 0 && g.bc[4] == BC_INFLOW) {
-        aadd(lq + (size_t)u * (size_t)g.n + c, (C(1) - W[f]) * a);
-        aadd(lamJ + (idx)u * (idx)g.plane + f, a);
+        aadd(lq + qc, (C(1) - W[f]) * a);
+        aadd(lamJ + ckl((size_t)u * (size_t)g.plane + f, 5 * g.plane), a);
         return;
     }
-    aadd(lq + (size_t)u * (size_t)g.n + c, a);
+    aadd(lq + qc, a);
 }
 
 __global__ void k_adj_rk(const C *lout, C *lq0, C *lqs, C *Lb, long long n5, C w, C dt)
@@ -2133,11 +2145,11 @@ __global__ void k_adj_rhs(const S *q, const S *sig, const C *Lb, C *lq, C *lsig,
 #pragma unroll
         for (int u = 0; u < 5; u++) {
             C hi = C(0), lo = C(0);
-            if (f < nd) hi = Lb[(size_t)u * g.n + ((size_t)c3[2] * g.ny + c3[1]) * g.nx + c3[0]];
+            if (f < nd) hi = Lb[ckl((size_t)u * g.n + ((size_t)c3[2] * g.ny + c3[1]) * g.nx + c3[0], 5 * g.n)];
             if (f >= 1) {
                 int cc[3] = {c3[0], c3[1], c3[2]};
                 cc[D] = f - 1;
-                lo = Lb[(size_t)u * g.n + ((size_t)cc[2] * g.ny + cc[1]) * g.nx + cc[0]];
+                lo = Lb[ckl((size_t)u * g.n + ((size_t)cc[2] * g.ny + cc[1]) * g.nx + cc[0], 5 * g.n)];
             }
             Fb[u] = (hi - lo) * inv_dx;
         }
@@ -2198,7 +2210,7 @@ __device__ __forceinline__ bool nbr(const Geom &g, int i, int j, int k, int d, i
         if (g.bc[d] != BC_PERIODIC) return false;
         c[ax] = c[ax] < 0 ? c[ax] + n[ax] : c[ax] - n[ax];
     }
-    out = ((idx)c[2] * (idx)g.ny + (idx)c[1]) * (idx)g.nx + (idx)c[0];
+    out = ck(((idx)c[2] * (idx)g.ny + (idx)c[1]) * (idx)g.nx + (idx)c[0], g.n);
     return true;
 }
 
@@ -2307,7 +2319,8 @@ __global__ void k_adj_jets(const double *jets, const C *lamJ, double *gw, int nx
         double x = (i + 0.5) * dx, y = (j + 0.5) * dx;
         double r = sqrt((x - jt[0]) * (x - jt[0]) + (y - jt[1]) * (y - jt[1]));
         double sn = 0.5 * (1.0 - tanh((r - jt[2]) / (jt[6] * dx)));
-        acc += sn * (jt[3] * double(lamJ[3 * plane + f]) + jt[3] * jt[4] * double(lamJ[4 * plane + f]));
+        acc += sn * (jt[3] * double(lamJ[ckl(3 * plane + f, 5 * plane)]) +
+                     jt[3] * jt[4] * double(lamJ[ckl(4 * plane + f, 5 * plane)]));
     }
     __shared__ double red[256];
     red[threadIdx.x] = acc;

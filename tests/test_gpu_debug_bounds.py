@@ -1,8 +1,10 @@
 """The bounds-checking debug build (libigr_debug.so, IGR_DEBUG_BOUNDS): every
 global index the forward kernels form is checked against its array's length.
 Run over odd shapes (the one- and four-cell kernel forms), boundary
-kinds, inflow jets, the scheme alternatives, viscous terms, the host RK base,
-batches and the allocation-free solve, no index may fall outside its array;
+kinds, inflow jets, the scheme alternatives, viscous terms, the increment
+storage forms, the host RK base, batches (grouped launches), the
+allocation-free solve and the adjoint kernels, no index may fall outside
+its array;
 the self-test shows that a single out-of-range index is counted (and not
 dereferenced). This stands in for a memory checker."""
 import ctypes as C
@@ -116,6 +118,21 @@ def test_no_index_out_of_bounds(debug_lib):
                                      None) == igr.OK
     torch.cuda.synchronize()
     assert _hits(L) == 0
+    # the adjoint kernels (scatter through the boundary mapping and the jet
+    # blend, the transposed sweeps' neighbour gathers, the jet reduction)
+    for c, prec in ((_jets(), "f64"), (Case("a", 13, 9, 7, 1 / 13, alpha=1 / 169, sweeps=2,
+                                            bc=(PERIODIC, PERIODIC, OUTFLOW, OUTFLOW, PERIODIC, PERIODIC)), "f32")):
+        q0 = inputs.jet_initial_state(c) if c.jets else _state(c, 5)
+        dt, ct = igr.storage_torch_dtype(prec), igr.compute_torch_dtype(prec)
+        rng = np.random.Generator(np.random.Philox(11))
+        with igr.Solver(c, prec) as s:
+            q = torch.from_numpy(q0).to(dt).cuda()
+            sig = torch.zeros(s.shape, dtype=dt, device="cuda")
+            lq = torch.from_numpy(rng.normal(size=q0.shape)).to(ct).cuda()
+            ls = torch.from_numpy(rng.normal(size=s.shape)).to(ct).cuda()
+            s.adjoint_step(q, sig, lq, ls, 1e-3)
+            s.sync()
+        assert _hits(L) == 0, (c.name, prec)
 
 
 def test_normal_library_has_no_counter():
