@@ -1426,6 +1426,45 @@ __device__ __forceinline__ C2 rec3_right2(C2 c, C2 d, C2 e)
 }
 
 constexpr int TILE2 = 3 * PH * PW;  // pairs in one plane tile
+// Layout of one plane tile: the pairs (rho, m_x) and (m_y, m_z) of a cell
+// side by side, one 16-byte quad per cell (two in FP64) for cells 0..PH*PW-1,
+// then the pairs (E, Sigma) of all cells. A stencil point is then one
+// 16-byte shared load and one 8-byte load (FP32) instead of three 8-byte
+// loads: the same shared-memory bandwidth in fewer instructions.
+constexpr int QUADS = 2 * PH * PW;  // offset (in pairs) of the (E, Sigma) pairs
+__device__ __forceinline__ int pair_at(int p, int e) { return p < 2 ? 2 * e + p : QUADS + e; }
+// the pairs (rho, m_x), (m_y, m_z) of tile cell e
+__device__ __forceinline__ void ld_quad(const float2 *T, int e, float2 &a, float2 &b)
+{
+    const float4 q = *reinterpret_cast<const float4 *>(T + 2 * e);
+    a = make_float2(q.x, q.y);
+    b = make_float2(q.z, q.w);
+}
+__device__ __forceinline__ void ld_quad(const double2 *T, int e, double2 &a, double2 &b)
+{
+    a = T[2 * e];
+    b = T[2 * e + 1];
+}
+__device__ __forceinline__ void st_quad(float2 *T, int e, float2 a, float2 b)
+{
+    *reinterpret_cast<float4 *>(T + 2 * e) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st_quad(double2 *T, int e, double2 a, double2 b)
+{
+    T[2 * e] = a;
+    T[2 * e + 1] = b;
+}
+// the three pairs of tile cell e
+__device__ __forceinline__ void ld_cell(const C2 *T, int e, C2 &a, C2 &b, C2 &c)
+{
+    ld_quad(T, e, a, b);
+    c = T[QUADS + e];
+}
+__device__ __forceinline__ void st_cell(C2 *T, int e, C2 a, C2 b, C2 c)
+{
+    st_quad(T, e, a, b);
+    T[QUADS + e] = c;
+}
 constexpr int NFX = 5 * TY * (TX + 1), NFY = 5 * (TY + 1) * TX;  // one parity of the face buffers
 constexpr int RING = 7;             // plane tiles resident: k-2..k+3 and k+4 in flight
 
@@ -1485,11 +1524,13 @@ __device__ __forceinline__ void tile_face(const C2 *T, int at, int step, C gamma
 {
     C2 s[6][3];
 #pragma unroll
-    for (int m = 0; m < 6; m++)
-#pragma unroll
-        for (int p = 0; p < 3; p++)
-            s[m][p] = (ORD == 3 && (m == 0 || m == 5)) ? bcast(C(0))
-                                                       : T[p * PH * PW + cks(at + m * step, PH * PW)];
+    for (int m = 0; m < 6; m++) {
+        if (ORD == 3 && (m == 0 || m == 5)) {
+            s[m][0] = s[m][1] = s[m][2] = bcast(C(0));
+        } else {
+            ld_cell(T, cks(at + m * step, PH * PW), s[m][0], s[m][1], s[m][2]);
+        }
+    }
     face_from_stencil<D, ORD>(s, gamma, gm1, F, bad);
 }
 
@@ -1497,7 +1538,8 @@ __device__ __forceinline__ void tile_face(const C2 *T, int at, int step, C gamma
 // Velocity u = m / rho of the tile cell at pair offset `at`.
 __device__ __forceinline__ void tvel(const C2 *T, int at, C u[3])
 {
-    C2 a = T[cks(at, PH * PW)], b = T[PH * PW + cks(at, PH * PW)];
+    C2 a, b;
+    ld_quad(T, cks(at, PH * PW), a, b);
     C r = rcp(a.x);
     u[0] = a.y * r;
     u[1] = b.x * r;
@@ -1639,7 +1681,7 @@ __device__ __forceinline__ void flux_body(const QIn &qin, const S *__restrict__ 
                     for (int u = 0; u < 5; u++) v[u] = wf * v[u] + J[(idx)u * pl + ck(goff[r], g.plane)];
                 }
 #pragma unroll
-                for (int p = 0; p < 3; p++) T[p * PH * PW + cks(soff[r], PH * PW)] = pset(v[2 * p], v[2 * p + 1]);
+                st_cell(T, cks(soff[r], PH * PW), pset(v[0], v[1]), pset(v[2], v[3]), pset(v[4], v[5]));
             }
     }
 
@@ -1663,7 +1705,7 @@ __device__ __forceinline__ void flux_body(const QIn &qin, const S *__restrict__ 
 #pragma unroll
                     for (int u = 0; u < 6; u++) {
                         if constexpr (kAsyncTile)
-                            cp_async_elem(&T[(u >> 1) * PH * PW + cks(soff[r], PH * PW)].x + (u & 1),
+                            cp_async_elem(&T[pair_at(u >> 1, cks(soff[r], PH * PW))].x + (u & 1),
                                           CKP(fin(u) + zb + goff[r], fin(u), g.n));
                         else
                             Rg[r][u] = ldr(CKP(fin(u) + zb + goff[r], fin(u), g.n));
@@ -1679,18 +1721,15 @@ __device__ __forceinline__ void flux_body(const QIn &qin, const S *__restrict__ 
 #pragma unroll
             for (int r = 0; r < LPT; r++)
                 if (soff[r] >= 0) {
-                    const int so = cks(soff[r], PH * PW);
-                    T[so] = pset(cvq<HASD>(Rq[r][0]), cvq<HASD>(Rq[r][1]));
-                    T[PH * PW + so] = pset(cvq<HASD>(Rq[r][2]), cvq<HASD>(Rq[r][3]));
-                    T[2 * PH * PW + so] = pset(cvq<HASD>(Rq[r][4]), cv(Rs[r]));
+                    st_cell(T, cks(soff[r], PH * PW), pset(cvq<HASD>(Rq[r][0]), cvq<HASD>(Rq[r][1])),
+                            pset(cvq<HASD>(Rq[r][2]), cvq<HASD>(Rq[r][3])), pset(cvq<HASD>(Rq[r][4]), cv(Rs[r])));
                 }
         } else {
 #pragma unroll
             for (int r = 0; r < LPT; r++)
                 if (soff[r] >= 0)
-#pragma unroll
-                    for (int p = 0; p < 3; p++)
-                        T[p * PH * PW + cks(soff[r], PH * PW)] = pset(cv(Rg[r][2 * p]), cv(Rg[r][2 * p + 1]));
+                    st_cell(T, cks(soff[r], PH * PW), pset(cv(Rg[r][0]), cv(Rg[r][1])), pset(cv(Rg[r][2]), cv(Rg[r][3])),
+                            pset(cv(Rg[r][4]), cv(Rg[r][5])));
         }
     };
     __syncthreads();
@@ -1728,8 +1767,8 @@ __device__ __forceinline__ void flux_body(const QIn &qin, const S *__restrict__ 
             for (int u = 0; u < 5; u++) rhs.p[u][c] = Lv[u];
             nonfinite |= !isfinite((Lv[0] + Lv[1]) + (Lv[2] + Lv[3]) + Lv[4]);
         } else {
-            const int tc = cks(tcell, PH * PW);
-            C2 a = T[tc], b = T[PH * PW + tc], e = T[2 * PH * PW + tc];
+            C2 a, b, e;
+            ld_cell(T, cks(tcell, PH * PW), a, b, e);
             const C qsv[5] = {a.x, a.y, b.x, b.y, e.x};
             if (mode == FLUX_STAGE1 && base_out.p[0]) {
                 // the RK base q^n for stages 2 and 3 (exact: qsv holds stored values)
@@ -1775,8 +1814,7 @@ __device__ __forceinline__ void flux_body(const QIn &qin, const S *__restrict__ 
 #pragma unroll
             for (int m = 0; m < 6; m++) {
                 const C2 *T = P + ro[m];
-#pragma unroll
-                for (int p = 0; p < 3; p++) sz[m][p] = T[p * PH * PW + cks(tcell, PH * PW)];
+                ld_cell(T, cks(tcell, PH * PW), sz[m][0], sz[m][1], sz[m][2]);
             }
             face_from_stencil<2, ORD>(sz, gamma, gm1, Fzp, bad);  // z-face k + 1/2
             if constexpr (VISC) {
