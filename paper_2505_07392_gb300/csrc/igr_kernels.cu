@@ -976,8 +976,9 @@ __device__ __forceinline__ Vec4<T> ld4_mapped(const T *__restrict__ a, const Geo
 }
 
 // 4 raw state values (cells x .. x+3) and their stage values, as StateIO
-struct QRaw4Inc {  // four stage values q_s = RN32(q^n + d_s), summed as they arrive
-    C v[4];
+struct QRaw4Inc {
+    Vec4<QB> b;
+    V4 d;
 };
 template <bool INC> struct StateIO4;
 template <> struct StateIO4<false> {  // (used where the state has the storage type)
@@ -991,26 +992,23 @@ template <> struct StateIO4<false> {  // (used where the state has the storage t
 };
 template <> struct StateIO4<true> {
     using Raw = QRaw4Inc;
-    // The sum is formed when the values are loaded: the 4 FP32 values it
-    // keeps take fewer registers than the raw base and increments (6), which
-    // the 4-cell source holds one plane ahead for 8 cells.
     template <bool HASD>
     static __device__ __forceinline__ QRaw4Inc ld(const QIn &q, int u, const Geom &g, idx rowoff, int x)
     {
         QRaw4Inc r;
-        cv4(ld4_mapped(q.b[u], g, rowoff, x), r.v);
-        if constexpr (HASD) {
-            C d[4];
-            cv4(ld4_mapped(q.d[u], g, rowoff, x), d);
-#pragma unroll
-            for (int c = 0; c < 4; c++) r.v[c] = C(__fadd_rn(float(r.v[c]), float(d[c])));
-        }
+        r.b = ld4_mapped(q.b[u], g, rowoff, x);
+        if constexpr (HASD) r.d = ld4_mapped(q.d[u], g, rowoff, x);
         return r;
     }
     template <bool HASD> static __device__ __forceinline__ void val(const QRaw4Inc &r, C o[4])
     {
+        cv4(r.b, o);
+        if constexpr (HASD) {
+            C d[4];
+            cv4(r.d, d);
 #pragma unroll
-        for (int c = 0; c < 4; c++) o[c] = r.v[c];
+            for (int c = 0; c < 4; c++) o[c] = C(__fadd_rn(float(o[c]), float(d[c])));
+        }
     }
 };
 using QRaw4 = StateIO4<kInc>::Raw;
