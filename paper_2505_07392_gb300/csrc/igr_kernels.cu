@@ -1610,11 +1610,11 @@ constexpr int FLUX_MAXREG = sizeof(C) == 8 ? 224 : 128;
 // d_{s+1} = RN16(w [(q_s - q^n) + dt L]) into `out`, and stage 3 stores the
 // FP32 state q^n + w [(q_s - q^n) + dt L] into `outb`.
 template <int mode, int ORD, bool VISC>
-__device__ __forceinline__ void flux_body(const QIn &qin, const S *__restrict__ sig, const QBIn &qn,
-                                          const Fout<5> &out, const QBOut &outb, const Frhs &rhs,
-                                          const Fout<5> &base_out, const Geom &g, C gamma, C half_inv_dx,
+__device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ sig, const QBIn qn,
+                                          const Fout<5> out, const QBOut outb, const Frhs rhs,
+                                          const Fout<5> base_out, const Geom g, C gamma, C half_inv_dx,
                                           const Scalars *sc, double *blockmax, int *err, const C *W,
-                                          const C *J, int zc, int cz0, C mu, C lamv, const BlockPos &bp)
+                                          const C *J, int zc, int cz0, C mu, C lamv, const BlockPos bp)
 {
     constexpr bool HASD = kInc && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3);
     // field u of the stored input (u < 5: q, 5: Sigma) where the state has the storage type
