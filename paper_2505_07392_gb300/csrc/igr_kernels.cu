@@ -1465,9 +1465,7 @@ __device__ __forceinline__ void st_cell(C2 *T, int e, C2 a, C2 b, C2 c)
     st_quad(T, e, a, b);
     T[QUADS + e] = c;
 }
-// one parity of the face buffers: the x-faces at the high end of each row
-// (the others stay in the row warps' registers), the y-faces of all columns
-constexpr int NFX = 5 * TY, NFY = 5 * (TY + 1) * TX;
+constexpr int NFX = 5 * TY * (TX + 1), NFY = 5 * (TY + 1) * TX;  // one parity of the face buffers
 constexpr int RING = 7;             // plane tiles resident: k-2..k+3 and k+4 in flight
 
 // Storage equal to the arithmetic type: plane tiles are copied global ->
@@ -1484,10 +1482,10 @@ __device__ __forceinline__ void cp_async_elem(C *dst, const S *src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// shared bytes: the ring of plane tiles (pairs), two sets of face fluxes
+// shared bytes: the ring of plane tiles (pairs), two sets of x- and y-face fluxes
 __host__ __device__ constexpr size_t flux_smem_bytes()
 {
-    return RING * TILE2 * sizeof(C2) + 2 * (NFX + NFY) * sizeof(C);
+    return RING * TILE2 * sizeof(C2) + 2 * (5 * TY * (TX + 1) + 5 * (TY + 1) * TX) * sizeof(C);
 }
 
 // tile cell e (0 <= e < NPLANE) -> position (lx, ly) in the PW x PH tile
@@ -1623,7 +1621,7 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
     auto fin = [&](int u) -> const S * { return u < 5 ? reinterpret_cast<const S *>(qin.b[u]) : sig; };
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *P = reinterpret_cast<C2 *>(smem_raw);        // [RING][3][PH][PW]
-    C *FXb = reinterpret_cast<C *>(P + RING * TILE2); // [2][5][TY]: x-face at each row's high end
+    C *FXb = reinterpret_cast<C *>(P + RING * TILE2); // [2][5][TY][TX+1]
     C *FYb = FXb + 2 * NFX;                           // [2][5][TY+1][TX]
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int x0 = bp.x * TX, y0 = bp.y * TY;
@@ -1749,29 +1747,16 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
     C Fzm[5], Fzp[5];
     QB qnv[5];  // q^n of plane k - 1 (stages 2 and 3), loaded one iteration ahead
 
-    // The x-face at the low side of each row-warp lane's cell, kept in
-    // registers from the plane's face evaluation to its divergence (the face
-    // at the high side is the next lane's, taken by a shuffle; the row's last
-    // one comes from the face buffer)
-    C Fxo[5];
-    // the high-side x-faces of plane kk (all lanes of a row warp take part)
-    auto x_high = [&](int kk, C (&hi)[5]) {
-        const C *FX = FXb + (kk & 1) * NFX;
-#pragma unroll
-        for (int u = 0; u < 5; u++) {
-            const C nb = __shfl_down_sync(0xffffffffu, Fxo[u], 1);
-            const C end = FX[cks(u * TY + w, NFX)];
-            hi[u] = lane == 31 ? end : nb;
-        }
-    };
     // divergence and stage combination of plane kk (face buffers of parity kk)
-    auto finish = [&](int kk, const C2 *T, const C (&hi)[5]) {
+    auto finish = [&](int kk, const C2 *T) {
+        const C *FX = FXb + (kk & 1) * NFX;
         const C *FY = FYb + (kk & 1) * NFY;
         idx c = ck((idx)kk * pl + own, g.n);
         C Lv[5];
 #pragma unroll
         for (int u = 0; u < 5; u++) {
-            C dfx = hi[u] - Fxo[u];
+            C dfx = FX[cks((u * TY + w) * (TX + 1) + lane + 1, NFX)] -
+                    FX[cks((u * TY + w) * (TX + 1) + lane, NFX)];
             C dfy = FY[cks((u * (TY + 1) + w + 1) * TX + lane, NFY)] -
                     FY[cks((u * (TY + 1) + w) * TX + lane, NFY)];
             C dfz = Fzp[u] - Fzm[u];
@@ -1817,11 +1802,7 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
         const bool more = k + 4 <= k1 + 2;  // plane k + 4 feeds the z-faces
         if (more) fetch(k + 4, P + ro[6]);
         if (rowwarp) {
-            if (k > k0) {
-                C hi[5];
-                x_high(k - 1, hi);
-                if (active) finish(k - 1, P + ro[1], hi);
-            }
+            if (k > k0 && active) finish(k - 1, P + ro[1]);
 #pragma unroll
             for (int u = 0; u < 5; u++) Fzm[u] = Fzp[u];
             if (k >= k0 && active && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3)) {
@@ -1865,7 +1846,7 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
                 tile_face<0, ORD>(T, (w + 3) * PW + lane, 1, gamma, gm1, F, bad);
                 if constexpr (VISC) visc_x((w + 3) * PW + lane + 2);
 #pragma unroll
-                for (int u = 0; u < 5; u++) Fxo[u] = F[u];
+                for (int u = 0; u < 5; u++) FX[cks((u * TY + w) * (TX + 1) + lane, NFX)] = F[u];
                 // y-face below row w in column lane (tile rows w-3..w+2)
                 tile_face<1, ORD>(T, w * PW + lane + 3, PW, gamma, gm1, F, bad);
                 if constexpr (VISC) visc_y((w + 2) * PW + lane + 3);
@@ -1882,7 +1863,7 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
                     tile_face<0, ORD>(T, (lane + 3) * PW + TX, 1, gamma, gm1, F, bad);
                     if constexpr (VISC) visc_x((lane + 3) * PW + TX + 2);
 #pragma unroll
-                    for (int u = 0; u < 5; u++) FX[cks(u * TY + lane, NFX)] = F[u];
+                    for (int u = 0; u < 5; u++) FX[cks((u * TY + lane) * (TX + 1) + TX, NFX)] = F[u];
                 }
             }
         }
@@ -1895,11 +1876,7 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
     }
     // the last plane (its faces are behind the final barrier; after the
     // rotation plane k1 - 1 sits at ro[1])
-    if (rowwarp) {
-        C hi[5];
-        x_high(k1 - 1, hi);
-        if (active) finish(k1 - 1, P + ro[1], hi);
-    }
+    if (active) finish(k1 - 1, P + ro[1]);
     if (nonfinite || bad) atomicOr(err, (nonfinite ? ERRF_NONFINITE : 0) | (bad ? ERRF_FACE : 0));
     if (mode == FLUX_STAGE3) {
         double m = block_max<NT>(double(smax));
