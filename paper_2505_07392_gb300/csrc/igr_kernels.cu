@@ -616,9 +616,9 @@ __device__ __forceinline__ C source_b(const C (&D)[3][3], C alpha_s)
 // also stores the stage's density rounded to the storage type (rho_out),
 // which the Jacobi sweeps of the stage read.
 template <bool HASD>
-__device__ __forceinline__ void source_body(const QIn &q, S *__restrict__ b, S *__restrict__ rho_out,
-                                            const Geom &g, C alpha_s, const C *W, const C *J, int zc,
-                                            const BlockPos &bp)
+__device__ __forceinline__ void source_body(const QIn q, S *__restrict__ b, S *__restrict__ rho_out,
+                                            const Geom g, C alpha_s, const C *W, const C *J, int zc,
+                                            const BlockPos bp)
 {
     __shared__ C U[3][HY][HX];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
@@ -736,8 +736,8 @@ __device__ __forceinline__ C jacobi_cell(C r0, const C (&e)[6], const C (&rn)[6]
 }
 
 __device__ __forceinline__ void jacobi_body(const S *__restrict__ q, const S *__restrict__ b, const S *sin,
-                                            S *sout, const Geom &g, C beta, int zc, int colour,
-                                            const BlockPos &bp)
+                                            S *sout, const Geom g, C beta, int zc, int colour,
+                                            const BlockPos bp)
 {
     __shared__ C R[HY][HX], SG[HY][HX];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
@@ -1023,8 +1023,8 @@ template <bool HASD> __device__ __forceinline__ void cvq4(const QRaw4 &r, C o[4]
 }
 
 __device__ __forceinline__ void jacobi_v4_body(const S *__restrict__ q, const S *__restrict__ b, const S *sin,
-                                               S *sout, const Geom &g, C beta, int zc, int colour,
-                                               const BlockPos &bp)
+                                               S *sout, const Geom g, C beta, int zc, int colour,
+                                               const BlockPos bp)
 {
     __shared__ __align__(16) C R[HY][HXV];
     __shared__ __align__(16) C SG[HY][HXV];
@@ -1206,9 +1206,9 @@ __global__ void __launch_bounds__(BT, JACOBI_V4_BLOCKS) k_jacobi_v4(const S *__r
 // which is Eq. igrelliptic's left side with G = D / (2 dx). k_source takes the
 // same differences and source_b, so both forms give the same bits.
 template <bool HASD>
-__device__ __forceinline__ void source_v4_body(const QIn &q, S *__restrict__ b, S *__restrict__ rho_out,
-                                               const Geom &g, C alpha_s, const C *W, const C *J, int zc,
-                                               const BlockPos &bp)
+__device__ __forceinline__ void source_v4_body(const QIn q, S *__restrict__ b, S *__restrict__ rho_out,
+                                               const Geom g, C alpha_s, const C *W, const C *J, int zc,
+                                               const BlockPos bp)
 {
     __shared__ __align__(16) C U[3][HY][HXV];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
