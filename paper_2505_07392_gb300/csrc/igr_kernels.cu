@@ -1357,10 +1357,12 @@ __device__ __forceinline__ void source_v4_body(const QIn q, S *__restrict__ b, S
         for (int c = 0; c < VX; c++) rho0[c] = rhop[c];
     }
 }
-// the increment modes' 4-cell source holds raw FP32 values and 16-bit
-// increments one plane ahead: two blocks per SM (a few spilled registers)
-// against one without the bound
-constexpr int SOURCE_V4_BLOCKS = kInc ? 2 : 1;
+// Two blocks per SM (at most 128 registers): the kernel waits on load
+// latency, and one block per SM, which a free register choice gives (about
+// 156 registers), runs it 1.6x slower. The increment modes' form, which
+// holds raw FP32 values and 16-bit increments one plane ahead, spills a few
+// registers under this bound and still runs faster. FP64 keeps one block.
+constexpr int SOURCE_V4_BLOCKS = sizeof(C) == 8 ? 1 : 2;
 template <bool HASD>
 __global__ void __launch_bounds__(BT, SOURCE_V4_BLOCKS) k_source_v4(QIn q, S *__restrict__ b, S *__restrict__ rho_out, Geom g,
                                                    C alpha_s, const C *W, const C *J, int zc)
