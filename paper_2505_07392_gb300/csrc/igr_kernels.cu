@@ -1619,8 +1619,28 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
                                           const C *J, int zc, int cz0, C mu, C lamv, const BlockPos bp)
 {
     constexpr bool HASD = kInc && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3);
+    // The five fields of every state buffer lie g.n values apart: their
+    // addresses come from the first field's pointer and that stride, so the
+    // kernel holds one pointer per buffer (and not five).
+    const size_t fs = (size_t)g.n;
+    const QB *const qb0 = qin.b[0];
+    const S *const qd0 = qin.d[0];
+    const QB *const qn0 = qn.p[0];
+    S *const out0 = out.p[0];
+    QB *const outb0 = outb.p[0];
+    // raw state value u at offset c (StateIO's layout, one pointer per buffer)
+    auto ldq_raw = [&](int u, idx c) -> QRaw {
+        if constexpr (kInc) {
+            QRawInc r;
+            r.b = __ldg(qb0 + u * fs + c);
+            r.d = HASD ? ldr(qd0 + u * fs + c) : S(0.0f);
+            return *reinterpret_cast<QRaw *>(&r);
+        } else {
+            return *reinterpret_cast<const QRaw *>(reinterpret_cast<const S *>(qb0) + u * fs + c);
+        }
+    };
     // field u of the stored input (u < 5: q, 5: Sigma) where the state has the storage type
-    auto fin = [&](int u) -> const S * { return u < 5 ? reinterpret_cast<const S *>(qin.b[u]) : sig; };
+    auto fin = [&](int u) -> const S * { return u < 5 ? reinterpret_cast<const S *>(qb0) + u * fs : sig; };
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *P = reinterpret_cast<C2 *>(smem_raw);        // [RING][3][PH][PW]
     C *FXb = reinterpret_cast<C *>(P + RING * TILE2); // [2][5][TY][TX+1]
@@ -1675,7 +1695,7 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
                 C v[6];
                 const idx c = ck(zb + goff[r], g.n);
 #pragma unroll
-                for (int u = 0; u < 5; u++) v[u] = ldq<HASD>(qin, u, c);
+                for (int u = 0; u < 5; u++) v[u] = cvq<HASD>(ldq_raw(u, c));
                 v[5] = ldc(sig + c);
                 if (blend) {
                     C wf = C(1) - W[ck(goff[r], g.plane)];
@@ -1701,7 +1721,7 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
                 if constexpr (kInc) {
                     const idx c = ck(zb + goff[r], g.n);
 #pragma unroll
-                    for (int u = 0; u < 5; u++) Rq[r][u] = ldqr<HASD>(qin, u, c);
+                    for (int u = 0; u < 5; u++) Rq[r][u] = ldq_raw(u, c);
                     Rs[r] = ldr(sig + c);
                 } else {
 #pragma unroll
@@ -1785,9 +1805,9 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
                 for (int u = 0; u < 5; u++) {
                     const C inc = w32 * ((qsv[u] - qb[u]) + dt32 * Lv[u]);
                     if (mode == FLUX_STAGE3)
-                        o[u] = stc(outb.p[u] + c, qb[u] + inc);  // q^n+1 in FP32
+                        o[u] = stc(outb0 + u * fs + c, qb[u] + inc);  // q^n+1 in FP32
                     else
-                        o[u] = stc(out.p[u] + c, inc);  // the increment d_s+1, rounded to 16 bits
+                        o[u] = stc(out0 + u * fs + c, inc);  // the increment d_s+1, rounded to 16 bits
                 }
             } else {
                 rk_store5(out, c, qb, qsv, Lv, dt32, dt, w32, wd, o);
@@ -1810,7 +1830,7 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
             if (k >= k0 && active && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3)) {
                 idx c = ck((idx)k * pl + own, g.n);
 #pragma unroll
-                for (int u = 0; u < 5; u++) qnv[u] = __ldg(qn.p[u] + c);
+                for (int u = 0; u < 5; u++) qnv[u] = __ldg(qn0 + u * fs + c);
             }
             C2 sz[6][3];  // z-stencil: planes k - 2..k + 3 at this cell
 #pragma unroll
