@@ -1619,9 +1619,12 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
                                           const C *J, int zc, int cz0, C mu, C lamv, const BlockPos bp)
 {
     constexpr bool HASD = kInc && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3);
-    // The five fields of every state buffer lie g.n values apart: their
-    // addresses come from the first field's pointer and that stride, so the
-    // kernel holds one pointer per buffer (and not five).
+    // The five fields of every state buffer lie g.n values apart. In the
+    // increment modes, which read and write more buffers, their addresses
+    // come from the first field's pointer and that stride, so the kernel
+    // holds one pointer per buffer: fewer constant-bank reloads of pointers
+    // (9 against 26 per cell) for more 64-bit adds, 4.5% faster at full size;
+    // the other forms keep a pointer per field (the same or 1% faster).
     const size_t fs = (size_t)g.n;
     const QB *const qb0 = qin.b[0];
     const S *const qd0 = qin.d[0];
@@ -1636,11 +1639,11 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
             r.d = HASD ? ldr(qd0 + u * fs + c) : S(0.0f);
             return *reinterpret_cast<QRaw *>(&r);
         } else {
-            return *reinterpret_cast<const QRaw *>(reinterpret_cast<const S *>(qb0) + u * fs + c);
+            return ldqr<HASD>(qin, u, c);
         }
     };
     // field u of the stored input (u < 5: q, 5: Sigma) where the state has the storage type
-    auto fin = [&](int u) -> const S * { return u < 5 ? reinterpret_cast<const S *>(qb0) + u * fs : sig; };
+    auto fin = [&](int u) -> const S * { return u < 5 ? reinterpret_cast<const S *>(qin.b[u]) : sig; };
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *P = reinterpret_cast<C2 *>(smem_raw);        // [RING][3][PH][PW]
     C *FXb = reinterpret_cast<C *>(P + RING * TILE2); // [2][5][TY][TX+1]
@@ -1702,7 +1705,6 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
 #pragma unroll
                     for (int u = 0; u < 5; u++) v[u] = wf * v[u] + J[(idx)u * pl + ck(goff[r], g.plane)];
                 }
-#pragma unroll
                 st_cell(T, cks(soff[r], PH * PW), pset(v[0], v[1]), pset(v[2], v[3]), pset(v[4], v[5]));
             }
     }
@@ -1830,7 +1832,7 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
             if (k >= k0 && active && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3)) {
                 idx c = ck((idx)k * pl + own, g.n);
 #pragma unroll
-                for (int u = 0; u < 5; u++) qnv[u] = __ldg(qn0 + u * fs + c);
+                for (int u = 0; u < 5; u++) qnv[u] = __ldg(kInc ? qn0 + u * fs + c : qn.p[u] + c);
             }
             C2 sz[6][3];  // z-stencil: planes k - 2..k + 3 at this cell
 #pragma unroll
