@@ -162,6 +162,8 @@ __device__ __forceinline__ float cv(__nv_bfloat16 v) { return __bfloat162float(v
 struct QIn {
     const QB *b[5];
     const S *d[5];
+    size_t fs;  // values between consecutive fields of b and of d (the increment
+                // modes address the fields from b[0] and d[0] with it)
 };
 struct QRawInc {  // one raw state value of the increment modes
     QB b;
@@ -181,8 +183,8 @@ template <> struct StateIO<true> {
     template <bool HASD> static __device__ __forceinline__ QRawInc ld(const QIn &q, int u, idx c)
     {
         QRawInc r;
-        r.b = __ldg(q.b[u] + c);
-        r.d = HASD ? ldr(q.d[u] + c) : S(0.0f);
+        r.b = __ldg(q.b[0] + u * q.fs + c);
+        r.d = HASD ? ldr(q.d[0] + u * q.fs + c) : S(0.0f);
         return r;
     }
     // the stage value q_s = RN32(q^n + d_s) (q^n itself without increments)
@@ -996,8 +998,8 @@ template <> struct StateIO4<true> {
     static __device__ __forceinline__ QRaw4Inc ld(const QIn &q, int u, const Geom &g, idx rowoff, int x)
     {
         QRaw4Inc r;
-        r.b = ld4_mapped(q.b[u], g, rowoff, x);
-        if constexpr (HASD) r.d = ld4_mapped(q.d[u], g, rowoff, x);
+        r.b = ld4_mapped(q.b[0] + u * q.fs, g, rowoff, x);
+        if constexpr (HASD) r.d = ld4_mapped(q.d[0] + u * q.fs, g, rowoff, x);
         return r;
     }
     template <bool HASD> static __device__ __forceinline__ void val(const QRaw4Inc &r, C o[4])
@@ -2504,6 +2506,7 @@ QIn state_in(const void *q, const void *qd, long long n)
         f.b[u] = q ? (const QB *)q + u * n : nullptr;
         f.d[u] = qd ? (const S *)qd + u * n : nullptr;
     }
+    f.fs = (size_t)n;
     return f;
 }
 
