@@ -1282,13 +1282,14 @@ __device__ __forceinline__ void source_v4_body(const QIn q, S *__restrict__ b, S
     C rho0[VX], rhop[VX];  // densities of the own cells at k and k + 1
     own_u(k0 - 1, um, rhop);
     own_u(k0, u0, rho0);
-    // raw values one iteration ahead: own cells at k + 1, halo at k (planes >= 0)
+    // raw values one iteration ahead: own cells at k + 1, halo at k (planes >= 0).
+    // The increment modes' stages 2 and 3 (base and increments, 6 registers
+    // per field and 4 cells) load the halo when it is used instead, which
+    // keeps the registers under two blocks per SM with fewer spills.
+    constexpr bool kHaloAhead = !(kInc && HASD);
     QRaw4 nc[4], nh[4];
     QRaw nxh[4];
-    auto pre = [&](int kk) {
-        idx pz = (idx)zmap(kk + 1, g) * pl + rowj;
-#pragma unroll
-        for (int f = 0; f < 4; f++) nc[f] = ldq4<HASD>(q, f, g, pz, i0);
+    auto halo = [&](int kk) {
         if (htask == 0) {
 #pragma unroll
             for (int f = 0; f < 4; f++) nh[f] = ldq4<HASD>(q, f, g, (idx)kk * pl + hrow, hx);
@@ -1297,8 +1298,15 @@ __device__ __forceinline__ void source_v4_body(const QIn q, S *__restrict__ b, S
             for (int f = 0; f < 4; f++) nxh[f] = ldqr<HASD>(q, f, ck((idx)kk * pl + hrow + hx, g.n));
         }
     };
+    auto pre = [&](int kk) {
+        idx pz = (idx)zmap(kk + 1, g) * pl + rowj;
+#pragma unroll
+        for (int f = 0; f < 4; f++) nc[f] = ldq4<HASD>(q, f, g, pz, i0);
+        if (kHaloAhead) halo(kk);
+    };
     pre(k0);
     for (int k = k0; k < k1; k++) {
+        if (!kHaloAhead) halo(k);
         u4(nc, up, rhop);
         C hu[3][VX];
         if (htask == 0) {
