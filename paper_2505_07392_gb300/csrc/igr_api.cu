@@ -73,6 +73,7 @@ struct igr_ctx {
     // the last stage (created by its first call)
     cudaStream_t copy_st;
     cudaEvent_t slab_ev[kOutSlabs + 1];
+    cudaEvent_t in_ev[2];  // igr_step_host: rho and m copied in (c->st), the energy field too (copy_st)
     std::vector<int> ev_class;
     long long prof_launches[KC_COUNT];
     double prof_ms[KC_COUNT];
@@ -432,13 +433,20 @@ static igr_status launch_sweeps(igr_ctx *c, const Tiles &t, const void *q, const
     return IGR_OK;
 }
 
+static igr_status refresh_speed(igr_ctx *c);
+static igr_status finalize_dt(igr_ctx *c, double fixed_dt);
+
 // One stage: source, sweeps, flux. With host_out (the last stage of
 // igr_step_host) the flux runs in z-slabs of whole chunks, and each slab's
 // planes of `out` are copied to host_out on copy_st as soon as the slab is
 // done, while the next slabs compute; c->st then waits for the copies.
 // qd: the stage's increments (increment modes, stages 2 and 3), else NULL.
+// With q_ready (stage 1 of igr_step_host) the energy field of qs may still
+// be arriving: the source and the sweeps read only rho and m, so they run
+// first; then c->st waits for q_ready and the step's dt is formed from the
+// whole state just before the flux, its first reader.
 static igr_status run_stage(igr_ctx *c, int mode, const void *qs, const void *qd, const void *qn, void *out,
-                            void *base_out = nullptr, void *host_out = nullptr)
+                            void *base_out = nullptr, void *host_out = nullptr, cudaEvent_t q_ready = nullptr)
 {
     prof_begin(c, KC_SOURCE);
     CU(c, c->ops->source(c->g, c->p, c->tiles, inflow_of(c), qs, qd, c->b, c->rho16, c->st));
@@ -450,6 +458,12 @@ static igr_status run_stage(igr_ctx *c, int mode, const void *qs, const void *qd
     igr_status s = launch_sweeps(c, c->tiles, qj, c->b, c->sig[c->cur], c->sig[1 - c->cur], c->cfg.sweeps, &res);
     if (s != IGR_OK) return s;
     c->cur = res == c->sig[0] ? 0 : 1;
+    if (q_ready) {
+        CU(c, cudaStreamWaitEvent(c->st, q_ready, 0));
+        s = refresh_speed(c);
+        if (s == IGR_OK) s = finalize_dt(c, 0.0);
+        if (s != IGR_OK) return s;
+    }
     if (!host_out) {
         prof_begin(c, KC_FLUX);
         CU(c, c->ops->flux(c->g, c->p, c->tiles, inflow_of(c), mode, qs, qd, c->sig[c->cur], qn, out,
@@ -659,6 +673,7 @@ igr_status igr_destroy(igr_ctx *c)
     if (c->copy_st) {
         cudaStreamSynchronize(c->copy_st);
         for (cudaEvent_t e : c->slab_ev) cudaEventDestroy(e);
+        for (cudaEvent_t e : c->in_ev) cudaEventDestroy(e);
         cudaStreamDestroy(c->copy_st);
     }
     delete c;
@@ -766,33 +781,46 @@ igr_status igr_get_state(igr_ctx *c, void *q, void *sigma, igr_dtype dtype, int 
 
 // One SSP-RK3 step; with host_out the final state is also copied there,
 // overlapped with the last stage (see run_stage).
-static igr_status one_step(igr_ctx *c, double fixed_dt, void *host_out)
+// dt of the step (the CFL rule on the wave-speed maxima of the current
+// state, or fixed_dt > 0) into the device scalars
+static igr_status finalize_dt(igr_ctx *c, double fixed_dt)
 {
-    if (fixed_dt <= 0.0) {
-        igr_status s = refresh_speed(c);
-        if (s != IGR_OK) return s;
-    }
     prof_begin(c, KC_OTHER);
     k_finalize_dt<<<1, 1024, 0, c->st>>>(c->blockmax, c->speed_nblocks, c->sc, c->cfg.cfl * c->cfg.dx,
                                         fixed_dt);
     CU(c, cudaGetLastError());
     prof_end(c);
+    return IGR_OK;
+}
+
+// One SSP-RK3 step. q_ready (igr_step_host): the energy field of q^n is
+// still being copied in until that event; stage 1 forms dt after its sweeps.
+static igr_status one_step(igr_ctx *c, double fixed_dt, void *host_out, cudaEvent_t q_ready = nullptr)
+{
     igr_status s;
+    if (!q_ready) {
+        if (fixed_dt <= 0.0) {
+            s = refresh_speed(c);
+            if (s != IGR_OK) return s;
+        }
+        s = finalize_dt(c, fixed_dt);
+        if (s != IGR_OK) return s;
+    }
     if (c->hbase) {
         // RK base in host memory: stage 1 copies q^n there while it reads it,
         // stages 2 and 3 read it back; the two device buffers alternate
-        s = run_stage(c, FLUX_STAGE1, c->q[0], nullptr, c->q[0], c->q[1], c->hbase_dev);
+        s = run_stage(c, FLUX_STAGE1, c->q[0], nullptr, c->q[0], c->q[1], c->hbase_dev, nullptr, q_ready);
         if (s == IGR_OK) s = run_stage(c, FLUX_STAGE2, c->q[1], nullptr, c->hbase_dev, c->q[0]);
         if (s == IGR_OK) s = run_stage(c, FLUX_STAGE3, c->q[0], nullptr, c->hbase_dev, c->q[1], nullptr, host_out);
         std::swap(c->q[0], c->q[1]);
     } else if (c->inc) {
         // FP32 state q^n, 16-bit increments: stage s reads q^n + d_s
-        s = run_stage(c, FLUX_STAGE1, c->q[0], nullptr, c->q[0], c->q[1]);
+        s = run_stage(c, FLUX_STAGE1, c->q[0], nullptr, c->q[0], c->q[1], nullptr, nullptr, q_ready);
         if (s == IGR_OK) s = run_stage(c, FLUX_STAGE2, c->q[0], c->q[1], c->q[0], c->q[2]);
         if (s == IGR_OK) s = run_stage(c, FLUX_STAGE3, c->q[0], c->q[2], c->q[0], c->qalt, nullptr, host_out);
         std::swap(c->q[0], c->qalt);
     } else {
-        s = run_stage(c, FLUX_STAGE1, c->q[0], nullptr, c->q[0], c->q[1]);
+        s = run_stage(c, FLUX_STAGE1, c->q[0], nullptr, c->q[0], c->q[1], nullptr, nullptr, q_ready);
         if (s == IGR_OK) s = run_stage(c, FLUX_STAGE2, c->q[1], nullptr, c->q[0], c->q[2]);
         if (s == IGR_OK) s = run_stage(c, FLUX_STAGE3, c->q[2], nullptr, c->q[0], c->q[0], nullptr, host_out);
     }
@@ -839,15 +867,25 @@ igr_status igr_step_host(igr_ctx *c, const void *q_in, void *q_out, int nsteps, 
     if (!c->copy_st) {
         CU(c, cudaStreamCreateWithFlags(&c->copy_st, cudaStreamNonBlocking));
         for (cudaEvent_t &e : c->slab_ev) CU(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        for (cudaEvent_t &e : c->in_ev) CU(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    // q in; Sigma stays on the device (as with igr_set_conserved)
-    igr_status s = copy_in(c, q_in, c->q[0], 5 * c->g.n, dtype, 0, state_dtype(c->cfg.prec));
-    if (s != IGR_OK) return s;
+    // q in (the host buffer has the state type); Sigma stays on the device
+    // (as with igr_set_conserved). rho and m come first on c->st, then the
+    // energy field on copy_st while stage 1's source and sweeps, which read
+    // rho and m only, run; stage 1 waits for it before its dt and flux.
+    const size_t sb = c->ops->state_bytes, nb = (size_t)c->g.n * sb;
+    CU(c, cudaMemcpyAsync(c->q[0], q_in, 4 * nb, cudaMemcpyHostToDevice, c->st));
+    CU(c, cudaEventRecord(c->in_ev[0], c->st));
+    CU(c, cudaStreamWaitEvent(c->copy_st, c->in_ev[0], 0));
+    CU(c, cudaMemcpyAsync((char *)c->q[0] + 4 * nb, (const char *)q_in + 4 * nb, nb, cudaMemcpyHostToDevice,
+                          c->copy_st));
+    CU(c, cudaEventRecord(c->in_ev[1], c->copy_st));
     c->speed_nblocks = 0;
     c->warn_flags = 0;
     CU(c, cudaMemsetAsync(&c->sc->err, 0, sizeof(int), c->st));
+    igr_status s;
     for (int n = 0; n < nsteps; n++) {
-        s = one_step(c, 0.0, n == nsteps - 1 ? q_out : nullptr);
+        s = one_step(c, 0.0, n == nsteps - 1 ? q_out : nullptr, n == 0 ? c->in_ev[1] : nullptr);
         if (s != IGR_OK) return s;
     }
     return read_flags(c);  // synchronises the stream, which waits for the copies
