@@ -964,6 +964,60 @@ __device__ __forceinline__ void sh_ld4(const double *p, double v[4])
 constexpr int HXV = TXV + 2 * VX;           // interior at column VX (16-byte aligned)
 constexpr int NYH = 2 * BX, NXH = 2 * BY;   // 4-wide y-halo tasks, scalar x-halo tasks
 
+// The update of four cells (x-consecutive, of one row) as two packed FP32x2
+// pairs, cells (0, 1) and (2, 3); lane for lane the sequence of jacobi_cell
+// (faces -x, +x, -y, +y, -z, +z). r0, s0: the cells; rl, sl / rr, sr: the
+// x-neighbours left of cell 0 and right of cell 3; ry0 / ry1 (sy0 / sy1):
+// the rows below / above; rm, sm / rp, sp: the planes below / above; bv:
+// the source; hb = beta / 2 and the face factors of the four cells' outer
+// faces (the inner x-faces are always hb).
+__device__ __forceinline__ void jacobi4_packed(const float (&r0)[4], const float (&s0)[4], float rl, float sl,
+                                               float rr, float sr, const float (&ry0)[4], const float (&ry1)[4],
+                                               const float (&sy0)[4], const float (&sy1)[4], const float (&rm)[4],
+                                               const float (&sm)[4], const float (&rp)[4], const float (&sp)[4],
+                                               const float (&bv)[4], float hb, float exm, float exp_, float eym,
+                                               float eyp, float ezm, float ezp, float (&o)[4])
+{
+    const float2 r01 = make_float2(r0[0], r0[1]), r23 = make_float2(r0[2], r0[3]), r12 = make_float2(r0[1], r0[2]);
+    const float2 s01 = make_float2(s0[0], s0[1]), s23 = make_float2(s0[2], s0[3]), s12 = make_float2(s0[1], s0[2]);
+    const float2 rxm[2] = {make_float2(rl, r0[0]), r12}, rxp[2] = {r12, make_float2(r0[3], rr)};
+    const float2 sxm[2] = {make_float2(sl, s0[0]), s12}, sxp[2] = {s12, make_float2(s0[3], sr)};
+    const float2 exmp[2] = {make_float2(exm, hb), make_float2(hb, hb)};
+    const float2 expp[2] = {make_float2(hb, hb), make_float2(hb, exp_)};
+    const float2 rc[2] = {r01, r23};
+    (void)s01;
+    (void)s23;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int c = 2 * h;
+        float2 c0 = pmul(exmp[h], padd(rc[h], rxm[h]));
+        float2 c1 = pmul(expp[h], padd(rc[h], rxp[h]));
+        float2 c2 = pmul(make_float2(eym, eym), padd(rc[h], make_float2(ry0[c], ry0[c + 1])));
+        float2 c3 = pmul(make_float2(eyp, eyp), padd(rc[h], make_float2(ry1[c], ry1[c + 1])));
+        float2 c4 = pmul(make_float2(ezm, ezm), padd(rc[h], make_float2(rm[c], rm[c + 1])));
+        float2 c5 = pmul(make_float2(ezp, ezp), padd(rc[h], make_float2(rp[c], rp[c + 1])));
+        float2 diag = padd(padd(padd(padd(padd(padd(rc[h], c0), c1), c2), c3), c4), c5);
+        float2 off = pmul(c0, sxm[h]);
+        off = pfma(c1, sxp[h], off);
+        off = pfma(c2, make_float2(sy0[c], sy0[c + 1]), off);
+        off = pfma(c3, make_float2(sy1[c], sy1[c + 1]), off);
+        off = pfma(c4, make_float2(sm[c], sm[c + 1]), off);
+        off = pfma(c5, make_float2(sp[c], sp[c + 1]), off);
+        float2 num = padd(make_float2(bv[c], bv[c + 1]), off);
+        float2 res = pmul(num, make_float2(rcp(diag.x), rcp(diag.y)));
+        o[c] = res.x;
+        o[c + 1] = res.y;
+    }
+}
+__device__ __forceinline__ void jacobi4_packed(const double (&)[4], const double (&)[4], double, double, double,
+                                               double, const double (&)[4], const double (&)[4],
+                                               const double (&)[4], const double (&)[4], const double (&)[4],
+                                               const double (&)[4], const double (&)[4], const double (&)[4],
+                                               const double (&)[4], double, double, double, double, double,
+                                               double, double, double (&)[4])
+{
+}  // (FP64 takes the scalar cells)
+
 // 4 raw values of field a at cells (x .. x+3) of row-plane offset rowoff:
 // one 4-wide load when the cells lie inside the row, mapped single loads otherwise
 template <class T>
@@ -1024,12 +1078,12 @@ template <bool HASD> __device__ __forceinline__ void cvq4(const QRaw4 &r, C o[4]
     StateIO4<kInc>::val<HASD>(r, o);
 }
 
-__device__ __forceinline__ void jacobi_v4_body(const S *__restrict__ q, const S *__restrict__ b, const S *sin,
-                                               S *sout, const Geom g, C beta, int zc, int colour,
-                                               const BlockPos bp)
+// The four-cell sweep of any block (tiles that cross the grid's edge in x
+// or y: lanes past the row's end, rows past the last, mapped loads).
+__device__ __forceinline__ void jacobi_v4_edge(const S *__restrict__ q, const S *__restrict__ b, const S *sin,
+                                               S *sout, const Geom &g, C beta, int zc, int colour,
+                                               const BlockPos &bp, C (*R)[HXV], C (*SG)[HXV])
 {
-    __shared__ __align__(16) C R[HY][HXV];
-    __shared__ __align__(16) C SG[HY][HXV];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int x0 = bp.x * TXV, y0 = bp.y * BY;
     const int i0 = x0 + VX * tx, j = y0 + ty;
@@ -1128,37 +1182,9 @@ __device__ __forceinline__ void jacobi_v4_body(const S *__restrict__ q, const S 
             sh_ld4(&SG[ty][col], sy0);
             sh_ld4(&SG[ty + 2][col], sy1);
             if constexpr (sizeof(C) == 4) {
-                // cells (0, 1) and (2, 3) as packed pairs; the faces in the
-                // order -x, +x, -y, +y, -z, +z as in the scalar form
-                const C rl = R[ty + 1][col - 1], sl = SG[ty + 1][col - 1];
-                const C rr = R[ty + 1][col + VX], sr = SG[ty + 1][col + VX];
-                const C2 r01 = pset(r0[0], r0[1]), r23 = pset(r0[2], r0[3]), r12 = pset(r0[1], r0[2]);
-                const C2 s01 = pset(s0[0], s0[1]), s23 = pset(s0[2], s0[3]), s12 = pset(s0[1], s0[2]);
-                const C2 rxm[2] = {pset(rl, r0[0]), r12}, rxp[2] = {r12, pset(r0[3], rr)};
-                const C2 sxm[2] = {pset(sl, s0[0]), s12}, sxp[2] = {s12, pset(s0[3], sr)};
-                const C2 exmp[2] = {pset(exm, hb), bcast(hb)}, expp[2] = {bcast(hb), pset(hb, exp_)};
-                const C2 rc[2] = {r01, r23};
-#pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    const int c = 2 * h;
-                    C2 c0 = pmul(exmp[h], padd(rc[h], rxm[h]));
-                    C2 c1 = pmul(expp[h], padd(rc[h], rxp[h]));
-                    C2 c2 = pmul(bcast(eym), padd(rc[h], pset(ry0[c], ry0[c + 1])));
-                    C2 c3 = pmul(bcast(eyp), padd(rc[h], pset(ry1[c], ry1[c + 1])));
-                    C2 c4 = pmul(bcast(ezm), padd(rc[h], pset(rm[c], rm[c + 1])));
-                    C2 c5 = pmul(bcast(ezp), padd(rc[h], pset(rp[c], rp[c + 1])));
-                    C2 diag = padd(padd(padd(padd(padd(padd(rc[h], c0), c1), c2), c3), c4), c5);
-                    C2 off = pmul(c0, sxm[h]);
-                    off = pfma(c1, sxp[h], off);
-                    off = pfma(c2, pset(sy0[c], sy0[c + 1]), off);
-                    off = pfma(c3, pset(sy1[c], sy1[c + 1]), off);
-                    off = pfma(c4, pset(sm[c], sm[c + 1]), off);
-                    off = pfma(c5, pset(sp[c], sp[c + 1]), off);
-                    C2 num = padd(pset(bv[c], bv[c + 1]), off);
-                    C2 res = pmul(num, pset(rcp(diag.x), rcp(diag.y)));
-                    o[c] = res.x;
-                    o[c + 1] = res.y;
-                }
+                jacobi4_packed(r0, s0, R[ty + 1][col - 1], SG[ty + 1][col - 1], R[ty + 1][col + VX],
+                               SG[ty + 1][col + VX], ry0, ry1, sy0, sy1, rm, sm, rp, sp, bv, hb, exm, exp_, eym,
+                               eyp, ezm, ezp, o);
 #pragma unroll
                 for (int c = 0; c < VX; c++)
                     if (colour >= 0 && ((i0 + c + j + k) & 1) != colour) o[c] = s0[c];
@@ -1187,6 +1213,145 @@ __device__ __forceinline__ void jacobi_v4_body(const S *__restrict__ q, const S 
             r0[c] = rp[c]; s0[c] = sp[c];
         }
     }
+}
+// The four-cell sweep of a block whose tile lies inside the grid in x and y
+// (FP32 arithmetic): every lane owns four cells of a row, its loads are
+// whole 4-wide rows, and the halo offsets are mapped once. Warps 0 and 1
+// load the rows below and above the tile, lanes 0..15 of warp 2 the cells
+// left and right of its rows. The update is jacobi4_packed, as in
+// jacobi_v4_edge, so both give the same bits. RB: a red-black half-sweep of
+// the given colour (cells of the other colour keep and write back Sigma).
+template <bool RB>
+__device__ __forceinline__ void jacobi_v4_full(const S *__restrict__ q, const S *__restrict__ b, const S *sin,
+                                               S *sout, const Geom &g, C beta, int zc, int colour,
+                                               const BlockPos &bp, C (*R)[HXV], C (*SG)[HXV])
+{
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = bp.x * TXV, y0 = bp.y * BY;
+    const int i0 = x0 + VX * tx, j = y0 + ty;
+    const int k0 = bp.z * zc, k1 = min(g.nz, k0 + zc);
+    const idx pl = (idx)g.plane;
+    const idx own = (idx)j * (idx)g.nx + (idx)i0;
+    // halo: warp 0 the row below the tile, warp 1 the row above (4-wide),
+    // warp 2 lanes 0..7 the cells left of rows 0..7, lanes 8..15 right
+    const bool yh = ty < 2, xh = ty == 2 && tx < 2 * BY;
+    int hsy = 0, hsx = 0;
+    idx hoff = 0;
+    if (yh) {
+        hsy = ty ? HY - 1 : 0;
+        hsx = VX + VX * tx;
+        hoff = (idx)map_axis(y0 + (ty ? BY : -1), g.ny, g.bc[2], g.bc[3]) * (idx)g.nx + (idx)i0;
+    } else if (xh) {
+        const int side = tx / BY, r = tx % BY;
+        hsy = 1 + r;
+        hsx = side ? VX + TXV : VX - 1;
+        hoff = (idx)(y0 + r) * (idx)g.nx + (idx)map_axis(side ? x0 + TXV : x0 - 1, g.nx, g.bc[0], g.bc[1]);
+    }
+    const C hb = C(0.5) * beta;
+    const C exm = (i0 > 0 || g.bc[0] == BC_PERIODIC) ? hb : C(0);
+    const C exp_ = (i0 + VX - 1 < g.nx - 1 || g.bc[1] == BC_PERIODIC) ? hb : C(0);
+    const C eym = (j > 0 || g.bc[2] == BC_PERIODIC) ? hb : C(0);
+    const C eyp = (j < g.ny - 1 || g.bc[3] == BC_PERIODIC) ? hb : C(0);
+
+    C rm[VX], sm[VX], r0[VX], s0[VX], rp[VX], sp[VX];
+    {
+        C t[VX];
+        const idx zm = (idx)zmap(k0 - 1, g) * pl + own, z0 = (idx)k0 * pl + own;
+        cv4(ld4r(CKP4(q + zm, q, g.n)), t);
+        cv4(ld4r(CKP4(sin + zm, sin, g.n)), sm);
+#pragma unroll
+        for (int c = 0; c < VX; c++) rm[c] = rcp(t[c]);
+        cv4(ld4r(CKP4(q + z0, q, g.n)), t);
+        cv4(ld4r(CKP4(sin + z0, sin, g.n)), s0);
+#pragma unroll
+        for (int c = 0; c < VX; c++) r0[c] = rcp(t[c]);
+    }
+    // raw values one iteration ahead: own cells at k + 1, halo and b at k
+    V4 ncr, ncs, nb, nhr, nhs;
+    S nxr = S(1.0f), nxs = S(0.0f);
+    auto pre = [&](int kk) {
+        const idx pz = (idx)zmap(kk + 1, g) * pl + own, pk = (idx)kk * pl;
+        ncr = ld4r(CKP4(q + pz, q, g.n));
+        ncs = ld4r(CKP4(sin + pz, sin, g.n));
+        nb = ld4r(CKP4(b + pk + own, b, g.n));
+        if (yh) {
+            nhr = ld4r(CKP4(q + pk + hoff, q, g.n));
+            nhs = ld4r(CKP4(sin + pk + hoff, sin, g.n));
+        } else if (xh) {
+            nxr = ldr(CKP(q + pk + hoff, q, g.n));
+            nxs = ldr(CKP(sin + pk + hoff, sin, g.n));
+        }
+    };
+    pre(k0);
+    const int col = VX + VX * tx;
+    for (int k = k0; k < k1; k++) {
+        C bv[VX], t[VX];
+        cv4(ncr, t);
+        cv4(ncs, sp);
+#pragma unroll
+        for (int c = 0; c < VX; c++) rp[c] = rcp(t[c]);
+        cv4(nb, bv);
+        C hr[VX], hsg[VX];
+        if (yh) {
+            cv4(nhr, t);
+            cv4(nhs, hsg);
+#pragma unroll
+            for (int c = 0; c < VX; c++) hr[c] = rcp(t[c]);
+        } else if (xh) {
+            hr[0] = rcp(cv(nxr));
+            hsg[0] = cv(nxs);
+        }
+        if (k + 1 < k1) pre(k + 1);
+        __syncthreads();
+        sh_st4(&R[ty + 1][col], r0);
+        sh_st4(&SG[ty + 1][col], s0);
+        if (yh) {
+            sh_st4(&R[cks(hsy, HY)][cks4(hsx, HXV)], hr);
+            sh_st4(&SG[cks(hsy, HY)][cks4(hsx, HXV)], hsg);
+        } else if (xh) {
+            R[cks(hsy, HY)][cks(hsx, HXV)] = hr[0];
+            SG[cks(hsy, HY)][cks(hsx, HXV)] = hsg[0];
+        }
+        __syncthreads();
+        const C ezm = (k > 0 || g.bc[4] == BC_PERIODIC) ? hb : C(0);
+        const C ezp = (k < g.nz - 1 || g.bc[5] == BC_PERIODIC) ? hb : C(0);
+        C ry0[VX], ry1[VX], sy0[VX], sy1[VX], o[VX];
+        sh_ld4(&R[ty][col], ry0);
+        sh_ld4(&R[ty + 2][col], ry1);
+        sh_ld4(&SG[ty][col], sy0);
+        sh_ld4(&SG[ty + 2][col], sy1);
+        jacobi4_packed(r0, s0, R[ty + 1][col - 1], SG[ty + 1][col - 1], R[ty + 1][col + VX], SG[ty + 1][col + VX],
+                       ry0, ry1, sy0, sy1, rm, sm, rp, sp, bv, hb, exm, exp_, eym, eyp, ezm, ezp, o);
+        if constexpr (RB) {
+#pragma unroll
+            for (int c = 0; c < VX; c++)
+                if (((i0 + c + j + k) & 1) != colour) o[c] = s0[c];
+        }
+        st4(CKP4(sout + (idx)k * pl + own, sout, g.n), o);
+#pragma unroll
+        for (int c = 0; c < VX; c++) {
+            rm[c] = r0[c]; sm[c] = s0[c];
+            r0[c] = rp[c]; s0[c] = sp[c];
+        }
+    }
+}
+
+__device__ __forceinline__ void jacobi_v4_body(const S *__restrict__ q, const S *__restrict__ b, const S *sin,
+                                               S *sout, const Geom g, C beta, int zc, int colour,
+                                               const BlockPos bp)
+{
+    __shared__ __align__(16) C R[HY][HXV];
+    __shared__ __align__(16) C SG[HY][HXV];
+    if constexpr (sizeof(C) == 4) {
+        if (bp.x * TXV + TXV <= g.nx && bp.y * BY + BY <= g.ny) {  // block-uniform
+            if (colour < 0)
+                jacobi_v4_full<false>(q, b, sin, sout, g, beta, zc, colour, bp, R, SG);
+            else
+                jacobi_v4_full<true>(q, b, sin, sout, g, beta, zc, colour, bp, R, SG);
+            return;
+        }
+    }
+    jacobi_v4_edge(q, b, sin, sout, g, beta, zc, colour, bp, R, SG);
 }
 constexpr int JACOBI_V4_BLOCKS = sizeof(S) == 2 ? 3 : sizeof(S) == 4 ? 2 : 1;  // resident per SM
 __global__ void __launch_bounds__(BT, JACOBI_V4_BLOCKS) k_jacobi_v4(const S *__restrict__ q, const S *__restrict__ b,
