@@ -1286,32 +1286,27 @@ __device__ __forceinline__ void jacobi_v4_full(const S *__restrict__ q, const S 
     const int col = VX + VX * tx;
     for (int k = k0; k < k1; k++) {
         C bv[VX], t[VX];
+        __syncthreads();  // the tile of plane k - 1 is read
+        sh_st4(&R[ty + 1][col], r0);
+        sh_st4(&SG[ty + 1][col], s0);
+        if (yh) {
+            C hr[VX], hsg[VX];
+            cv4(nhr, t);
+            cv4(nhs, hsg);
+#pragma unroll
+            for (int c = 0; c < VX; c++) hr[c] = rcp(t[c]);
+            sh_st4(&R[cks(hsy, HY)][cks4(hsx, HXV)], hr);
+            sh_st4(&SG[cks(hsy, HY)][cks4(hsx, HXV)], hsg);
+        } else if (xh) {
+            R[cks(hsy, HY)][cks(hsx, HXV)] = rcp(cv(nxr));
+            SG[cks(hsy, HY)][cks(hsx, HXV)] = cv(nxs);
+        }
         cv4(ncr, t);
         cv4(ncs, sp);
 #pragma unroll
         for (int c = 0; c < VX; c++) rp[c] = rcp(t[c]);
         cv4(nb, bv);
-        C hr[VX], hsg[VX];
-        if (yh) {
-            cv4(nhr, t);
-            cv4(nhs, hsg);
-#pragma unroll
-            for (int c = 0; c < VX; c++) hr[c] = rcp(t[c]);
-        } else if (xh) {
-            hr[0] = rcp(cv(nxr));
-            hsg[0] = cv(nxs);
-        }
         if (k + 1 < k1) pre(k + 1);
-        __syncthreads();
-        sh_st4(&R[ty + 1][col], r0);
-        sh_st4(&SG[ty + 1][col], s0);
-        if (yh) {
-            sh_st4(&R[cks(hsy, HY)][cks4(hsx, HXV)], hr);
-            sh_st4(&SG[cks(hsy, HY)][cks4(hsx, HXV)], hsg);
-        } else if (xh) {
-            R[cks(hsy, HY)][cks(hsx, HXV)] = hr[0];
-            SG[cks(hsy, HY)][cks(hsx, HXV)] = hsg[0];
-        }
         __syncthreads();
         const C ezm = (k > 0 || g.bc[4] == BC_PERIODIC) ? hb : C(0);
         const C ezp = (k < g.nz - 1 || g.bc[5] == BC_PERIODIC) ? hb : C(0);
@@ -1359,6 +1354,21 @@ __global__ void __launch_bounds__(BT, JACOBI_V4_BLOCKS) k_jacobi_v4(const S *__r
                                                                   int colour)
 {
     jacobi_v4_body(q, b, sin, sout, g, beta, zc, colour, BlockPos::of_launch());
+}
+// Grids whose every 4-cell tile lies inside (rows a multiple of 128 cells,
+// a multiple of 8 rows; FP32 arithmetic) launch the full-tile body alone:
+// without the edge body in the same kernel it keeps its values in registers
+// (the combined kernel spills).
+template <bool RB>
+__global__ void __launch_bounds__(BT, JACOBI_V4_BLOCKS) k_jacobi_v4_full(const S *__restrict__ q,
+                                                                       const S *__restrict__ b, const S *sin,
+                                                                       S *sout, Geom g, C beta, int zc, int colour)
+{
+    if constexpr (sizeof(C) == 4) {
+        __shared__ __align__(16) C R[HY][HXV];
+        __shared__ __align__(16) C SG[HY][HXV];
+        jacobi_v4_full<RB>(q, b, sin, sout, g, beta, zc, colour, BlockPos::of_launch(), R, SG);
+    }
 }
 
 
@@ -2707,6 +2717,13 @@ cudaError_t launch_jacobi(const Geom &g, const Phys &p, const Tiles &t, const vo
                           const void *b, const void *s_in, void *s_out, int colour, cudaStream_t st)
 {
     if (t.vec_jacobi && g.nx % VX == 0) {
+        if (sizeof(C) == 4 && g.nx % TXV == 0 && g.ny % BY == 0) {
+            auto kern = colour < 0 ? k_jacobi_v4_full<false> : k_jacobi_v4_full<true>;
+            kern<<<grid_of(g, TXV, BY, t.zc_jacobi), dim3(BX, BY), 0, st>>>(
+                (const S *)q, (const S *)b, (const S *)s_in, (S *)s_out, g, C(p.alpha / (p.dx * p.dx)),
+                t.zc_jacobi, colour);
+            return cudaGetLastError();
+        }
         k_jacobi_v4<<<grid_of(g, TXV, BY, t.zc_jacobi), dim3(BX, BY), 0, st>>>(
             (const S *)q, (const S *)b, (const S *)s_in, (S *)s_out, g, C(p.alpha / (p.dx * p.dx)),
             t.zc_jacobi, colour);

@@ -104,29 +104,34 @@ def _jets_case(n=40):
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32", "f16", "bf16", "f16inc", "bf16inc"])
-@pytest.mark.parametrize("kind", ["jets", "tgv_rbgs", "wide", "wide_rbgs"])
+@pytest.mark.parametrize("kind", ["jets", "tgv_rbgs", "wide", "wide_rbgs", "full", "full_rbgs"])
 def test_kernel_forms_give_the_same_bits(precision, kind):
     """Every combination of the one- and four-cell forms of the source and
     Jacobi kernels gives the same bits. Rows of 40 and 24 cells: the default
     rule picks the one-cell forms there, the four-cell forms are forced, and
     every block of the four-cell forms is an edge block. Rows of 260 cells
     and 20 rows: blocks of 128 x 8 cells inside the grid (no mapped loads)
-    beside edge blocks in x and y."""
+    beside edge blocks in x and y. Rows of 128 cells and 16 rows: every
+    block inside, the sweep launched as the full-tile kernel alone."""
     import torch
     from dataclasses import replace
     from paper_2505_07392_gb300 import igr
-    if kind in ("jets", "wide"):
+    if kind in ("jets", "wide", "full"):
         case = _jets_case()
         if kind == "wide":
             case = replace(case, nx=260, ny=20, nz=12)
+        if kind == "full":
+            case = replace(case, nx=128, ny=16, nz=12)
         q0 = torch.from_numpy(inputs.jet_initial_state(case))
     else:
         case = replace(inputs.tgv(24, instance=3), sigma_solver=1)
         if kind == "wide_rbgs":
             case = replace(case, nx=260, ny=20, nz=12)
+        if kind == "full_rbgs":
+            case = replace(case, nx=128, ny=16, nz=12)
         q0 = torch.from_numpy(inputs.initial_state(case))
     q0 = q0.to(igr.state_torch_dtype(precision)).cuda()
-    if not kind.startswith("wide"):
+    if kind in ("jets", "tgv_rbgs"):
         with igr.Solver(case, precision) as s:
             assert s.kernel_forms() == (0, 0)
     ref = _alone(case, q0, precision, 3, forms=(0, 0))
