@@ -1045,6 +1045,13 @@ template <> struct StateIO4<false> {  // (used where the state has the storage t
         return ld4_mapped(reinterpret_cast<const S *>(q.b[u]), g, rowoff, x);
     }
     template <bool HASD> static __device__ __forceinline__ void val(const V4 &r, C o[4]) { cv4(r, o); }
+    // cells off .. off+3 inside one row: one 4-wide load
+    template <bool HASD>
+    static __device__ __forceinline__ V4 ldd(const QIn &q, int u, const Geom &g, idx off)
+    {
+        const S *f = reinterpret_cast<const S *>(q.b[u]);
+        return ld4r(CKP4(f + off, f, g.n));
+    }
 };
 template <> struct StateIO4<true> {
     using Raw = QRaw4Inc;
@@ -1054,6 +1061,14 @@ template <> struct StateIO4<true> {
         QRaw4Inc r;
         r.b = ld4_mapped(q.b[0] + u * q.fs, g, rowoff, x);
         if constexpr (HASD) r.d = ld4_mapped(q.d[0] + u * q.fs, g, rowoff, x);
+        return r;
+    }
+    template <bool HASD>
+    static __device__ __forceinline__ QRaw4Inc ldd(const QIn &q, int u, const Geom &g, idx off)
+    {
+        QRaw4Inc r;
+        r.b = ld4r(CKP4(q.b[0] + u * q.fs + off, q.b[0], 5 * g.n));
+        if constexpr (HASD) r.d = ld4r(CKP4(q.d[0] + u * q.fs + off, q.d[0], 5 * g.n));
         return r;
     }
     template <bool HASD> static __device__ __forceinline__ void val(const QRaw4Inc &r, C o[4])
@@ -1542,6 +1557,160 @@ __device__ __forceinline__ void source_v4_body(const QIn q, S *__restrict__ b, S
         for (int c = 0; c < VX; c++) rho0[c] = rhop[c];
     }
 }
+// 4 raw state values (cells off .. off+3 of field u, inside one row)
+template <bool HASD>
+__device__ __forceinline__ QRaw4 ldq4d(const QIn &q, int u, const Geom &g, idx off)
+{
+    return StateIO4<kInc>::ldd<HASD>(q, u, g, off);
+}
+
+// The 4-cell source of a grid whose every tile lies inside (rows a multiple
+// of 128 cells, a multiple of 8 rows): the body of source_v4_body without
+// lanes past the row's end, with whole 4-wide loads and halo offsets mapped
+// once (warps 0 and 1: the rows below and above; lanes 0..15 of warp 2: the
+// cells left and right of the rows). The same operations per cell, so the
+// same bits.
+template <bool HASD>
+__device__ __forceinline__ void source_v4_full(const QIn q, S *__restrict__ b, S *__restrict__ rho_out,
+                                               const Geom g, C alpha_s, const C *W, const C *J, int zc,
+                                               const BlockPos bp)
+{
+    __shared__ __align__(16) C U[3][HY][HXV];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = bp.x * TXV, y0 = bp.y * BY;
+    const int i0 = x0 + VX * tx, j = y0 + ty;
+    const int k0 = bp.z * zc, k1 = min(g.nz, k0 + zc);
+    const idx pl = (idx)g.plane;
+    const idx own = (idx)j * (idx)g.nx + (idx)i0;
+    const bool yh = ty < 2, xh = ty == 2 && tx < 2 * BY;
+    int hsy = 0, hsx = 0;
+    idx hoff = 0;
+    if (yh) {
+        hsy = ty ? HY - 1 : 0;
+        hsx = VX + VX * tx;
+        hoff = (idx)map_axis(y0 + (ty ? BY : -1), g.ny, g.bc[2], g.bc[3]) * (idx)g.nx + (idx)i0;
+    } else if (xh) {
+        const int side = tx / BY, r = tx % BY;
+        hsy = 1 + r;
+        hsx = side ? VX + TXV : VX - 1;
+        hoff = (idx)(y0 + r) * (idx)g.nx + (idx)map_axis(side ? x0 + TXV : x0 - 1, g.nx, g.bc[0], g.bc[1]);
+    }
+    auto u4 = [&](const QRaw4 (&r)[4], C u[3][VX], C rho[VX]) {
+        C m[VX], rr[VX];
+        cvq4<HASD>(r[0], rho);
+#pragma unroll
+        for (int c = 0; c < VX; c++) rr[c] = rcp(rho[c]);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            cvq4<HASD>(r[1 + a], m);
+#pragma unroll
+            for (int c = 0; c < VX; c++) u[a][c] = mul_rn(m[c], rr[c]);
+        }
+    };
+    auto own_u = [&](int kk, C u[3][VX], C rho[VX]) {
+        const idx zb = (idx)zmap(kk, g) * pl + own;
+        C v[4][VX];
+#pragma unroll
+        for (int f = 0; f < 4; f++) cvq4<HASD>(ldq4d<HASD>(q, f, g, zb), v[f]);
+#pragma unroll
+        for (int c = 0; c < VX; c++) rho[c] = v[0][c];
+        if (kk < 0 && g.bc[4] == BC_INFLOW) {
+#pragma unroll
+            for (int c = 0; c < VX; c++) {
+                const idx fc = ck(own + (idx)c, g.plane);
+                C w = C(1) - W[fc];
+#pragma unroll
+                for (int f = 0; f < 4; f++) v[f][c] = fma_rn(w, v[f][c], J[(idx)f * pl + fc]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < VX; c++) {
+            C r = rcp(v[0][c]);
+#pragma unroll
+            for (int a = 0; a < 3; a++) u[a][c] = mul_rn(v[1 + a][c], r);
+        }
+    };
+    C um[3][VX], u0[3][VX], up[3][VX];
+    C rho0[VX], rhop[VX];
+    own_u(k0 - 1, um, rhop);
+    own_u(k0, u0, rho0);
+    constexpr bool kHaloAhead = !(kInc && HASD);
+    QRaw4 nc[4], nh[4];
+    QRaw nxh[4];
+    auto halo = [&](int kk) {
+        if (yh) {
+#pragma unroll
+            for (int f = 0; f < 4; f++) nh[f] = ldq4d<HASD>(q, f, g, (idx)kk * pl + hoff);
+        } else if (xh) {
+#pragma unroll
+            for (int f = 0; f < 4; f++) nxh[f] = ldqr<HASD>(q, f, ck((idx)kk * pl + hoff, g.n));
+        }
+    };
+    auto pre = [&](int kk) {
+        const idx pz = (idx)zmap(kk + 1, g) * pl + own;
+#pragma unroll
+        for (int f = 0; f < 4; f++) nc[f] = ldq4d<HASD>(q, f, g, pz);
+        if (kHaloAhead) halo(kk);
+    };
+    pre(k0);
+    const int col = VX + VX * tx;
+    for (int k = k0; k < k1; k++) {
+        if (!kHaloAhead) halo(k);
+        __syncthreads();  // readers of the previous plane are done
+#pragma unroll
+        for (int a = 0; a < 3; a++) sh_st4(&U[a][ty + 1][col], u0[a]);
+        if (yh) {
+            C hu[3][VX], hrho[VX];
+            u4(nh, hu, hrho);
+#pragma unroll
+            for (int a = 0; a < 3; a++) sh_st4(&U[a][cks(hsy, HY)][cks4(hsx, HXV)], hu[a]);
+        } else if (xh) {
+            C r = rcp(cvq<HASD>(nxh[0]));
+#pragma unroll
+            for (int a = 0; a < 3; a++) U[a][cks(hsy, HY)][cks(hsx, HXV)] = mul_rn(cvq<HASD>(nxh[1 + a]), r);
+        }
+        u4(nc, up, rhop);
+        if (k + 1 < k1) pre(k + 1);
+        __syncthreads();
+        C ym[3][VX], yp[3][VX], o[VX];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            sh_ld4(&U[a][ty][col], ym[a]);
+            sh_ld4(&U[a][ty + 2][col], yp[a]);
+        }
+        C xl[3], xr[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            xl[a] = U[a][ty + 1][col - 1];
+            xr[a] = U[a][ty + 1][col + VX];
+        }
+#pragma unroll
+        for (int c = 0; c < VX; c++) {
+            C D[3][3];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                C xm = c > 0 ? u0[a][c - 1] : xl[a];
+                C xp = c < VX - 1 ? u0[a][c + 1] : xr[a];
+                D[a][0] = xp - xm;
+                D[a][1] = yp[a][c] - ym[a][c];
+                D[a][2] = up[a][c] - um[a][c];
+            }
+            o[c] = source_b(D, alpha_s);
+        }
+        st4(CKP4(b + (idx)k * pl + own, b, g.n), o);
+        if constexpr (kInc) st4(CKP4(rho_out + (idx)k * pl + own, rho_out, g.n), rho0);
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int c = 0; c < VX; c++) {
+                um[a][c] = u0[a][c];
+                u0[a][c] = up[a][c];
+            }
+#pragma unroll
+        for (int c = 0; c < VX; c++) rho0[c] = rhop[c];
+    }
+}
+
 // Two blocks per SM (at most 128 registers): the kernel waits on load
 // latency, and one block per SM, which a free register choice gives (about
 // 156 registers), runs it 1.6x slower. The increment modes' form, which
@@ -1553,6 +1722,13 @@ __global__ void __launch_bounds__(BT, SOURCE_V4_BLOCKS) k_source_v4(QIn q, S *__
                                                    C alpha_s, const C *W, const C *J, int zc)
 {
     source_v4_body<HASD>(q, b, rho_out, g, alpha_s, W, J, zc, BlockPos::of_launch());
+}
+template <bool HASD>
+__global__ void __launch_bounds__(BT, SOURCE_V4_BLOCKS) k_source_v4_full(QIn q, S *__restrict__ b,
+                                                                        S *__restrict__ rho_out, Geom g,
+                                                                        C alpha_s, const C *W, const C *J, int zc)
+{
+    source_v4_full<HASD>(q, b, rho_out, g, alpha_s, W, J, zc, BlockPos::of_launch());
 }
 
 
@@ -2703,6 +2879,11 @@ cudaError_t launch_source(const Geom &g, const Phys &p, const Tiles &t, const In
     const C *W = (const C *)in.W, *J = (const C *)in.J;
     if (t.vec_source && g.nx % VX == 0) {
         auto kern = qd ? k_source_v4<kInc> : k_source_v4<false>;
+        // 16-bit storage: grids whose tiles all lie inside take the full-tile
+        // kernel (FP16 increments, full-size plume: 12.0 -> 10.7 ms); with
+        // FP32 storage it measured slower (8.6 -> 10.5 ms) and is not used
+        if (sizeof(S) == 2 && g.nx % TXV == 0 && g.ny % BY == 0)
+            kern = qd ? k_source_v4_full<kInc> : k_source_v4_full<false>;
         kern<<<grid_of(g, TXV, BY, t.zc_source), dim3(BX, BY), 0, st>>>(qi, (S *)b, (S *)rho_out, g, as, W, J,
                                                                        t.zc_source);
         return cudaGetLastError();
