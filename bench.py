@@ -453,8 +453,8 @@ def issue_roofline(case, res, precision, clocks, sms):
 def run_batch(args, sync_all=lambda: None):
     """64 periodic Taylor-Green instances of uneven size (edges drawn from
     {48,64,80,96,128}) advanced together: each kernel class one grouped
-    launch over all instances, one CUDA graph per step; z-chunks and kernel
-    forms autotuned per distinct size."""
+    launch over all instances (largest first), one CUDA graph per step;
+    z-chunks and kernel forms autotuned for the batch (igr_autotune_batch)."""
     import torch
     from paper_2505_07392_gb300 import igr
     cases = inputs.tgv_batch(count=args.batch_count)
@@ -463,13 +463,10 @@ def run_batch(args, sync_all=lambda: None):
     with igr.Batch(cases, args.precision) as b:
         for c, inst in zip(cases, b.instances):
             inst.set_state(torch.from_numpy(inputs.initial_state(c)).to(st).cuda())
-            torch.cuda.synchronize()
-            key = (c.nx, c.ny, c.nz)
-            if key not in tuned:
-                tuned[key] = (inst.autotune(reps=3), inst.kernel_forms())
-            else:
-                inst.set_tiles(*tuned[key][0])
-                inst.set_kernel_forms(*tuned[key][1])
+        torch.cuda.synchronize()
+        b.autotune(reps=3)
+        for c, inst in zip(cases, b.instances):
+            tuned.setdefault((c.nx, c.ny, c.nz), (inst.tiles(), inst.kernel_forms()))
         b.step(args.warmup, sync=True)
         sync_all()
         torch.cuda.synchronize()

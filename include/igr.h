@@ -396,6 +396,19 @@ igr_status igr_create_batch(const igr_config *cfgs, int n, const igr_allocator *
                             void *cuda_stream, igr_batch **out);
 igr_ctx *igr_batch_instance(igr_batch *b, int i);
 igr_status igr_step_batch(igr_batch *b, int nsteps);
+/* igr_autotune_batch chooses every instance's launch shape for running in
+ * the batch: first each distinct problem (grid, boundaries, precision,
+ * scheme) alone as igr_autotune does, its shape given to the instances of
+ * the same problem; then, per kernel class, all instances' z-chunks scaled
+ * by a common factor 1..32 (clamped to each grid) with the grouped launches
+ * timed over the whole batch (reps each, on the batch's stream), the fastest
+ * kept. In a batch the other instances' blocks fill the GPU, so the chunks
+ * come out longer than a lone instance's. Only scratch buffers are written:
+ * states, Sigma and dt are unchanged. Call it after every instance's
+ * igr_set_state; it synchronises. Results of later steps are bitwise the
+ * same for any launch shape. Grouped launches order the instances largest
+ * first (cells), whatever the order of cfgs. */
+igr_status igr_autotune_batch(igr_batch *b, int reps);
 igr_status igr_sync_batch(igr_batch *b);
 const char *igr_batch_last_error(const igr_batch *b);
 igr_status igr_destroy_batch(igr_batch *b);

@@ -100,6 +100,7 @@ def lib():
             "igr_create_batch": (i, [C.POINTER(Config), i, C.POINTER(Allocator), p, C.POINTER(p)]),
             "igr_batch_instance": (p, [p, i]),
             "igr_step_batch": (i, [p, i]),
+            "igr_autotune_batch": (i, [p, i]),
             "igr_sync_batch": (i, [p]),
             "igr_batch_last_error": (C.c_char_p, [p]),
             "igr_destroy_batch": (i, [p]),
@@ -513,6 +514,16 @@ class Batch:
             raise IGRError(s, lib().igr_batch_last_error(self.h).decode())
         if sync:
             self.sync()
+
+    def autotune(self, reps: int = 3):
+        """igr_autotune_batch: every instance's launch shape for the batch
+        (each distinct problem tuned alone, then the z-chunks of each kernel
+        class scaled together over the whole batch). Returns each instance's
+        (zc_source, zc_jacobi, zc_flux)."""
+        s = lib().igr_autotune_batch(self.h, int(reps))
+        if s != OK:
+            raise IGRError(s, lib().igr_batch_last_error(self.h).decode())
+        return [inst.tiles() for inst in self.instances]
 
     def sync(self):
         s = lib().igr_sync_batch(self.h)

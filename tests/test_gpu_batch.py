@@ -72,6 +72,40 @@ def test_batch_equals_single_bitwise(precision):
         assert torch.isfinite(qb.float()).all()
 
 
+def test_batch_autotune_keeps_state_and_bits():
+    """igr_autotune_batch writes only scratch (states and Sigma unchanged),
+    gives every instance z-chunks within [4, nz], and the batch then steps
+    to the bits of lone contexts (uneven sizes, red-black sweeps, an inflow
+    face, instances given largest last)."""
+    import torch
+    from paper_2505_07392_gb300 import igr
+    from dataclasses import replace
+    cases = [inputs.tgv(16, instance=0), replace(inputs.tgv(16, instance=3), sigma_solver=1), _jets_case(20),
+             inputs.tgv(24, instance=1), inputs.tgv(32, instance=2)]
+    precision = "f16inc"
+    dt = igr.state_torch_dtype(precision)
+    q0 = [torch.from_numpy(inputs.jet_initial_state(c) if c.jets else inputs.initial_state(c)).to(dt).cuda()
+          for c in cases]
+    torch.cuda.synchronize()
+    with igr.Batch(cases, precision) as b:
+        for inst, q in zip(b.instances, q0):
+            inst.set_state(q)
+        before = [inst.get_state() for inst in b.instances]
+        tiles = b.autotune(reps=1)
+        after = [inst.get_state() for inst in b.instances]
+        for (qa, sa), (qb, sb) in zip(before, after):
+            assert torch.equal(qa, qb) and torch.equal(sa, sb)
+        for c, t in zip(cases, tiles):
+            assert all(min(4, c.nz) <= z <= c.nz for z in t), (c.name, t)
+        b.step(2)
+        b.step(3, sync=True)
+        got = [inst.get_state() for inst in b.instances]
+    for c, q, (qb, sb) in zip(cases, q0, got):
+        qa, sa = _alone(c, q, precision, 5)
+        assert torch.equal(qa, qb), c.name
+        assert torch.equal(sa, sb), c.name
+
+
 def test_results_do_not_depend_on_z_chunks():
     import torch
     from paper_2505_07392_gb300 import igr
