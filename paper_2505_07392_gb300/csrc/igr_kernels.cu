@@ -2833,6 +2833,25 @@ __global__ void __launch_bounds__(BT, JACOBI_V4_BLOCKS) k_jacobi_v4_group(const 
     jacobi_v4_body(d.q, d.b, d.sin, d.sout, d.g, d.beta, d.zc, colour,
                    BlockPos::of_index(blockIdx.x - d.blk0, d.gx, d.gy));
 }
+template <bool HASD>
+__global__ void __launch_bounds__(BT, SOURCE_V4_BLOCKS) k_source_v4_full_group(const __grid_constant__ Group<SourceInst> a)
+{
+    const SourceInst &d = a.d[group_find(a, blockIdx.x)];
+    source_v4_full<HASD>(d.q, d.b, d.rho_out, d.g, d.alpha_s, d.W, d.J, d.zc,
+                         BlockPos::of_index(blockIdx.x - d.blk0, d.gx, d.gy));
+}
+template <bool RB>
+__global__ void __launch_bounds__(BT, JACOBI_V4_BLOCKS) k_jacobi_v4_full_group(const __grid_constant__ Group<JacobiInst> a,
+                                                                              int colour)
+{
+    if constexpr (sizeof(C) == 4) {
+        __shared__ __align__(16) C R[HY][HXV];
+        __shared__ __align__(16) C SG[HY][HXV];
+        const JacobiInst &d = a.d[group_find(a, blockIdx.x)];
+        jacobi_v4_full<RB>(d.q, d.b, d.sin, d.sout, d.g, d.beta, d.zc, colour,
+                           BlockPos::of_index(blockIdx.x - d.blk0, d.gx, d.gy), R, SG);
+    }
+}
 template <int mode, int ORD, bool VISC>
 __global__ void __maxnreg__(FLUX_MAXREG) k_flux_group(const __grid_constant__ Group<FluxInst> a)
 {
@@ -3010,7 +3029,12 @@ cudaError_t launch_source_group(const SourceCall *calls, int n, cudaStream_t st)
 {
     for (int i = 0; i < n; i++)
         if ((kInc != (calls[i].rho_out != nullptr)) || (!kInc && calls[i].qd)) return cudaErrorInvalidValue;
-    auto vec = [](const SourceCall &c) { return c.t.vec_source && c.g.nx % VX == 0 ? 1 : 0; };
+    // 0: one cell per thread, 1: four cells, 2: four cells, every tile inside
+    // the grid (16-bit storage; as launch_source)
+    auto vec = [](const SourceCall &c) {
+        if (!c.t.vec_source || c.g.nx % VX != 0) return 0;
+        return sizeof(S) == 2 && c.g.nx % TXV == 0 && c.g.ny % BY == 0 ? 2 : 1;
+    };
     auto key = [&](const SourceCall &c) { return 2 * vec(c) + (c.qd ? 1 : 0); };
     return by_runs(calls, n, key, [&](const SourceCall *cs, int m) {
         Group<SourceInst> a;
@@ -3034,8 +3058,9 @@ cudaError_t launch_source_group(const SourceCall *calls, int n, cudaStream_t st)
             d.blk0 = blk;
             blk += (int)(gr.x * gr.y * gr.z);
         }
-        auto kern = v ? (cs[0].qd ? k_source_v4_group<kInc> : k_source_v4_group<false>)
-                      : (cs[0].qd ? k_source_group<kInc> : k_source_group<false>);
+        auto kern = v == 2 ? (cs[0].qd ? k_source_v4_full_group<kInc> : k_source_v4_full_group<false>)
+                    : v ? (cs[0].qd ? k_source_v4_group<kInc> : k_source_v4_group<false>)
+                        : (cs[0].qd ? k_source_group<kInc> : k_source_group<false>);
         kern<<<blk, dim3(BX, BY), 0, st>>>(a);
         return cudaGetLastError();
     });
@@ -3043,7 +3068,12 @@ cudaError_t launch_source_group(const SourceCall *calls, int n, cudaStream_t st)
 
 cudaError_t launch_jacobi_group(const JacobiCall *calls, int n, int colour, cudaStream_t st)
 {
-    auto vec = [](const JacobiCall &c) { return c.t.vec_jacobi && c.g.nx % VX == 0 ? 1 : 0; };
+    // 0: one cell per thread, 1: four cells, 2: four cells, every tile inside
+    // the grid (FP32 arithmetic; as launch_jacobi)
+    auto vec = [](const JacobiCall &c) {
+        if (!c.t.vec_jacobi || c.g.nx % VX != 0) return 0;
+        return sizeof(C) == 4 && c.g.nx % TXV == 0 && c.g.ny % BY == 0 ? 2 : 1;
+    };
     return by_runs(calls, n, vec, [&](const JacobiCall *cs, int m) {
         Group<JacobiInst> a;
         a.count = m;
@@ -3065,8 +3095,14 @@ cudaError_t launch_jacobi_group(const JacobiCall *calls, int n, int colour, cuda
             d.blk0 = blk;
             blk += (int)(gr.x * gr.y * gr.z);
         }
-        if (v) k_jacobi_v4_group<<<blk, dim3(BX, BY), 0, st>>>(a, colour);
-        else k_jacobi_group<<<blk, dim3(BX, BY), 0, st>>>(a, colour);
+        if (v == 2) {
+            auto kern = colour < 0 ? k_jacobi_v4_full_group<false> : k_jacobi_v4_full_group<true>;
+            kern<<<blk, dim3(BX, BY), 0, st>>>(a, colour);
+        } else if (v) {
+            k_jacobi_v4_group<<<blk, dim3(BX, BY), 0, st>>>(a, colour);
+        } else {
+            k_jacobi_group<<<blk, dim3(BX, BY), 0, st>>>(a, colour);
+        }
         return cudaGetLastError();
     });
 }

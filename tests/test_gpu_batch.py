@@ -51,9 +51,13 @@ def test_batch_equals_single_bitwise(precision):
     # uneven sizes, different sweep counts, red-black sweeps, 3rd-order
     # faces and an inflow face in one batch: the grouped launches split by
     # kernel form and scheme, every instance keeps its own buffers
+    # 128 x 128 x 12 and 128 x 16 x 12 (red-black): every 4-cell tile inside,
+    # the full-tile source and sweep bodies in their own grouped launches
     cases = [inputs.tgv(16, instance=0), inputs.tgv(24, instance=1), inputs.tgv(20, instance=2),
              inputs.blast(12, sweeps=4), replace(inputs.tgv(16, instance=3), sigma_solver=1),
-             replace(inputs.blast(12, sweeps=3), order=3), _jets_case(20)]
+             replace(inputs.blast(12, sweeps=3), order=3), _jets_case(20),
+             replace(inputs.tgv(128, instance=4), nz=12),
+             replace(inputs.tgv(128, instance=5), ny=16, nz=12, sigma_solver=1)]
     dt = igr.state_torch_dtype(precision)
     q0 = [torch.from_numpy(inputs.jet_initial_state(c) if c.jets else inputs.initial_state(c)).to(dt).cuda()
           for c in cases]
