@@ -334,14 +334,29 @@ __device__ __forceinline__ C rec_right(C b, C c, C d, C e, C f)
 //   c = sqrt(gamma p / rho).
 // (The factor 1/2 is applied once, in the divergence.) Flags a non-positive
 // face density or pressure.
+// The warning flag of non-positive face states. In the 16-bit storage forms
+// it is a running minimum of the face densities and pressures, tested once
+// per block (fewer instructions per face: their flux kernel ran 2.4% faster
+// at full size); FP32 and FP64 storage keep a boolean per face (the minimum
+// measured 0.9% slower there). A face whose four values are all NaN sets
+// the boolean and not the minimum; its outputs raise the non-finite error.
+constexpr bool kFaceMin = sizeof(S) == 2;
+using FaceFlag = std::conditional<kFaceMin, C, bool>::type;
+__device__ __forceinline__ void flag_face(bool &f, C a, C b, C c, C d) { f |= !(fmin(fmin(a, b), fmin(c, d)) > C(0)); }
+template <class T> __device__ __forceinline__ void flag_face(T &f, C a, C b, C c, C d)
+{
+    f = fmin(f, fmin(fmin(a, b), fmin(c, d)));
+}
+__device__ __forceinline__ bool flag_bad(bool f) { return f; }
+template <class T> __device__ __forceinline__ bool flag_bad(T f) { return !(f > T(0)); }
 template <int D>
-__device__ __forceinline__ void lf_flux2(const C *L, const C *R, C gamma, C gm1, C *G, bool &bad)
+__device__ __forceinline__ void lf_flux2(const C *L, const C *R, C gamma, C gm1, C *G, FaceFlag &bad)
 {
     C rL = rcp(L[0]), rR = rcp(R[0]);
     C uL = L[1 + D] * rL, uR = R[1 + D] * rR;
     C pL = gm1 * (L[4] - C(0.5) * ((L[1] * L[1] + L[2] * L[2] + L[3] * L[3]) * rL));
     C pR = gm1 * (R[4] - C(0.5) * ((R[1] * R[1] + R[2] * R[2] + R[3] * R[3]) * rR));
-    bad |= !(fmin(fmin(L[0], R[0]), fmin(pL, pR)) > C(0));
+    flag_face(bad, L[0], R[0], pL, pR);
     C aL = fabs(uL) + sqrt_c(gamma * pL * rL);
     C aR = fabs(uR) + sqrt_c(gamma * pR * rR);
     C lam = fmax(aL, aR);  // a NaN speed comes with a flagged face
@@ -1749,6 +1764,9 @@ constexpr int PW = TX + 6, PH = TY + 6;          // plane tile with a halo of 3
 // the interior's corners (the viscous faces' tangential neighbours)
 constexpr int NPLANE = TY * PW + 6 * TX + 4;
 constexpr int LPT = (NPLANE + NT - 1) / NT;      // tile cells loaded per thread
+// every thread has a first tile cell (its test is dropped in the 16-bit
+// forms, where that measured faster; FP32/FP64 keep it)
+constexpr bool kR0 = sizeof(S) == 2 && NPLANE >= NT;
 
 // The plane tiles keep the six face variables as three pairs, (rho, m_x),
 // (m_y, m_z), (E, Sigma): a stencil point of a pair is one 8-byte (16-byte in
@@ -1862,7 +1880,7 @@ __device__ __forceinline__ void plane_cell(int e, int &lx, int &ly)
 
 template <int D, int ORD>
 __device__ __forceinline__ void face_from_stencil(const C2 (&s)[6][3], C gamma, C gm1, C *F,
-                                                  bool &bad)
+                                                  FaceFlag &bad)
 {
     C L[6], R[6];
 #pragma unroll
@@ -1883,7 +1901,7 @@ __device__ __forceinline__ void face_from_stencil(const C2 (&s)[6][3], C gamma, 
 // at element `at`, `step` elements apart
 template <int D, int ORD>
 __device__ __forceinline__ void tile_face(const C2 *T, int at, int step, C gamma, C gm1, C *F,
-                                          bool &bad)
+                                          FaceFlag &bad)
 {
     C2 s[6][3];
 #pragma unroll
@@ -2020,7 +2038,7 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
     const idx own = (idx)(j * g.nx + i);
     const int tcell = (w + 3) * PW + lane + 3;  // this row-warp lane's cell in a tile
     const C gm1 = gamma - C(1);
-    bool bad = false;       // a face state with rho <= 0 or p <= 0 (warning)
+    FaceFlag bad = FaceFlag(kFaceMin ? 1 : 0);  // face states with rho <= 0 or p <= 0 (warning)
     bool nonfinite = false; // a non-finite output (error)
     // ring slot offsets (in pairs) of planes k-2..k+4 in iteration k, rotated
     // once per plane: plane kk sits in slot (kk - k0 + 3) mod RING
@@ -2055,7 +2073,7 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
         const bool blend = kk < 0 && g.bc[4] == BC_INFLOW;
 #pragma unroll
         for (int r = 0; r < LPT; r++)
-            if (soff[r] >= 0) {
+            if ((kR0 && r == 0) || soff[r] >= 0) {
                 C v[6];
                 const idx c = ck(zb + goff[r], g.n);
 #pragma unroll
@@ -2080,7 +2098,7 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
         const idx zb = (idx)zmap(kk, g) * pl;
 #pragma unroll
         for (int r = 0; r < LPT; r++)
-            if (soff[r] >= 0) {
+            if ((kR0 && r == 0) || soff[r] >= 0) {
                 if constexpr (kInc) {
                     const idx c = ck(zb + goff[r], g.n);
 #pragma unroll
@@ -2105,14 +2123,14 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
         } else if constexpr (kInc) {
 #pragma unroll
             for (int r = 0; r < LPT; r++)
-                if (soff[r] >= 0) {
+                if ((kR0 && r == 0) || soff[r] >= 0) {
                     st_cell(T, cks(soff[r], PH * PW), pset(cvq<HASD>(Rq[r][0]), cvq<HASD>(Rq[r][1])),
                             pset(cvq<HASD>(Rq[r][2]), cvq<HASD>(Rq[r][3])), pset(cvq<HASD>(Rq[r][4]), cv(Rs[r])));
                 }
         } else {
 #pragma unroll
             for (int r = 0; r < LPT; r++)
-                if (soff[r] >= 0)
+                if ((kR0 && r == 0) || soff[r] >= 0)
                     st_cell(T, cks(soff[r], PH * PW), pset(cv(Rg[r][0]), cv(Rg[r][1])), pset(cv(Rg[r][2]), cv(Rg[r][3])),
                             pset(cv(Rg[r][4]), cv(Rg[r][5])));
         }
@@ -2262,7 +2280,8 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
     // the last plane (its faces are behind the final barrier; after the
     // rotation plane k1 - 1 sits at ro[1])
     if (active) finish(k1 - 1, P + ro[1]);
-    if (nonfinite || bad) atomicOr(err, (nonfinite ? ERRF_NONFINITE : 0) | (bad ? ERRF_FACE : 0));
+    const bool badf = flag_bad(bad);
+    if (nonfinite || badf) atomicOr(err, (nonfinite ? ERRF_NONFINITE : 0) | (badf ? ERRF_FACE : 0));
     if (mode == FLUX_STAGE3) {
         double m = block_max<NT>(double(smax));
         if (tid == 0)

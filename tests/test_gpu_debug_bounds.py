@@ -85,7 +85,11 @@ def test_no_index_out_of_bounds(debug_lib):
               (replace(inputs.blast(20, sweeps=2), order=3, sigma_solver=1), "f32"),
               (replace(Case("v", 13, 8, 11, 1 / 13, alpha=1 / 169, sweeps=2, bc=(OUTFLOW,) * 6), mu=1e-3), "f64"),
               (replace(_jets(16), mu=1e-3, zeta=1e-3), "bf16"), (_jets(24), "f16inc"),
-              (Case("odd", 36, 12, 8, 1 / 36, alpha=1 / 36 ** 2, sweeps=2, bc=(OUTFLOW,) * 6), "bf16inc")]
+              (Case("odd", 36, 12, 8, 1 / 36, alpha=1 / 36 ** 2, sweeps=2, bc=(OUTFLOW,) * 6), "bf16inc"),
+              # rows of 128 cells, 16 rows: the full-tile sweep and source kernels
+              (Case("full", 128, 16, 6, 1 / 128, alpha=1 / 128 ** 2, sweeps=2, bc=(PERIODIC,) * 6), "f16inc"),
+              (replace(Case("full", 128, 16, 6, 1 / 128, alpha=1 / 128 ** 2, sweeps=2,
+                            bc=(OUTFLOW,) * 4 + (PERIODIC,) * 2), sigma_solver=1), "f32")]
     for c, prec in cases:
         q0 = inputs.jet_initial_state(c) if c.jets else _state(c, c.nx)
         dt, st = igr.state_torch_dtype(prec), igr.storage_torch_dtype(prec)
@@ -105,7 +109,8 @@ def test_no_index_out_of_bounds(debug_lib):
     with igr.Solver(c, "f16", host_rk_base=True) as s:
         s.set_state(torch.from_numpy(inputs.initial_state(c)).half().cuda())
         s.step(2)
-    cases = [inputs.tgv(12), inputs.tgv(16, instance=1), replace(inputs.blast(10, sweeps=2), order=3)]
+    cases = [inputs.tgv(12), inputs.tgv(16, instance=1), replace(inputs.blast(10, sweeps=2), order=3),
+             replace(inputs.tgv(128, instance=2), ny=16, nz=6)]  # grouped full-tile source and sweep
     with igr.Batch(cases, "f16") as b:
         for inst, cc in zip(b.instances, cases):
             inst.set_state(torch.from_numpy(inputs.initial_state(cc)).half().cuda())
