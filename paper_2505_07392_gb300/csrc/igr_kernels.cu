@@ -1248,13 +1248,14 @@ __device__ __forceinline__ void jacobi_v4_edge(const S *__restrict__ q, const S 
 // (FP32 arithmetic): every lane owns four cells of a row, its loads are
 // whole 4-wide rows, and the halo offsets are mapped once. Warps 0 and 1
 // load the rows below and above the tile, lanes 0..15 of warp 2 the cells
-// left and right of its rows. The update is jacobi4_packed, as in
-// jacobi_v4_edge, so both give the same bits. RB: a red-black half-sweep of
-// the given colour (cells of the other colour keep and write back Sigma).
+// left and right of its rows. The plane tile is double buffered, so a plane
+// needs one barrier. The update is jacobi4_packed, as in jacobi_v4_edge, so
+// both give the same bits. RB: a red-black half-sweep of the given colour
+// (cells of the other colour keep and write back Sigma).
 template <bool RB>
 __device__ __forceinline__ void jacobi_v4_full(const S *__restrict__ q, const S *__restrict__ b, const S *sin,
                                                S *sout, const Geom &g, C beta, int zc, int colour,
-                                               const BlockPos &bp, C (*R)[HXV], C (*SG)[HXV])
+                                               const BlockPos &bp, C (*R2)[HY][HXV], C (*SG2)[HY][HXV])
 {
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x0 = bp.x * TXV, y0 = bp.y * BY;
@@ -1316,7 +1317,9 @@ __device__ __forceinline__ void jacobi_v4_full(const S *__restrict__ q, const S 
     const int col = VX + VX * tx;
     for (int k = k0; k < k1; k++) {
         C bv[VX], t[VX];
-        __syncthreads();  // the tile of plane k - 1 is read
+        // two tile buffers, planes alternating: the buffer written here was
+        // last read two planes ago, before the barrier of the previous plane
+        C (*R)[HXV] = R2[(k - k0) & 1], (*SG)[HXV] = SG2[(k - k0) & 1];
         sh_st4(&R[ty + 1][col], r0);
         sh_st4(&SG[ty + 1][col], s0);
         if (yh) {
@@ -1365,8 +1368,8 @@ __device__ __forceinline__ void jacobi_v4_body(const S *__restrict__ q, const S 
                                                S *sout, const Geom g, C beta, int zc, int colour,
                                                const BlockPos bp)
 {
-    __shared__ __align__(16) C R[HY][HXV];
-    __shared__ __align__(16) C SG[HY][HXV];
+    __shared__ __align__(16) C R[2][HY][HXV];
+    __shared__ __align__(16) C SG[2][HY][HXV];
     if constexpr (sizeof(C) == 4) {
         if (bp.x * TXV + TXV <= g.nx && bp.y * BY + BY <= g.ny) {  // block-uniform
             if (colour < 0)
@@ -1376,7 +1379,7 @@ __device__ __forceinline__ void jacobi_v4_body(const S *__restrict__ q, const S 
             return;
         }
     }
-    jacobi_v4_edge(q, b, sin, sout, g, beta, zc, colour, bp, R, SG);
+    jacobi_v4_edge(q, b, sin, sout, g, beta, zc, colour, bp, R[0], SG[0]);
 }
 constexpr int JACOBI_V4_BLOCKS = sizeof(S) == 2 ? 3 : sizeof(S) == 4 ? 2 : 1;  // resident per SM
 __global__ void __launch_bounds__(BT, JACOBI_V4_BLOCKS) k_jacobi_v4(const S *__restrict__ q, const S *__restrict__ b,
@@ -1395,8 +1398,8 @@ __global__ void __launch_bounds__(BT, JACOBI_V4_BLOCKS) k_jacobi_v4_full(const S
                                                                        S *sout, Geom g, C beta, int zc, int colour)
 {
     if constexpr (sizeof(C) == 4) {
-        __shared__ __align__(16) C R[HY][HXV];
-        __shared__ __align__(16) C SG[HY][HXV];
+        __shared__ __align__(16) C R[2][HY][HXV];
+        __shared__ __align__(16) C SG[2][HY][HXV];
         jacobi_v4_full<RB>(q, b, sin, sout, g, beta, zc, colour, BlockPos::of_launch(), R, SG);
     }
 }
@@ -1583,14 +1586,14 @@ __device__ __forceinline__ QRaw4 ldq4d(const QIn &q, int u, const Geom &g, idx o
 // of 128 cells, a multiple of 8 rows): the body of source_v4_body without
 // lanes past the row's end, with whole 4-wide loads and halo offsets mapped
 // once (warps 0 and 1: the rows below and above; lanes 0..15 of warp 2: the
-// cells left and right of the rows). The same operations per cell, so the
-// same bits.
+// cells left and right of the rows), and the plane tile double buffered.
+// The same operations per cell, so the same bits.
 template <bool HASD>
 __device__ __forceinline__ void source_v4_full(const QIn q, S *__restrict__ b, S *__restrict__ rho_out,
                                                const Geom g, C alpha_s, const C *W, const C *J, int zc,
                                                const BlockPos bp)
 {
-    __shared__ __align__(16) C U[3][HY][HXV];
+    __shared__ __align__(16) C U2[2][3][HY][HXV];  // plane tiles of u, two planes alternating
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x0 = bp.x * TXV, y0 = bp.y * BY;
     const int i0 = x0 + VX * tx, j = y0 + ty;
@@ -1671,7 +1674,9 @@ __device__ __forceinline__ void source_v4_full(const QIn q, S *__restrict__ b, S
     const int col = VX + VX * tx;
     for (int k = k0; k < k1; k++) {
         if (!kHaloAhead) halo(k);
-        __syncthreads();  // readers of the previous plane are done
+        // the buffer written here was last read two planes ago, before the
+        // barrier of the previous plane: one barrier per plane
+        C (*U)[HY][HXV] = U2[(k - k0) & 1];
 #pragma unroll
         for (int a = 0; a < 3; a++) sh_st4(&U[a][ty + 1][col], u0[a]);
         if (yh) {
@@ -2864,8 +2869,8 @@ __global__ void __launch_bounds__(BT, JACOBI_V4_BLOCKS) k_jacobi_v4_full_group(c
                                                                               int colour)
 {
     if constexpr (sizeof(C) == 4) {
-        __shared__ __align__(16) C R[HY][HXV];
-        __shared__ __align__(16) C SG[HY][HXV];
+        __shared__ __align__(16) C R[2][HY][HXV];
+        __shared__ __align__(16) C SG[2][HY][HXV];
         const JacobiInst &d = a.d[group_find(a, blockIdx.x)];
         jacobi_v4_full<RB>(d.q, d.b, d.sin, d.sout, d.g, d.beta, d.zc, colour,
                            BlockPos::of_index(blockIdx.x - d.blk0, d.gx, d.gy), R, SG);
