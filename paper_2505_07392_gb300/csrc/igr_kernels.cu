@@ -2209,20 +2209,38 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
     for (int k = k0 - 1; k < k1; k++) {
         const bool more = k + 4 <= k1 + 2;  // plane k + 4 feeds the z-faces
         if (more) fetch(k + 4, P + ro[6]);
+        const C2 *T = P + ro[2];  // plane k
+        C *FX = FXb + (k & 1) * NFX;
+        C *FY = FYb + (k & 1) * NFY;
+        C F[5];
+        const C2 *Tm = P + ro[1], *Tp = P + ro[3];  // planes k - 1, k + 1 (viscous terms)
+        const C inv_dx = C(2) * half_inv_dx;
+        // viscous x-face between tile cells a and a + 1 (same row)
+        auto visc_x = [&](int a) {
+            visc_face<0>(T, a, T, a + 1, T, a - PW, T, a + PW, T, a + 1 - PW, T, a + 1 + PW, Tm, a, Tp,
+                         a, Tm, a + 1, Tp, a + 1, mu, lamv, inv_dx, F);
+        };
+        // viscous y-face between tile cells a and a + PW (same column)
+        auto visc_y = [&](int a) {
+            visc_face<1>(T, a, T, a + PW, T, a - 1, T, a + 1, T, a + PW - 1, T, a + PW + 1, Tm, a, Tp,
+                         a, Tm, a + PW, Tp, a + PW, mu, lamv, inv_dx, F);
+        };
         if (rowwarp) {
-            if (k > k0 && active) finish(k - 1, P + ro[1]);
+            if (active) {
+                if (k > k0) finish(k - 1, P + ro[1]);
+                if (k >= k0 && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3)) {
+                    idx c = ck((idx)k * pl + own, g.n);
+#pragma unroll
+                    for (int u = 0; u < 5; u++) qnv[u] = __ldg(kInc ? qn0 + u * fs + c : qn.p[u] + c);
+                }
+            }
 #pragma unroll
             for (int u = 0; u < 5; u++) Fzm[u] = Fzp[u];
-            if (k >= k0 && active && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3)) {
-                idx c = ck((idx)k * pl + own, g.n);
-#pragma unroll
-                for (int u = 0; u < 5; u++) qnv[u] = __ldg(kInc ? qn0 + u * fs + c : qn.p[u] + c);
-            }
             C2 sz[6][3];  // z-stencil: planes k - 2..k + 3 at this cell
 #pragma unroll
             for (int m = 0; m < 6; m++) {
-                const C2 *T = P + ro[m];
-                ld_cell(T, cks(tcell, PH * PW), sz[m][0], sz[m][1], sz[m][2]);
+                const C2 *Tz = P + ro[m];
+                ld_cell(Tz, cks(tcell, PH * PW), sz[m][0], sz[m][1], sz[m][2]);
             }
             face_from_stencil<2, ORD>(sz, gamma, gm1, Fzp, bad);  // z-face k + 1/2
             if constexpr (VISC) {
@@ -2231,25 +2249,7 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
                              tcell + 1, Ta, tcell - PW, Ta, tcell + PW, Tb, tcell - PW, Tb, tcell + PW,
                              mu, lamv, C(2) * half_inv_dx, Fzp);
             }
-        }
-        if (k >= k0) {
-            const C2 *T = P + ro[2];
-            C *FX = FXb + (k & 1) * NFX;
-            C *FY = FYb + (k & 1) * NFY;
-            C F[5];
-            const C2 *Tm = P + ro[1], *Tp = P + ro[3];  // planes k - 1, k + 1 (viscous terms)
-            const C inv_dx = C(2) * half_inv_dx;
-            // viscous x-face between tile cells a and a + 1 (same row)
-            auto visc_x = [&](int a) {
-                visc_face<0>(T, a, T, a + 1, T, a - PW, T, a + PW, T, a + 1 - PW, T, a + 1 + PW, Tm, a, Tp,
-                             a, Tm, a + 1, Tp, a + 1, mu, lamv, inv_dx, F);
-            };
-            // viscous y-face between tile cells a and a + PW (same column)
-            auto visc_y = [&](int a) {
-                visc_face<1>(T, a, T, a + PW, T, a - 1, T, a + 1, T, a + PW - 1, T, a + PW + 1, Tm, a, Tp,
-                             a, Tm, a + PW, Tp, a + PW, mu, lamv, inv_dx, F);
-            };
-            if (rowwarp) {
+            if (k >= k0) {
                 // x-face at the low side of cell `lane` of row w (tile cells lane-3..lane+2)
                 tile_face<0, ORD>(T, (w + 3) * PW + lane, 1, gamma, gm1, F, bad);
                 if constexpr (VISC) visc_x((w + 3) * PW + lane + 2);
@@ -2260,19 +2260,19 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
                 if constexpr (VISC) visc_y((w + 2) * PW + lane + 3);
 #pragma unroll
                 for (int u = 0; u < 5; u++) FY[cks((u * (TY + 1) + w) * TX + lane, NFY)] = F[u];
-            } else {
-                // y-face above the last row, column lane
-                tile_face<1, ORD>(T, TY * PW + lane + 3, PW, gamma, gm1, F, bad);
-                if constexpr (VISC) visc_y((TY + 2) * PW + lane + 3);
+            }
+        } else if (k >= k0) {
+            // y-face above the last row, column lane
+            tile_face<1, ORD>(T, TY * PW + lane + 3, PW, gamma, gm1, F, bad);
+            if constexpr (VISC) visc_y((TY + 2) * PW + lane + 3);
 #pragma unroll
-                for (int u = 0; u < 5; u++) FY[cks((u * (TY + 1) + TY) * TX + lane, NFY)] = F[u];
-                if (lane < TY) {
-                    // x-face at the high end of row `lane`
-                    tile_face<0, ORD>(T, (lane + 3) * PW + TX, 1, gamma, gm1, F, bad);
-                    if constexpr (VISC) visc_x((lane + 3) * PW + TX + 2);
+            for (int u = 0; u < 5; u++) FY[cks((u * (TY + 1) + TY) * TX + lane, NFY)] = F[u];
+            if (lane < TY) {
+                // x-face at the high end of row `lane`
+                tile_face<0, ORD>(T, (lane + 3) * PW + TX, 1, gamma, gm1, F, bad);
+                if constexpr (VISC) visc_x((lane + 3) * PW + TX + 2);
 #pragma unroll
-                    for (int u = 0; u < 5; u++) FX[cks((u * TY + lane) * (TX + 1) + TX, NFX)] = F[u];
-                }
+                for (int u = 0; u < 5; u++) FX[cks((u * TY + lane) * (TX + 1) + TX, NFX)] = F[u];
             }
         }
         if (more) land(P + ro[6]);
