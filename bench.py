@@ -50,13 +50,13 @@ FALLBACK_HBM_GBS = 6800.0
 # Both from ncu captures of the flux kernel on the 512 x 512 x 128 plume,
 # mean of the three stage launches of one step.
 NCU_INSTR = {
-    "flux_f16inc": {"warp_instr_per_cell": 21.029, "src": "e3e838a6730a35f3"},
+    "flux_f16inc": {"warp_instr_per_cell": 20.389, "src": "89af10b10a3eb717"},
     "flux_f16": {"warp_instr_per_cell": 22.945, "src": "8eb9327fb53b00ea"},
     "flux_f32": {"warp_instr_per_cell": 20.479, "src": "8eb9327fb53b00ea"},
 }
 
 NCU_TRAFFIC = {
-    "flux_f16inc": {"bytes_per_cell": 44.370, "src": "e3e838a6730a35f3"},
+    "flux_f16inc": {"bytes_per_cell": 44.360, "src": "89af10b10a3eb717"},
     "flux_f16": {"bytes_per_cell": 29.105, "src": "8eb9327fb53b00ea"},
     "flux_f32": {"bytes_per_cell": 58.879, "src": "8eb9327fb53b00ea"},
 }
@@ -363,9 +363,10 @@ def run_e2e(s, case, precision, steps, sync_all):
             raise igr.IGRError(st, L.igr_last_error(s.h).decode())
 
     check(L.igr_get_state(s.h, pq, None, code, 0))
-    # single-copy bandwidth each way over the first 4 GiB of the buffer
+    # single-copy bandwidth each way over the whole buffer (the link's rate
+    # can differ between a few GiB and the state's size on some boxes)
     flat = hq.view(-1)
-    k = min(flat.numel(), (4 << 30) // flat.element_size())
+    k = flat.numel()
     dbuf = torch.empty(k, dtype=dt, device=s.device)
     bw = {}
     for name, dst, src in (("h2d_gbs", dbuf, flat[:k]), ("d2h_gbs", flat[:k], dbuf)):
