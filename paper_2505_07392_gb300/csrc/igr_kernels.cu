@@ -1920,6 +1920,28 @@ __device__ __forceinline__ void tile_face(const C2 *T, int at, int step, C gamma
     face_from_stencil<D, ORD>(s, gamma, gm1, F, bad);
 }
 
+// tile_face with the stencil's point 3 (the cell the face lies below / left of
+// the row warp's own cell) given: the row warp holds it from its z-stencil
+template <int D, int ORD>
+__device__ __forceinline__ void tile_face_c(const C2 *T, int at, int step, const C2 (&c3)[3], C gamma, C gm1,
+                                            C *F, FaceFlag &bad)
+{
+    C2 s[6][3];
+#pragma unroll
+    for (int m = 0; m < 6; m++) {
+        if (ORD == 3 && (m == 0 || m == 5)) {
+            s[m][0] = s[m][1] = s[m][2] = bcast(C(0));
+        } else if (m == 3) {
+            s[m][0] = c3[0];
+            s[m][1] = c3[1];
+            s[m][2] = c3[2];
+        } else {
+            ld_cell(T, cks(at + m * step, PH * PW), s[m][0], s[m][1], s[m][2]);
+        }
+    }
+    face_from_stencil<D, ORD>(s, gamma, gm1, F, bad);
+}
+
 // ------------------------------------------------------- viscous stresses
 // Velocity u = m / rho of the tile cell at pair offset `at`.
 __device__ __forceinline__ void tvel(const C2 *T, int at, C u[3])
@@ -2156,7 +2178,12 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
     QB qnv[5];  // q^n of plane k - 1 (stages 2 and 3), loaded one iteration ahead
 
     // divergence and stage combination of plane kk (face buffers of parity kk)
-    auto finish = [&](int kk, const C2 *T) {
+    // The three pairs of a row-warp lane's own cell in plane k, taken from its
+    // z-stencil (the stencil's centre plane): they are point 3 of the lane's
+    // x- and y-face stencils in plane k and the stage input the divergence of
+    // plane k combines in the next iteration, so none is loaded twice.
+    C2 cc[3];
+    auto finish = [&](int kk) {
         const C *FX = FXb + (kk & 1) * NFX;
         const C *FY = FYb + (kk & 1) * NFY;
         idx c = ck((idx)kk * pl + own, g.n);
@@ -2175,8 +2202,7 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
             for (int u = 0; u < 5; u++) rhs.p[u][c] = Lv[u];
             nonfinite |= !isfinite((Lv[0] + Lv[1]) + (Lv[2] + Lv[3]) + Lv[4]);
         } else {
-            C2 a, b, e;
-            ld_cell(T, cks(tcell, PH * PW), a, b, e);
+            const C2 a = cc[0], b = cc[1], e = cc[2];  // plane kk at this cell
             const C qsv[5] = {a.x, a.y, b.x, b.y, e.x};
             if (mode == FLUX_STAGE1 && base_out.p[0]) {
                 // the RK base q^n for stages 2 and 3 (exact: qsv holds stored values)
@@ -2227,7 +2253,7 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
         };
         if (rowwarp) {
             if (active) {
-                if (k > k0) finish(k - 1, P + ro[1]);
+                if (k > k0) finish(k - 1);
                 if (k >= k0 && (mode == FLUX_STAGE2 || mode == FLUX_STAGE3)) {
                     idx c = ck((idx)k * pl + own, g.n);
 #pragma unroll
@@ -2243,6 +2269,9 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
                 ld_cell(Tz, cks(tcell, PH * PW), sz[m][0], sz[m][1], sz[m][2]);
             }
             face_from_stencil<2, ORD>(sz, gamma, gm1, Fzp, bad);  // z-face k + 1/2
+            cc[0] = sz[2][0];  // plane k at this cell
+            cc[1] = sz[2][1];
+            cc[2] = sz[2][2];
             if constexpr (VISC) {
                 const C2 *Ta = P + ro[2], *Tb = P + ro[3];  // planes k, k + 1
                 visc_face<2>(Ta, tcell, Tb, tcell, Ta, tcell - 1, Ta, tcell + 1, Tb, tcell - 1, Tb,
@@ -2251,12 +2280,12 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
             }
             if (k >= k0) {
                 // x-face at the low side of cell `lane` of row w (tile cells lane-3..lane+2)
-                tile_face<0, ORD>(T, (w + 3) * PW + lane, 1, gamma, gm1, F, bad);
+                tile_face_c<0, ORD>(T, (w + 3) * PW + lane, 1, cc, gamma, gm1, F, bad);
                 if constexpr (VISC) visc_x((w + 3) * PW + lane + 2);
 #pragma unroll
                 for (int u = 0; u < 5; u++) FX[cks((u * TY + w) * (TX + 1) + lane, NFX)] = F[u];
                 // y-face below row w in column lane (tile rows w-3..w+2)
-                tile_face<1, ORD>(T, w * PW + lane + 3, PW, gamma, gm1, F, bad);
+                tile_face_c<1, ORD>(T, w * PW + lane + 3, PW, cc, gamma, gm1, F, bad);
                 if constexpr (VISC) visc_y((w + 2) * PW + lane + 3);
 #pragma unroll
                 for (int u = 0; u < 5; u++) FY[cks((u * (TY + 1) + w) * TX + lane, NFY)] = F[u];
@@ -2282,9 +2311,9 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
         for (int m = 0; m + 1 < RING; m++) ro[m] = ro[m + 1];
         ro[RING - 1] = r0;
     }
-    // the last plane (its faces are behind the final barrier; after the
-    // rotation plane k1 - 1 sits at ro[1])
-    if (active) finish(k1 - 1, P + ro[1]);
+    // the last plane (its faces are behind the final barrier; its cell's
+    // values are in cc from the last z-stencil)
+    if (active) finish(k1 - 1);
     const bool badf = flag_bad(bad);
     if (nonfinite || badf) atomicOr(err, (nonfinite ? ERRF_NONFINITE : 0) | (badf ? ERRF_FACE : 0));
     if (mode == FLUX_STAGE3) {
