@@ -2175,6 +2175,16 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
     C smax = C(0);  // running wave-speed maximum (FP32 here: FP64 is slow on this GPU)
 
     C Fzm[5], Fzp[5];
+    // planes k and k + 1 at a row-warp lane's cell before iteration k: the
+    // z-stencils of consecutive planes share them, so each iteration loads
+    // four of its six points (shared loads are the flux kernel's most
+    // contended resource; the copies are register moves). Not in the
+    // viscous kernels, whose extra registers would spill.
+    C2 zq[2][3];
+    if (!VISC && rowwarp) {
+        ld_cell(P + ro[2], cks(tcell, PH * PW), zq[0][0], zq[0][1], zq[0][2]);  // plane k0 - 1
+        ld_cell(P + ro[3], cks(tcell, PH * PW), zq[1][0], zq[1][1], zq[1][2]);  // plane k0
+    }
     QB qnv[5];  // q^n of plane k - 1 (stages 2 and 3), loaded one iteration ahead
 
     // divergence and stage combination of plane kk (face buffers of parity kk)
@@ -2265,8 +2275,19 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
             C2 sz[6][3];  // z-stencil: planes k - 2..k + 3 at this cell
 #pragma unroll
             for (int m = 0; m < 6; m++) {
-                const C2 *Tz = P + ro[m];
-                ld_cell(Tz, cks(tcell, PH * PW), sz[m][0], sz[m][1], sz[m][2]);
+                if (!VISC && (m == 2 || m == 3)) {  // planes k, k + 1: points 3, 4 of the previous z-stencil
+#pragma unroll
+                    for (int p = 0; p < 3; p++) sz[m][p] = zq[m - 2][p];
+                } else {
+                    ld_cell(P + ro[m], cks(tcell, PH * PW), sz[m][0], sz[m][1], sz[m][2]);
+                }
+            }
+            if constexpr (!VISC) {
+#pragma unroll
+                for (int p = 0; p < 3; p++) {
+                    zq[0][p] = sz[3][p];
+                    zq[1][p] = sz[4][p];
+                }
             }
             face_from_stencil<2, ORD>(sz, gamma, gm1, Fzp, bad);  // z-face k + 1/2
             cc[0] = sz[2][0];  // plane k at this cell
