@@ -994,14 +994,12 @@ __device__ __forceinline__ void jacobi4_packed(const float (&r0)[4], const float
                                                float eyp, float ezm, float ezp, float (&o)[4])
 {
     const float2 r01 = make_float2(r0[0], r0[1]), r23 = make_float2(r0[2], r0[3]), r12 = make_float2(r0[1], r0[2]);
-    const float2 s01 = make_float2(s0[0], s0[1]), s23 = make_float2(s0[2], s0[3]), s12 = make_float2(s0[1], s0[2]);
+    const float2 s12 = make_float2(s0[1], s0[2]);
     const float2 rxm[2] = {make_float2(rl, r0[0]), r12}, rxp[2] = {r12, make_float2(r0[3], rr)};
     const float2 sxm[2] = {make_float2(sl, s0[0]), s12}, sxp[2] = {s12, make_float2(s0[3], sr)};
     const float2 exmp[2] = {make_float2(exm, hb), make_float2(hb, hb)};
     const float2 expp[2] = {make_float2(hb, hb), make_float2(hb, exp_)};
     const float2 rc[2] = {r01, r23};
-    (void)s01;
-    (void)s23;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const int c = 2 * h;
@@ -1031,7 +1029,7 @@ __device__ __forceinline__ void jacobi4_packed(const double (&)[4], const double
                                                const double (&)[4], double, double, double, double, double,
                                                double, double, double (&)[4])
 {
-}  // (FP64 takes the scalar cells)
+}  // FP64 takes the scalar cells; this overload only lets the FP32 call compile in the FP64 build
 
 // 4 raw values of field a at cells (x .. x+3) of row-plane offset rowoff:
 // one 4-wide load when the cells lie inside the row, mapped single loads otherwise
