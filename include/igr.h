@@ -196,10 +196,14 @@ igr_status igr_step(igr_ctx *ctx, int nsteps, double fixed_dt, double *t_inout);
 /* nsteps SSP-RK3 steps from host memory to host memory: q_in (5 n values,
  * the state dtype, best pinned) is copied in, Sigma stays on the device
  * (as with igr_set_conserved), the steps run, and the final q is written to
- * q_out. The last stage's flux kernel runs in z-slabs and each slab is
- * copied out while the next ones compute, so most of the read-back
- * overlaps the last stage. q_in and q_out may be the same buffer. dt
- * follows the CFL rule. Synchronises and reports asynchronous errors. */
+ * q_out. rho and m are copied first; the energy field follows on a second
+ * stream while the first stage's source and sweeps (which read rho and m
+ * only) run, and the first step's dt is formed just before its first flux.
+ * The last stage's flux kernel runs in z-slabs and each slab is copied out
+ * while the next ones compute, so part of the read-back overlaps the last
+ * stage. q_in and q_out may be the same buffer and must not be written
+ * during the call. dt follows the CFL rule. Synchronises and reports
+ * asynchronous errors. */
 igr_status igr_step_host(igr_ctx *ctx, const void *q_in, void *q_out, int nsteps, igr_dtype dtype);
 
 /* Sigma solve alone, on caller device buffers: q in the state dtype,
