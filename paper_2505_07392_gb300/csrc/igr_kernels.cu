@@ -2178,6 +2178,11 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
     // four of its six points (shared loads are the flux kernel's most
     // contended resource; the copies are register moves). Not in the
     // viscous kernels, whose extra registers would spill.
+    // this lane's x-face (at the low side of its cell) and y-face (below its
+    // row) of the last plane: the divergence of that plane takes them from
+    // registers and only the faces of its neighbours from the face buffers
+    constexpr bool kOwnFaces = sizeof(C) == 4;
+    C Fxo[5], Fyo[5];
     C2 zq[2][3];
     if (!VISC && rowwarp) {
         ld_cell(P + ro[2], cks(tcell, PH * PW), zq[0][0], zq[0][1], zq[0][2]);  // plane k0 - 1
@@ -2198,10 +2203,13 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
         C Lv[5];
 #pragma unroll
         for (int u = 0; u < 5; u++) {
-            C dfx = FX[cks((u * TY + w) * (TX + 1) + lane + 1, NFX)] -
-                    FX[cks((u * TY + w) * (TX + 1) + lane, NFX)];
-            C dfy = FY[cks((u * (TY + 1) + w + 1) * TX + lane, NFY)] -
-                    FY[cks((u * (TY + 1) + w) * TX + lane, NFY)];
+            // the faces above and right of the cell from the buffers, the two
+            // below and left of it computed by this lane (Fxo, Fyo; FP64
+            // arithmetic reads them back, its extra registers would spill)
+            const C fxl = kOwnFaces ? Fxo[u] : FX[cks((u * TY + w) * (TX + 1) + lane, NFX)];
+            const C fyl = kOwnFaces ? Fyo[u] : FY[cks((u * (TY + 1) + w) * TX + lane, NFY)];
+            C dfx = FX[cks((u * TY + w) * (TX + 1) + lane + 1, NFX)] - fxl;
+            C dfy = FY[cks((u * (TY + 1) + w + 1) * TX + lane, NFY)] - fyl;
             C dfz = Fzp[u] - Fzm[u];
             Lv[u] = -((dfx + dfy) + dfz) * half_inv_dx;
         }
@@ -2302,12 +2310,18 @@ __device__ __forceinline__ void flux_body(const QIn qin, const S *__restrict__ s
                 tile_face_c<0, ORD>(T, (w + 3) * PW + lane, 1, cc, gamma, gm1, F, bad);
                 if constexpr (VISC) visc_x((w + 3) * PW + lane + 2);
 #pragma unroll
-                for (int u = 0; u < 5; u++) FX[cks((u * TY + w) * (TX + 1) + lane, NFX)] = F[u];
+                for (int u = 0; u < 5; u++) {
+                    FX[cks((u * TY + w) * (TX + 1) + lane, NFX)] = F[u];
+                    if constexpr (kOwnFaces) Fxo[u] = F[u];
+                }
                 // y-face below row w in column lane (tile rows w-3..w+2)
                 tile_face_c<1, ORD>(T, w * PW + lane + 3, PW, cc, gamma, gm1, F, bad);
                 if constexpr (VISC) visc_y((w + 2) * PW + lane + 3);
 #pragma unroll
-                for (int u = 0; u < 5; u++) FY[cks((u * (TY + 1) + w) * TX + lane, NFY)] = F[u];
+                for (int u = 0; u < 5; u++) {
+                    FY[cks((u * (TY + 1) + w) * TX + lane, NFY)] = F[u];
+                    if constexpr (kOwnFaces) Fyo[u] = F[u];
+                }
             }
         } else if (k >= k0) {
             // y-face above the last row, column lane
