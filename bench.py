@@ -50,13 +50,13 @@ FALLBACK_HBM_GBS = 6800.0
 # Both from ncu captures of the flux kernel on the 512 x 512 x 128 plume,
 # mean of the three stage launches of one step.
 NCU_INSTR = {
-    "flux_f16inc": {"warp_instr_per_cell": 21.566, "src": "5400db6b906e2396"},
+    "flux_f16inc": {"warp_instr_per_cell": 21.159, "src": "475b84c12d696731"},
     "flux_f16": {"warp_instr_per_cell": 22.945, "src": "8eb9327fb53b00ea"},
     "flux_f32": {"warp_instr_per_cell": 20.479, "src": "8eb9327fb53b00ea"},
 }
 
 NCU_TRAFFIC = {
-    "flux_f16inc": {"bytes_per_cell": 44.350, "src": "5400db6b906e2396"},
+    "flux_f16inc": {"bytes_per_cell": 44.333, "src": "475b84c12d696731"},
     "flux_f16": {"bytes_per_cell": 29.105, "src": "8eb9327fb53b00ea"},
     "flux_f32": {"bytes_per_cell": 58.879, "src": "8eb9327fb53b00ea"},
 }
