@@ -85,6 +85,8 @@ def test_host_only_calls(libigr):
     assert L.igr_step_host(None, None, None, 1, igr.DT_F32) == igr.ERR_INVALID_ARG
     assert L.igr_set_kernel_forms(None, 0, 0) == igr.ERR_INVALID_ARG
     assert L.igr_get_kernel_forms(None, ctypes.byref(i), ctypes.byref(i)) == igr.ERR_INVALID_ARG
+    assert L.igr_autotune_batch(None, 3) == igr.ERR_INVALID_ARG
+    assert L.igr_step_batch(None, 1) == igr.ERR_INVALID_ARG
 
 
 def test_missing_library_fails_loudly(tmp_path):
